@@ -1,0 +1,396 @@
+/*
+ * Oracle for the exact closest-pair family -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, FP64 CPU brute force of what the GPU library computes.  Only the
+ * test suite, the smoke check and the benchmark's CPU-baseline leg may load it;
+ * the library never calls it and shares no code with it.
+ *
+ * Every answer here is a plain definition written out (the method reaches the
+ * brute-force answer exactly), so each function is a direct loop over all pairs:
+ *
+ *   oracle_cpp        closest pair, Sec. 3 (problem statement) with the
+ *                     Euclidean distance of Sec. 2; optional index gap `excl`
+ *   oracle_znorm      z-normalised l-mers (l-mers as defined in Sec. 2)
+ *   oracle_tsmm       motif pair: closest pair of z-normalised l-mers, Sec. 3
+ *   oracle_tsmm_pairs / oracle_tsmm_rows   the same distance for chosen pairs
+ *                     or rows (sampled checks at full size)
+ *   oracle_frnn       R-neighbourhoods N(i) for all i, Sec. 3.5 (d <= R,
+ *                     symmetric insertion into N(i) and N(j))
+ *   oracle_frnn_rows  N(i) for chosen rows
+ *   oracle_twolocus   argmax |P_A(i,j) - P_B(i,j)|, Sec. 6, with the
+ *                     match-count correlation of Sec. 2 / Sec. 5.3
+ *   oracle_twolocus_tables / oracle_twolocus_rows   3x3 tables for chosen
+ *                     pairs, best partner for chosen rows
+ *
+ * Readings taken where the paper is silent (each also listed in the design
+ * notes): ties go to the lexicographically smallest (d^2, i, j) with i < j;
+ * z-normalisation uses the population standard deviation; a motif pair needs
+ * j - i >= excl; FRNN uses "<= R" and excludes the point itself; two-locus
+ * compares |u_A*m2 - u_B*m1| exactly in integers (u = matches).
+ *
+ * Build: plain C99, -O2 -ffp-contract=off (no FMA contraction, so every sum is
+ * a rounded add of a rounded product, in index order), OpenMP over the outer
+ * loop only; the per-pair arithmetic is unchanged by the thread count.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_OK 0
+#define ORACLE_ERR_ARG 1
+#define ORACLE_ERR_CAPACITY 2
+#define ORACLE_ERR_NUMERIC 5
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* (d2, i, j) is lexicographically smaller than (bd2, bi, bj) */
+static int lex_less(double d2, int64_t i, int64_t j, double bd2, int64_t bi, int64_t bj) {
+  if (d2 < bd2) return 1;
+  if (d2 > bd2) return 0;
+  if (i < bi) return 1;
+  if (i > bi) return 0;
+  return j < bj;
+}
+
+/* Squared Euclidean distance, Sec. 2: sum over k = 0..d-1 of (x_k - y_k)^2, in k order. */
+static double sqdist(const double* x, const double* y, int64_t d) {
+  double s = 0.0;
+  for (int64_t k = 0; k < d; ++k) {
+    double t = x[k] - y[k];
+    s = s + t * t;
+  }
+  return s;
+}
+
+double oracle_sqdist(const double* x, const double* y, int64_t d) { return sqdist(x, y, d); }
+
+/*
+ * Closest pair (Sec. 3): over all 0 <= i < j < n with j - i >= excl, the pair with the
+ * least distance.  excl = 1 gives the plain CPP.  Returns (-1,-1,+inf) when no pair is valid.
+ */
+int oracle_cpp(const double* x, int64_t n, int64_t d, int64_t excl,
+               int64_t* bi, int64_t* bj, double* bd2) {
+  if (!x || n < 0 || d <= 0 || excl < 1 || !bi || !bj || !bd2) return ORACLE_ERR_ARG;
+  double best = INFINITY;
+  int64_t best_i = -1, best_j = -1;
+#pragma omp parallel
+  {
+    double lb = INFINITY;
+    int64_t li = -1, lj = -1;
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+      for (int64_t j = i + excl; j < n; ++j) {
+        double s = sqdist(x + i * d, x + j * d, d);
+        if (li < 0 || lex_less(s, i, j, lb, li, lj)) { lb = s; li = i; lj = j; }
+      }
+    }
+#pragma omp critical
+    {
+      if (li >= 0 && (best_i < 0 || lex_less(lb, li, lj, best, best_i, best_j))) {
+        best = lb; best_i = li; best_j = lj;
+      }
+    }
+  }
+  *bi = best_i; *bj = best_j; *bd2 = best;
+  return ORACLE_OK;
+}
+
+/*
+ * z-normalisation of the l-mers T_i = a_i .. a_{i+l-1} (Sec. 2), i = 0 .. N-l:
+ *   mu_i = (sum_k a_{i+k}) / l,  sigma_i = sqrt((sum_k (a_{i+k} - mu_i)^2) / l),
+ *   z_ik = (a_{i+k} - mu_i) / sigma_i.
+ * Sums in k order.  z may be NULL (only mu, sigma wanted).  sigma = 0 -> ERR_NUMERIC.
+ */
+static int znorm_row(const double* a, int64_t l, double* mu_out, double* sd_out, double* z) {
+  double s = 0.0;
+  for (int64_t k = 0; k < l; ++k) s = s + a[k];
+  double mu = s / (double)l;
+  double v = 0.0;
+  for (int64_t k = 0; k < l; ++k) {
+    double t = a[k] - mu;
+    v = v + t * t;
+  }
+  double sd = sqrt(v / (double)l);
+  if (mu_out) *mu_out = mu;
+  if (sd_out) *sd_out = sd;
+  if (!(sd > 0.0)) return ORACLE_ERR_NUMERIC;
+  if (z)
+    for (int64_t k = 0; k < l; ++k) z[k] = (a[k] - mu) / sd;
+  return ORACLE_OK;
+}
+
+int oracle_znorm(const double* a, int64_t N, int64_t l, double* z, double* mu, double* sigma) {
+  if (!a || l < 1 || N < l) return ORACLE_ERR_ARG;
+  int64_t n = N - l + 1;
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+  for (int64_t i = 0; i < n; ++i) {
+    double m, s;
+    int rc = znorm_row(a + i, l, &m, &s, z ? z + i * l : NULL);
+    if (mu) mu[i] = m;
+    if (sigma) sigma[i] = s;
+    bad |= (rc != ORACLE_OK);
+  }
+  return bad ? ORACLE_ERR_NUMERIC : ORACLE_OK;
+}
+
+/* Motif pair (Sec. 3): closest pair of z-normalised l-mers with j - i >= excl. */
+int oracle_tsmm(const double* a, int64_t N, int64_t l, int64_t excl,
+                int64_t* bi, int64_t* bj, double* bd2) {
+  if (!a || l < 1 || N < l || excl < 1) return ORACLE_ERR_ARG;
+  int64_t n = N - l + 1;
+  double* z = (double*)malloc((size_t)n * (size_t)l * sizeof(double));
+  if (!z) return ORACLE_ERR_ARG;
+  int rc = oracle_znorm(a, N, l, z, NULL, NULL);
+  if (rc == ORACLE_OK) rc = oracle_cpp(z, n, l, excl, bi, bj, bd2);
+  free(z);
+  return rc;
+}
+
+/* The motif distance of chosen pairs (I[p], J[p]), each l-mer normalised on its own. */
+int oracle_tsmm_pairs(const double* a, int64_t N, int64_t l, const int64_t* I, const int64_t* J,
+                      int64_t np, double* out_d2) {
+  if (!a || l < 1 || N < l || np < 0 || !I || !J || !out_d2) return ORACLE_ERR_ARG;
+  int64_t n = N - l + 1;
+  int bad = 0;
+#pragma omp parallel reduction(| : bad)
+  {
+    double* zi = (double*)malloc((size_t)l * sizeof(double));
+    double* zj = (double*)malloc((size_t)l * sizeof(double));
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t p = 0; p < np; ++p) {
+      if (I[p] < 0 || I[p] >= n || J[p] < 0 || J[p] >= n) { bad |= 1; out_d2[p] = NAN; continue; }
+      int r1 = znorm_row(a + I[p], l, NULL, NULL, zi);
+      int r2 = znorm_row(a + J[p], l, NULL, NULL, zj);
+      out_d2[p] = (r1 || r2) ? NAN : sqdist(zi, zj, l);
+      bad |= (r1 || r2) ? 2 : 0;
+    }
+    free(zi);
+    free(zj);
+  }
+  return bad ? ((bad & 1) ? ORACLE_ERR_ARG : ORACLE_ERR_NUMERIC) : ORACLE_OK;
+}
+
+/*
+ * For each chosen row r = rows[p]: the lexicographically smallest (d2, min(r,j), max(r,j))
+ * over all j with |r - j| >= excl (partners on both sides).  best_j = -1 if none.
+ */
+int oracle_tsmm_rows(const double* a, int64_t N, int64_t l, int64_t excl, const int64_t* rows,
+                     int64_t nr, int64_t* best_j, double* best_d2) {
+  if (!a || l < 1 || N < l || excl < 1 || nr < 0 || !rows || !best_j || !best_d2)
+    return ORACLE_ERR_ARG;
+  int64_t n = N - l + 1;
+  for (int64_t p = 0; p < nr; ++p)
+    if (rows[p] < 0 || rows[p] >= n) return ORACLE_ERR_ARG;
+  double* z = (double*)malloc((size_t)n * (size_t)l * sizeof(double));
+  if (!z) return ORACLE_ERR_ARG;
+  int rc = oracle_znorm(a, N, l, z, NULL, NULL);
+  if (rc == ORACLE_OK) {
+    for (int64_t p = 0; p < nr; ++p) {
+      int64_t r = rows[p];
+      double bd = INFINITY;
+      int64_t bjj = -1;
+#pragma omp parallel
+      {
+        double lb = INFINITY;
+        int64_t lj = -1;
+#pragma omp for schedule(static)
+        for (int64_t j = 0; j < n; ++j) {
+          int64_t gap = j > r ? j - r : r - j;
+          if (gap < excl) continue;
+          double s = sqdist(z + r * l, z + j * l, l);
+          int64_t lo = r < j ? r : j, hi = r < j ? j : r;
+          int64_t llo = lj < 0 ? 0 : (r < lj ? r : lj), lhi = lj < 0 ? 0 : (r < lj ? lj : r);
+          if (lj < 0 || lex_less(s, lo, hi, lb, llo, lhi)) { lb = s; lj = j; }
+        }
+#pragma omp critical
+        {
+          if (lj >= 0) {
+            int64_t lo = r < lj ? r : lj, hi = r < lj ? lj : r;
+            int64_t blo = bjj < 0 ? 0 : (r < bjj ? r : bjj), bhi = bjj < 0 ? 0 : (r < bjj ? bjj : r);
+            if (bjj < 0 || lex_less(lb, lo, hi, bd, blo, bhi)) { bd = lb; bjj = lj; }
+          }
+        }
+      }
+      best_j[p] = bjj;
+      best_d2[p] = bd;
+    }
+  }
+  free(z);
+  return rc;
+}
+
+/*
+ * FRNN (Sec. 3.5): N(i) = { j != i : d(a_i, a_j) <= R }, decided as
+ * sum_k (x_ik - x_jk)^2 <= R*R in FP64 (k order).  Output CSR: row_ptr[n+1], cols ascending
+ * per row.  If cap < total pairs, returns ORACLE_ERR_CAPACITY with *total set.
+ */
+static int frnn_pred(const double* x, const double* y, int64_t d, double rr) {
+  return sqdist(x, y, d) <= rr;
+}
+
+int oracle_frnn(const double* x, int64_t n, int64_t d, double R, int64_t* row_ptr, int32_t* cols,
+                int64_t cap, int64_t* total) {
+  if (!x || n < 0 || d <= 0 || !(R >= 0.0) || !row_ptr || !total || n > INT32_MAX) return ORACLE_ERR_ARG;
+  double rr = R * R;
+  row_ptr[0] = 0;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t c = 0;
+    for (int64_t j = 0; j < n; ++j)
+      if (j != i && frnn_pred(x + i * d, x + j * d, d, rr)) ++c;
+    row_ptr[i + 1] = c;
+  }
+  for (int64_t i = 0; i < n; ++i) row_ptr[i + 1] += row_ptr[i];
+  *total = row_ptr[n];
+  if (!cols || cap < row_ptr[n]) return ORACLE_ERR_CAPACITY;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t o = row_ptr[i];
+    for (int64_t j = 0; j < n; ++j)
+      if (j != i && frnn_pred(x + i * d, x + j * d, d, rr)) cols[o++] = (int32_t)j;
+  }
+  return ORACLE_OK;
+}
+
+/* N(r) for chosen rows; neighbours of rows[p] land in cols[offs[p] .. offs[p+1]). */
+int oracle_frnn_rows(const double* x, int64_t n, int64_t d, double R, const int64_t* rows,
+                     int64_t nr, int64_t* offs, int32_t* cols, int64_t cap) {
+  if (!x || n < 0 || d <= 0 || !(R >= 0.0) || !rows || !offs || nr < 0) return ORACLE_ERR_ARG;
+  double rr = R * R;
+  offs[0] = 0;
+  for (int64_t p = 0; p < nr; ++p) {
+    if (rows[p] < 0 || rows[p] >= n) return ORACLE_ERR_ARG;
+    int64_t c = 0;
+#pragma omp parallel for reduction(+ : c) schedule(static)
+    for (int64_t j = 0; j < n; ++j)
+      if (j != rows[p] && frnn_pred(x + rows[p] * d, x + j * d, d, rr)) ++c;
+    offs[p + 1] = offs[p] + c;
+  }
+  if (!cols || cap < offs[nr]) return ORACLE_ERR_CAPACITY;
+  for (int64_t p = 0; p < nr; ++p) {
+    int64_t o = offs[p];
+    for (int64_t j = 0; j < n; ++j)
+      if (j != rows[p] && frnn_pred(x + rows[p] * d, x + j * d, d, rr)) cols[o++] = (int32_t)j;
+  }
+  return ORACLE_OK;
+}
+
+/*
+ * Two-locus (Sec. 6).  g is int8 [S][m1+m2], genotype of SNP s for subject t at g[s*(m1+m2)+t];
+ * subjects 0..m1-1 are cases (matrix A), m1..m1+m2-1 controls (matrix B).
+ * For a pair (i, j) and a group, tab[3*a+b] counts the subjects with g_i = a and g_j = b;
+ * the matches of Sec. 2 are u = tab[0] + tab[4] + tab[8], the correlation of Sec. 5.3 is
+ * u / (group size), so |P_A - P_B| * m1 * m2 = |u_A * m2 - u_B * m1|.
+ */
+static void table_of(const int8_t* gi, const int8_t* gj, int64_t lo, int64_t hi, int32_t* tab) {
+  for (int q = 0; q < 9; ++q) tab[q] = 0;
+  for (int64_t t = lo; t < hi; ++t) tab[3 * gi[t] + gj[t]] += 1;
+}
+
+static int64_t score_of(const int32_t* ta, const int32_t* tb, int64_t m1, int64_t m2) {
+  int64_t ua = (int64_t)ta[0] + ta[4] + ta[8];
+  int64_t ub = (int64_t)tb[0] + tb[4] + tb[8];
+  int64_t s = ua * m2 - ub * m1;
+  return s < 0 ? -s : s;
+}
+
+static int geno_ok(const int8_t* g, int64_t S, int64_t m) {
+  for (int64_t q = 0; q < S * m; ++q)
+    if (g[q] < 0 || g[q] > 2) return 0;
+  return 1;
+}
+
+/* (score, i, j) beats (bs, bi, bj): larger score first, then smaller i, then smaller j */
+static int tl_better(int64_t s, int64_t i, int64_t j, int64_t bs, int64_t bi, int64_t bj) {
+  if (s != bs) return s > bs;
+  if (i != bi) return i < bi;
+  return j < bj;
+}
+
+int oracle_twolocus(const int8_t* g, int64_t S, int64_t m1, int64_t m2, int64_t* bi, int64_t* bj,
+                    int64_t* score, int32_t* countsA, int32_t* countsB) {
+  if (!g || S < 0 || m1 < 1 || m2 < 1 || !bi || !bj || !score) return ORACLE_ERR_ARG;
+  int64_t m = m1 + m2;
+  if (!geno_ok(g, S, m)) return ORACLE_ERR_ARG;
+  int64_t best = -1, best_i = -1, best_j = -1;
+#pragma omp parallel
+  {
+    int64_t ls = -1, li = -1, lj = -1;
+    int32_t ta[9], tb[9];
+#pragma omp for schedule(dynamic, 8)
+    for (int64_t i = 0; i < S; ++i) {
+      for (int64_t j = i + 1; j < S; ++j) {
+        table_of(g + i * m, g + j * m, 0, m1, ta);
+        table_of(g + i * m, g + j * m, m1, m, tb);
+        int64_t s = score_of(ta, tb, m1, m2);
+        if (li < 0 || tl_better(s, i, j, ls, li, lj)) { ls = s; li = i; lj = j; }
+      }
+    }
+#pragma omp critical
+    {
+      if (li >= 0 && (best_i < 0 || tl_better(ls, li, lj, best, best_i, best_j))) {
+        best = ls; best_i = li; best_j = lj;
+      }
+    }
+  }
+  *bi = best_i; *bj = best_j; *score = best;
+  if (best_i >= 0) {
+    int32_t ta[9], tb[9];
+    table_of(g + best_i * m, g + best_j * m, 0, m1, ta);
+    table_of(g + best_i * m, g + best_j * m, m1, m, tb);
+    if (countsA) memcpy(countsA, ta, sizeof ta);
+    if (countsB) memcpy(countsB, tb, sizeof tb);
+  }
+  return ORACLE_OK;
+}
+
+/* 3x3 tables and score for chosen pairs; tabA/tabB are [np][9]. */
+int oracle_twolocus_tables(const int8_t* g, int64_t S, int64_t m1, int64_t m2, const int64_t* I,
+                           const int64_t* J, int64_t np, int32_t* tabA, int32_t* tabB, int64_t* score) {
+  if (!g || m1 < 1 || m2 < 1 || !I || !J || np < 0 || !tabA || !tabB || !score) return ORACLE_ERR_ARG;
+  int64_t m = m1 + m2;
+  for (int64_t p = 0; p < np; ++p) {
+    if (I[p] < 0 || I[p] >= S || J[p] < 0 || J[p] >= S) return ORACLE_ERR_ARG;
+    table_of(g + I[p] * m, g + J[p] * m, 0, m1, tabA + 9 * p);
+    table_of(g + I[p] * m, g + J[p] * m, m1, m, tabB + 9 * p);
+    score[p] = score_of(tabA + 9 * p, tabB + 9 * p, m1, m2);
+  }
+  return ORACLE_OK;
+}
+
+/* For each chosen SNP r: its best partner j != r (score, then lowest (min, max) pair). */
+int oracle_twolocus_rows(const int8_t* g, int64_t S, int64_t m1, int64_t m2, const int64_t* rows,
+                         int64_t nr, int64_t* best_j, int64_t* best_score) {
+  if (!g || m1 < 1 || m2 < 1 || !rows || nr < 0 || !best_j || !best_score) return ORACLE_ERR_ARG;
+  int64_t m = m1 + m2;
+  for (int64_t p = 0; p < nr; ++p)
+    if (rows[p] < 0 || rows[p] >= S) return ORACLE_ERR_ARG;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t p = 0; p < nr; ++p) {
+    int64_t r = rows[p], bs = -1, bjj = -1;
+    int32_t ta[9], tb[9];
+    for (int64_t j = 0; j < S; ++j) {
+      if (j == r) continue;
+      int64_t lo = r < j ? r : j, hi = r < j ? j : r;
+      table_of(g + lo * m, g + hi * m, 0, m1, ta);
+      table_of(g + lo * m, g + hi * m, m1, m, tb);
+      int64_t s = score_of(ta, tb, m1, m2);
+      int64_t blo = bjj < 0 ? 0 : (r < bjj ? r : bjj), bhi = bjj < 0 ? 0 : (r < bjj ? bjj : r);
+      if (bjj < 0 || tl_better(s, lo, hi, bs, blo, bhi)) { bs = s; bjj = j; }
+    }
+    best_j[p] = bjj;
+    best_score[p] = bs;
+  }
+  return ORACLE_OK;
+}

@@ -1,0 +1,116 @@
+"""Pins for the closest-pair oracle (Sec. 3 problem statement, Sec. 2 distance).
+
+Each test ties the oracle to something other than itself: the paper's printed
+worked example (Sec. 3.2), a library routine (scipy pdist), an independent
+algorithm (sorted adjacent gaps in 1-D), a planted pair, and invariants.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial.distance import pdist, squareform
+
+import oracle
+from paper_1407_5609_gb300 import synth
+
+
+def _golden_rows(path):
+    rows = []
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            name, r, th, printed, tol = line.split()
+            rows.append((name, float(r), float(th), float(printed), float(tol)))
+    return rows
+
+
+def test_sec3_2_worked_reference_points(golden_dir):
+    """d(r,x) - d(r,y) for the reference points of Sec. 3.2 matches the printed values."""
+    rows = _golden_rows(os.path.join(golden_dir, "sec3_2_reference_points.txt"))
+    assert len(rows) == 5
+    x = np.array([0.0, 0.0]); y = np.array([1.0, 0.0])
+    for name, rad, th, printed, tol in rows:
+        t = math.radians(th)
+        r = np.array([rad * math.cos(t), rad * math.sin(t)])
+        got = math.sqrt(oracle.sqdist(r, x)) - math.sqrt(oracle.sqdist(r, y))
+        assert abs(got - printed) <= tol, (name, got, printed)
+
+
+def _lexmin_from_matrix(D, excl=1):
+    n = D.shape[0]
+    best = (math.inf, -1, -1)
+    for i in range(n):
+        for j in range(i + excl, n):
+            cand = (D[i, j], i, j)
+            if cand < best:
+                best = cand
+    return best
+
+
+@pytest.mark.parametrize("n,d,seed", [(2, 3, 1), (37, 5, 2), (200, 7, 3), (150, 64, 4)])
+def test_cpp_matches_scipy_pdist(n, d, seed):
+    x = synth.rng_for(seed).standard_normal((n, d))
+    D = squareform(pdist(x, "sqeuclidean"))
+    ed, ei, ej = _lexmin_from_matrix(D)
+    i, j, d2 = oracle.cpp(x)
+    assert (i, j) == (ei, ej)
+    assert d2 == pytest.approx(ed, rel=1e-12)
+
+
+def test_cpp_one_dimension_sorted_gaps():
+    """In 1-D the closest pair is the smallest gap between sorted neighbours."""
+    x = synth.rng_for(7).random(2000)
+    order = np.argsort(x, kind="stable")
+    gaps = np.diff(x[order])
+    k = int(np.argmin(gaps))
+    a, b = sorted((int(order[k]), int(order[k + 1])))
+    i, j, d2 = oracle.cpp(x[:, None])
+    assert (i, j) == (a, b)
+    assert math.sqrt(d2) == pytest.approx(gaps[k], rel=1e-12)
+
+
+def test_cpp_planted_pair_full_size():
+    """The 4096 x 32 uniform workload: the pair planted at distance 1e-3 is the answer."""
+    x, plant = synth.make_cpp()
+    i, j, d2 = oracle.cpp(x)
+    assert (i, j) == plant
+    assert math.sqrt(d2) == pytest.approx(1e-3, rel=1e-9)
+
+
+def test_cpp_ties_go_to_lowest_pair():
+    x = synth.rng_for(11).random((40, 4))
+    x[9] = x[3]    # d = 0 at (3, 9)
+    x[7] = x[5]    # d = 0 at (5, 7)
+    x[30] = x[2]   # d = 0 at (2, 30) -> lexicographically first
+    assert oracle.cpp(x) == (2, 30, 0.0)
+
+
+def test_cpp_permutation_and_translation_invariance():
+    x = synth.rng_for(12).random((300, 6))
+    i, j, d2 = oracle.cpp(x)
+    perm = synth.rng_for(13).permutation(300)
+    inv = np.argsort(perm)
+    pi, pj, pd2 = oracle.cpp(x[perm])
+    assert sorted((int(perm[pi]), int(perm[pj]))) == [i, j]
+    assert pd2 == d2
+    ti, tj, td2 = oracle.cpp(x + 0.25)
+    assert (ti, tj) == (i, j) and td2 == pytest.approx(d2, rel=1e-12)
+    assert inv.shape == perm.shape
+
+
+def test_cpp_index_gap():
+    x = synth.rng_for(14).random((100, 3))
+    x[11] = x[10] + 1e-9
+    i, j, _ = oracle.cpp(x, excl=1)
+    assert (i, j) == (10, 11)
+    i, j, d2 = oracle.cpp(x, excl=2)
+    D = squareform(pdist(x, "sqeuclidean"))
+    assert (d2, i, j) == pytest.approx(_lexmin_from_matrix(D, excl=2), rel=1e-12)
+
+
+@pytest.mark.parametrize("n", [0, 1])
+def test_cpp_degenerate_sizes(n):
+    assert oracle.cpp(np.zeros((n, 3))) == (-1, -1, math.inf)

@@ -1,0 +1,70 @@
+"""Pins for the FRNN oracle (Sec. 3.5): N(i) = {j != i : d(a_i, a_j) <= R}, symmetric.
+
+Pinned against scipy's cKDTree (a library routine), exact boundary cases for
+"<= R", and the symmetry of the neighbourhoods.
+"""
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+import oracle
+from paper_1407_5609_gb300 import synth
+
+
+def _pairs_from_csr(row_ptr, cols):
+    out = set()
+    for i in range(row_ptr.shape[0] - 1):
+        for j in cols[row_ptr[i]:row_ptr[i + 1]]:
+            out.add((i, int(j)))
+    return out
+
+
+@pytest.mark.parametrize("n,d,R,seed", [(3000, 3, 0.004, 41), (1500, 7, 0.25, 42), (500, 1, 1e-3, 43)])
+def test_frnn_matches_ckdtree(n, d, R, seed):
+    if d == 3:
+        x = synth.make_frnn_mixture(n=n, seed=seed).astype(np.float64)
+    else:
+        x = synth.rng_for(seed).random((n, d))
+    row_ptr, cols = oracle.frnn(x, R)
+    got = _pairs_from_csr(row_ptr, cols)
+    tree = cKDTree(x)
+    ref = set()
+    for i, j in tree.query_pairs(R * (1 + 1e-12)):
+        ref.add((i, j)); ref.add((j, i))
+    # pairs within a 1e-12 relative band of R may be decided differently by the tree's arithmetic
+    band = {(i, j) for (i, j) in ref ^ got
+            if abs(np.sqrt(((x[i] - x[j]) ** 2).sum()) - R) <= 1e-12 * R}
+    assert (got ^ ref) == band
+    assert len(got) > 0
+
+
+def test_frnn_symmetric_sorted_no_self():
+    x = synth.make_frnn_mixture(n=2000, seed=44).astype(np.float64)
+    row_ptr, cols = oracle.frnn(x, 0.005)
+    assert row_ptr[-1] % 2 == 0
+    pairs = _pairs_from_csr(row_ptr, cols)
+    assert all((j, i) in pairs for (i, j) in pairs)
+    assert all(i != j for (i, j) in pairs)
+    for i in range(2000):
+        seg = cols[row_ptr[i]:row_ptr[i + 1]]
+        assert np.all(np.diff(seg) > 0)
+
+
+def test_frnn_boundary_is_inclusive():
+    """Exactly representable distance R is inside the neighbourhood (the '<= R' of Sec. 3.5)."""
+    x = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0], [0.0, 0.75, 0.0], [0.0, 0.0, 2.0]])
+    row_ptr, cols = oracle.frnn(x, 0.5)
+    assert _pairs_from_csr(row_ptr, cols) == {(0, 1), (1, 0)}
+    row_ptr, cols = oracle.frnn(x, 0.75)
+    assert _pairs_from_csr(row_ptr, cols) == {(0, 1), (1, 0), (0, 2), (2, 0)}
+    row_ptr, cols = oracle.frnn(x, 0.0)
+    assert row_ptr[-1] == 0
+
+
+def test_frnn_rows_match_full():
+    x = synth.make_frnn_mixture(n=1500, seed=45).astype(np.float64)
+    row_ptr, cols = oracle.frnn(x, 0.006)
+    rows = np.array([0, 7, 100, 1499, 7])
+    offs, rc = oracle.frnn_rows(x, 0.006, rows)
+    for p, r in enumerate(rows):
+        np.testing.assert_array_equal(rc[offs[p]:offs[p + 1]], cols[row_ptr[r]:row_ptr[r + 1]])
