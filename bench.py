@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Benchmark of the exact all-pairs hot path on GB300.
+
+Default workload: the motif pair of an FP32 random walk of 262,144 samples (cumsum of N(0,1)),
+l = 512, trivial-match exclusion 256: 261,633 z-normalised 512-mers, 3.416e10 eligible pairs.
+One step = one full ``tsmm_motif`` call (z-normalisation, dense all-pairs stage with its fused
+min/threshold epilogue, FP64 recheck, result read-back) through the C ABI, inputs resident in HBM.
+
+Prints one JSON line (rank 0).  ``--impl reference`` instead times the CPU oracle on a bounded
+sample of the same workload.  Other workloads for the per-row measurements: ``--workload
+twolocus`` (4096 SNPs x 8192 subjects) and ``--workload cpp`` (4096 x 32 FP64 points).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact-CPP pair evals/s (d=512) BF16-filter vs FP32 plain, same answer; % roofline"
+UNIT = "pairs/s"
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
+POPC_PEAK_TOPS = 152 * 16 * 2.070e9 / 1e12               # SMs x 16 POPC/clk x max SM clock
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p["hbm_gbs"], "bf16_tflops": p["bf16_tflops"],
+                "bf16_tflops_sustained": p.get("bf16_tflops_sustained"), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ workloads
+class TSMM:
+    name = "tsmm"
+
+    def __init__(self, args):
+        from paper_1407_5609_gb300 import synth
+        self.N, self.l, self.excl = 262144, 512, 256
+        self.series = synth.make_random_walk(self.N)
+        n = self.N - self.l + 1
+        m = n - self.excl
+        self.units = m * (m + 1) // 2                # eligible pairs (j - i >= excl)
+        self.flop_per_unit = 2 * self.l               # one dot product of length l per pair
+        self.config = {"workload": f"tsmm random walk N={self.N} l={self.l} excl={self.excl}",
+                       "n_lmers": n, "pairs_per_step": self.units,
+                       "l2": "per step the prep rewrites the 268 MB (16-bit) / 536 MB (FP32) row matrix, > L2"}
+
+    def setup(self, dev):
+        import torch
+        self.dev_series = torch.from_numpy(self.series).to(dev)
+
+    def step(self, capi, mode):
+        return capi.tsmm_motif(self.dev_series, self.l, self.excl, mode=mode)
+
+    def e2e_step(self, capi, mode, host, dev_buf):
+        dev_buf.copy_(host, non_blocking=True)
+        return capi.tsmm_motif(dev_buf, self.l, self.excl, mode=mode)
+
+    def host_input(self):
+        return self.series, self.N * 4
+
+    def oracle_sample(self, oracle, rows):
+        import numpy as np
+        n = self.N - self.l + 1
+        rr = np.linspace(0, n - 1, rows).astype(np.int64)
+        t = time.perf_counter()
+        oracle.tsmm_rows(self.series, self.l, self.excl, rr)
+        dt = time.perf_counter() - t
+        pairs = int(sum(max(0, n - r - self.excl) + max(0, r - self.excl + 1) for r in rr))
+        return pairs, dt, f"best partner of {rows} rows evenly spaced over the {n} l-mers ({pairs} pairs)"
+
+
+class TwoLocus:
+    name = "twolocus"
+
+    def __init__(self, args):
+        from paper_1407_5609_gb300 import synth
+        self.g, _ = synth.make_genotypes()
+        self.planes = synth.pack_planes(self.g, 4096, 4096)
+        S = 4096
+        self.units = S * (S - 1) // 2
+        self.flop_per_unit = 2 * 4096 // 32          # POPC per pair: 2 groups x 128 32-bit words
+        self.config = {"workload": "two-locus S=4096 m_cases=4096 m_controls=4096", "pairs_per_step": self.units,
+                       "l2": "8 MiB of planes stay in L2 (the kernel is POPC-bound, not memory-bound)"}
+
+    def setup(self, dev):
+        import numpy as np
+        import torch
+        self.dev_planes = torch.from_numpy(self.planes.view(np.int64)).to(dev)
+
+    def step(self, capi, mode):
+        return capi.twolocus_scan(self.dev_planes, 4096, 4096)
+
+    def e2e_step(self, capi, mode, host, dev_buf):
+        dev_buf.copy_(host, non_blocking=True)
+        return capi.twolocus_scan(dev_buf, 4096, 4096)
+
+    def host_input(self):
+        import numpy as np
+        return self.planes.view(np.int64), self.planes.nbytes
+
+    def oracle_sample(self, oracle, rows):
+        import numpy as np
+        rr = np.linspace(0, 4095, rows).astype(np.int64)
+        t = time.perf_counter()
+        oracle.twolocus_rows(self.g, 4096, 4096, rr)
+        dt = time.perf_counter() - t
+        pairs = rows * 4095
+        return pairs, dt, f"best partner of {rows} SNPs evenly spaced over 4096 ({pairs} pairs)"
+
+
+class CPP:
+    name = "cpp"
+
+    def __init__(self, args):
+        from paper_1407_5609_gb300 import synth
+        self.x, _ = synth.make_cpp()
+        self.units = 4096 * 4095 // 2
+        self.flop_per_unit = 2 * 32
+        self.config = {"workload": "closest pair n=4096 d=32 FP64 uniform + planted pair", "pairs_per_step": self.units,
+                       "l2": "1 MiB input, L2-resident; latency-bound"}
+
+    def setup(self, dev):
+        import torch
+        self.dev_x = torch.from_numpy(self.x).to(dev)
+
+    def step(self, capi, mode):
+        return capi.cpp_closest_pair(self.dev_x, mode=mode)
+
+    def e2e_step(self, capi, mode, host, dev_buf):
+        dev_buf.copy_(host, non_blocking=True)
+        return capi.cpp_closest_pair(dev_buf, mode=mode)
+
+    def host_input(self):
+        return self.x, self.x.nbytes
+
+    def oracle_sample(self, oracle, rows):
+        t = time.perf_counter()
+        oracle.cpp(self.x)
+        return self.units, time.perf_counter() - t, "the full workload"
+
+
+WORKLOADS = {"tsmm": TSMM, "twolocus": TwoLocus, "cpp": CPP}
+
+
+# ------------------------------------------------------------------ helpers
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("gram_tc.cu", "gram_simt.cu", "twolocus.cu", "common.cuh"):
+        p = os.path.join(ROOT, "paper_1407_5609_gb300", "csrc", f)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(key):
+    """DRAM bytes per launch from a committed ncu capture, if the kernel sources are unchanged since."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            rec = json.load(f).get(key)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def cpu_baseline(wl, target_s=12.0):
+    import oracle
+    pairs, dt, _ = wl.oracle_sample(oracle, 2)
+    rows = max(2, int(2 * target_s / max(dt, 1e-3)))
+    pairs, dt, sample = wl.oracle_sample(oracle, rows)
+    return {"value": pairs / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": sample, "seconds": round(dt, 2)}
+
+
+def timed_steps(fn, steps, stream, torch, flush=None):
+    """Per-step CUDA events on `stream`; an optional L2 flush between steps stays outside them."""
+    evs = []
+    for _ in range(steps):
+        if flush is not None:
+            flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs), r
+
+
+# ------------------------------------------------------------------ arms
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1407_5609_gb300 import build, capi
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    wl = WORKLOADS[args.workload](args)
+    wl.setup(dev)
+    mode = args.mode or ("filter_bf16" if capi.filters_available() else "plain_fp32")
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = (lambda: flush_buf.zero_()) if args.flush_l2 else None
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    for _ in range(args.warmup):
+        ref = wl.step(capi, mode)
+    barrier()
+
+    # timed region (device-resident inputs)
+    capi.cpp_set_stage_timing(True)
+    dense_ms = []
+    launches0 = capi.cpp_launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+
+    def one():
+        r = wl.step(capi, mode)
+        st = capi.cpp_stage_times()
+        if len(st) >= 2:
+            dense_ms.append(st[1])
+        return r
+    barrier()
+    total_ms, res = timed_steps(one, args.steps, stream, torch, flush)
+    barrier()
+    clk = clocks.stop()
+    launches = capi.cpp_launch_count() - launches0
+    capi.cpp_set_stage_timing(False)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = wl.units * args.steps * world / (total_ms / 1e3)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": {"plain_fp32": "f32", "filter_fp16": "f16", "filter_bf16": "bf16"}.get(mode, "i32"),
+           "data": "synthetic", "config": dict(wl.config, mode=mode, flush_l2_between_steps=bool(flush),
+                                               parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+           "answer": {k: res[k] for k in ("i", "j", "dist2", "score") if k in res},
+           "gpu_launches": launches}
+
+    # roofline of the dominant kernel
+    pk = peaks()
+    if wl.name in ("tsmm", "cpp"):
+        avg_ms = statistics.mean(dense_ms) if dense_ms else None
+        flops = wl.units * wl.flop_per_unit
+        if mode == "plain_fp32":
+            peak, bound, unit, src = FP32_ALU_PEAK_TFLOPS, "alu", "TFLOP/s", "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"
+        else:
+            peak, bound, unit, src = pk["bf16_tflops"], "tensor", "TFLOP/s", f"{pk['source']} bf16 burst"
+        ach = flops / (avg_ms / 1e3) / 1e12 if avg_ms else None
+        key = f"dense_{mode}@{wl.name}"
+        out["roofline"] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                           "frac": ach / peak if ach else None, "traffic": recorded_traffic(key),
+                           "kernel": "dense all-pairs stage (gram_tc / gram_simt)", "peak_source": src,
+                           "launch_ms": avg_ms, "algorithmic_flop_per_launch": flops}
+    elif wl.name == "twolocus":
+        per_step_ms = total_ms / args.steps
+        pops = wl.units * wl.flop_per_unit
+        ach = pops / (per_step_ms / 1e3) / 1e12
+        out["roofline"] = {"bound": "alu", "achieved": ach, "peak": POPC_PEAK_TOPS, "unit": "Tpopc/s",
+                           "frac": ach / POPC_PEAK_TOPS, "traffic": recorded_traffic("twolocus_scan@twolocus"),
+                           "kernel": "twolocus_scan_kernel (step time)",
+                           "peak_source": "derived: 152 SM x 16 POPC/clk x 2070 MHz"}
+    out["clocks"] = clk
+
+    # the same answer from the plain FP32 path, and its throughput
+    if wl.name in ("tsmm", "cpp") and mode != "plain_fp32" and not args.no_compare:
+        barrier()
+        pms, pres = timed_steps(lambda: wl.step(capi, "plain_fp32"), max(1, min(args.steps, 3)), stream, torch, flush)
+        out["plain_fp32"] = {"value": wl.units * max(1, min(args.steps, 3)) / (pms / 1e3), "unit": UNIT,
+                             "ms_per_step": pms / max(1, min(args.steps, 3)),
+                             "same_answer": (pres["i"], pres["j"], pres["dist2"]) == (res["i"], res["j"], res["dist2"])}
+
+    # end to end through the public API from pinned host memory
+    if not args.no_e2e:
+        host_np, nbytes = wl.host_input()
+        host = torch.from_numpy(host_np).pin_memory()
+        dev_buf = torch.empty_like(host, device=dev)
+        barrier()
+        ems, _ = timed_steps(lambda: wl.e2e_step(capi, mode, host, dev_buf), args.steps, stream, torch, flush)
+        out["e2e"] = {"value": wl.units * args.steps / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                      # the call reads its 64-byte scalar block twice (dense searches) or the result struct
+                      "d2h_bytes_per_step": 128 if wl.name in ("tsmm", "cpp") else ctypes.sizeof(capi.twolocus_result)}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    wl = WORKLOADS[args.workload](args)
+    rows = 2
+    pairs, dt, _ = wl.oracle_sample(oracle, rows)
+    rows = max(2, int(rows * 4.0 / max(dt, 1e-3)))       # about 4 s of oracle work per step
+    for _ in range(args.warmup):
+        wl.oracle_sample(oracle, 2)
+    tot_pairs, tot_s, sample = 0, 0.0, ""
+    for _ in range(args.steps):
+        p, s, sample = wl.oracle_sample(oracle, rows)
+        tot_pairs += p
+        tot_s += s
+    value = tot_pairs / tot_s
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": dict(wl.config, mode="oracle"),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": f"per step: {sample}"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tsmm")
+    ap.add_argument("--mode", choices=["plain_fp32", "filter_fp16", "filter_bf16"], default=None)
+    ap.add_argument("--flush-l2", dest="flush_l2", action="store_true", default=True)
+    ap.add_argument("--no-flush-l2", dest="flush_l2", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * cppgb.h -- exact closest-pair family on GB300 (sm_103a): C ABI.
+ *
+ * Implements the exact (brute-force-equivalent) search of Rajasekaran & Pathak,
+ * "Efficient Algorithms for the Closest Pair Problem and Applications":
+ *   - closest pair (CPP) of n points in R^d           (Sec. 3 problem statement; distance of Sec. 2)
+ *   - motif pair of a time series: closest pair of its z-normalised l-mers  (Sec. 2, Sec. 3)
+ *   - fixed-radius near neighbours N(i) for all i     (Sec. 3.5)
+ *   - two-locus association: argmax_{i,j} |P_A(i,j) - P_B(i,j)|  (Sec. 6, correlation of Sec. 5.3)
+ *
+ * Conventions shared by every entry point
+ *   - Data pointers (points, series, planes, outputs named as device) are DEVICE pointers
+ *     owned by the caller.  Result structs (`out`) and scalar out-params are HOST pointers.
+ *   - `ws` is a caller-provided DEVICE workspace of at least the matching *_workspace_size()
+ *     bytes, 256-byte aligned.  The library allocates nothing on these paths.  For the dense
+ *     searches (cpp_closest_pair, tsmm_motif) any workspace beyond that size enlarges the
+ *     candidate buffer of the filter stage.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Each call enqueues its
+ *     kernels on `stream` and waits for that stream before returning, so the results are
+ *     valid on return.  Calls on one stream are serialised; a workspace must not be shared
+ *     by calls that may run at the same time.
+ *   - Indices are 0-based (the paper counts from 1).  Pairs are reported with i < j.
+ *   - Ties are broken towards the lexicographically smallest (i, j).
+ *   - Return value: CPPGB_OK or one of the error codes below; cpp_last_error() then
+ *     returns a message (per calling thread).  No exception crosses this boundary.
+ */
+#ifndef CPPGB_H
+#define CPPGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define CPPGB_OK 0
+#define CPPGB_ERR_ARG 1      /* bad size, pointer, alignment or mode */
+#define CPPGB_ERR_CAPACITY 2 /* workspace or output buffer too small; required size reported */
+#define CPPGB_ERR_TIMEOUT 3  /* a bounded device-side wait gave up */
+#define CPPGB_ERR_CUDA 4     /* a CUDA runtime call failed */
+#define CPPGB_ERR_NUMERIC 5  /* e.g. an l-mer with zero variance, or a non-finite input */
+
+/* element type of a point array */
+#define CPPGB_F32 0
+#define CPPGB_F64 1
+
+/* how the dense all-pairs stage evaluates distances; every mode returns the exact answer */
+#define CPPGB_MODE_PLAIN_FP32 0  /* FP32 CUDA-core Gram tiles, rigorous bound, FP64 recheck */
+#define CPPGB_MODE_FILTER_BF16 1 /* BF16 tensor-core Gram tiles (tcgen05), bound, FP64 recheck */
+#define CPPGB_MODE_FILTER_FP16 2 /* FP16 tensor-core Gram tiles (tcgen05), bound, FP64 recheck */
+
+/* Result of a closest-pair style search. */
+typedef struct {
+  int64_t i, j;          /* the pair, i < j; both -1 when no pair is valid */
+  double dist;           /* FP64 Euclidean distance of the pair (Sec. 2) */
+  double dist2;          /* its square, summed in coordinate order in FP64 */
+  double filter_err;     /* max |dist2_fp64 - dist2_filter| over the rechecked candidates */
+  double filter_bound;   /* final upper bound on dist2 reached by the dense stage */
+  int64_t n_emitted;     /* candidate pairs the dense stage emitted */
+  int64_t n_rechecked;   /* candidates whose lower bound met the final upper bound (FP64-rechecked) */
+} cpp_pair_result;
+
+/*
+ * cpp_closest_pair -- closest pair of n points in R^d: the general form of the problem stated at
+ * the start of Sec. 3, with the Euclidean distance of Sec. 2.
+ *   pts    device, row-major [n][ld] of `dtype` (CPPGB_F32 or CPPGB_F64); d <= ld.
+ *   n      number of points (0 and 1 give i = j = -1).   d in [1, 4096].
+ *   mode   CPPGB_MODE_*.
+ *   out    host; filled on CPPGB_OK.
+ * Errors: CPPGB_ERR_ARG (sizes, null pointers, mode), CPPGB_ERR_CAPACITY (ws too small, or more
+ *         candidate pairs tie within the filter's error bound than the workspace holds: then
+ *         out->n_emitted holds the number needed, 24 bytes each), CPPGB_ERR_NUMERIC (non-finite
+ *         coordinates), CPPGB_ERR_CUDA.
+ */
+size_t cpp_closest_pair_workspace_size(int64_t n, int64_t d, int mode);
+int cpp_closest_pair(const void* pts, int dtype, int64_t n, int64_t d, int64_t ld, int mode,
+                     cpp_pair_result* out, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * tsmm_motif -- time-series motif pair: of all pairs of l-mers of the series, the pair at least
+ * distance (Sec. 3; l-mers T_i = a_i..a_{i+l-1} as defined in Sec. 2).  Each l-mer is z-normalised with its own
+ * mean and population standard deviation before the Euclidean distance is taken; a pair (i, j)
+ * is eligible when j - i >= excl (trivial-match exclusion).
+ *   series device FP32 [N].   l in [2, 4096], N >= l.   excl >= 1.
+ *   out    host; dist2 is the FP64 squared distance of the z-normalised l-mers.
+ * Errors: CPPGB_ERR_ARG, CPPGB_ERR_CAPACITY (as for cpp_closest_pair), CPPGB_ERR_NUMERIC (an
+ *         l-mer of zero variance or a non-finite sample), CPPGB_ERR_CUDA.
+ */
+size_t tsmm_motif_workspace_size(int64_t N, int64_t l, int mode);
+int tsmm_motif(const float* series, int64_t N, int64_t l, int64_t excl, int mode,
+               cpp_pair_result* out, void* ws, size_t ws_bytes, void* stream);
+
+/* Result of a two-locus scan. */
+typedef struct {
+  int64_t i, j;        /* best SNP pair, i < j; -1 when S < 2 */
+  int64_t score;       /* |u_A * m_controls - u_B * m_cases| = |P_A - P_B| * m_cases * m_controls */
+  int32_t countsA[9];  /* cases: countsA[3a+b] = #subjects with g_i = a, g_j = b */
+  int32_t countsB[9];  /* controls, same layout */
+} twolocus_result;
+
+/*
+ * twolocus_scan -- two-locus association (Sec. 6): the SNP pair maximising |P_A(i,j) - P_B(i,j)|,
+ * where P_Q(i,j) is the fraction of subjects of group Q whose genotypes at SNPs i and j match
+ * (the correlation of Sec. 5.3; matches as in Sec. 2).  Exact integer arithmetic.
+ *   planes device uint64 [S][2 groups][2 planes][W]: group 0 = cases (m_cases subjects),
+ *          group 1 = controls; plane 0 has bit [g == 1], plane 1 bit [g == 2] (the one-hot code
+ *          of Sec. 5.3 with the g == 0 plane implied); bit b of word w is subject 64w+b; bits
+ *          at or beyond the group size must be 0.
+ *   W      words per plane, W >= ceil(max(m_cases, m_controls) / 64).
+ *   out    host; counts are the full 3x3 tables of the winning pair.
+ * Errors: CPPGB_ERR_ARG (sizes: S < 2^31, m_cases * m_controls < 2^40), CPPGB_ERR_CAPACITY, CPPGB_ERR_CUDA.
+ */
+size_t twolocus_scan_workspace_size(int64_t S, int64_t W);
+int twolocus_scan(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls,
+                  twolocus_result* out, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * frnn_query -- fixed-radius near neighbours (Sec. 3.5): for every point p_i its R-neighbourhood
+ * N(i) = { j != i : d(p_i, p_j) <= R }, with j in N(i) iff i in N(j).  The decision is the FP64
+ * test sum_k (x_ik - x_jk)^2 <= R*R (coordinate order).
+ *   pts      device FP32 row-major [n][ld], d in [1, 4] (uniform-grid cell hash) or
+ *            d in [5, 4096] (tiled all-pairs with a radius test).
+ *   R        radius, finite and >= 0.
+ *   row_ptr  device int64 [n+1], CSR offsets (written).
+ *   cols     device int32 [cols_cap], neighbour indices ascending within each row (written).
+ *   n_pairs_out host; the number of directed pairs (= row_ptr[n]) -- set also when cols_cap is
+ *            too small, in which case CPPGB_ERR_CAPACITY is returned and cols is untouched.
+ */
+size_t frnn_query_workspace_size(int64_t n, int d);
+int frnn_query(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t* row_ptr, int32_t* cols,
+               int64_t cols_cap, int64_t* n_pairs_out, void* ws, size_t ws_bytes, void* stream);
+
+/* One instance of a batch. */
+typedef struct {
+  const float* pts; /* device FP32 [n][d] row-major (ld = d) */
+  int64_t n;
+  int32_t d;        /* 1 .. 256 */
+  int32_t pad_;
+  double R;         /* FRNN radius for this instance (< 0: no FRNN output) */
+} cpp_instance;
+
+/*
+ * cpp_batch -- many independent CPP + FRNN instances of uneven n and d in one persistent launch
+ * (the problems of Sec. 3 and Sec. 3.5, instance by instance).
+ *   inst        host array [count].
+ *   out_cpp     host [count]: closest pair of each instance (as cpp_closest_pair, FP32 plain mode).
+ *   pair_counts host int64 [count]: number of undirected pairs (i < j) with d <= R per instance.
+ *   pairs       device int32 [pairs_cap][2]: the (i, j) pairs, instance after instance, ascending (i, j).
+ * Errors: CPPGB_ERR_ARG, CPPGB_ERR_CAPACITY (pairs_cap or ws too small), CPPGB_ERR_CUDA.
+ */
+size_t cpp_batch_workspace_size(const cpp_instance* inst, int64_t count);
+int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp, int64_t* pair_counts,
+              int32_t* pairs, int64_t pairs_cap, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Diagnostics (no counterpart in the paper; used to measure the library).
+ * cpp_set_stage_timing(1) makes the dense searches record CUDA events on their stream around
+ * their stages; cpp_stage_times() then copies the last call's stage durations in milliseconds
+ * (per calling thread) into ms[0..cap) as [prep, dense all-pairs stage, FP64 recheck] and returns
+ * how many it wrote.  cpp_launch_count() returns the number of kernels this library has launched
+ * in the process so far.
+ */
+void cpp_set_stage_timing(int on);
+int cpp_stage_times(double* ms, int cap);
+int64_t cpp_launch_count(void);
+
+/* 1 when this build carries the tensor-core filter modes (CPPGB_MODE_FILTER_*), else 0. */
+int cpp_filter_available(void);
+
+/* Message for the last non-OK status returned on the calling thread ("" if none). */
+const char* cpp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPPGB_H */

@@ -1,0 +1,270 @@
+"""Thin Python binding of the C ABI in ``include/cppgb.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Tensors must already live on
+the current CUDA device; the binding passes their raw pointers, sizes a workspace with the
+matching ``*_workspace_size`` query (allocated through torch), passes the current torch stream,
+and turns a non-OK status into :class:`CppgbError`.  All computation happens in the library's
+CUDA kernels; if ``libcppgb.so`` is missing the import fails loudly (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcppgb.so")
+
+OK, ERR_ARG, ERR_CAPACITY, ERR_TIMEOUT, ERR_CUDA, ERR_NUMERIC = 0, 1, 2, 3, 4, 5
+F32, F64 = 0, 1
+MODES = {"plain_fp32": 0, "filter_bf16": 1, "filter_fp16": 2}
+
+
+class CppgbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+class cpp_pair_result(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_int64), ("j", ctypes.c_int64), ("dist", ctypes.c_double),
+                ("dist2", ctypes.c_double), ("filter_err", ctypes.c_double), ("filter_bound", ctypes.c_double),
+                ("n_emitted", ctypes.c_int64), ("n_rechecked", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class twolocus_result(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_int64), ("j", ctypes.c_int64), ("score", ctypes.c_int64),
+                ("countsA", ctypes.c_int32 * 9), ("countsB", ctypes.c_int32 * 9)]
+
+    def as_dict(self):
+        return {"i": self.i, "j": self.j, "score": self.score,
+                "countsA": np.array(list(self.countsA), dtype=np.int32),
+                "countsB": np.array(list(self.countsB), dtype=np.int32)}
+
+
+class cpp_instance(ctypes.Structure):
+    _fields_ = [("pts", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("R", ctypes.c_double)]
+
+
+_i64, _sz, _vp, _int = ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_int
+
+# name -> (restype, argtypes); the order of this table is the order of include/cppgb.h
+SIGNATURES = {
+    "cpp_closest_pair_workspace_size": (_sz, [_i64, _i64, _int]),
+    "cpp_closest_pair": (_int, [_vp, _int, _i64, _i64, _i64, _int, ctypes.POINTER(cpp_pair_result), _vp, _sz, _vp]),
+    "tsmm_motif_workspace_size": (_sz, [_i64, _i64, _int]),
+    "tsmm_motif": (_int, [_vp, _i64, _i64, _i64, _int, ctypes.POINTER(cpp_pair_result), _vp, _sz, _vp]),
+    "twolocus_scan_workspace_size": (_sz, [_i64, _i64]),
+    "twolocus_scan": (_int, [_vp, _i64, _i64, _i64, _i64, ctypes.POINTER(twolocus_result), _vp, _sz, _vp]),
+    "frnn_query_workspace_size": (_sz, [_i64, _int]),
+    "frnn_query": (_int, [_vp, _i64, _int, _i64, ctypes.c_double, _vp, _vp, _i64, ctypes.POINTER(_i64), _vp, _sz,
+                          _vp]),
+    "cpp_batch_workspace_size": (_sz, [ctypes.POINTER(cpp_instance), _i64]),
+    "cpp_batch": (_int, [ctypes.POINTER(cpp_instance), _i64, ctypes.POINTER(cpp_pair_result), ctypes.POINTER(_i64),
+                         _vp, _i64, _vp, _sz, _vp]),
+    "cpp_set_stage_timing": (None, [_int]),
+    "cpp_stage_times": (_int, [ctypes.POINTER(ctypes.c_double), _int]),
+    "cpp_launch_count": (_i64, []),
+    "cpp_filter_available": (_int, []),
+    "cpp_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is not built; run paper_1407_5609_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _raise(status: int):
+    if status != OK:
+        raise CppgbError(status, lib().cpp_last_error().decode(errors="replace"))
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    # 256-byte alignment: torch's CUDA allocator hands out 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _mode(mode) -> int:
+    return MODES[mode] if isinstance(mode, str) else int(mode)
+
+
+def _check_cuda(t: torch.Tensor, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+
+
+# ---------------------------------------------------------------- entry points
+def filters_available() -> bool:
+    return bool(lib().cpp_filter_available())
+
+
+def cpp_set_stage_timing(on: bool = True) -> None:
+    lib().cpp_set_stage_timing(1 if on else 0)
+
+
+def cpp_stage_times() -> list:
+    buf = (ctypes.c_double * 8)()
+    k = lib().cpp_stage_times(buf, 8)
+    return [buf[q] for q in range(k)]
+
+
+def cpp_launch_count() -> int:
+    return int(lib().cpp_launch_count())
+
+
+def cpp_closest_pair_workspace_size(n: int, d: int, mode="plain_fp32") -> int:
+    return int(lib().cpp_closest_pair_workspace_size(n, d, _mode(mode)))
+
+
+def cpp_closest_pair(pts: torch.Tensor, mode="plain_fp32", ws: torch.Tensor | None = None, stream=None) -> dict:
+    """Closest pair of the rows of ``pts`` (float32/float64 [n][d] on the GPU)."""
+    _check_cuda(pts, "pts")
+    if pts.dim() != 2 or pts.stride(1) != 1:
+        raise ValueError("pts must be 2-D with unit column stride")
+    dtype = {torch.float32: F32, torch.float64: F64}[pts.dtype]
+    n, d = pts.shape
+    m = _mode(mode)
+    need = cpp_closest_pair_workspace_size(n, d, m)
+    if ws is None:
+        ws = _workspace(need, pts.device)
+    out = cpp_pair_result()
+    call = lambda w: lib().cpp_closest_pair(pts.data_ptr() if n else None, dtype, n, d, pts.stride(0) if n else d,
+                                            m, ctypes.byref(out), w.data_ptr(), w.numel(), _stream(stream))
+    st = call(ws)
+    if st == ERR_CAPACITY and out.n_emitted > 0:   # many exact ties: retry once with room for all candidates
+        st = call(_workspace(need + 24 * int(out.n_emitted * 1.05) + 4096, pts.device))
+    _raise(st)
+    return out.as_dict()
+
+
+def tsmm_motif_workspace_size(N: int, l: int, mode="plain_fp32") -> int:
+    return int(lib().tsmm_motif_workspace_size(N, l, _mode(mode)))
+
+
+def tsmm_motif(series: torch.Tensor, l: int, excl: int, mode="plain_fp32", ws: torch.Tensor | None = None,
+               stream=None) -> dict:
+    """Motif pair of the float32 series (1-D, on the GPU): closest pair of z-normalised l-mers."""
+    _check_cuda(series, "series")
+    if series.dim() != 1 or series.dtype != torch.float32 or not series.is_contiguous():
+        raise ValueError("series must be a contiguous 1-D float32 tensor")
+    N = series.shape[0]
+    m = _mode(mode)
+    if ws is None:
+        ws = _workspace(tsmm_motif_workspace_size(N, l, m), series.device)
+    out = cpp_pair_result()
+    call = lambda w: lib().tsmm_motif(series.data_ptr(), N, l, excl, m, ctypes.byref(out), w.data_ptr(), w.numel(),
+                                      _stream(stream))
+    st = call(ws)
+    if st == ERR_CAPACITY and out.n_emitted > 0:   # many exact ties: retry once with room for all candidates
+        need = tsmm_motif_workspace_size(N, l, m)
+        st = call(_workspace(need + 24 * int(out.n_emitted * 1.05) + 4096, series.device))
+    _raise(st)
+    return out.as_dict()
+
+
+def twolocus_scan_workspace_size(S: int, W: int) -> int:
+    return int(lib().twolocus_scan_workspace_size(S, W))
+
+
+def twolocus_scan(planes: torch.Tensor, m_cases: int, m_controls: int, ws: torch.Tensor | None = None,
+                  stream=None) -> dict:
+    """Two-locus scan over bitplanes uint64-as-int64 [S][2][2][W] on the GPU."""
+    _check_cuda(planes, "planes")
+    if planes.dim() != 4 or planes.shape[1:3] != (2, 2) or planes.element_size() != 8 or not planes.is_contiguous():
+        raise ValueError("planes must be a contiguous 64-bit tensor [S][2][2][W]")
+    S, W = planes.shape[0], planes.shape[3]
+    if ws is None:
+        ws = _workspace(twolocus_scan_workspace_size(S, W), planes.device)
+    out = twolocus_result()
+    _raise(lib().twolocus_scan(planes.data_ptr() if S else None, S, W, m_cases, m_controls, ctypes.byref(out),
+                               ws.data_ptr(), ws.numel(), _stream(stream)))
+    return out.as_dict()
+
+
+def frnn_query_workspace_size(n: int, d: int) -> int:
+    return int(lib().frnn_query_workspace_size(n, d))
+
+
+def frnn_query(pts: torch.Tensor, R: float, cols_cap: int | None = None, ws: torch.Tensor | None = None,
+               stream=None):
+    """R-neighbourhoods of the rows of float32 ``pts`` [n][d]: returns (row_ptr int64, cols int32)."""
+    _check_cuda(pts, "pts")
+    if pts.dim() != 2 or pts.dtype != torch.float32 or pts.stride(1) != 1:
+        raise ValueError("pts must be float32 [n][d] with unit column stride")
+    n, d = pts.shape
+    if ws is None:
+        ws = _workspace(frnn_query_workspace_size(n, d), pts.device)
+    row_ptr = torch.empty(n + 1, dtype=torch.int64, device=pts.device)
+    total = _i64(0)
+    cap = int(cols_cap) if cols_cap is not None else max(16 * n, 1024)
+    while True:
+        cols = torch.empty(max(cap, 1), dtype=torch.int32, device=pts.device)
+        st = lib().frnn_query(pts.data_ptr() if n else None, n, d, pts.stride(0) if n else d, float(R),
+                              row_ptr.data_ptr(), cols.data_ptr(), cap, ctypes.byref(total), ws.data_ptr(),
+                              ws.numel(), _stream(stream))
+        if st == ERR_CAPACITY and cols_cap is None and total.value > cap:
+            cap = total.value
+            continue
+        _raise(st)
+        return row_ptr, cols[:total.value]
+
+
+def cpp_batch_workspace_size(instances) -> int:
+    arr = (cpp_instance * len(instances))(*instances)
+    return int(lib().cpp_batch_workspace_size(arr, len(instances)))
+
+
+def cpp_batch(points: list, radii: list, pairs_cap: int | None = None, ws: torch.Tensor | None = None,
+              stream=None):
+    """Closest pair + R-pairs of every instance in one call.
+
+    ``points`` is a list of float32 [n][d] CUDA tensors (contiguous), ``radii`` their R.
+    Returns (list of result dicts, pair_counts int64 numpy, pairs int32 tensor [P][2]).
+    """
+    count = len(points)
+    inst = []
+    for p, R in zip(points, radii):
+        _check_cuda(p, "points")
+        if p.dim() != 2 or p.dtype != torch.float32 or not p.is_contiguous():
+            raise ValueError("each instance must be a contiguous float32 [n][d] tensor")
+        inst.append(cpp_instance(p.data_ptr(), p.shape[0], p.shape[1], 0, float(R)))
+    arr = (cpp_instance * count)(*inst)
+    device = points[0].device if count else torch.device("cuda")
+    if ws is None:
+        ws = _workspace(int(lib().cpp_batch_workspace_size(arr, count)), device)
+    outs = (cpp_pair_result * max(count, 1))()
+    counts = (_i64 * max(count, 1))()
+    cap = int(pairs_cap) if pairs_cap is not None else 1 << 20
+    pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=device)
+    _raise(lib().cpp_batch(arr, count, outs, counts, pairs.data_ptr(), cap, ws.data_ptr(), ws.numel(),
+                           _stream(stream)))
+    c = np.array(list(counts)[:count], dtype=np.int64)
+    return [outs[q].as_dict() for q in range(count)], c, pairs[:int(c.sum())]

@@ -1,0 +1,322 @@
+// C-ABI entry points: argument checks, workspace layout, stage sequencing, result read-back.
+#include <math.h>
+#include <stdarg.h>
+#include <string.h>
+
+#include "common.cuh"
+
+#include <atomic>
+
+namespace cppgb {
+
+static thread_local char g_err[512] = "";
+static std::atomic<long long> g_launches{0};
+static std::atomic<int> g_timing{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Per-thread CUDA events for the optional stage timing of the dense searches.
+struct StageTimer {
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double ms[3] = {0, 0, 0};
+  int n = 0;
+  bool ready = false;
+  bool init() {
+    if (!ready) {
+      for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return false;
+      ready = true;
+    }
+    return true;
+  }
+};
+static thread_local StageTimer g_timer;
+
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+namespace {
+
+constexpr double kU32 = 5.9604644775390625e-08;  // 2^-24
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+int check_device() {
+  int dev = 0, major = 0, minor = 0;
+  CPPGB_CUDA_TRY(cudaGetDevice(&dev));
+  CPPGB_CUDA_TRY(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+  CPPGB_CUDA_TRY(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+  if (major != 10 || minor != 3)
+    return set_error(CPPGB_ERR_CUDA, "this library is built for sm_103a only; device %d is sm_%d%d", dev, major, minor);
+  return CPPGB_OK;
+}
+
+bool is_filter(int mode) { return mode == CPPGB_MODE_FILTER_BF16 || mode == CPPGB_MODE_FILTER_FP16; }
+bool mode_ok(int mode) { return mode == CPPGB_MODE_PLAIN_FP32 || is_filter(mode); }
+
+// ---------------------------------------------------------------- dense search layout
+struct DenseLayout {
+  int64_t n, n_pad, Kp, cap;
+  size_t elem;
+  DenseScalars* sc;
+  float* norms;
+  float* eps;
+  void* X;
+  Candidate* cand;
+  double* d2buf;
+  size_t bytes;
+};
+
+// The candidate buffer takes whatever the caller's workspace holds beyond the fixed part, at
+// least the default capacity that *_workspace_size() reports.
+DenseLayout dense_layout(void* ws, int64_t n, int64_t d, int mode, size_t ws_bytes = 0) {
+  DenseLayout L;
+  L.n = n;
+  L.n_pad = round_up(n > 0 ? n : 1, 256);
+  L.Kp = round_up(d, is_filter(mode) ? 64 : 16);
+  L.elem = is_filter(mode) ? 2 : 4;
+  int64_t cap = 4 * n;
+  cap = cap < (1 << 16) ? (1 << 16) : (cap > (1 << 22) ? (1 << 22) : cap);
+  Carver c(ws);
+  L.sc = c.take<DenseScalars>(1);
+  L.norms = c.take<float>(L.n_pad);
+  L.eps = c.take<float>(L.n_pad);
+  L.X = c.take<char>((size_t)L.n_pad * L.Kp * L.elem);
+  const size_t fixed = c.bytes() + 512;
+  if (ws_bytes > fixed) {
+    int64_t fit = (int64_t)((ws_bytes - fixed) / (sizeof(Candidate) + sizeof(double)));
+    if (fit > cap) cap = fit;
+  }
+  L.cap = cap;
+  L.cand = c.take<Candidate>(L.cap);
+  L.d2buf = c.take<double>(L.cap);
+  L.bytes = c.bytes();
+  return L;
+}
+
+// e_acc = kappa * max |x~|^2 bounds the Gram-form error |D~ - |x~_i - x~_j|^2|:
+//   FP32 FFMA:  2 gamma_K |x||y| (dot) + gamma_K (|x|^2 + |y|^2) (norms) + 3 roundings of the
+//               epilogue on magnitudes <= 2 (|x|^2 + |y|^2)  ->  (4 gamma_K + 8u) max|x|^2
+//   tensor cores (exact 16-bit products, FP32 accumulation whose internal rounding is not
+//               specified to be round-to-nearest): the dot term padded to 2 * K * 2^-22 |x||y|,
+//               norms from the prep's two-level sums (22u each) and the same epilogue terms.
+float kappa_for(int mode, int64_t Kp) {
+  double K = (double)Kp;
+  if (!is_filter(mode)) {
+    double g = K * kU32 / (1.0 - K * kU32);
+    return (float)((4.0 * g + 8.0 * kU32) * 1.01);
+  }
+  return (float)((2.0 * 2.0 * K * 0x1p-22 + 2.0 * 22.0 * kU32 + 8.0 * kU32) * 1.01);
+}
+
+struct Source {
+  bool lmers;
+  const void* pts;
+  int dtype;
+  int64_t d, ld;
+  const float* series;
+  int64_t l;
+};
+
+int dense_search(const Source& src, int64_t n, int64_t d, int64_t excl, int mode, cpp_pair_result* out, void* ws,
+                 size_t ws_bytes, cudaStream_t st) {
+  DenseLayout L = dense_layout(ws, n, d, mode, ws_bytes);
+  if (ws_bytes < L.bytes)
+    return set_error(CPPGB_ERR_CAPACITY, "workspace too small: %zu bytes given, %zu needed", ws_bytes, L.bytes);
+  if (((uintptr_t)ws & 255) != 0) return set_error(CPPGB_ERR_ARG, "workspace must be 256-byte aligned");
+  if (is_filter(mode) && !gram_tc_available())
+    return set_error(CPPGB_ERR_ARG, "tensor-core filter modes are not available in this build");
+
+  const bool timing = g_timing.load() != 0 && g_timer.init();
+  g_timer.n = 0;
+  if (timing) CPPGB_CUDA_TRY(cudaEventRecord(g_timer.ev[0], st));
+  int rc;
+  if ((rc = launch_init_scalars(L.sc, st))) return rc;
+  if (src.lmers)
+    rc = launch_prep_lmers(src.series, n, src.l, mode, L.X, L.n_pad, L.Kp, L.norms, L.eps, L.sc, st);
+  else
+    rc = launch_prep_points(src.pts, src.dtype, n, d, src.ld, mode, L.X, L.n_pad, L.Kp, L.norms, L.eps, L.sc, st);
+  if (rc) return rc;
+  if ((rc = launch_bounds(L.sc, kappa_for(mode, L.Kp), st))) return rc;
+  if (timing) CPPGB_CUDA_TRY(cudaEventRecord(g_timer.ev[1], st));
+
+  DenseScalars h;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (is_filter(mode))
+      rc = launch_gram_tc(L.X, mode, n, L.n_pad, L.Kp, excl, L.norms, L.sc, L.cand, L.cap, st);
+    else
+      rc = launch_gram_simt((const float*)L.X, n, L.Kp, excl, L.norms, L.sc, L.cand, L.cap, st);
+    if (rc) return rc;
+    if (timing) CPPGB_CUDA_TRY(cudaEventRecord(g_timer.ev[2], st));
+    CPPGB_CUDA_TRY(cudaMemcpyAsync(&h, L.sc, sizeof h, cudaMemcpyDeviceToHost, st));
+    CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h.status & 1u) return set_error(CPPGB_ERR_NUMERIC, "non-finite input value");
+    if (h.status & 2u) return set_error(CPPGB_ERR_NUMERIC, "an l-mer has zero variance");
+    if ((int64_t)h.n_cand <= L.cap) break;
+    if (pass == 1) {
+      // report the number of candidates a larger workspace would have to hold
+      memset(out, 0, sizeof *out);
+      out->i = out->j = -1;
+      out->n_emitted = (int64_t)h.n_cand;
+      return set_error(CPPGB_ERR_CAPACITY,
+                       "candidate buffer overflow (%llu > %lld) at the final bound: many pairs tie within the "
+                       "filter's error; pass a workspace of %zu bytes",
+                       (unsigned long long)h.n_cand, (long long)L.cap,
+                       dense_layout(nullptr, n, d, mode).bytes +
+                           (size_t)(h.n_cand - L.cap) * (sizeof(Candidate) + sizeof(double)) + 4096);
+    }
+    // The bound U is final now; a second pass emits only pairs whose lower bound meets it.
+    CPPGB_CUDA_TRY(cudaMemsetAsync(&L.sc->n_cand, 0, sizeof(L.sc->n_cand), st));
+  }
+  const int64_t n_live = (int64_t)h.n_cand;
+  if (src.lmers)
+    rc = launch_recheck_lmers(src.series, src.l, L.sc, L.cand, L.cap, L.d2buf, n_live, st);
+  else
+    rc = launch_recheck_points(src.pts, src.dtype, d, src.ld, L.sc, L.cand, L.cap, L.d2buf, n_live, st);
+  if (rc) return rc;
+  if (timing) CPPGB_CUDA_TRY(cudaEventRecord(g_timer.ev[3], st));
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(&h, L.sc, sizeof h, cudaMemcpyDeviceToHost, st));
+  CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
+  if (timing) {
+    float a = 0, b = 0, c = 0;
+    CPPGB_CUDA_TRY(cudaEventElapsedTime(&a, g_timer.ev[0], g_timer.ev[1]));
+    CPPGB_CUDA_TRY(cudaEventElapsedTime(&b, g_timer.ev[1], g_timer.ev[2]));
+    CPPGB_CUDA_TRY(cudaEventElapsedTime(&c, g_timer.ev[2], g_timer.ev[3]));
+    g_timer.ms[0] = a; g_timer.ms[1] = b; g_timer.ms[2] = c;
+    g_timer.n = 3;
+  }
+
+  cpp_pair_result r;
+  memset(&r, 0, sizeof r);
+  double best;
+  memcpy(&best, &h.best_bits, sizeof best);
+  if (h.best_ij == ~0ull || !(best < INFINITY)) {
+    r.i = r.j = -1;
+    r.dist = r.dist2 = INFINITY;
+  } else {
+    r.i = (int64_t)(h.best_ij >> 32);
+    r.j = (int64_t)(h.best_ij & 0xffffffffu);
+    r.dist2 = best;
+    r.dist = sqrt(best);
+  }
+  float fe, fb;
+  memcpy(&fe, &h.ferr_bits, 4);
+  memcpy(&fb, &h.U_bits, 4);
+  r.filter_err = fe;
+  r.filter_bound = fb;
+  r.n_emitted = (int64_t)h.n_cand;
+  r.n_rechecked = (int64_t)h.n_rech;
+  *out = r;
+  return CPPGB_OK;
+}
+
+}  // namespace
+}  // namespace cppgb
+
+using namespace cppgb;
+
+extern "C" {
+
+const char* cpp_last_error(void) { return g_err; }
+
+int cpp_filter_available(void) { return gram_tc_available() ? 1 : 0; }
+
+void cpp_set_stage_timing(int on) { g_timing.store(on ? 1 : 0); }
+
+int cpp_stage_times(double* ms, int cap) {
+  int k = 0;
+  for (; k < g_timer.n && k < cap; ++k) ms[k] = g_timer.ms[k];
+  return k;
+}
+
+int64_t cpp_launch_count(void) { return (int64_t)g_launches.load(); }
+
+// ------------------------------------------------------------------ closest pair
+size_t cpp_closest_pair_workspace_size(int64_t n, int64_t d, int mode) {
+  if (n < 0 || d < 1 || !mode_ok(mode)) return 0;
+  return dense_layout(nullptr, n, d, mode).bytes;
+}
+
+int cpp_closest_pair(const void* pts, int dtype, int64_t n, int64_t d, int64_t ld, int mode, cpp_pair_result* out,
+                     void* ws, size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  if (!out) return set_error(CPPGB_ERR_ARG, "out is NULL");
+  if (n < 0 || n > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "n out of range (%lld)", (long long)n);
+  if (d < 1 || d > 4096 || ld < d) return set_error(CPPGB_ERR_ARG, "need 1 <= d <= 4096 and ld >= d");
+  if (dtype != CPPGB_F32 && dtype != CPPGB_F64) return set_error(CPPGB_ERR_ARG, "dtype must be CPPGB_F32 or CPPGB_F64");
+  if (!mode_ok(mode)) return set_error(CPPGB_ERR_ARG, "unknown mode %d", mode);
+  if (n > 0 && !pts) return set_error(CPPGB_ERR_ARG, "pts is NULL");
+  if (!ws) return set_error(CPPGB_ERR_ARG, "workspace is NULL");
+  int rc = check_device();
+  if (rc) return rc;
+  Source src{false, pts, dtype, d, ld, nullptr, 0};
+  return dense_search(src, n, d, 1, mode, out, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ motif pair
+size_t tsmm_motif_workspace_size(int64_t N, int64_t l, int mode) {
+  if (l < 2 || N < l || !mode_ok(mode)) return 0;
+  return dense_layout(nullptr, N - l + 1, l, mode).bytes;
+}
+
+int tsmm_motif(const float* series, int64_t N, int64_t l, int64_t excl, int mode, cpp_pair_result* out, void* ws,
+               size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  if (!out) return set_error(CPPGB_ERR_ARG, "out is NULL");
+  if (!series) return set_error(CPPGB_ERR_ARG, "series is NULL");
+  if (l < 2 || l > 4096 || N < l) return set_error(CPPGB_ERR_ARG, "need 2 <= l <= 4096 and N >= l");
+  if (N - l + 1 > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "too many l-mers");
+  if (excl < 1) return set_error(CPPGB_ERR_ARG, "excl must be >= 1");
+  if (!mode_ok(mode)) return set_error(CPPGB_ERR_ARG, "unknown mode %d", mode);
+  if (!ws) return set_error(CPPGB_ERR_ARG, "workspace is NULL");
+  int rc = check_device();
+  if (rc) return rc;
+  Source src{true, nullptr, CPPGB_F32, l, l, series, l};
+  return dense_search(src, N - l + 1, l, excl, mode, out, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ two-locus
+size_t twolocus_scan_workspace_size(int64_t S, int64_t W) {
+  if (S < 0 || W < 1) return 0;
+  Carver c(nullptr);
+  c.take<twolocus_result>(1);
+  c.take<char>((size_t)16 * (size_t)(twolocus_num_partials(S) > 0 ? twolocus_num_partials(S) : 1));
+  return c.bytes();
+}
+
+int twolocus_scan(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls,
+                  twolocus_result* out, void* ws, size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  if (!out) return set_error(CPPGB_ERR_ARG, "out is NULL");
+  if (S < 0 || S > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "S out of range");
+  if (m_cases < 1 || m_controls < 1) return set_error(CPPGB_ERR_ARG, "group sizes must be >= 1");
+  if (W < (m_cases + 63) / 64 || W < (m_controls + 63) / 64)
+    return set_error(CPPGB_ERR_ARG, "W = %lld words cannot hold the groups", (long long)W);
+  if ((double)m_cases * (double)m_controls >= 1099511627776.0)
+    return set_error(CPPGB_ERR_ARG, "m_cases * m_controls must be < 2^40");
+  if (S > 0 && !planes) return set_error(CPPGB_ERR_ARG, "planes is NULL");
+  if (!ws) return set_error(CPPGB_ERR_ARG, "workspace is NULL");
+  size_t need = twolocus_scan_workspace_size(S, W);
+  if (ws_bytes < need) return set_error(CPPGB_ERR_CAPACITY, "workspace too small: %zu given, %zu needed", ws_bytes, need);
+  if (((uintptr_t)ws & 255) != 0) return set_error(CPPGB_ERR_ARG, "workspace must be 256-byte aligned");
+  int rc = check_device();
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  Carver c(ws);
+  twolocus_result* dres = c.take<twolocus_result>(1);
+  const int64_t np = twolocus_num_partials(S);
+  void* partials = c.take<char>((size_t)16 * (size_t)(np > 0 ? np : 1));
+  if ((rc = launch_twolocus(planes, S, W, m_cases, m_controls, partials, np, dres, st))) return rc;
+  twolocus_result h;
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(&h, dres, sizeof h, cudaMemcpyDeviceToHost, st));
+  CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
+  *out = h;
+  return CPPGB_OK;
+}
+
+}  // extern "C"

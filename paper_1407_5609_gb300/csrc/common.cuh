@@ -1,0 +1,147 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/cppgb.h"
+
+namespace cppgb {
+
+// ------------------------------------------------------------------ errors
+int set_error(int code, const char* fmt, ...);
+
+#define CPPGB_CUDA_TRY(expr)                                                              \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return ::cppgb::set_error(CPPGB_ERR_CUDA, "%s failed: %s (%s:%d)", #expr,            \
+                                cudaGetErrorString(e_), __FILE__, __LINE__);              \
+  } while (0)
+
+// Every kernel launch is followed by this check, which also counts the launch.
+void note_launch();
+#define CPPGB_LAUNCH_CHECK()     \
+  do {                           \
+    ::cppgb::note_launch();      \
+    CPPGB_CUDA_TRY(cudaGetLastError()); \
+  } while (0)
+
+// ------------------------------------------------------------------ workspace
+// Carves a caller-provided device buffer into 256-byte aligned pieces.  With base == nullptr it
+// only measures (used by the *_workspace_size queries), so both paths share one layout.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+  size_t bytes() const { return (off + 255) & ~size_t(255); }
+};
+
+// ------------------------------------------------------------------ dense stage state
+// One emitted candidate pair of the dense all-pairs stage.
+struct Candidate {
+  int32_t i, j;  // global row indices, i < j
+  float d2f;     // filtered squared distance D~ (FP32 Gram value)
+  float pad;
+};
+
+// Bound parameters of the dense stage for one problem (all in squared-distance units unless noted).
+struct BoundParams {
+  float eps_pair;  // eps_i + eps_j upper bound, in distance units
+  float e_acc;     // bound on |D~ - |x~_i - x~_j|^2| from the Gram arithmetic
+};
+
+// Scalars of one dense all-pairs search, living in the workspace.
+struct DenseScalars {
+  BoundParams bp;               // written on the device once the row errors are known
+  unsigned int U_bits;          // running upper bound on the best true d^2 (non-negative float bits)
+  unsigned int eps_bits;        // max over rows of eps_i (distance from the exact row, float bits)
+  unsigned int n2_bits;         // max over rows of |x~_i|^2 (float bits)
+  unsigned int status;          // device-side flags: 1 = non-finite input, 2 = zero-variance l-mer
+  unsigned long long n_cand;    // candidates emitted (may exceed capacity -> overflow)
+  unsigned long long n_rech;    // candidates rechecked in FP64
+  unsigned long long best_bits; // FP64 bits of the best rechecked d^2
+  unsigned long long best_ij;   // (i << 32) | j of the best pair among equal d^2
+  unsigned int ferr_bits;       // max |d2_fp64 - D~| over rechecked candidates (float bits)
+  unsigned int pad[1];
+};
+
+// True distance d of a pair with filtered value D~ satisfies
+//   sqrt(max(D~ - e_acc, 0)) - eps_pair  <=  d  <=  sqrt(D~ + e_acc) + eps_pair.
+// upper_d2(D~) bounds d^2 from above; theta(U) is the largest D~ whose lower bound on d^2 is
+// still <= U.  Both are rounded outwards by a relative pad that covers the FP32 evaluation and
+// the FP64 rounding of the reference distances.
+__device__ __forceinline__ float upper_d2(float D, BoundParams bp) {
+  float s = sqrtf(fmaxf(D + bp.e_acc, 0.f)) + bp.eps_pair;
+  return s * s * (1.f + 0x1p-19f) + 1e-30f;
+}
+__device__ __forceinline__ float theta_of(float U, BoundParams bp) {
+  float s = sqrtf(U * (1.f + 0x1p-19f)) + bp.eps_pair;
+  return (s * s + bp.e_acc) * (1.f + 0x1p-19f) + 1e-30f;
+}
+
+// atomic min/max on non-negative floats through their bit patterns (monotone for x >= 0)
+__device__ __forceinline__ void atomic_min_nonneg(unsigned int* addr, float v) {
+  atomicMin(addr, __float_as_uint(fmaxf(v, 0.f)));
+}
+__device__ __forceinline__ void atomic_max_nonneg(unsigned int* addr, float v) {
+  atomicMax(addr, __float_as_uint(fmaxf(v, 0.f)));
+}
+
+// Upper-triangular tile list: tiles (bi, bj) with bj - bi >= delta among nb x nb blocks, in the
+// order t -> (r, c) of a lower-triangular walk of an m x m triangle, m = nb - delta,
+// bi = c, bj = r + delta.  Consecutive t share the column block bj (its tile stays in L2).
+__host__ __device__ __forceinline__ int64_t tri_count(int64_t m) { return m > 0 ? m * (m + 1) / 2 : 0; }
+__device__ __forceinline__ void tri_decode(int64_t t, int64_t delta, int64_t* bi, int64_t* bj) {
+  int64_t r = (int64_t)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while (r > 0 && r * (r + 1) / 2 > t) --r;
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  int64_t c = t - r * (r + 1) / 2;
+  *bi = c;
+  *bj = r + delta;
+}
+
+// ------------------------------------------------------------------ launchers (host side)
+// Point / l-mer preparation: writes X [n_pad][Kp] (FP32, FP16 or BF16 by `mode`), row norms
+// |x~_i|^2 (FP32), row errors eps_i, and their maxima into the scalars.
+int launch_prep_points(const void* pts, int dtype, int64_t n, int64_t d, int64_t ld, int mode, void* X,
+                       int64_t n_pad, int64_t Kp, float* norms, float* eps, DenseScalars* sc,
+                       cudaStream_t st);
+int launch_prep_lmers(const float* series, int64_t n, int64_t l, int mode, void* X, int64_t n_pad,
+                      int64_t Kp, float* norms, float* eps, DenseScalars* sc, cudaStream_t st);
+
+// Dense all-pairs stage on FP32 CUDA cores.
+int launch_gram_simt(const float* X, int64_t n, int64_t Kp, int64_t excl, const float* norms,
+                     DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st);
+// Dense all-pairs stage on tcgen05 tensor cores (FP16 or BF16 operands).
+int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp, int64_t excl,
+                   const float* norms, DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st);
+bool gram_tc_available();
+
+// FP64 recheck of the surviving candidates and the lexicographic (d^2, i, j) minimum.
+// Source of the exact coordinates: points (dtype F32/F64, [n][ld]) or a series with l-mers.
+// n_live = min(candidates emitted, cap), read back by the host after the dense stage.
+int launch_recheck_points(const void* pts, int dtype, int64_t d, int64_t ld, DenseScalars* sc, const Candidate* cand, int64_t cap, double* d2buf,
+                          int64_t n_live, cudaStream_t st);
+int launch_recheck_lmers(const float* series, int64_t l, DenseScalars* sc,
+                         const Candidate* cand, int64_t cap, double* d2buf, int64_t n_live,
+                         cudaStream_t st);
+
+// Scalars reset and the bound parameters: e_acc = kappa * max_i |x~_i|^2, eps_pair = 2 max_i eps_i.
+int launch_init_scalars(DenseScalars* sc, cudaStream_t st);
+int launch_bounds(DenseScalars* sc, float kappa, cudaStream_t st);
+
+// Two-locus scan.
+int launch_twolocus(const uint64_t* planes, int64_t S, int64_t W, int64_t m1, int64_t m2, void* partials,
+                    int64_t n_partials, twolocus_result* dev_out, cudaStream_t st);
+int64_t twolocus_num_partials(int64_t S);
+
+}  // namespace cppgb

@@ -1,0 +1,148 @@
+// Dense all-pairs stage on FP32 CUDA cores (the plain comparison path).
+//
+// Every pair (i, j), i < j, j - i >= excl, of the n rows of X is evaluated in the Gram form
+//   D~_ij = |x~_i|^2 + |x~_j|^2 - 2 x~_i . x~_j
+// over 128 x 128 tiles of the upper triangle (FFMA, 8 x 8 accumulators per thread).  The tile
+// epilogue is fused: the tile minimum tightens a global upper bound U on the best true d^2, and
+// every pair whose lower bound could still be <= U is emitted as a candidate for the FP64
+// recheck.  The brute force over all pairs is the O(n^2 l) algorithm stated in Sec. 3.
+#include "common.cuh"
+
+namespace cppgb {
+namespace {
+
+constexpr int BM = 128, BK = 16, PAD = 4, NT = 256;
+
+// (the accumulation bound used with these tiles is derived on the host: sequential FFMA over Kp)
+__global__ void __launch_bounds__(NT, 2)
+    gram_simt_kernel(const float* __restrict__ X, int64_t n, int64_t Kp, int64_t excl, int64_t delta,
+                     const float* __restrict__ norms, DenseScalars* sc,
+                     Candidate* __restrict__ cand, int64_t cap) {
+  __shared__ __align__(16) float As[2][BK][BM + PAD];
+  __shared__ __align__(16) float Bs[2][BK][BM + PAD];
+  __shared__ float red[NT / 32];
+
+  int64_t bi, bj;
+  tri_decode((int64_t)blockIdx.x, delta, &bi, &bj);
+  const int64_t row0 = bi * BM, col0 = bj * BM;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int lrow = tid >> 2, lk = (tid & 3) * 4;
+
+  const float* Ag = X + (row0 + lrow) * Kp + lk;
+  const float* Bg = X + (col0 + lrow) * Kp + lk;
+  const int64_t half = 64 * Kp;
+
+  float acc[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+
+  float4 a0 = *reinterpret_cast<const float4*>(Ag), a1 = *reinterpret_cast<const float4*>(Ag + half);
+  float4 b0 = *reinterpret_cast<const float4*>(Bg), b1 = *reinterpret_cast<const float4*>(Bg + half);
+  auto stash = [&](int buf) {
+    As[buf][lk + 0][lrow] = a0.x; As[buf][lk + 1][lrow] = a0.y; As[buf][lk + 2][lrow] = a0.z; As[buf][lk + 3][lrow] = a0.w;
+    As[buf][lk + 0][lrow + 64] = a1.x; As[buf][lk + 1][lrow + 64] = a1.y; As[buf][lk + 2][lrow + 64] = a1.z; As[buf][lk + 3][lrow + 64] = a1.w;
+    Bs[buf][lk + 0][lrow] = b0.x; Bs[buf][lk + 1][lrow] = b0.y; Bs[buf][lk + 2][lrow] = b0.z; Bs[buf][lk + 3][lrow] = b0.w;
+    Bs[buf][lk + 0][lrow + 64] = b1.x; Bs[buf][lk + 1][lrow + 64] = b1.y; Bs[buf][lk + 2][lrow + 64] = b1.z; Bs[buf][lk + 3][lrow + 64] = b1.w;
+  };
+  stash(0);
+  __syncthreads();
+
+  const int64_t nk = Kp / BK;
+  for (int64_t kt = 0; kt < nk; ++kt) {
+    const int cur = (int)(kt & 1);
+    if (kt + 1 < nk) {
+      const int64_t o = (kt + 1) * BK;
+      a0 = *reinterpret_cast<const float4*>(Ag + o);
+      a1 = *reinterpret_cast<const float4*>(Ag + half + o);
+      b0 = *reinterpret_cast<const float4*>(Bg + o);
+      b1 = *reinterpret_cast<const float4*>(Bg + half + o);
+    }
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      float4 ra0 = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
+      float4 ra1 = *reinterpret_cast<const float4*>(&As[cur][k][64 + ty * 4]);
+      float4 rb0 = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
+      float4 rb1 = *reinterpret_cast<const float4*>(&Bs[cur][k][64 + tx * 4]);
+      float ra[8] = {ra0.x, ra0.y, ra0.z, ra0.w, ra1.x, ra1.y, ra1.z, ra1.w};
+      float rb[8] = {rb0.x, rb0.y, rb0.z, rb0.w, rb1.x, rb1.y, rb1.z, rb1.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(ra[r], rb[c], acc[r][c]);
+    }
+    if (kt + 1 < nk) stash(cur ^ 1);
+    __syncthreads();
+  }
+
+  // ---- fused epilogue: D~, tile minimum, bound update, candidate emission
+  int64_t gi[8], gj[8];
+  float nx[8], ny[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    gi[r] = row0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + r - 4);
+    gj[r] = col0 + (r < 4 ? tx * 4 + r : 64 + tx * 4 + r - 4);
+    nx[r] = norms[gi[r]];
+    ny[r] = norms[gj[r]];
+  }
+  float tmin = __int_as_float(0x7f800000);
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      bool ok = gi[r] < n && gj[c] < n && gj[c] - gi[r] >= excl;
+      float D = fmaf(-2.f, acc[r][c], nx[r] + ny[c]);
+      D = ok ? D : __int_as_float(0x7f800000);
+      acc[r][c] = D;
+      tmin = fminf(tmin, D);
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+  if ((tid & 31) == 0) red[tid >> 5] = tmin;
+  __syncthreads();
+  tmin = red[0];
+#pragma unroll
+  for (int w = 1; w < NT / 32; ++w) tmin = fminf(tmin, red[w]);
+  if (tmin == __int_as_float(0x7f800000)) return;  // no valid pair in this tile
+
+  const BoundParams bp = sc->bp;
+  const float ub = upper_d2(tmin, bp);
+  const float Ug = __uint_as_float(*reinterpret_cast<volatile unsigned int*>(&sc->U_bits));
+  const float th = theta_of(fminf(Ug, ub), bp);
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (acc[r][c] <= th) {
+        unsigned long long k = atomicAdd(&sc->n_cand, 1ull);
+        if ((int64_t)k < cap) {
+          Candidate cd;
+          cd.i = (int32_t)gi[r];
+          cd.j = (int32_t)gj[c];
+          cd.d2f = acc[r][c];
+          cd.pad = 0.f;
+          cand[k] = cd;
+        }
+      }
+    }
+  if (tid == 0) atomic_min_nonneg(&sc->U_bits, ub);
+}
+
+}  // namespace
+
+int launch_gram_simt(const float* X, int64_t n, int64_t Kp, int64_t excl, const float* norms, DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st) {
+  if (Kp % BK) return set_error(CPPGB_ERR_ARG, "internal: Kp %% 16 != 0");
+  const int64_t nb = (n + BM - 1) / BM;
+  // smallest block offset whose tiles hold a pair with j - i >= excl
+  int64_t delta = excl <= BM - 1 ? 0 : (excl - (BM - 1) + BM - 1) / BM;
+  const int64_t m = nb - delta;
+  const int64_t tiles = tri_count(m);
+  if (tiles <= 0) return CPPGB_OK;
+  if (tiles > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "too many tiles (%lld)", (long long)tiles);
+  gram_simt_kernel<<<(unsigned)tiles, NT, 0, st>>>(X, n, Kp, excl, delta, norms, sc, cand, cap);
+  CPPGB_LAUNCH_CHECK();
+  return CPPGB_OK;
+}
+
+}  // namespace cppgb
