@@ -101,7 +101,7 @@ class TSMM:
 
     def __init__(self, args):
         from paper_1407_5609_gb300 import synth
-        self.N, self.l, self.excl = 262144, 512, 256
+        self.N, self.l, self.excl = args.series_len, 512, 256
         self.series = synth.make_random_walk(self.N)
         n = self.N - self.l + 1
         m = n - self.excl
@@ -407,6 +407,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tsmm")
     ap.add_argument("--mode", choices=["plain_fp32", "filter_fp16", "filter_bf16"], default=None)
+    ap.add_argument("--series-len", type=int, default=262144,
+                    help="motif workload length (smaller values only for profiler captures)")
     ap.add_argument("--flush-l2", dest="flush_l2", action="store_true", default=True)
     ap.add_argument("--no-flush-l2", dest="flush_l2", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -117,6 +117,21 @@ int twolocus_scan(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases,
                   twolocus_result* out, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * twolocus_scan_noalloc -- the same scan and result as twolocus_scan, without a workspace.  The
+ * paper has no counterpart; this exists for callers that cannot allocate device memory: code
+ * embedded in a host framework that owns all device memory and offers no allocation hook, and
+ * latency-critical loops that cannot afford cudaMalloc/cudaFree, which may synchronise the whole
+ * device.  Its scratch is a fixed 1 MiB array inside the library, so S is limited to 23,104 SNPs
+ * (larger S returns CPPGB_ERR_CAPACITY with a message); every device that loads the library keeps
+ * that 1 MiB until the process exits.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call outside any stream capture.  All calls on a
+ * device share the array: calls whose work may overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  Planes and out are as for twolocus_scan.
+ */
+int twolocus_scan_noalloc(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls,
+                          twolocus_result* out, void* stream);
+
+/*
  * frnn_query -- fixed-radius near neighbours (Sec. 3.5): for every point p_i its R-neighbourhood
  * N(i) = { j != i : d(p_i, p_j) <= R }, with j in N(i) iff i in N(j).  The decision is the FP64
  * test sum_k (x_ik - x_jk)^2 <= R*R (coordinate order).

@@ -62,6 +62,7 @@ SIGNATURES = {
     "tsmm_motif": (_int, [_vp, _i64, _i64, _i64, _int, ctypes.POINTER(cpp_pair_result), _vp, _sz, _vp]),
     "twolocus_scan_workspace_size": (_sz, [_i64, _i64]),
     "twolocus_scan": (_int, [_vp, _i64, _i64, _i64, _i64, ctypes.POINTER(twolocus_result), _vp, _sz, _vp]),
+    "twolocus_scan_noalloc": (_int, [_vp, _i64, _i64, _i64, _i64, ctypes.POINTER(twolocus_result), _vp]),
     "frnn_query_workspace_size": (_sz, [_i64, _int]),
     "frnn_query": (_int, [_vp, _i64, _int, _i64, ctypes.c_double, _vp, _vp, _i64, ctypes.POINTER(_i64), _vp, _sz,
                           _vp]),
@@ -206,6 +207,19 @@ def twolocus_scan(planes: torch.Tensor, m_cases: int, m_controls: int, ws: torch
     out = twolocus_result()
     _raise(lib().twolocus_scan(planes.data_ptr() if S else None, S, W, m_cases, m_controls, ctypes.byref(out),
                                ws.data_ptr(), ws.numel(), _stream(stream)))
+    return out.as_dict()
+
+
+def twolocus_scan_noalloc(planes: torch.Tensor, m_cases: int, m_controls: int, stream=None) -> dict:
+    """As :func:`twolocus_scan`, through the entry point that uses the library's fixed scratch
+    instead of a workspace (for callers that cannot allocate device memory)."""
+    _check_cuda(planes, "planes")
+    if planes.dim() != 4 or planes.shape[1:3] != (2, 2) or planes.element_size() != 8 or not planes.is_contiguous():
+        raise ValueError("planes must be a contiguous 64-bit tensor [S][2][2][W]")
+    S, W = planes.shape[0], planes.shape[3]
+    out = twolocus_result()
+    _raise(lib().twolocus_scan_noalloc(planes.data_ptr() if S else None, S, W, m_cases, m_controls,
+                                       ctypes.byref(out), _stream(stream)))
     return out.as_dict()
 
 

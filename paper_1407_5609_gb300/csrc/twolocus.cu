@@ -10,6 +10,8 @@
 //   eq = ~(P1_i ^ P1_j) & ~(P2_i ^ P2_j),   u = popcount(eq) - (pad bits, which are 0 in both).
 // The hot loop is thus two LOP3 and one POPC per 32 subjects and pair.  The full 3x3 contingency
 // tables of the winning pair are then counted with AND + POPC of the planes and the marginals.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace cppgb {
@@ -212,4 +214,78 @@ int launch_twolocus(const uint64_t* planes, int64_t S, int64_t W, int64_t m1, in
   return CPPGB_OK;
 }
 
+// ------------------------------------------------------------------ allocation-free variant
+// twolocus_scan_noalloc keeps its scratch (the per-block partials and the device copy of the
+// result) in this fixed array instead of a caller workspace.  Every device that loads the library
+// holds the array until the process exits.  Layout: [0, 256) the result, [256, end) the partials.
+constexpr size_t kNoAllocScratchBytes = size_t(1) << 20;
+static __device__ __align__(256) unsigned char twolocus_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static void* g_noalloc_ptr[kMaxDevices];
+static std::mutex g_noalloc_mu;
+
+// Device address of the array on the current device, looked up once per device.  In host code the
+// array's name is only a host-side stand-in, so the kernels get this address instead.
+static int noalloc_scratch_address(void** out) {
+  int dev = 0;
+  CPPGB_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(CPPGB_ERR_ARG, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, twolocus_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return set_error(CPPGB_ERR_CUDA, "cudaGetSymbolAddress of the two-locus scratch failed: %s",
+                       cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return CPPGB_OK;
+}
+
+static bool noalloc_fits(int64_t S) {
+  return 256 + (size_t)16 * (size_t)twolocus_num_partials(S) <= kNoAllocScratchBytes;
+}
+
+// Largest S whose partials fit the array.
+static int64_t noalloc_max_snps() {
+  int64_t s = 0;
+  while (noalloc_fits(s + 1)) ++s;
+  return s;
+}
+
 }  // namespace cppgb
+
+extern "C" int twolocus_scan_noalloc(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases,
+                                     int64_t m_controls, twolocus_result* out, void* stream) {
+  using namespace cppgb;
+  if (!out) return set_error(CPPGB_ERR_ARG, "out is NULL");
+  if (S < 0 || S > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "S out of range");
+  if (m_cases < 1 || m_controls < 1) return set_error(CPPGB_ERR_ARG, "group sizes must be >= 1");
+  if (W < (m_cases + 63) / 64 || W < (m_controls + 63) / 64)
+    return set_error(CPPGB_ERR_ARG, "W = %lld words cannot hold the groups", (long long)W);
+  if ((double)m_cases * (double)m_controls >= 1099511627776.0)
+    return set_error(CPPGB_ERR_ARG, "m_cases * m_controls must be < 2^40");
+  if (S > 0 && !planes) return set_error(CPPGB_ERR_ARG, "planes is NULL");
+  if (!noalloc_fits(S))
+    return set_error(CPPGB_ERR_CAPACITY,
+                     "S = %lld SNPs needs more than the %zu-byte fixed scratch of twolocus_scan_noalloc "
+                     "(at most %lld SNPs); use twolocus_scan with a workspace",
+                     (long long)S, kNoAllocScratchBytes, (long long)noalloc_max_snps());
+  void* base = nullptr;
+  int rc = noalloc_scratch_address(&base);
+  if (rc) return rc;
+  // Nothing in the array has to start at zero: the scan writes every partial slot it later reads
+  // (empty tiles write a sentinel) and the finishing kernel writes the whole result.
+  cudaStream_t st = (cudaStream_t)stream;
+  twolocus_result* dres = (twolocus_result*)base;
+  void* partials = (char*)base + 256;
+  if ((rc = launch_twolocus(planes, S, W, m_cases, m_controls, partials, twolocus_num_partials(S), dres, st)))
+    return rc;
+  twolocus_result h;
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(&h, dres, sizeof h, cudaMemcpyDeviceToHost, st));
+  CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
+  *out = h;
+  return CPPGB_OK;
+}
