@@ -1,13 +1,477 @@
-// Dense all-pairs stage on tcgen05 tensor cores (placeholder until the kernel lands).
+// Dense all-pairs stage on the 5th-generation tensor cores (tcgen05), FP16 or BF16 operands.
+//
+// Same contract as the FP32 stage (gram_simt.cu): every pair (i, j), i < j, j - i >= excl, of the
+// rows of X gets D~_ij = |x~_i|^2 + |x~_j|^2 - 2 x~_i . x~_j, the tile minima tighten the global
+// upper bound U, and pairs whose lower bound can still reach U are emitted for the FP64 recheck.
+// This is the brute-force O(n^2 l) evaluation of Sec. 3 with the Gram products on tensor cores.
+//
+// Kernel organisation (one persistent CTA per SM, 6 warps):
+//   warp 0      TMA producer: 128x64 (A) and 256x64 (B) 16-bit tiles, 128-byte swizzle, into a
+//               4-stage shared-memory ring guarded by full/empty mbarriers
+//   warp 1      allocates 512 TMEM columns; one lane issues tcgen05.mma (M=128, N=256, K=16) into
+//               one of two 256-column FP32 accumulators, commits to the ring and to the epilogue
+//   warps 2-5   epilogue: tcgen05.ld of the accumulator rows, D~ = nx + (ny - 2 S), running minima,
+//               threshold test per 32-column chunk, rare candidate emission, bound publication
+// Tiles are 128 rows x 256 columns of the upper triangle, walked in bands of 16 column blocks (the
+// band's B panels stay in L2 while the row panels stream once per band).  Every mbarrier wait is
+// bounded (about 2 s of %globaltimer): on a timeout the CTA flags CPPGB_ERR_TIMEOUT, drains what it
+// issued, frees its TMEM and exits.
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace cppgb {
+namespace {
 
-bool gram_tc_available() { return false; }
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int NTHREADS = 192;
+constexpr int BAND = 16;      // column blocks per band
+constexpr int MAX_BANDS = 480;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr unsigned long long WAIT_NS = 2000000000ull;
 
-int launch_gram_tc(const void*, int, int64_t, int64_t, int64_t, int64_t, const float*, DenseScalars*, Candidate*,
-                   int64_t, cudaStream_t) {
-  return set_error(CPPGB_ERR_ARG, "tensor-core filter modes are not available in this build");
+// Tile schedule: bands of column blocks; inside a band, row-block-major.  off[b] = tiles before
+// band b; nfull[b] = leading row blocks whose every column block in the band holds a valid pair.
+struct TileSched {
+  int64_t n, excl;
+  int32_t nbands, nbi, nbj, pad;
+  int64_t off[MAX_BANDS + 1];
+  int32_t nfull[MAX_BANDS];
+};
+
+// first column block bj whose tile (bi, bj) holds a pair with j - i >= excl (j < n); -1 if none
+__host__ __device__ __forceinline__ int64_t first_bj(int64_t bi, int64_t n, int64_t excl) {
+  const int64_t need = excl + (int64_t)BM * bi;  // smallest admissible j for the tile's first row
+  if (n - 1 < need) return -1;
+  const int64_t v = need - (BN - 1);
+  return v <= 0 ? 0 : (v + BN - 1) / BN;
+}
+__host__ __device__ __forceinline__ int64_t row_count(int64_t bi, int64_t bj0, int64_t bj1, int64_t n,
+                                                      int64_t excl) {
+  const int64_t f = first_bj(bi, n, excl);
+  if (f < 0) return 0;
+  const int64_t lo = f > bj0 ? f : bj0;
+  return bj1 > lo ? bj1 - lo : 0;
+}
+
+// `band` is the caller's cursor: each role walks its tiles in increasing t, so it only moves forward.
+__device__ __forceinline__ void decode_tile(const TileSched& ts, int64_t t, int* band, int64_t* bi, int64_t* bj) {
+  int b = *band;
+  while (b + 1 < ts.nbands && ts.off[b + 1] <= t) ++b;
+  *band = b;
+  const int64_t bj0 = (int64_t)b * BAND;
+  const int64_t bj1 = bj0 + BAND < ts.nbj ? bj0 + BAND : ts.nbj;
+  const int64_t w = bj1 - bj0;
+  int64_t r = t - ts.off[b];
+  const int64_t full = (int64_t)ts.nfull[b] * w;
+  if (r < full) {
+    *bi = r / w;
+    *bj = bj0 + r % w;
+    return;
+  }
+  r -= full;
+  for (int64_t row = ts.nfull[b]; row < ts.nbi; ++row) {
+    const int64_t c = row_count(row, bj0, bj1, ts.n, ts.excl);
+    if (r < c) {
+      *bi = row;
+      *bj = bj1 - c + r;
+      return;
+    }
+    r -= c;
+  }
+  *bi = 0;
+  *bj = 0;  // unreachable for t < total
+}
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of parity `parity` to complete; false on timeout or abort.
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > WAIT_NS) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major tile written by TMA with the 128-byte swizzle;
+// rows of 128 bytes, 8-row groups 1024 bytes apart (stride byte offset), fixed version bits 0b001,
+// swizzle mode 2 (128 B).  The leading byte offset is unused for this layout.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = F16 (0) or BF16 (1), both K-major, N, M.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t ab) {
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct SmemCtl {
+  uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TileSched ts, int64_t total,
+                   uint32_t ab_fmt, const float* __restrict__ norms, DenseScalars* sc, Candidate* __restrict__ cand,
+                   int64_t cap, int64_t kchunks) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  SmemCtl* ctl = (SmemCtl*)(smem + STAGES * STAGE_BYTES);
+  volatile int* abort_flag = &ctl->abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&ctl->full[s], 1);
+      mbar_init(&ctl->empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&ctl->tfull[a], 1);
+      mbar_init(&ctl->tempty[a], 4);
+    }
+    mbar_init(&ctl->drain, 1);
+    ctl->abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = ctl->tmem_base;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmap) : "memory");
+      uint32_t stage = 0, phase = 0;
+      int64_t issued = 0;
+      int band = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        int64_t bi, bj;
+        decode_tile(ts, t, &band, &bi, &bj);
+        for (int64_t kc = 0; kc < kchunks; ++kc) {
+          if (!mbar_wait(&ctl->empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
+          uint8_t* sa = smem + stage * STAGE_BYTES;
+          mbar_arrive_expect_tx(&ctl->full[stage], STAGE_BYTES);
+          tma_load_2d(sa, &tmap, &ctl->full[stage], (int)(kc * BK), (int)(bi * BM));
+          tma_load_2d(sa + A_BYTES, &tmap, &ctl->full[stage], (int)(kc * BK), (int)(bj * BN));
+          tma_load_2d(sa + A_BYTES + BM * BK * 2, &tmap, &ctl->full[stage], (int)(kc * BK), (int)(bj * BN + BM));
+          ++issued;
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(&sc->status, 4u);
+      }
+      // drain: every issued copy must have landed before the CTA may exit
+      const int64_t last = issued < STAGES ? issued : STAGES;
+      for (int64_t q = 1; q <= last; ++q) {
+        const int64_t u = issued - q;                // use index of that copy
+        const uint32_t s = (uint32_t)(u % STAGES), par = (uint32_t)((u / STAGES) & 1);
+        uint64_t t0 = globaltimer();
+        while (!mbar_try_wait(&ctl->full[s], par) && globaltimer() - t0 < WAIT_NS) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(ab_fmt);
+      uint32_t stage = 0, phase = 0;
+      int64_t it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
+        const uint32_t acc = (uint32_t)(it & 1), use = (uint32_t)((it >> 1) & 1);
+        if (!mbar_wait(&ctl->tempty[acc], use ^ 1u, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t dtmem = tmem_base + acc * (uint32_t)BN;
+        for (int64_t kc = 0; kc < kchunks; ++kc) {
+          if (!mbar_wait(&ctl->full[stage], phase, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
+          const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)  // advance 16 elements = 32 bytes inside the swizzle atom
+            mma_f16(dtmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (kc | kk) != 0);
+          mma_commit(&ctl->empty[stage]);
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        mma_commit(&ctl->tfull[acc]);
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(&sc->status, 4u);
+      }
+      // drain: the commit arrives once every MMA issued so far has completed; TMEM is freed after
+      mma_commit(&ctl->drain);
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(&ctl->drain, 0) && globaltimer() - t0 < WAIT_NS) {
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue (warps 2..5)
+    const uint32_t quarter = (uint32_t)(warp & 3);  // TMEM lanes 32*quarter .. +31
+    const BoundParams bp = sc->bp;
+    float tmin = __int_as_float(0x7f800000);
+    float Usnap = __uint_as_float(*reinterpret_cast<volatile unsigned int*>(&sc->U_bits));
+    // Emission threshold: -inf until this thread has a finite bound, so masked (+inf) entries
+    // can never pass it.
+    float th = Usnap < __int_as_float(0x7f800000) ? theta_of(Usnap, bp) : __int_as_float(0xff800000);
+    int64_t it = 0;
+    int band = 0;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+      int64_t bi, bj;
+      decode_tile(ts, t, &band, &bi, &bj);
+      const uint32_t acc = (uint32_t)(it & 1), use = (uint32_t)((it >> 1) & 1);
+      const bool got = __all_sync(0xffffffffu, mbar_wait(&ctl->tfull[acc], use, abort_flag));
+      if (!got) {
+        if (lane == 0) {
+          *abort_flag = 1;
+          atomicOr(&sc->status, 4u);
+        }
+        break;
+      }
+      tc_fence_after();
+      const int64_t row0 = bi * BM, col0 = bj * BN;
+      const int64_t i = row0 + quarter * 32 + lane;
+      const float nx = norms[i];
+      const bool edge = (row0 + BM - 1 >= ts.n) || (col0 + BN - 1 >= ts.n) || (col0 - (row0 + BM - 1) < ts.excl);
+      const uint32_t tbase = tmem_base + ((quarter * 32u) << 16) + acc * (uint32_t)BN;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        __syncwarp();
+        tmem_ld32(tbase + (uint32_t)(c * 32), r);
+        const float4* ny4 = reinterpret_cast<const float4*>(norms + col0 + c * 32);
+        float dp[32];
+        float cmin = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 v = __ldg(ny4 + q);
+          dp[4 * q + 0] = fmaf(-2.f, __uint_as_float(r[4 * q + 0]), v.x);
+          dp[4 * q + 1] = fmaf(-2.f, __uint_as_float(r[4 * q + 1]), v.y);
+          dp[4 * q + 2] = fmaf(-2.f, __uint_as_float(r[4 * q + 2]), v.z);
+          dp[4 * q + 3] = fmaf(-2.f, __uint_as_float(r[4 * q + 3]), v.w);
+        }
+        if (edge) {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const int64_t j = col0 + c * 32 + k;
+            if (!(i < ts.n && j < ts.n && j - i >= ts.excl)) dp[k] = __int_as_float(0x7f800000);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 32; ++k) cmin = fminf(cmin, dp[k]);
+        const float cD = nx + cmin;
+        if (cD < tmin) {
+          tmin = cD;
+          th = theta_of(fminf(Usnap, upper_d2(tmin, bp)), bp);
+        }
+        if (cD <= th) {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const float D = nx + dp[k];
+            if (D <= th) {
+              const unsigned long long slot = atomicAdd(&sc->n_cand, 1ull);
+              if ((int64_t)slot < cap) {
+                Candidate cd;
+                cd.i = (int32_t)i;
+                cd.j = (int32_t)(col0 + c * 32 + k);
+                cd.d2f = D;
+                cd.pad = 0.f;
+                cand[slot] = cd;
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl->tempty[acc]);
+      // publish the warp's bound if it improves the global one, then refresh the snapshot
+      float wmin = tmin;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) wmin = fminf(wmin, __shfl_xor_sync(0xffffffffu, wmin, o));
+      float Unew = 0.f;
+      if (lane == 0) {
+        const float ub = upper_d2(wmin, bp);
+        if (ub < Usnap) atomic_min_nonneg(&sc->U_bits, ub);
+        Unew = __uint_as_float(*reinterpret_cast<volatile unsigned int*>(&sc->U_bits));
+      }
+      Unew = __shfl_sync(0xffffffffu, Unew, 0);
+      if (Unew < Usnap) {
+        Usnap = Unew;
+        th = theta_of(fminf(Usnap, upper_d2(tmin, bp)), bp);
+      }
+      if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
+    }
+    tc_fence_before();
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+}  // namespace
+
+bool gram_tc_available() { return true; }
+
+int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp, int64_t excl, const float* norms,
+                   DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st) {
+  if (Kp % BK || n_pad % BN) return set_error(CPPGB_ERR_ARG, "internal: tensor-core stage needs Kp %% 64 == 0");
+  if (((uintptr_t)X & 15) != 0) return set_error(CPPGB_ERR_ARG, "internal: row matrix must be 16-byte aligned");
+  if (n_pad > 0x7fffffffLL || Kp > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "problem too large for TMA coordinates");
+  TileSched ts;  // kernel parameter (copied at launch)
+  ts.n = n;
+  ts.excl = excl;
+  ts.nbi = (int32_t)(n_pad / BM);
+  ts.nbj = (int32_t)(n_pad / BN);
+  ts.nbands = (int32_t)((ts.nbj + BAND - 1) / BAND);
+  if (ts.nbands > MAX_BANDS) return set_error(CPPGB_ERR_ARG, "n too large for the tensor-core tile schedule");
+  int64_t total = 0;
+  for (int b = 0; b < ts.nbands; ++b) {
+    const int64_t bj0 = (int64_t)b * BAND, bj1 = bj0 + BAND < ts.nbj ? bj0 + BAND : ts.nbj;
+    ts.off[b] = total;
+    int32_t nf = 0;
+    bool in_full = true;
+    for (int64_t bi = 0; bi < ts.nbi; ++bi) {
+      const int64_t c = row_count(bi, bj0, bj1, n, excl);
+      if (in_full && c == bj1 - bj0) ++nf;
+      else in_full = false;
+      total += c;
+    }
+    ts.nfull[b] = nf;
+  }
+  ts.off[ts.nbands] = total;
+  if (total == 0) return CPPGB_OK;
+
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return set_error(CPPGB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  CUtensorMap tmap;
+  const cuuint64_t gdim[2] = {(cuuint64_t)Kp, (cuuint64_t)n_pad};
+  const cuuint64_t gstride[1] = {(cuuint64_t)Kp * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType dt =
+      mode == CPPGB_MODE_FILTER_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  CUresult cr = enc(&tmap, dt, 2, const_cast<void*>(X), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return set_error(CPPGB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+
+  int dev = 0, sms = 0;
+  CPPGB_CUDA_TRY(cudaGetDevice(&dev));
+  CPPGB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const size_t smem = (size_t)STAGES * STAGE_BYTES + sizeof(SmemCtl) + 1024;
+  CPPGB_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t grid = total < sms ? total : sms;
+  gram_tc_kernel<<<(unsigned)grid, NTHREADS, smem, st>>>(tmap, ts, total, mode == CPPGB_MODE_FILTER_BF16 ? 1u : 0u,
+                                                         norms, sc, cand, cap, Kp / BK);
+  CPPGB_LAUNCH_CHECK();
+  return CPPGB_OK;
 }
 
 }  // namespace cppgb

@@ -62,7 +62,7 @@ __device__ void recheck_body(Getter get, DenseScalars* sc, const Candidate* __re
   if (c >= live_count(sc, cap)) return;
   const float th = theta_of(__uint_as_float(sc->U_bits), sc->bp);
   Candidate cd = cand[c];
-  if (!(cd.d2f <= th)) {
+  if (!(cd.d2f <= th) || !(cd.d2f < __int_as_float(0x7f800000))) {
     d2buf[c] = -1.0;
     return;
   }
