@@ -65,7 +65,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -206,7 +206,56 @@ class CPP:
         return self.units, time.perf_counter() - t, "the full workload"
 
 
-WORKLOADS = {"tsmm": TSMM, "twolocus": TwoLocus, "cpp": CPP}
+class FRNN:
+    name = "frnn"
+
+    def __init__(self, args):
+        from paper_1407_5609_gb300 import synth
+        self.x = synth.make_frnn_mixture()
+        self.n = self.x.shape[0]
+        self.R = 0.002
+        self.units = self.n * (self.n - 1) // 2          # brute-force-equivalent pairs per step
+        self.config = {"workload": "frnn 64-component gaussian mixture n=1048576 d=3 sigma=0.01 R=0.002",
+                       "pairs_per_step": self.units,
+                       "l2": "12.6 MB of points + 60 MB of CSR output per step; flushed between steps"}
+        self.nnz = None
+
+    def setup(self, dev):
+        import torch
+        self.dev_x = torch.from_numpy(self.x).to(dev)
+        self.cap = None
+
+    def step(self, capi, mode):
+        rp, cols = capi.frnn_query(self.dev_x, self.R, cols_cap=self.cap)
+        if self.cap is None:
+            self.cap = int(cols.shape[0]) + 1024
+        self.nnz = int(cols.shape[0])
+        return {"n_pairs_directed": self.nnz}
+
+    def e2e_step(self, capi, mode, host, dev_buf):
+        dev_buf.copy_(host, non_blocking=True)
+        rp, cols = capi.frnn_query(dev_buf, self.R, cols_cap=self.cap)
+        cols.cpu()                                        # the result goes back to the host
+        return {"n_pairs_directed": int(cols.shape[0])}
+
+    def host_input(self):
+        return self.x, self.x.nbytes
+
+    def algorithmic_bytes(self):
+        return self.x.nbytes + (self.n + 1) * 8 + 4 * (self.nnz or 0)
+
+    def oracle_sample(self, oracle, rows):
+        import numpy as np
+        rr = np.linspace(0, self.n - 1, rows).astype(np.int64)
+        xd = self.x.astype(np.float64)
+        t = time.perf_counter()
+        oracle.frnn_rows(xd, self.R, rr)
+        dt = time.perf_counter() - t
+        pairs = rows * (self.n - 1)
+        return pairs, dt, f"N(i) of {rows} points evenly spaced over the {self.n} ({pairs} pairs)"
+
+
+WORKLOADS = {"tsmm": TSMM, "twolocus": TwoLocus, "cpp": CPP, "frnn": FRNN}
 
 
 # ------------------------------------------------------------------ helpers
@@ -232,10 +281,18 @@ def recorded_traffic(key):
     return rec.get("bytes_per_launch")
 
 
+def calibrate_rows(wl, oracle, target_s):
+    """Rows of the oracle sample that take about target_s (fixed cost + per-row cost, two probes)."""
+    _, t2, _ = wl.oracle_sample(oracle, 2)
+    _, t8, _ = wl.oracle_sample(oracle, 8)
+    per_row = max((t8 - t2) / 6.0, 1e-4)
+    fixed = max(t2 - 2 * per_row, 0.0)
+    return max(2, int((target_s - fixed) / per_row))
+
+
 def cpu_baseline(wl, target_s=12.0):
     import oracle
-    pairs, dt, _ = wl.oracle_sample(oracle, 2)
-    rows = max(2, int(2 * target_s / max(dt, 1e-3)))
+    rows = calibrate_rows(wl, oracle, target_s)
     pairs, dt, sample = wl.oracle_sample(oracle, rows)
     return {"value": pairs / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": sample, "seconds": round(dt, 2)}
@@ -313,8 +370,10 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": {"plain_fp32": "f32", "filter_fp16": "f16", "filter_bf16": "bf16"}.get(mode, "i32"),
-           "data": "synthetic", "config": dict(wl.config, mode=mode, flush_l2_between_steps=bool(flush),
+           "dtype": ({"plain_fp32": "f32", "filter_fp16": "f16", "filter_bf16": "bf16"}.get(mode)
+                     if wl.name in ("tsmm", "cpp") else {"frnn": "f32", "twolocus": "u64"}[wl.name]),
+           "data": "synthetic", "config": dict(wl.config, mode=mode if wl.name in ("tsmm", "cpp") else None,
+                                               flush_l2_between_steps=bool(flush),
                                                parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
            "answer": {k: res[k] for k in ("i", "j", "dist2", "score") if k in res},
            "gpu_launches": launches}
@@ -334,6 +393,13 @@ def run_ours(args):
                            "frac": ach / peak if ach else None, "traffic": recorded_traffic(key),
                            "kernel": "dense all-pairs stage (gram_tc / gram_simt)", "peak_source": src,
                            "launch_ms": avg_ms, "algorithmic_flop_per_launch": flops}
+    elif wl.name == "frnn":
+        per_step_ms = total_ms / args.steps
+        gbs = wl.algorithmic_bytes() / (per_step_ms / 1e3) / 1e9
+        out["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                           "frac": gbs / pk["hbm_gbs"], "traffic": recorded_traffic("frnn_query@frnn"),
+                           "kernel": "frnn_query step (grid build + 27-cell count and fill passes)",
+                           "peak_source": f"{pk['source']} hbm copy"}
     elif wl.name == "twolocus":
         per_step_ms = total_ms / args.steps
         pops = wl.units * wl.flop_per_unit
@@ -360,8 +426,10 @@ def run_ours(args):
         barrier()
         ems, _ = timed_steps(lambda: wl.e2e_step(capi, mode, host, dev_buf), args.steps, stream, torch, flush)
         out["e2e"] = {"value": wl.units * args.steps / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                      # the call reads its 64-byte scalar block twice (dense searches) or the result struct
-                      "d2h_bytes_per_step": 128 if wl.name in ("tsmm", "cpp") else ctypes.sizeof(capi.twolocus_result)}
+                      # dense searches read their 64-byte scalar block twice; two-locus its result struct;
+                      # FRNN the CSR (row pointers and columns) plus its two status reads
+                      "d2h_bytes_per_step": {"tsmm": 128, "cpp": 128, "frnn": 4 * (wl.nnz or 0) + 16}.get(
+                          wl.name, ctypes.sizeof(capi.twolocus_result))}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
@@ -378,9 +446,7 @@ def run_reference(args):
         return
     import oracle
     wl = WORKLOADS[args.workload](args)
-    rows = 2
-    pairs, dt, _ = wl.oracle_sample(oracle, rows)
-    rows = max(2, int(rows * 4.0 / max(dt, 1e-3)))       # about 4 s of oracle work per step
+    rows = calibrate_rows(wl, oracle, 4.0)               # about 4 s of oracle work per step
     for _ in range(args.warmup):
         wl.oracle_sample(oracle, 2)
     tot_pairs, tot_s, sample = 0, 0.0, ""
@@ -402,7 +468,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tsmm")

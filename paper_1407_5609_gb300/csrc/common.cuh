@@ -121,6 +121,9 @@ int launch_prep_lmers(const float* series, int64_t n, int64_t l, int mode, void*
 // Dense all-pairs stage on FP32 CUDA cores.
 int launch_gram_simt(const float* X, int64_t n, int64_t Kp, int64_t excl, const float* norms,
                      DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st);
+// Fixed-radius variant: emits every pair i < j with D~ <= theta(rr) (rr = R^2 rounded up to FP32).
+int launch_gram_simt_radius(const float* X, int64_t n, int64_t Kp, const float* norms, DenseScalars* sc,
+                            Candidate* cand, int64_t cap, float rr, cudaStream_t st);
 // Dense all-pairs stage on tcgen05 tensor cores (FP16 or BF16 operands).
 int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp, int64_t excl,
                    const float* norms, DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st);
@@ -138,6 +141,11 @@ int launch_recheck_lmers(const float* series, int64_t l, DenseScalars* sc,
 // Scalars reset and the bound parameters: e_acc = kappa * max_i |x~_i|^2, eps_pair = 2 max_i eps_i.
 int launch_init_scalars(DenseScalars* sc, cudaStream_t st);
 int launch_bounds(DenseScalars* sc, float kappa, cudaStream_t st);
+
+// Exclusive prefix sums; out has n + 1 entries (out[n] = total); tmp holds scan_temp_elems(n) int64.
+size_t scan_temp_elems(int64_t n);
+int launch_exclusive_scan_i32(const int32_t* in, int64_t n, int64_t* out, int64_t* tmp, cudaStream_t st);
+int launch_exclusive_scan_i64(const int64_t* in, int64_t n, int64_t* out, int64_t* tmp, cudaStream_t st);
 
 // Two-locus scan.
 int launch_twolocus(const uint64_t* planes, int64_t S, int64_t W, int64_t m1, int64_t m2, void* partials,

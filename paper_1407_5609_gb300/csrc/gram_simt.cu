@@ -13,11 +13,15 @@ namespace {
 
 constexpr int BM = 128, BK = 16, PAD = 4, NT = 256;
 
+// RADIUS = false: closest-pair epilogue (tile minimum, bound update, emission against the bound).
+// RADIUS = true:  fixed-radius epilogue (Sec. 3.5): emit every pair whose lower bound on d is <= R,
+//                 i.e. D~ <= theta(R^2); no bound update.
 // (the accumulation bound used with these tiles is derived on the host: sequential FFMA over Kp)
+template <bool RADIUS>
 __global__ void __launch_bounds__(NT, 2)
     gram_simt_kernel(const float* __restrict__ X, int64_t n, int64_t Kp, int64_t excl, int64_t delta,
                      const float* __restrict__ norms, DenseScalars* sc,
-                     Candidate* __restrict__ cand, int64_t cap) {
+                     Candidate* __restrict__ cand, int64_t cap, float rr) {
   __shared__ __align__(16) float As[2][BK][BM + PAD];
   __shared__ __align__(16) float Bs[2][BK][BM + PAD];
   __shared__ float red[NT / 32];
@@ -97,19 +101,24 @@ __global__ void __launch_bounds__(NT, 2)
       acc[r][c] = D;
       tmin = fminf(tmin, D);
     }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
-  if ((tid & 31) == 0) red[tid >> 5] = tmin;
-  __syncthreads();
-  tmin = red[0];
-#pragma unroll
-  for (int w = 1; w < NT / 32; ++w) tmin = fminf(tmin, red[w]);
-  if (tmin == __int_as_float(0x7f800000)) return;  // no valid pair in this tile
-
+  float th, ub = 0.f;
   const BoundParams bp = sc->bp;
-  const float ub = upper_d2(tmin, bp);
-  const float Ug = __uint_as_float(*reinterpret_cast<volatile unsigned int*>(&sc->U_bits));
-  const float th = theta_of(fminf(Ug, ub), bp);
+  if (RADIUS) {
+    th = theta_of(rr, bp);
+  } else {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+    if ((tid & 31) == 0) red[tid >> 5] = tmin;
+    __syncthreads();
+    tmin = red[0];
+#pragma unroll
+    for (int w = 1; w < NT / 32; ++w) tmin = fminf(tmin, red[w]);
+    if (tmin == __int_as_float(0x7f800000)) return;  // no valid pair in this tile
+
+    ub = upper_d2(tmin, bp);
+    const float Ug = __uint_as_float(*reinterpret_cast<volatile unsigned int*>(&sc->U_bits));
+    th = theta_of(fminf(Ug, ub), bp);
+  }
 #pragma unroll
   for (int r = 0; r < 8; ++r)
 #pragma unroll
@@ -126,12 +135,14 @@ __global__ void __launch_bounds__(NT, 2)
         }
       }
     }
-  if (tid == 0) atomic_min_nonneg(&sc->U_bits, ub);
+  if (!RADIUS && tid == 0) atomic_min_nonneg(&sc->U_bits, ub);
 }
 
 }  // namespace
 
-int launch_gram_simt(const float* X, int64_t n, int64_t Kp, int64_t excl, const float* norms, DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st) {
+template <bool RADIUS>
+static int launch_simt(const float* X, int64_t n, int64_t Kp, int64_t excl, const float* norms, DenseScalars* sc,
+                       Candidate* cand, int64_t cap, float rr, cudaStream_t st) {
   if (Kp % BK) return set_error(CPPGB_ERR_ARG, "internal: Kp %% 16 != 0");
   const int64_t nb = (n + BM - 1) / BM;
   // smallest block offset whose tiles hold a pair with j - i >= excl
@@ -140,9 +151,19 @@ int launch_gram_simt(const float* X, int64_t n, int64_t Kp, int64_t excl, const 
   const int64_t tiles = tri_count(m);
   if (tiles <= 0) return CPPGB_OK;
   if (tiles > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "too many tiles (%lld)", (long long)tiles);
-  gram_simt_kernel<<<(unsigned)tiles, NT, 0, st>>>(X, n, Kp, excl, delta, norms, sc, cand, cap);
+  gram_simt_kernel<RADIUS><<<(unsigned)tiles, NT, 0, st>>>(X, n, Kp, excl, delta, norms, sc, cand, cap, rr);
   CPPGB_LAUNCH_CHECK();
   return CPPGB_OK;
+}
+
+int launch_gram_simt(const float* X, int64_t n, int64_t Kp, int64_t excl, const float* norms, DenseScalars* sc,
+                     Candidate* cand, int64_t cap, cudaStream_t st) {
+  return launch_simt<false>(X, n, Kp, excl, norms, sc, cand, cap, 0.f, st);
+}
+
+int launch_gram_simt_radius(const float* X, int64_t n, int64_t Kp, const float* norms, DenseScalars* sc,
+                            Candidate* cand, int64_t cap, float rr, cudaStream_t st) {
+  return launch_simt<true>(X, n, Kp, 1, norms, sc, cand, cap, rr, st);
 }
 
 }  // namespace cppgb

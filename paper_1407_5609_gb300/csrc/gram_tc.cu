@@ -12,7 +12,7 @@
 //               one of two 256-column FP32 accumulators, commits to the ring and to the epilogue
 //   warps 2-5   epilogue: tcgen05.ld of the accumulator rows, D~ = nx + (ny - 2 S), running minima,
 //               threshold test per 32-column chunk, rare candidate emission, bound publication
-// Tiles are 128 rows x 256 columns of the upper triangle, walked in bands of 16 column blocks (the
+// Tiles are 128 rows x 256 columns of the upper triangle, walked in bands of 64 column blocks (the
 // band's B panels stay in L2 while the row panels stream once per band).  Every mbarrier wait is
 // bounded (about 2 s of %globaltimer): on a timeout the CTA flags CPPGB_ERR_TIMEOUT, drains what it
 // issued, frees its TMEM and exits.
@@ -26,7 +26,7 @@ namespace {
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int NTHREADS = 192;
-constexpr int BAND = 16;      // column blocks per band
+constexpr int BAND = 64;      // column blocks per band (16 MB of B panels stay in L2)
 constexpr int MAX_BANDS = 480;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long WAIT_NS = 2000000000ull;

@@ -1,0 +1,111 @@
+"""GPU parity of frnn_query (Sec. 3.5) against the FP64 oracle: CSR row pointers and column lists
+must be identical (every pair decided by the same FP64 test, columns ascending)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import device, to_dev
+from paper_1407_5609_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _capi():
+    from paper_1407_5609_gb300 import capi
+    return capi
+
+
+def _run(x, R, **kw):
+    capi = _capi()
+    dev = device()
+    rp, cols = capi.frnn_query(to_dev(np.asarray(x, dtype=np.float32), dev), R, **kw)
+    return rp.cpu().numpy(), cols.cpu().numpy()
+
+
+def _check(x, R):
+    rp, cols = _run(x, R)
+    orp, ocols = oracle.frnn(np.asarray(x, dtype=np.float32).astype(np.float64), R)
+    np.testing.assert_array_equal(rp, orp)
+    np.testing.assert_array_equal(cols, ocols)
+    return rp, cols
+
+
+@pytest.mark.parametrize("n,R,seed", [(3000, 0.004, 1), (5000, 0.01, 2), (257, 0.05, 3), (2, 1.0, 4)])
+def test_frnn_mixture_d3(n, R, seed):
+    rp, _ = _check(synth.make_frnn_mixture(n=n, seed=seed), R)
+    assert rp[-1] % 2 == 0
+
+
+@pytest.mark.parametrize("d,n,R,seed", [(1, 4000, 1e-4, 5), (2, 3000, 0.01, 6), (4, 2500, 0.12, 7)])
+def test_frnn_grid_dimensions(d, n, R, seed):
+    x = synth.rng_for(seed).random((n, d)).astype(np.float32)
+    _check(x, R)
+
+
+@pytest.mark.parametrize("d,n,R,seed", [(5, 800, 0.2, 8), (7, 1500, 0.3, 9), (16, 600, 0.9, 10), (33, 300, 1.5, 11)])
+def test_frnn_dense_high_dimension(d, n, R, seed):
+    x = synth.rng_for(seed).random((n, d)).astype(np.float32)
+    rp, _ = _check(x, R)
+    assert rp[-1] > 0
+
+
+def test_frnn_boundary_inclusive_and_exact():
+    """Distances exactly equal to R (exactly representable) are neighbours; slightly above are not."""
+    g = np.arange(0, 40, dtype=np.float32) * np.float32(0.25)
+    x = np.stack(np.meshgrid(g, g[:5], g[:3], indexing="ij"), axis=-1).reshape(-1, 3)
+    _check(x, 0.25)
+    _check(x, np.nextafter(0.25, 0.0))
+    _check(x, 0.5)
+
+
+def test_frnn_radius_zero_and_duplicates():
+    x = synth.rng_for(12).random((400, 3)).astype(np.float32)
+    rp, _ = _check(x, 0.0)
+    assert rp[-1] == 0
+    x[100:110] = x[5]
+    rp, _ = _check(x, 0.0)
+    assert rp[-1] == 11 * 10
+
+
+def test_frnn_capacity_reporting():
+    capi = _capi()
+    dev = device()
+    x = to_dev(synth.make_frnn_mixture(n=2000, seed=13), dev)
+    with pytest.raises(capi.CppgbError) as e:
+        capi.frnn_query(x, 0.01, cols_cap=3)
+    assert e.value.status == capi.ERR_CAPACITY
+
+
+def test_frnn_non_finite():
+    capi = _capi()
+    x = synth.rng_for(14).random((100, 3)).astype(np.float32)
+    x[3, 1] = np.inf
+    with pytest.raises(capi.CppgbError) as e:
+        _run(x, 0.1)
+    assert e.value.status == capi.ERR_NUMERIC
+
+
+def test_frnn_full_size_sampled():
+    """2^20 points of the 64-component mixture, R = 0.002: sampled rows against the oracle, and
+    the global invariants (symmetric pair count, ascending rows, no self pairs)."""
+    x = synth.make_frnn_mixture()
+    rp, cols = _run(x, 0.002)
+    n = x.shape[0]
+    assert rp.shape == (n + 1,) and rp[0] == 0 and rp[-1] % 2 == 0
+    assert np.all(np.diff(rp) >= 0)
+    deg = np.diff(rp)
+    rows = np.concatenate([synth.rng_for(15).integers(0, n, 48), np.argsort(deg)[-8:], np.argsort(deg)[:8]])
+    offs, ocols = oracle.frnn_rows(x.astype(np.float64), 0.002, rows)
+    for p, r in enumerate(rows):
+        np.testing.assert_array_equal(cols[rp[r]:rp[r + 1]], ocols[offs[p]:offs[p + 1]])
+    # symmetry on the sampled rows: j in N(r) implies r in N(j)
+    for r in rows[:24]:
+        for j in cols[rp[r]:rp[r + 1]]:
+            seg = cols[rp[j]:rp[j + 1]]
+            k = np.searchsorted(seg, r)
+            assert k < seg.shape[0] and seg[k] == r
+    # ascending, no self pairs (whole output)
+    row_of = np.repeat(np.arange(n), deg)
+    assert not np.any(cols == row_of)
+    same_row = row_of[1:] == row_of[:-1]
+    assert np.all(cols[1:][same_row] > cols[:-1][same_row])
