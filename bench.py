@@ -255,7 +255,64 @@ class FRNN:
         return pairs, dt, f"N(i) of {rows} points evenly spaced over the {self.n} ({pairs} pairs)"
 
 
-WORKLOADS = {"tsmm": TSMM, "twolocus": TwoLocus, "cpp": CPP, "frnn": FRNN}
+class Batch:
+    name = "batch"
+
+    def __init__(self, args):
+        from paper_1407_5609_gb300 import synth
+        self.batch = synth.make_batch()
+        self.units = sum(b.pts.shape[0] * (b.pts.shape[0] - 1) // 2 for b in self.batch)
+        self.flop_per_unit = None
+        self.flops = sum(b.pts.shape[0] * (b.pts.shape[0] - 1) // 2 * 2 * b.pts.shape[1] for b in self.batch)
+        self.config = {"workload": "batch of 2048 CPP+FRNN instances, n log-uniform [256, 65536], d in {8,16,32,64,128}, "
+                                   "uniform or 16-component mixture, planted pair at 1e-3, R = 2e-3",
+                       "pairs_per_step": self.units,
+                       "l2": "4.8 GB of points per step, > L2"}
+
+    def setup(self, dev):
+        import torch
+        from paper_1407_5609_gb300 import capi
+        self.pts = [torch.from_numpy(b.pts).to(dev) for b in self.batch]
+        self.radii = [b.R for b in self.batch]
+        inst = [capi.cpp_instance(p.data_ptr(), p.shape[0], p.shape[1], 0, r) for p, r in zip(self.pts, self.radii)]
+        self.ws = torch.empty(capi.cpp_batch_workspace_size(inst), dtype=torch.uint8, device=dev)
+        self.pairs = torch.empty((1 << 20, 2), dtype=torch.int32, device=dev)
+
+    def step(self, capi, mode):
+        res, counts, _ = capi.cpp_batch(self.pts, self.radii, ws=self.ws, pairs=self.pairs)
+        return {"instances": len(res), "pairs_within_R": int(counts.sum())}
+
+    def per_instance_step(self, capi):
+        n = 0
+        for p, r in zip(self.pts, self.radii):
+            capi.cpp_closest_pair(p, mode="plain_fp32")
+            rp, cols = capi.frnn_query(p, r)
+            n += int(cols.shape[0]) // 2
+        return n
+
+    def e2e_step(self, capi, mode, host, dev_buf):
+        for hp, dp in zip(host, dev_buf):
+            dp.copy_(hp, non_blocking=True)
+        res, counts, pairs = capi.cpp_batch(dev_buf, self.radii, ws=self.ws, pairs=self.pairs)
+        pairs[:int(counts.sum())].cpu()
+        return {"instances": len(res)}
+
+    def host_input(self):
+        return [b.pts for b in self.batch], sum(b.pts.nbytes for b in self.batch)
+
+    def oracle_sample(self, oracle, rows):
+        import numpy as np
+        t = time.perf_counter()
+        pairs = 0
+        for b in self.batch[:max(1, rows)]:
+            xd = b.pts.astype(np.float64)
+            oracle.cpp(xd)
+            oracle.frnn(xd, b.R)
+            pairs += b.pts.shape[0] * (b.pts.shape[0] - 1) // 2
+        return pairs, time.perf_counter() - t, f"closest pair + R-pairs of the first {rows} instances ({pairs} pairs)"
+
+
+WORKLOADS = {"tsmm": TSMM, "twolocus": TwoLocus, "cpp": CPP, "frnn": FRNN, "batch": Batch}
 
 
 # ------------------------------------------------------------------ helpers
@@ -371,7 +428,7 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": ({"plain_fp32": "f32", "filter_fp16": "f16", "filter_bf16": "bf16"}.get(mode)
-                     if wl.name in ("tsmm", "cpp") else {"frnn": "f32", "twolocus": "u64"}[wl.name]),
+                     if wl.name in ("tsmm", "cpp") else {"frnn": "f32", "twolocus": "u64", "batch": "f32"}[wl.name]),
            "data": "synthetic", "config": dict(wl.config, mode=mode if wl.name in ("tsmm", "cpp") else None,
                                                flush_l2_between_steps=bool(flush),
                                                parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
@@ -393,6 +450,19 @@ def run_ours(args):
                            "frac": ach / peak if ach else None, "traffic": recorded_traffic(key),
                            "kernel": "dense all-pairs stage (gram_tc / gram_simt)", "peak_source": src,
                            "launch_ms": avg_ms, "algorithmic_flop_per_launch": flops}
+    elif wl.name == "batch":
+        per_step_ms = total_ms / args.steps
+        ach = wl.flops / (per_step_ms / 1e3) / 1e12
+        out["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                           "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": recorded_traffic("batch@batch"),
+                           "kernel": "cpp_batch step (persistent FP32 tile kernel dominates)",
+                           "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                           "algorithmic_flop_per_step": wl.flops}
+        if not args.no_compare:
+            barrier()
+            pms, _ = timed_steps(lambda: wl.per_instance_step(capi), 1, stream, torch, flush)
+            out["per_instance_launches"] = {"ms_per_step": pms, "value": wl.units / (pms / 1e3), "unit": UNIT,
+                                            "calls_per_step": 2 * len(wl.batch)}
     elif wl.name == "frnn":
         per_step_ms = total_ms / args.steps
         gbs = wl.algorithmic_bytes() / (per_step_ms / 1e3) / 1e9
@@ -421,14 +491,19 @@ def run_ours(args):
     # end to end through the public API from pinned host memory
     if not args.no_e2e:
         host_np, nbytes = wl.host_input()
-        host = torch.from_numpy(host_np).pin_memory()
-        dev_buf = torch.empty_like(host, device=dev)
+        if isinstance(host_np, list):
+            host = [torch.from_numpy(h).pin_memory() for h in host_np]
+            dev_buf = [torch.empty_like(h, device=dev) for h in host]
+        else:
+            host = torch.from_numpy(host_np).pin_memory()
+            dev_buf = torch.empty_like(host, device=dev)
         barrier()
         ems, _ = timed_steps(lambda: wl.e2e_step(capi, mode, host, dev_buf), args.steps, stream, torch, flush)
         out["e2e"] = {"value": wl.units * args.steps / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                       # dense searches read their 64-byte scalar block twice; two-locus its result struct;
                       # FRNN the CSR (row pointers and columns) plus its two status reads
-                      "d2h_bytes_per_step": {"tsmm": 128, "cpp": 128, "frnn": 4 * (wl.nnz or 0) + 16}.get(
+                      "d2h_bytes_per_step": {"tsmm": 128, "cpp": 128, "frnn": 4 * (wl.nnz or 0) + 16,
+                                             "batch": 2048 * (64 + 8) + 24}.get(
                           wl.name, ctypes.sizeof(capi.twolocus_result))}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

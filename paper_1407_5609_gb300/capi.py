@@ -257,11 +257,13 @@ def cpp_batch_workspace_size(instances) -> int:
 
 
 def cpp_batch(points: list, radii: list, pairs_cap: int | None = None, ws: torch.Tensor | None = None,
-              stream=None):
+              stream=None, pairs: torch.Tensor | None = None):
     """Closest pair + R-pairs of every instance in one call.
 
-    ``points`` is a list of float32 [n][d] CUDA tensors (contiguous), ``radii`` their R.
-    Returns (list of result dicts, pair_counts int64 numpy, pairs int32 tensor [P][2]).
+    ``points`` is a list of float32 [n][d] CUDA tensors (contiguous), ``radii`` their R (< 0: no
+    pair list).  Repeated calls with the same workspace and ``pairs`` buffer replay the library's
+    captured CUDA graph.  Returns (list of result dicts, pair_counts int64 numpy, pairs int32
+    tensor [P][2]).
     """
     count = len(points)
     inst = []
@@ -276,8 +278,11 @@ def cpp_batch(points: list, radii: list, pairs_cap: int | None = None, ws: torch
         ws = _workspace(int(lib().cpp_batch_workspace_size(arr, count)), device)
     outs = (cpp_pair_result * max(count, 1))()
     counts = (_i64 * max(count, 1))()
-    cap = int(pairs_cap) if pairs_cap is not None else 1 << 20
-    pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=device)
+    if pairs is None:
+        cap = int(pairs_cap) if pairs_cap is not None else 1 << 20
+        pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=device)
+    else:
+        cap = int(pairs.shape[0])
     _raise(lib().cpp_batch(arr, count, outs, counts, pairs.data_ptr(), cap, ws.data_ptr(), ws.numel(),
                            _stream(stream)))
     c = np.array(list(counts)[:count], dtype=np.int64)

@@ -14,6 +14,7 @@ static std::atomic<long long> g_launches{0};
 static std::atomic<int> g_timing{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // Per-thread CUDA events for the optional stage timing of the dense searches.
 struct StageTimer {

@@ -22,6 +22,7 @@ int set_error(int code, const char* fmt, ...);
 
 // Every kernel launch is followed by this check, which also counts the launch.
 void note_launch();
+void note_launches(long long k);  // adjusts the count (kernels captured into or replayed from a graph)
 #define CPPGB_LAUNCH_CHECK()     \
   do {                           \
     ::cppgb::note_launch();      \

@@ -1,0 +1,99 @@
+"""GPU parity of cpp_batch: every instance's closest pair (Sec. 3) and its pairs within R_q
+(Sec. 3.5) must equal the oracle's, instance by instance, from one persistent graph launch."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import device, to_dev
+from paper_1407_5609_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _capi():
+    from paper_1407_5609_gb300 import capi
+    return capi
+
+
+def _oracle_pairs(x, R):
+    rp, cols = oracle.frnn(x.astype(np.float64), R)
+    out = []
+    for i in range(x.shape[0]):
+        for j in cols[rp[i]:rp[i + 1]]:
+            if j > i:
+                out.append((i, int(j)))
+    return out
+
+
+def _check_batch(insts, radii, repeat=1):
+    capi = _capi()
+    dev = device()
+    pts = [to_dev(np.ascontiguousarray(x, dtype=np.float32), dev) for x in insts]
+    for _ in range(repeat):
+        res, counts, pairs = capi.cpp_batch(pts, radii)
+        pairs = pairs.cpu().numpy()
+        off = 0
+        for q, (x, R) in enumerate(zip(insts, radii)):
+            xd = np.asarray(x, dtype=np.float32).astype(np.float64)
+            oi, oj, od2 = oracle.cpp(xd) if xd.shape[0] else (-1, -1, np.inf)
+            assert (res[q]["i"], res[q]["j"]) == (oi, oj), (q, res[q], (oi, oj, od2))
+            if oi >= 0:
+                assert res[q]["dist2"] == od2
+            got = [tuple(p) for p in pairs[off:off + counts[q]]]
+            off += counts[q]
+            if R >= 0 and xd.shape[0]:
+                assert got == _oracle_pairs(xd, R), q
+            else:
+                assert got == []
+    return res, counts
+
+
+def test_batch_mixed_instances_twice():
+    g = synth.rng_for(71)
+    insts, radii = [], []
+    for q, (n, d) in enumerate([(2, 8), (3, 1), (129, 16), (300, 33), (1000, 8), (700, 64), (257, 128), (50, 200),
+                                (1500, 16), (640, 5), (90, 2), (2000, 32)]):
+        x = g.random((n, d)).astype(np.float32)
+        if n > 3:
+            x[n - 2] = x[n // 3] + np.float32(1e-3) * g.standard_normal(d).astype(np.float32) / np.sqrt(d)
+        insts.append(x)
+        radii.append(float([0.05, 0.3, -1.0, 0.6][q % 4]))
+    _check_batch(insts, radii, repeat=2)
+
+
+def test_batch_edge_instances():
+    g = synth.rng_for(72)
+    ident = np.tile(g.random((1, 6)).astype(np.float32), (40, 1))
+    insts = [np.zeros((0, 4), np.float32), g.random((1, 4)).astype(np.float32), ident, g.random((200, 4)).astype(np.float32)]
+    res, counts = _check_batch(insts, [0.1, 0.1, 0.0, -1.0])
+    assert (res[0]["i"], res[1]["i"]) == (-1, -1)
+    assert counts[2] == 40 * 39 // 2
+
+
+def test_batch_generator_workload_sampled():
+    """The 2048-instance workload: instances of up to 3000 points are checked in full; every
+    instance's reported pair is rechecked by the oracle and must not be farther than its plant."""
+    capi = _capi()
+    dev = device()
+    batch = synth.make_batch()
+    pts = [to_dev(b.pts, dev) for b in batch]
+    res, counts, pairs = capi.cpp_batch(pts, [b.R for b in batch])
+    pairs = pairs.cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    checked = 0
+    for q, b in enumerate(batch):
+        xd = b.pts.astype(np.float64)
+        a, c = b.plant
+        plant_d2 = oracle.sqdist(xd[a], xd[c])
+        r = res[q]
+        assert r["i"] < r["j"] and r["dist2"] <= plant_d2
+        assert oracle.sqdist(xd[r["i"]], xd[r["j"]]) == r["dist2"]
+        got = {tuple(p) for p in pairs[offs[q]:offs[q + 1]]}
+        assert (a, c) in got                        # the plant lies within R = 2 x its distance
+        if b.pts.shape[0] <= 3000 and checked < 40:
+            oi, oj, od2 = oracle.cpp(xd)
+            assert (r["i"], r["j"], r["dist2"]) == (oi, oj, od2)
+            assert sorted(got) == _oracle_pairs(xd, b.R)
+            assert [tuple(p) for p in pairs[offs[q]:offs[q + 1]]] == sorted(got)
+            checked += 1
+    assert checked >= 20
