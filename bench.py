@@ -118,6 +118,11 @@ class TSMM:
     def step(self, capi, mode):
         return capi.tsmm_motif(self.dev_series, self.l, self.excl, mode=mode)
 
+    def shard_step(self, capi, mode, rank, world):
+        from paper_1407_5609_gb300 import shards
+        r = capi.tsmm_motif_shard(self.dev_series, self.l, self.excl, rank, world, mode=mode)
+        return shards.allreduce_result(r)
+
     def e2e_step(self, capi, mode, host, dev_buf):
         dev_buf.copy_(host, non_blocking=True)
         return capi.tsmm_motif(dev_buf, self.l, self.excl, mode=mode)
@@ -193,6 +198,10 @@ class CPP:
     def step(self, capi, mode):
         return capi.cpp_closest_pair(self.dev_x, mode=mode)
 
+    def shard_step(self, capi, mode, rank, world):
+        from paper_1407_5609_gb300 import shards
+        return shards.allreduce_result(capi.cpp_closest_pair_shard(self.dev_x, rank, world, mode=mode))
+
     def e2e_step(self, capi, mode, host, dev_buf):
         dev_buf.copy_(host, non_blocking=True)
         return capi.cpp_closest_pair(dev_buf, mode=mode)
@@ -260,11 +269,11 @@ class Batch:
 
     def __init__(self, args):
         from paper_1407_5609_gb300 import synth
-        self.batch = synth.make_batch()
+        self.batch = synth.make_batch(count=args.batch_count)
         self.units = sum(b.pts.shape[0] * (b.pts.shape[0] - 1) // 2 for b in self.batch)
         self.flop_per_unit = None
         self.flops = sum(b.pts.shape[0] * (b.pts.shape[0] - 1) // 2 * 2 * b.pts.shape[1] for b in self.batch)
-        self.config = {"workload": "batch of 2048 CPP+FRNN instances, n log-uniform [256, 65536], d in {8,16,32,64,128}, "
+        self.config = {"workload": f"batch of {len(self.batch)} CPP+FRNN instances, n log-uniform [256, 65536], d in {{8,16,32,64,128}}, "
                                    "uniform or 16-component mixture, planted pair at 1e-3, R = 2e-3",
                        "pairs_per_step": self.units,
                        "l2": "4.8 GB of points per step, > L2"}
@@ -316,9 +325,9 @@ WORKLOADS = {"tsmm": TSMM, "twolocus": TwoLocus, "cpp": CPP, "frnn": FRNN, "batc
 
 
 # ------------------------------------------------------------------ helpers
-def kernel_source_hash():
+def source_hash(files):
     h = hashlib.sha256()
-    for f in ("gram_tc.cu", "gram_simt.cu", "twolocus.cu", "common.cuh"):
+    for f in files:
         p = os.path.join(ROOT, "paper_1407_5609_gb300", "csrc", f)
         if os.path.exists(p):
             h.update(open(p, "rb").read())
@@ -333,18 +342,20 @@ def recorded_traffic(key):
             rec = json.load(f).get(key)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("source_hash") != kernel_source_hash():
+    if not rec or rec.get("source_hash") != source_hash(rec.get("sources", [])):
         return None
     return rec.get("bytes_per_launch")
 
 
-def calibrate_rows(wl, oracle, target_s):
-    """Rows of the oracle sample that take about target_s (fixed cost + per-row cost, two probes)."""
-    _, t2, _ = wl.oracle_sample(oracle, 2)
-    _, t8, _ = wl.oracle_sample(oracle, 8)
-    per_row = max((t8 - t2) / 6.0, 1e-4)
-    fixed = max(t2 - 2 * per_row, 0.0)
-    return max(2, int((target_s - fixed) / per_row))
+def d2h_bytes(wl, capi):
+    """Bytes a step reads back to the host through the public API."""
+    if wl.name in ("tsmm", "cpp"):
+        return 128                                      # the 64-byte scalar block, read twice
+    if wl.name == "frnn":
+        return 4 * (wl.nnz or 0) + 16                   # the column list plus two status words
+    if wl.name == "batch":
+        return len(wl.batch) * (64 + 8) + 24            # per-instance results and pair offsets
+    return ctypes.sizeof(capi.twolocus_result)
 
 
 def cpu_baseline(wl, target_s=12.0):
@@ -394,9 +405,14 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # N > 1: the motif / closest-pair searches are split into shards of one search (strong scaling,
+    # one all-gather of the 24-byte result per step); the other workloads run as replicas.
+    sharded = world > 1 and hasattr(wl, "shard_step")
+    step_fn = (lambda: wl.shard_step(capi, mode, rank, world)) if sharded else (lambda: wl.step(capi, mode))
+
     # warm-up
     for _ in range(args.warmup):
-        ref = wl.step(capi, mode)
+        ref = step_fn()
     barrier()
 
     # timed region (device-resident inputs)
@@ -407,7 +423,7 @@ def run_ours(args):
     clocks.start()
 
     def one():
-        r = wl.step(capi, mode)
+        r = step_fn()
         st = capi.cpp_stage_times()
         if len(st) >= 2:
             dense_ms.append(st[1])
@@ -422,16 +438,18 @@ def run_ours(args):
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
-    value = wl.units * args.steps * world / (total_ms / 1e3)
+    value = wl.units * args.steps * (1 if sharded else world) / (total_ms / 1e3)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None,
+           "scaling": "strong" if sharded else "weak", "vs_baseline": None,
            "dtype": ({"plain_fp32": "f32", "filter_fp16": "f16", "filter_bf16": "bf16"}.get(mode)
                      if wl.name in ("tsmm", "cpp") else {"frnn": "f32", "twolocus": "u64", "batch": "f32"}[wl.name]),
            "data": "synthetic", "config": dict(wl.config, mode=mode if wl.name in ("tsmm", "cpp") else None,
                                                flush_l2_between_steps=bool(flush),
-                                               parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+                                               parallelism=(f"{world} shards of one search + all-gather of the result"
+                                                            if sharded else f"replicas x{world}" if world > 1
+                                                            else "single GPU")),
            "answer": {k: res[k] for k in ("i", "j", "dist2", "score") if k in res},
            "gpu_launches": launches}
 
@@ -500,11 +518,7 @@ def run_ours(args):
         barrier()
         ems, _ = timed_steps(lambda: wl.e2e_step(capi, mode, host, dev_buf), args.steps, stream, torch, flush)
         out["e2e"] = {"value": wl.units * args.steps / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                      # dense searches read their 64-byte scalar block twice; two-locus its result struct;
-                      # FRNN the CSR (row pointers and columns) plus its two status reads
-                      "d2h_bytes_per_step": {"tsmm": 128, "cpp": 128, "frnn": 4 * (wl.nnz or 0) + 16,
-                                             "batch": 2048 * (64 + 8) + 24}.get(
-                          wl.name, ctypes.sizeof(capi.twolocus_result))}
+                      "d2h_bytes_per_step": d2h_bytes(wl, capi)}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
@@ -548,6 +562,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tsmm")
     ap.add_argument("--mode", choices=["plain_fp32", "filter_fp16", "filter_bf16"], default=None)
+    ap.add_argument("--batch-count", type=int, default=2048,
+                    help="instances of the batch workload (smaller values only for profiler captures)")
     ap.add_argument("--series-len", type=int, default=262144,
                     help="motif workload length (smaller values only for profiler captures)")
     ap.add_argument("--flush-l2", dest="flush_l2", action="store_true", default=True)

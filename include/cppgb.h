@@ -92,6 +92,20 @@ size_t tsmm_motif_workspace_size(int64_t N, int64_t l, int mode);
 int tsmm_motif(const float* series, int64_t N, int64_t l, int64_t excl, int mode,
                cpp_pair_result* out, void* ws, size_t ws_bytes, void* stream);
 
+/*
+ * Shards of the pair space (for running one search across several GPUs or calls).  The dense stage
+ * evaluates the pairs tile by tile; shard s of nshards (0 <= s < nshards) evaluates only the tiles
+ * t with t mod nshards == s and returns the exact best pair among them (i = j = -1 when it has
+ * none), with the same conventions as the unsharded call.  The lexicographically smallest
+ * (dist2, i, j) over the results of all nshards shards is exactly the result of the unsharded
+ * call; combining them is the caller's one exchange step.  Workspace sizes are those of the
+ * unsharded calls.  Errors as for the unsharded calls, plus CPPGB_ERR_ARG for a bad shard.
+ */
+int cpp_closest_pair_shard(const void* pts, int dtype, int64_t n, int64_t d, int64_t ld, int mode, int64_t shard,
+                           int64_t nshards, cpp_pair_result* out, void* ws, size_t ws_bytes, void* stream);
+int tsmm_motif_shard(const float* series, int64_t N, int64_t l, int64_t excl, int mode, int64_t shard,
+                     int64_t nshards, cpp_pair_result* out, void* ws, size_t ws_bytes, void* stream);
+
 /* Result of a two-locus scan. */
 typedef struct {
   int64_t i, j;        /* best SNP pair, i < j; -1 when S < 2 */

@@ -60,6 +60,10 @@ SIGNATURES = {
     "cpp_closest_pair": (_int, [_vp, _int, _i64, _i64, _i64, _int, ctypes.POINTER(cpp_pair_result), _vp, _sz, _vp]),
     "tsmm_motif_workspace_size": (_sz, [_i64, _i64, _int]),
     "tsmm_motif": (_int, [_vp, _i64, _i64, _i64, _int, ctypes.POINTER(cpp_pair_result), _vp, _sz, _vp]),
+    "cpp_closest_pair_shard": (_int, [_vp, _int, _i64, _i64, _i64, _int, _i64, _i64, ctypes.POINTER(cpp_pair_result),
+                                       _vp, _sz, _vp]),
+    "tsmm_motif_shard": (_int, [_vp, _i64, _i64, _i64, _int, _i64, _i64, ctypes.POINTER(cpp_pair_result), _vp, _sz,
+                                 _vp]),
     "twolocus_scan_workspace_size": (_sz, [_i64, _i64]),
     "twolocus_scan": (_int, [_vp, _i64, _i64, _i64, _i64, ctypes.POINTER(twolocus_result), _vp, _sz, _vp]),
     "twolocus_scan_noalloc": (_int, [_vp, _i64, _i64, _i64, _i64, ctypes.POINTER(twolocus_result), _vp]),
@@ -188,6 +192,40 @@ def tsmm_motif(series: torch.Tensor, l: int, excl: int, mode="plain_fp32", ws: t
         need = tsmm_motif_workspace_size(N, l, m)
         st = call(_workspace(need + 24 * int(out.n_emitted * 1.05) + 4096, series.device))
     _raise(st)
+    return out.as_dict()
+
+
+def cpp_closest_pair_shard(pts: torch.Tensor, shard: int, nshards: int, mode="plain_fp32",
+                           ws: torch.Tensor | None = None, stream=None) -> dict:
+    """Best pair among the dense-stage tiles t with t % nshards == shard (see include/cppgb.h)."""
+    _check_cuda(pts, "pts")
+    if pts.dim() != 2 or pts.stride(1) != 1:
+        raise ValueError("pts must be 2-D with unit column stride")
+    dtype = {torch.float32: F32, torch.float64: F64}[pts.dtype]
+    n, d = pts.shape
+    m = _mode(mode)
+    if ws is None:
+        ws = _workspace(cpp_closest_pair_workspace_size(n, d, m), pts.device)
+    out = cpp_pair_result()
+    _raise(lib().cpp_closest_pair_shard(pts.data_ptr() if n else None, dtype, n, d, pts.stride(0) if n else d, m,
+                                        shard, nshards, ctypes.byref(out), ws.data_ptr(), ws.numel(),
+                                        _stream(stream)))
+    return out.as_dict()
+
+
+def tsmm_motif_shard(series: torch.Tensor, l: int, excl: int, shard: int, nshards: int, mode="plain_fp32",
+                     ws: torch.Tensor | None = None, stream=None) -> dict:
+    """Motif search restricted to the dense-stage tiles t with t % nshards == shard."""
+    _check_cuda(series, "series")
+    if series.dim() != 1 or series.dtype != torch.float32 or not series.is_contiguous():
+        raise ValueError("series must be a contiguous 1-D float32 tensor")
+    N = series.shape[0]
+    m = _mode(mode)
+    if ws is None:
+        ws = _workspace(tsmm_motif_workspace_size(N, l, m), series.device)
+    out = cpp_pair_result()
+    _raise(lib().tsmm_motif_shard(series.data_ptr(), N, l, excl, m, shard, nshards, ctypes.byref(out),
+                                  ws.data_ptr(), ws.numel(), _stream(stream)))
     return out.as_dict()
 
 

@@ -125,7 +125,7 @@ struct Source {
 };
 
 int dense_search(const Source& src, int64_t n, int64_t d, int64_t excl, int mode, cpp_pair_result* out, void* ws,
-                 size_t ws_bytes, cudaStream_t st) {
+                 size_t ws_bytes, cudaStream_t st, int64_t shard = 0, int64_t nshards = 1) {
   DenseLayout L = dense_layout(ws, n, d, mode, ws_bytes);
   if (ws_bytes < L.bytes)
     return set_error(CPPGB_ERR_CAPACITY, "workspace too small: %zu bytes given, %zu needed", ws_bytes, L.bytes);
@@ -149,9 +149,9 @@ int dense_search(const Source& src, int64_t n, int64_t d, int64_t excl, int mode
   DenseScalars h;
   for (int pass = 0; pass < 2; ++pass) {
     if (is_filter(mode))
-      rc = launch_gram_tc(L.X, mode, n, L.n_pad, L.Kp, excl, L.norms, L.sc, L.cand, L.cap, st);
+      rc = launch_gram_tc(L.X, mode, n, L.n_pad, L.Kp, excl, L.norms, L.sc, L.cand, L.cap, st, shard, nshards);
     else
-      rc = launch_gram_simt((const float*)L.X, n, L.Kp, excl, L.norms, L.sc, L.cand, L.cap, st);
+      rc = launch_gram_simt((const float*)L.X, n, L.Kp, excl, L.norms, L.sc, L.cand, L.cap, st, shard, nshards);
     if (rc) return rc;
     if (timing) CPPGB_CUDA_TRY(cudaEventRecord(g_timer.ev[2], st));
     CPPGB_CUDA_TRY(cudaMemcpyAsync(&h, L.sc, sizeof h, cudaMemcpyDeviceToHost, st));
@@ -279,6 +279,48 @@ int tsmm_motif(const float* series, int64_t N, int64_t l, int64_t excl, int mode
   if (rc) return rc;
   Source src{true, nullptr, CPPGB_F32, l, l, series, l};
   return dense_search(src, N - l + 1, l, excl, mode, out, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ shards of the pair space
+static int shard_ok(int64_t shard, int64_t nshards) {
+  if (nshards < 1 || shard < 0 || shard >= nshards)
+    return set_error(CPPGB_ERR_ARG, "need 0 <= shard < nshards (got %lld of %lld)", (long long)shard,
+                     (long long)nshards);
+  return CPPGB_OK;
+}
+
+int cpp_closest_pair_shard(const void* pts, int dtype, int64_t n, int64_t d, int64_t ld, int mode, int64_t shard,
+                           int64_t nshards, cpp_pair_result* out, void* ws, size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  int rc = shard_ok(shard, nshards);
+  if (rc) return rc;
+  if (!out) return set_error(CPPGB_ERR_ARG, "out is NULL");
+  if (n < 0 || n > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "n out of range (%lld)", (long long)n);
+  if (d < 1 || d > 4096 || ld < d) return set_error(CPPGB_ERR_ARG, "need 1 <= d <= 4096 and ld >= d");
+  if (dtype != CPPGB_F32 && dtype != CPPGB_F64) return set_error(CPPGB_ERR_ARG, "dtype must be CPPGB_F32 or CPPGB_F64");
+  if (!mode_ok(mode)) return set_error(CPPGB_ERR_ARG, "unknown mode %d", mode);
+  if (n > 0 && !pts) return set_error(CPPGB_ERR_ARG, "pts is NULL");
+  if (!ws) return set_error(CPPGB_ERR_ARG, "workspace is NULL");
+  if ((rc = check_device())) return rc;
+  Source src{false, pts, dtype, d, ld, nullptr, 0};
+  return dense_search(src, n, d, 1, mode, out, ws, ws_bytes, (cudaStream_t)stream, shard, nshards);
+}
+
+int tsmm_motif_shard(const float* series, int64_t N, int64_t l, int64_t excl, int mode, int64_t shard,
+                     int64_t nshards, cpp_pair_result* out, void* ws, size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  int rc = shard_ok(shard, nshards);
+  if (rc) return rc;
+  if (!out) return set_error(CPPGB_ERR_ARG, "out is NULL");
+  if (!series) return set_error(CPPGB_ERR_ARG, "series is NULL");
+  if (l < 2 || l > 4096 || N < l) return set_error(CPPGB_ERR_ARG, "need 2 <= l <= 4096 and N >= l");
+  if (N - l + 1 > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "too many l-mers");
+  if (excl < 1) return set_error(CPPGB_ERR_ARG, "excl must be >= 1");
+  if (!mode_ok(mode)) return set_error(CPPGB_ERR_ARG, "unknown mode %d", mode);
+  if (!ws) return set_error(CPPGB_ERR_ARG, "workspace is NULL");
+  if ((rc = check_device())) return rc;
+  Source src{true, nullptr, CPPGB_F32, l, l, series, l};
+  return dense_search(src, N - l + 1, l, excl, mode, out, ws, ws_bytes, (cudaStream_t)stream, shard, nshards);
 }
 
 // ------------------------------------------------------------------ two-locus

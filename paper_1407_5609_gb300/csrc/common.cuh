@@ -120,14 +120,17 @@ int launch_prep_lmers(const float* series, int64_t n, int64_t l, int mode, void*
                       int64_t Kp, float* norms, float* eps, DenseScalars* sc, cudaStream_t st);
 
 // Dense all-pairs stage on FP32 CUDA cores.
+// shard / nshards: only the tiles t with t % nshards == shard are evaluated (a slice of the pair space).
 int launch_gram_simt(const float* X, int64_t n, int64_t Kp, int64_t excl, const float* norms,
-                     DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st);
+                     DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st, int64_t shard = 0,
+                     int64_t nshards = 1);
 // Fixed-radius variant: emits every pair i < j with D~ <= theta(rr) (rr = R^2 rounded up to FP32).
 int launch_gram_simt_radius(const float* X, int64_t n, int64_t Kp, const float* norms, DenseScalars* sc,
                             Candidate* cand, int64_t cap, float rr, cudaStream_t st);
 // Dense all-pairs stage on tcgen05 tensor cores (FP16 or BF16 operands).
 int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp, int64_t excl,
-                   const float* norms, DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st);
+                   const float* norms, DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st,
+                   int64_t shard = 0, int64_t nshards = 1);
 bool gram_tc_available();
 
 // FP64 recheck of the surviving candidates and the lexicographic (d^2, i, j) minimum.

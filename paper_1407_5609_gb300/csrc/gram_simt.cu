@@ -22,12 +22,12 @@ template <bool RADIUS>
 __global__ void __launch_bounds__(NT, 2)
     gram_simt_kernel(const float* __restrict__ X, int64_t n, int64_t Kp, int64_t excl, int64_t delta,
                      const float* __restrict__ norms, DenseScalars* sc,
-                     Candidate* __restrict__ cand, int64_t cap, float rr) {
+                     Candidate* __restrict__ cand, int64_t cap, float rr, int64_t shard, int64_t nshards) {
   __shared__ __align__(16) TileSmem sm;
   __shared__ float red[NT / 32];
 
   int64_t bi, bj;
-  tri_decode((int64_t)blockIdx.x, delta, &bi, &bj);
+  tri_decode((int64_t)blockIdx.x * nshards + shard, delta, &bi, &bj);
   const int64_t row0 = bi * BM, col0 = bj * BM;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   float acc[8][8];
@@ -95,28 +95,30 @@ __global__ void __launch_bounds__(NT, 2)
 
 template <bool RADIUS>
 static int launch_simt(const float* X, int64_t n, int64_t Kp, int64_t excl, const float* norms, DenseScalars* sc,
-                       Candidate* cand, int64_t cap, float rr, cudaStream_t st) {
+                       Candidate* cand, int64_t cap, float rr, cudaStream_t st, int64_t shard, int64_t nshards) {
   if (Kp % BK) return set_error(CPPGB_ERR_ARG, "internal: Kp %% 16 != 0");
   const int64_t nb = (n + BM - 1) / BM;
   // smallest block offset whose tiles hold a pair with j - i >= excl
   int64_t delta = excl <= BM - 1 ? 0 : (excl - (BM - 1) + BM - 1) / BM;
   const int64_t m = nb - delta;
-  const int64_t tiles = tri_count(m);
+  const int64_t all = tri_count(m);
+  const int64_t tiles = all > shard ? (all - shard + nshards - 1) / nshards : 0;  // this shard's tiles
   if (tiles <= 0) return CPPGB_OK;
   if (tiles > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "too many tiles (%lld)", (long long)tiles);
-  gram_simt_kernel<RADIUS><<<(unsigned)tiles, NT, 0, st>>>(X, n, Kp, excl, delta, norms, sc, cand, cap, rr);
+  gram_simt_kernel<RADIUS><<<(unsigned)tiles, NT, 0, st>>>(X, n, Kp, excl, delta, norms, sc, cand, cap, rr,
+                                                                   shard, nshards);
   CPPGB_LAUNCH_CHECK();
   return CPPGB_OK;
 }
 
 int launch_gram_simt(const float* X, int64_t n, int64_t Kp, int64_t excl, const float* norms, DenseScalars* sc,
-                     Candidate* cand, int64_t cap, cudaStream_t st) {
-  return launch_simt<false>(X, n, Kp, excl, norms, sc, cand, cap, 0.f, st);
+                     Candidate* cand, int64_t cap, cudaStream_t st, int64_t shard, int64_t nshards) {
+  return launch_simt<false>(X, n, Kp, excl, norms, sc, cand, cap, 0.f, st, shard, nshards);
 }
 
 int launch_gram_simt_radius(const float* X, int64_t n, int64_t Kp, const float* norms, DenseScalars* sc,
                             Candidate* cand, int64_t cap, float rr, cudaStream_t st) {
-  return launch_simt<true>(X, n, Kp, 1, norms, sc, cand, cap, rr, st);
+  return launch_simt<true>(X, n, Kp, 1, norms, sc, cand, cap, rr, st, 0, 1);
 }
 
 }  // namespace cppgb

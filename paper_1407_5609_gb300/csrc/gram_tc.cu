@@ -12,7 +12,7 @@
 //               one of two 256-column FP32 accumulators, commits to the ring and to the epilogue
 //   warps 2-5   epilogue: tcgen05.ld of the accumulator rows, D~ = nx + (ny - 2 S), running minima,
 //               threshold test per 32-column chunk, rare candidate emission, bound publication
-// Tiles are 128 rows x 256 columns of the upper triangle, walked in bands of 64 column blocks (the
+// Tiles are 128 rows x 256 columns of the upper triangle, walked in bands of 16 column blocks (the
 // band's B panels stay in L2 while the row panels stream once per band).  Every mbarrier wait is
 // bounded (about 2 s of %globaltimer): on a timeout the CTA flags CPPGB_ERR_TIMEOUT, drains what it
 // issued, frees its TMEM and exits.
@@ -26,7 +26,7 @@ namespace {
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int NTHREADS = 192;
-constexpr int BAND = 64;      // column blocks per band (16 MB of B panels stay in L2)
+constexpr int BAND = 16;  // column blocks per band (4 MB of B panels stay in L2); 8, 32, 64 measured slower
 constexpr int MAX_BANDS = 480;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long WAIT_NS = 2000000000ull;
@@ -35,7 +35,7 @@ constexpr unsigned long long WAIT_NS = 2000000000ull;
 // band b; nfull[b] = leading row blocks whose every column block in the band holds a valid pair.
 struct TileSched {
   int64_t n, excl;
-  int32_t nbands, nbi, nbj, pad;
+  int32_t nbands, nbi, nbj, band;
   int64_t off[MAX_BANDS + 1];
   int32_t nfull[MAX_BANDS];
 };
@@ -60,8 +60,8 @@ __device__ __forceinline__ void decode_tile(const TileSched& ts, int64_t t, int*
   int b = *band;
   while (b + 1 < ts.nbands && ts.off[b + 1] <= t) ++b;
   *band = b;
-  const int64_t bj0 = (int64_t)b * BAND;
-  const int64_t bj1 = bj0 + BAND < ts.nbj ? bj0 + BAND : ts.nbj;
+  const int64_t bj0 = (int64_t)b * ts.band;
+  const int64_t bj1 = bj0 + ts.band < ts.nbj ? bj0 + ts.band : ts.nbj;
   const int64_t w = bj1 - bj0;
   int64_t r = t - ts.off[b];
   const int64_t full = (int64_t)ts.nfull[b] * w;
@@ -178,6 +178,96 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// ------------------------------------------------------------------ shared epilogue
+// Per-thread epilogue state: running minimum of D~, snapshot of the global bound, emission threshold.
+struct EpiState {
+  float tmin, Usnap, th;
+};
+
+__device__ __forceinline__ void epi_init(EpiState& es, DenseScalars* sc, const BoundParams& bp) {
+  es.tmin = __int_as_float(0x7f800000);
+  es.Usnap = __uint_as_float(*reinterpret_cast<volatile unsigned int*>(&sc->U_bits));
+  // -inf until this thread has a finite bound, so masked (+inf) entries can never pass it
+  es.th = es.Usnap < __int_as_float(0x7f800000) ? theta_of(es.Usnap, bp) : __int_as_float(0xff800000);
+}
+
+// One thread = one accumulator row (TMEM lane) of a 128 x 256 tile: D~ = nx + (ny - 2 S) for its 256
+// columns in 32-column chunks, running minimum, threshold test per chunk, rare candidate emission.
+__device__ __forceinline__ void epi_tile(int64_t row0, int64_t col0, uint32_t tbase, int lane, uint32_t quarter,
+                                         int64_t n, int64_t excl, const float* __restrict__ norms,
+                                         const BoundParams& bp, DenseScalars* sc, Candidate* __restrict__ cand,
+                                         int64_t cap, EpiState& es) {
+  const int64_t i = row0 + quarter * 32 + lane;
+  const float nx = norms[i];
+  const bool edge = (row0 + BM - 1 >= n) || (col0 + BN - 1 >= n) || (col0 - (row0 + BM - 1) < excl);
+#pragma unroll 1
+  for (int c = 0; c < BN / 32; ++c) {
+    uint32_t r[32];
+    __syncwarp();
+    tmem_ld32(tbase + (uint32_t)(c * 32), r);
+    const float4* ny4 = reinterpret_cast<const float4*>(norms + col0 + c * 32);
+    float dp[32];
+    float cmin = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 v = __ldg(ny4 + q);
+      dp[4 * q + 0] = fmaf(-2.f, __uint_as_float(r[4 * q + 0]), v.x);
+      dp[4 * q + 1] = fmaf(-2.f, __uint_as_float(r[4 * q + 1]), v.y);
+      dp[4 * q + 2] = fmaf(-2.f, __uint_as_float(r[4 * q + 2]), v.z);
+      dp[4 * q + 3] = fmaf(-2.f, __uint_as_float(r[4 * q + 3]), v.w);
+    }
+    if (edge) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        const int64_t j = col0 + c * 32 + k;
+        if (!(i < n && j < n && j - i >= excl)) dp[k] = __int_as_float(0x7f800000);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) cmin = fminf(cmin, dp[k]);
+    const float cD = nx + cmin;
+    if (cD < es.tmin) {
+      es.tmin = cD;
+      es.th = theta_of(fminf(es.Usnap, upper_d2(es.tmin, bp)), bp);
+    }
+    if (cD <= es.th) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        const float D = nx + dp[k];
+        if (D <= es.th) {
+          const unsigned long long slot = atomicAdd(&sc->n_cand, 1ull);
+          if ((int64_t)slot < cap) {
+            Candidate cd;
+            cd.i = (int32_t)i;
+            cd.j = (int32_t)(col0 + c * 32 + k);
+            cd.d2f = D;
+            cd.pad = 0.f;
+            cand[slot] = cd;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Publish the warp's bound if it improves the global one, then refresh the snapshot.
+__device__ __forceinline__ void epi_publish(int lane, const BoundParams& bp, DenseScalars* sc, EpiState& es) {
+  float wmin = es.tmin;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wmin = fminf(wmin, __shfl_xor_sync(0xffffffffu, wmin, o));
+  float Unew = 0.f;
+  if (lane == 0) {
+    const float ub = upper_d2(wmin, bp);
+    if (ub < es.Usnap) atomic_min_nonneg(&sc->U_bits, ub);
+    Unew = __uint_as_float(*reinterpret_cast<volatile unsigned int*>(&sc->U_bits));
+  }
+  Unew = __shfl_sync(0xffffffffu, Unew, 0);
+  if (Unew < es.Usnap) {
+    es.Usnap = Unew;
+    es.th = theta_of(fminf(es.Usnap, upper_d2(es.tmin, bp)), bp);
+  }
+}
+
 struct SmemCtl {
   uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
   uint32_t tmem_base;
@@ -187,7 +277,7 @@ struct SmemCtl {
 __global__ void __launch_bounds__(NTHREADS, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TileSched ts, int64_t total,
                    uint32_t ab_fmt, const float* __restrict__ norms, DenseScalars* sc, Candidate* __restrict__ cand,
-                   int64_t cap, int64_t kchunks) {
+                   int64_t cap, int64_t kchunks, int64_t shard, int64_t nshards) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   SmemCtl* ctl = (SmemCtl*)(smem + STAGES * STAGE_BYTES);
@@ -228,7 +318,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
         int64_t bi, bj;
-        decode_tile(ts, t, &band, &bi, &bj);
+        decode_tile(ts, t * nshards + shard, &band, &bi, &bj);
         for (int64_t kc = 0; kc < kchunks; ++kc) {
           if (!mbar_wait(&ctl->empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
           uint8_t* sa = smem + stage * STAGE_BYTES;
@@ -294,16 +384,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ---------------------------------------------------------------- epilogue (warps 2..5)
     const uint32_t quarter = (uint32_t)(warp & 3);  // TMEM lanes 32*quarter .. +31
     const BoundParams bp = sc->bp;
-    float tmin = __int_as_float(0x7f800000);
-    float Usnap = __uint_as_float(*reinterpret_cast<volatile unsigned int*>(&sc->U_bits));
-    // Emission threshold: -inf until this thread has a finite bound, so masked (+inf) entries
-    // can never pass it.
-    float th = Usnap < __int_as_float(0x7f800000) ? theta_of(Usnap, bp) : __int_as_float(0xff800000);
+    EpiState es;
+    epi_init(es, sc, bp);
     int64_t it = 0;
     int band = 0;
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++it) {
       int64_t bi, bj;
-      decode_tile(ts, t, &band, &bi, &bj);
+      decode_tile(ts, t * nshards + shard, &band, &bi, &bj);
       const uint32_t acc = (uint32_t)(it & 1), use = (uint32_t)((it >> 1) & 1);
       const bool got = __all_sync(0xffffffffu, mbar_wait(&ctl->tfull[acc], use, abort_flag));
       if (!got) {
@@ -314,77 +401,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         break;
       }
       tc_fence_after();
-      const int64_t row0 = bi * BM, col0 = bj * BN;
-      const int64_t i = row0 + quarter * 32 + lane;
-      const float nx = norms[i];
-      const bool edge = (row0 + BM - 1 >= ts.n) || (col0 + BN - 1 >= ts.n) || (col0 - (row0 + BM - 1) < ts.excl);
       const uint32_t tbase = tmem_base + ((quarter * 32u) << 16) + acc * (uint32_t)BN;
-#pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
-        uint32_t r[32];
-        __syncwarp();
-        tmem_ld32(tbase + (uint32_t)(c * 32), r);
-        const float4* ny4 = reinterpret_cast<const float4*>(norms + col0 + c * 32);
-        float dp[32];
-        float cmin = __int_as_float(0x7f800000);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 v = __ldg(ny4 + q);
-          dp[4 * q + 0] = fmaf(-2.f, __uint_as_float(r[4 * q + 0]), v.x);
-          dp[4 * q + 1] = fmaf(-2.f, __uint_as_float(r[4 * q + 1]), v.y);
-          dp[4 * q + 2] = fmaf(-2.f, __uint_as_float(r[4 * q + 2]), v.z);
-          dp[4 * q + 3] = fmaf(-2.f, __uint_as_float(r[4 * q + 3]), v.w);
-        }
-        if (edge) {
-#pragma unroll
-          for (int k = 0; k < 32; ++k) {
-            const int64_t j = col0 + c * 32 + k;
-            if (!(i < ts.n && j < ts.n && j - i >= ts.excl)) dp[k] = __int_as_float(0x7f800000);
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < 32; ++k) cmin = fminf(cmin, dp[k]);
-        const float cD = nx + cmin;
-        if (cD < tmin) {
-          tmin = cD;
-          th = theta_of(fminf(Usnap, upper_d2(tmin, bp)), bp);
-        }
-        if (cD <= th) {
-#pragma unroll
-          for (int k = 0; k < 32; ++k) {
-            const float D = nx + dp[k];
-            if (D <= th) {
-              const unsigned long long slot = atomicAdd(&sc->n_cand, 1ull);
-              if ((int64_t)slot < cap) {
-                Candidate cd;
-                cd.i = (int32_t)i;
-                cd.j = (int32_t)(col0 + c * 32 + k);
-                cd.d2f = D;
-                cd.pad = 0.f;
-                cand[slot] = cd;
-              }
-            }
-          }
-        }
-      }
+      epi_tile(bi * BM, bj * BN, tbase, lane, quarter, ts.n, ts.excl, norms, bp, sc, cand, cap, es);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&ctl->tempty[acc]);
-      // publish the warp's bound if it improves the global one, then refresh the snapshot
-      float wmin = tmin;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) wmin = fminf(wmin, __shfl_xor_sync(0xffffffffu, wmin, o));
-      float Unew = 0.f;
-      if (lane == 0) {
-        const float ub = upper_d2(wmin, bp);
-        if (ub < Usnap) atomic_min_nonneg(&sc->U_bits, ub);
-        Unew = __uint_as_float(*reinterpret_cast<volatile unsigned int*>(&sc->U_bits));
-      }
-      Unew = __shfl_sync(0xffffffffu, Unew, 0);
-      if (Unew < Usnap) {
-        Usnap = Unew;
-        th = theta_of(fminf(Usnap, upper_d2(tmin, bp)), bp);
-      }
+      epi_publish(lane, bp, sc, es);
       if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
     }
     tc_fence_before();
@@ -421,7 +443,7 @@ EncodeTiledFn encode_fn() {
 bool gram_tc_available() { return true; }
 
 int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp, int64_t excl, const float* norms,
-                   DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st) {
+                   DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st, int64_t shard, int64_t nshards) {
   if (Kp % BK || n_pad % BN) return set_error(CPPGB_ERR_ARG, "internal: tensor-core stage needs Kp %% 64 == 0");
   if (((uintptr_t)X & 15) != 0) return set_error(CPPGB_ERR_ARG, "internal: row matrix must be 16-byte aligned");
   if (n_pad > 0x7fffffffLL || Kp > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "problem too large for TMA coordinates");
@@ -430,11 +452,14 @@ int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp
   ts.excl = excl;
   ts.nbi = (int32_t)(n_pad / BM);
   ts.nbj = (int32_t)(n_pad / BN);
-  ts.nbands = (int32_t)((ts.nbj + BAND - 1) / BAND);
-  if (ts.nbands > MAX_BANDS) return set_error(CPPGB_ERR_ARG, "n too large for the tensor-core tile schedule");
+  int band = BAND;
+  while ((ts.nbj + band - 1) / band > MAX_BANDS) band *= 2;
+  ts.band = band;
+  ts.nbands = (int32_t)((ts.nbj + band - 1) / band);
+
   int64_t total = 0;
   for (int b = 0; b < ts.nbands; ++b) {
-    const int64_t bj0 = (int64_t)b * BAND, bj1 = bj0 + BAND < ts.nbj ? bj0 + BAND : ts.nbj;
+    const int64_t bj0 = (int64_t)b * band, bj1 = bj0 + band < ts.nbj ? bj0 + band : ts.nbj;
     ts.off[b] = total;
     int32_t nf = 0;
     bool in_full = true;
@@ -447,6 +472,9 @@ int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp
     ts.nfull[b] = nf;
   }
   ts.off[ts.nbands] = total;
+  // this shard's tiles are t = k * nshards + shard; the kernel walks k
+  const int64_t all_tiles = total;
+  total = all_tiles > shard ? (all_tiles - shard + nshards - 1) / nshards : 0;
   if (total == 0) return CPPGB_OK;
 
   EncodeTiledFn enc = encode_fn();
@@ -465,11 +493,12 @@ int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp
   int dev = 0, sms = 0;
   CPPGB_CUDA_TRY(cudaGetDevice(&dev));
   CPPGB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const uint32_t ab = mode == CPPGB_MODE_FILTER_BF16 ? 1u : 0u;
   const size_t smem = (size_t)STAGES * STAGE_BYTES + sizeof(SmemCtl) + 1024;
   CPPGB_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t grid = total < sms ? total : sms;
-  gram_tc_kernel<<<(unsigned)grid, NTHREADS, smem, st>>>(tmap, ts, total, mode == CPPGB_MODE_FILTER_BF16 ? 1u : 0u,
-                                                         norms, sc, cand, cap, Kp / BK);
+  gram_tc_kernel<<<(unsigned)grid, NTHREADS, smem, st>>>(tmap, ts, total, ab,
+                                                         norms, sc, cand, cap, Kp / BK, shard, nshards);
   CPPGB_LAUNCH_CHECK();
   return CPPGB_OK;
 }

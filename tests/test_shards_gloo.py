@@ -1,0 +1,59 @@
+"""The exchange step of a sharded search, on CPU: two gloo ranks each contribute the best pair of
+their part of the pair space (computed by the oracle), and the all-reduce must give the answer of
+the whole search.  Also the host-side reduction's edge cases."""
+import math
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+import oracle
+from paper_1407_5609_gb300 import shards, synth
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, out_path):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    a = synth.make_random_walk(900, seed=81)
+    l, excl = 40, 20
+    n = a.shape[0] - l + 1
+    rows = np.arange(rank, n, world)                    # this rank's part: pairs touching its rows
+    bj, bd = oracle.tsmm_rows(a, l, excl, rows)
+    keys = [(float(d), int(min(r, j)), int(max(r, j))) for r, j, d in zip(rows, bj, bd) if j >= 0]
+    d2, i, j = min(keys)
+    local = {"i": i, "j": j, "dist2": d2, "dist": math.sqrt(d2), "n_emitted": 1, "n_rechecked": 1}
+    res = shards.allreduce_result(local)
+    if rank == 0:
+        np.save(out_path, np.array([res["i"], res["j"], res["dist2"], res["n_emitted"]]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_allreduce_two_gloo_ranks(tmp_path):
+    out = str(tmp_path / "res.npy")
+    mp.start_processes(_rank_main, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+    i, j, d2, ne = np.load(out)
+    a = synth.make_random_walk(900, seed=81)
+    oi, oj, od2 = oracle.tsmm(a, 40, 20)
+    assert (int(i), int(j)) == (oi, oj) and d2 == od2 and ne == 2
+
+
+def test_reduce_results_lexicographic_and_empty():
+    none = {"i": -1, "j": -1, "dist2": math.inf, "dist": math.inf}
+    r = shards.reduce_results([none, {"i": 5, "j": 9, "dist2": 1.0, "dist": 1.0},
+                               {"i": 3, "j": 11, "dist2": 1.0, "dist": 1.0}, {"i": 0, "j": 1, "dist2": 2.0, "dist": 1.4}])
+    assert (r["i"], r["j"]) == (3, 11)
+    assert shards.reduce_results([none, none])["i"] == -1
+    assert shards.reduce_results([])["i"] == -1
