@@ -166,15 +166,19 @@ typedef struct {
   const float* pts; /* device FP32 [n][d] row-major (ld = d) */
   int64_t n;
   int32_t d;        /* 1 .. 256 */
-  int32_t pad_;
+  int32_t path;     /* 0: library default (tensor cores from d >= 16), 1: FP32 CUDA-core tiles,
+                       2: BF16 tensor-core tiles -- the answer is exact either way */
   double R;         /* FRNN radius for this instance (< 0: no FRNN output) */
 } cpp_instance;
 
 /*
  * cpp_batch -- many independent CPP + FRNN instances of uneven n and d in one persistent launch
- * (the problems of Sec. 3 and Sec. 3.5, instance by instance).
+ * (the problems of Sec. 3 and Sec. 3.5, instance by instance).  Instances on the FP32 path share
+ * one persistent CUDA-core tile kernel, those on the tensor-core path one persistent tcgen05
+ * kernel (BF16 rows padded to 64, 128, 192 or 256 columns, one tensor map per width); both feed
+ * the same FP32 second pass and FP64 recheck, so the answer does not depend on the path.
  *   inst        host array [count].
- *   out_cpp     host [count]: closest pair of each instance (as cpp_closest_pair, FP32 plain mode).
+ *   out_cpp     host [count]: closest pair of each instance (identical to cpp_closest_pair).
  *   pair_counts host int64 [count]: number of undirected pairs (i < j) with d <= R per instance.
  *   pairs       device int32 [pairs_cap][2]: the (i, j) pairs, instance after instance, ascending (i, j).
  * Errors: CPPGB_ERR_ARG, CPPGB_ERR_CAPACITY (pairs_cap or ws too small), CPPGB_ERR_CUDA.

@@ -48,7 +48,7 @@ class twolocus_result(ctypes.Structure):
 
 
 class cpp_instance(ctypes.Structure):
-    _fields_ = [("pts", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("pad_", ctypes.c_int32),
+    _fields_ = [("pts", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("R", ctypes.c_double)]
 
 
@@ -294,22 +294,30 @@ def cpp_batch_workspace_size(instances) -> int:
     return int(lib().cpp_batch_workspace_size(arr, len(instances)))
 
 
+PATH_DEFAULT, PATH_FP32, PATH_TC = 0, 1, 2
+
+
 def cpp_batch(points: list, radii: list, pairs_cap: int | None = None, ws: torch.Tensor | None = None,
-              stream=None, pairs: torch.Tensor | None = None):
+              stream=None, pairs: torch.Tensor | None = None, paths=None):
     """Closest pair + R-pairs of every instance in one call.
 
     ``points`` is a list of float32 [n][d] CUDA tensors (contiguous), ``radii`` their R (< 0: no
-    pair list).  Repeated calls with the same workspace and ``pairs`` buffer replay the library's
-    captured CUDA graph.  Returns (list of result dicts, pair_counts int64 numpy, pairs int32
-    tensor [P][2]).
+    pair list), ``paths`` an optional per-instance tile path (PATH_DEFAULT, PATH_FP32 or
+    PATH_TC; a single int applies to all).  Repeated calls with the same workspace and ``pairs``
+    buffer replay the library's captured CUDA graph.  Returns (list of result dicts, pair_counts
+    int64 numpy, pairs int32 tensor [P][2]).
     """
     count = len(points)
+    if paths is None or isinstance(paths, int):
+        paths = [paths or 0] * count
+    if len(paths) != count:
+        raise ValueError("paths must give one entry per instance")
     inst = []
-    for p, R in zip(points, radii):
+    for p, R, path in zip(points, radii, paths):
         _check_cuda(p, "points")
         if p.dim() != 2 or p.dtype != torch.float32 or not p.is_contiguous():
             raise ValueError("each instance must be a contiguous float32 [n][d] tensor")
-        inst.append(cpp_instance(p.data_ptr(), p.shape[0], p.shape[1], 0, float(R)))
+        inst.append(cpp_instance(p.data_ptr(), p.shape[0], p.shape[1], int(path), float(R)))
     arr = (cpp_instance * count)(*inst)
     device = points[0].device if count else torch.device("cuda")
     if ws is None:

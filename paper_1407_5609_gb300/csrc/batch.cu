@@ -12,10 +12,18 @@
 // instance's exact closest pair (lexicographic (d^2, i, j)) and its exact pair list
 // { (i, j) : i < j, d <= R_q } (ascending).  The whole sequence is captured once into a CUDA graph
 // per argument set and replayed.
+//
+// Each instance takes one of two tile paths (cpp_instance.path): FP32 CUDA-core tiles of 128 x 128,
+// or BF16 tensor-core tiles of 128 x 256 (tcgen05, the dense-stage kernel's pipeline with one TMA
+// tensor map per 64-column class of d).  Tiles recorded by either path are recomputed in FP32 by the
+// same second pass.
+#include <cuda_bf16.h>
+
 #include <mutex>
 #include <vector>
 
 #include "common.cuh"
+#include "tc_ptx.cuh"
 #include "tile_simt.cuh"
 
 namespace cppgb {
@@ -24,20 +32,34 @@ namespace {
 struct BatchInst {
   const float* pts;  // caller's FP32 [n][d]
   int32_t n, d, Kp, has_r;
-  int64_t x_off;     // floats before this instance's rows in the packed X
-  int64_t row_off;   // rows before this instance (norms)
-  int64_t tile_off;  // tiles before this instance
+  int64_t x_off;     // floats before this instance's rows in the packed FP32 X
+  int64_t row_off;   // rows before this instance (FP32 norms)
+  int64_t tile_off;  // FP32-path tiles before this instance
   double rr;         // R * R (FP64 decision value)
   float rr32;        // R^2 rounded up to FP32 (radius emission)
-  float kappa;       // accumulation bound coefficient for Kp
+  float kappa;       // FP32 accumulation bound coefficient for Kp
+  // tensor-core path
+  int32_t tc, cls;        // tc = 1: BF16 tcgen05 tiles; class = Kp16 / 64 - 1
+  int32_t nbj16, nrow16;  // 256-column blocks; 128-row blocks that hold pairs
+  int64_t row_off16;      // rows before this instance in its class matrix
+  int64_t grow_off16;     // rows before this instance over all tensor-core instances (BF16 norms)
+  int64_t tile_off16;     // tensor-core tiles before this instance
+  float kappa16;          // BF16 / tensor-core accumulation bound coefficient for Kp16
+  float pad;
 };
 
 struct BatchState {
-  BoundParams bp;
+  BoundParams bp, bp16;
   unsigned int U_bits, n2_bits, status, ferr_bits;
+  unsigned int n2_16_bits, eps16_bits;
+  unsigned int tmin16_bits;  // smallest recorded tensor-core tile minimum (clamped at 0)
   unsigned long long best_bits, best_ij;
   int32_t n_rech, cursor;
-  int64_t pad;
+};
+
+constexpr int NCLS = 4;  // tensor-core classes: Kp16 = 64, 128, 192, 256
+struct BatchMaps {
+  CUtensorMap m[NCLS];
 };
 
 // candidate pair; the top bit of qk marks a closest-pair candidate (else a radius candidate)
@@ -47,11 +69,13 @@ struct BatchCand {
 };
 constexpr int32_t CPP_FLAG = (int32_t)0x80000000;
 
-// a tile whose minimum may reach its instance's closest pair
+// a 128 x 128 tile whose minimum may reach its instance's closest pair; the top bit of qf marks a
+// minimum measured by the tensor-core path (its bound parameters apply)
 struct TileRec {
-  int32_t q, bi, bj;
+  int32_t qf, bi, bj;
   float tmin;
 };
+constexpr int32_t TC_FLAG = (int32_t)0x80000000;
 
 struct BatchGlobals {
   unsigned long long n_cand, n_trec;
@@ -80,6 +104,10 @@ __global__ void batch_init_kernel(BatchState* st, int count, BatchGlobals* g) {
   BatchState s;
   s.bp.eps_pair = 0.f;
   s.bp.e_acc = 0.f;
+  s.bp16 = s.bp;
+  s.n2_16_bits = 0u;
+  s.eps16_bits = 0u;
+  s.tmin16_bits = 0x7f800000u;
   s.U_bits = 0x7f800000u;
   s.n2_bits = 0u;
   s.status = 0u;
@@ -88,40 +116,57 @@ __global__ void batch_init_kernel(BatchState* st, int count, BatchGlobals* g) {
   s.best_ij = ~0ull;
   s.n_rech = 0;
   s.cursor = 0;
-  s.pad = 0;
   st[q] = s;
 }
 
-// one warp per padded row of every instance; rows located through row_off by binary search
+// Consecutive rows per warp in the preparation kernels: the per-instance maxima are reduced in
+// registers over the run and flushed with one atomic per instance touched (a per-row atomic on
+// one address per instance serialises millions of updates).
+constexpr int PREP_RUN = 16;
+
+// FP32 rows of every instance (padded to Kp columns and to 128 rows) and their squared norms.
 __global__ void __launch_bounds__(256) batch_prep_kernel(const BatchInst* __restrict__ inst, const int64_t* __restrict__ row_offs,
                                                          int count, int64_t total_rows, float* __restrict__ X,
                                                          float* __restrict__ norms, BatchState* st, BatchGlobals* g) {
   const int lane = threadIdx.x & 31;
-  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (r >= total_rows) return;
-  const int q = find_inst(row_offs, count, r);
-  const BatchInst in = inst[q];
-  const int64_t lr = r - in.row_off;
-  float* out = X + in.x_off + lr * in.Kp;
-  float n2 = 0.f;
+  const int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * PREP_RUN;
+  if (r0 >= total_rows) return;
+  const int64_t r1 = r0 + PREP_RUN < total_rows ? r0 + PREP_RUN : total_rows;
+  int q = find_inst(row_offs, count, r0);
+  int64_t next = row_offs[q + 1];
+  BatchInst in = inst[q];
+  float m2 = 0.f;
   bool bad = false;
-  for (int k = lane; k < in.Kp; k += 32) {
-    float v = 0.f;
-    if (lr < in.n && k < in.d) {
-      v = in.pts[lr * in.d + k];
-      bad |= !isfinite(v);
+  for (int64_t r = r0; r < r1; ++r) {
+    if (r >= next) {
+      if (lane == 0) atomic_max_nonneg(&st[q].n2_bits, m2 * (1.f + 0x1p-12f));
+      m2 = 0.f;
+      do {
+        ++q;
+        next = row_offs[q + 1];
+      } while (r >= next);
+      in = inst[q];
     }
-    out[k] = v;
-    n2 = fmaf(v, v, n2);
-  }
+    const int64_t lr = r - in.row_off;
+    float* out = X + in.x_off + lr * in.Kp;
+    float n2 = 0.f;
+    for (int k = lane; k < in.Kp; k += 32) {
+      float v = 0.f;
+      if (lr < in.n && k < in.d) {
+        v = in.pts[lr * in.d + k];
+        bad |= !isfinite(v);
+      }
+      out[k] = v;
+      n2 = fmaf(v, v, n2);
+    }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
-  bad = __any_sync(0xffffffffu, bad);
-  if (lane == 0) {
-    norms[r] = n2;
-    atomic_max_nonneg(&st[q].n2_bits, n2 * (1.f + 0x1p-12f));
-    if (bad) atomicOr(&g->status, 1u);
+    for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+    if (lane == 0) norms[r] = n2;
+    m2 = fmaxf(m2, n2);
   }
+  if (lane == 0) atomic_max_nonneg(&st[q].n2_bits, m2 * (1.f + 0x1p-12f));
+  bad = __any_sync(0xffffffffu, bad);
+  if (bad && lane == 0) atomicOr(&g->status, 1u);
 }
 
 __global__ void batch_bounds_kernel(const BatchInst* __restrict__ inst, BatchState* st, int count) {
@@ -129,6 +174,66 @@ __global__ void batch_bounds_kernel(const BatchInst* __restrict__ inst, BatchSta
   if (q >= count) return;
   st[q].bp.eps_pair = 0.f;  // FP32 input stored exactly
   st[q].bp.e_acc = inst[q].kappa * __uint_as_float(st[q].n2_bits) * (1.f + 0x1p-20f);
+  st[q].bp16.eps_pair = 2.f * __uint_as_float(st[q].eps16_bits) * (1.f + 0x1p-20f);
+  st[q].bp16.e_acc = inst[q].kappa16 * __uint_as_float(st[q].n2_16_bits) * (1.f + 0x1p-20f);
+}
+
+// BF16 rows of the tensor-core instances (a run of PREP_RUN padded rows per warp); the row's
+// residual |x - x~| (exact in FP32) bounds the rounding, as in the dense stage's preparation.
+__global__ void __launch_bounds__(256) batch_prep16_kernel(const BatchInst* __restrict__ inst,
+                                                           const int64_t* __restrict__ grow_offs, int count,
+                                                           int64_t rows16, __nv_bfloat16* X16_0, __nv_bfloat16* X16_1,
+                                                           __nv_bfloat16* X16_2, __nv_bfloat16* X16_3,
+                                                           float* __restrict__ norms16, BatchState* st) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * PREP_RUN;
+  if (r0 >= rows16) return;
+  const int64_t r1 = r0 + PREP_RUN < rows16 ? r0 + PREP_RUN : rows16;
+  int q = find_inst(grow_offs, count, r0);
+  int64_t next = grow_offs[q + 1];
+  BatchInst in = inst[q];
+  float m2 = 0.f, me = 0.f;
+  for (int64_t r = r0; r < r1; ++r) {
+    if (r >= next) {
+      if (lane == 0) {
+        atomic_max_nonneg(&st[q].n2_16_bits, m2 * (1.f + 0x1p-12f));
+        atomic_max_nonneg(&st[q].eps16_bits, me * (1.f + 0x1p-10f));
+      }
+      m2 = me = 0.f;
+      do {
+        ++q;
+        next = grow_offs[q + 1];
+      } while (r >= next);
+      in = inst[q];
+    }
+    const int64_t lr = r - in.grow_off16;
+    const int Kp16 = 64 * (in.cls + 1);
+    __nv_bfloat16* base = in.cls == 0 ? X16_0 : in.cls == 1 ? X16_1 : in.cls == 2 ? X16_2 : X16_3;
+    __nv_bfloat16* out = base + (in.row_off16 + lr) * Kp16;
+    float n2 = 0.f, dd = 0.f;
+    for (int k = lane; k < Kp16; k += 32) {
+      float v = 0.f;
+      if (lr < in.n && k < in.d) v = in.pts[lr * in.d + k];
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      const float hv = __bfloat162float(h);
+      const float dl = v - hv;  // exact in FP32
+      out[k] = h;
+      n2 = fmaf(hv, hv, n2);
+      dd = fmaf(dl, dl, dd);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+      dd += __shfl_xor_sync(0xffffffffu, dd, o);
+    }
+    if (lane == 0) norms16[r] = n2;
+    m2 = fmaxf(m2, n2);
+    me = fmaxf(me, sqrtf(dd));
+  }
+  if (lane == 0) {
+    atomic_max_nonneg(&st[q].n2_16_bits, m2 * (1.f + 0x1p-12f));
+    atomic_max_nonneg(&st[q].eps16_bits, me * (1.f + 0x1p-10f));
+  }
 }
 
 // Persistent FP32 tile kernel over the concatenated tile lists.
@@ -208,7 +313,7 @@ __global__ void __launch_bounds__(TILE_NT, 2)
       // record the tile if its minimum can reach the bound published before it
       if (tmin <= theta_of(Ug, bp)) {
         const unsigned long long k = atomicAdd(&g->n_trec, 1ull);
-        if ((int64_t)k < trec_cap) trec[k] = TileRec{q, (int32_t)bi, (int32_t)bj, tmin};
+        if ((int64_t)k < trec_cap) trec[k] = TileRec{q, (int32_t)bi, (int32_t)bj, tmin};  // FP32-path record
       }
       if (ub < Ug) atomic_min_nonneg(&st[q].U_bits, ub);
     }
@@ -219,45 +324,465 @@ __global__ void __launch_bounds__(TILE_NT, 2)
 // their closest-pair candidates (D~ <= theta(U_final)).
 __global__ void __launch_bounds__(TILE_NT, 2)
     batch_tile_recheck_kernel(const BatchInst* __restrict__ inst, const float* __restrict__ X,
-                              const float* __restrict__ norms, const BatchState* st, BatchGlobals* g,
+                              const float* __restrict__ norms, BatchState* st, BatchGlobals* g,
                               const TileRec* __restrict__ trec, int64_t trec_cap, BatchCand* __restrict__ cand,
-                              int64_t cap) {
+                              int64_t cap, int tighten) {
   __shared__ __align__(16) TileSmem sm;
+  __shared__ int list[TILE_NT];
+  __shared__ int nlist;
+  __shared__ float red[TILE_NT / 32];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t nrec = (int64_t)g->n_trec < trec_cap ? (int64_t)g->n_trec : trec_cap;
-  for (int64_t t = blockIdx.x; t < nrec; t += gridDim.x) {
-    const TileRec tr = trec[t];
-    const BoundParams bp = st[tr.q].bp;
-    const float th = theta_of(__uint_as_float(st[tr.q].U_bits), bp);
-    if (!(tr.tmin <= th)) continue;  // uniform across the block
-    const BatchInst in = inst[tr.q];
-    const int64_t row0 = (int64_t)tr.bi * TILE_BM, col0 = (int64_t)tr.bj * TILE_BM;
-    float acc[8][8];
-    simt_tile_mainloop(X + in.x_off, in.Kp, row0, col0, sm, acc);
-    const float* nr = norms + in.row_off;
+  // tighten = 1: a tensor-core bound U comes from BF16 tile minima and cannot get below about
+  //   (sqrt(e_acc16) + eps16)^2; the tile(s) of each instance with the smallest recorded minimum
+  //   are recomputed in FP32 and U is lowered to the FP32 bound of their minimum.
+  // tighten = 0: every record whose minimum may still reach the final U is recomputed in FP32 and
+  //   its closest-pair candidates are emitted.
+  // Most records were written before their instance's bound settled: the block tests TILE_NT of
+  // them at once and recomputes only the survivors.
+  for (int64_t base = (int64_t)blockIdx.x * TILE_NT; base < nrec; base += (int64_t)gridDim.x * TILE_NT) {
+    if (tid == 0) nlist = 0;
+    __syncthreads();
+    if (base + tid < nrec) {
+      const TileRec tr = trec[base + tid];
+      const int q = tr.qf & ~TC_FLAG;
+      bool keep;
+      if (tighten) {
+        keep = (tr.qf & TC_FLAG) && fmaxf(tr.tmin, 0.f) <= __uint_as_float(st[q].tmin16_bits);
+      } else {
+        // the record's minimum was measured by its own path: test it with that path's bound parameters
+        keep = tr.tmin <= theta_of(__uint_as_float(st[q].U_bits), (tr.qf & TC_FLAG) ? st[q].bp16 : st[q].bp);
+      }
+      if (keep) list[atomicAdd(&nlist, 1)] = tid;
+    }
+    __syncthreads();
+    const int m = nlist;
+    for (int e = 0; e < m; ++e) {
+      const TileRec tr = trec[base + list[e]];
+      const int q = tr.qf & ~TC_FLAG;
+      const BoundParams bp = st[q].bp;
+      const float th = theta_of(__uint_as_float(st[q].U_bits), bp);
+      const BatchInst in = inst[q];
+      const int64_t row0 = (int64_t)tr.bi * TILE_BM, col0 = (int64_t)tr.bj * TILE_BM;
+      float acc[8][8];
+      simt_tile_mainloop(X + in.x_off, in.Kp, row0, col0, sm, acc);
+      const float* nr = norms + in.row_off;
+      float tmin = __int_as_float(0x7f800000);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int64_t i = row0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + r - 4);
-      const float nx = nr[i];
+      for (int r = 0; r < 8; ++r) {
+        const int64_t i = row0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + r - 4);
+        const float nx = nr[i];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const int64_t j = col0 + (c < 4 ? tx * 4 + c : 64 + tx * 4 + c - 4);
-        const float D = fmaf(-2.f, acc[r][c], nx + nr[j]);
-        if (i < in.n && j < in.n && j > i && D <= th) {
-          const unsigned long long k = atomicAdd(&g->n_cand, 1ull);
-          if ((int64_t)k < cap) {
-            BatchCand cd;
-            cd.qk = tr.q | CPP_FLAG;
-            cd.i = (int32_t)i;
-            cd.j = (int32_t)j;
-            cd.d2f = D;
-            cand[k] = cd;
+        for (int c = 0; c < 8; ++c) {
+          const int64_t j = col0 + (c < 4 ? tx * 4 + c : 64 + tx * 4 + c - 4);
+          const float D = fmaf(-2.f, acc[r][c], nx + nr[j]);
+          if (i < in.n && j < in.n && j > i) {
+            tmin = fminf(tmin, D);
+            if (!tighten && D <= th) {
+              const unsigned long long k = atomicAdd(&g->n_cand, 1ull);
+              if ((int64_t)k < cap) {
+                BatchCand cd;
+                cd.qk = q | CPP_FLAG;
+                cd.i = (int32_t)i;
+                cd.j = (int32_t)j;
+                cd.d2f = D;
+                cand[k] = cd;
+              }
+            }
           }
         }
       }
+      if (tighten) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+        if ((tid & 31) == 0) red[tid >> 5] = tmin;
+        __syncthreads();
+        if (tid == 0) {
+          for (int w = 1; w < TILE_NT / 32; ++w) tmin = fminf(tmin, red[w]);
+          if (tmin < __int_as_float(0x7f800000)) atomic_min_nonneg(&st[q].U_bits, upper_d2(tmin, bp));
+        }
+      }
     }
+    __syncthreads();  // the list and the tile buffers are reused
   }
 }
+
+
+// ---------------------------------------------------------------- tensor-core tiles
+namespace btc {
+using namespace tc;
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2, STAGE_BYTES = A_BYTES + BN * BK * 2;
+constexpr int GROUPS = 2;                    // epilogue groups, one TMEM accumulator each
+constexpr int NTHREADS = 64 + GROUPS * 128;  // producer warp, MMA warp, 2 x 4 epilogue warps
+constexpr uint32_t TMEM_COLS = 512;
+
+struct Ctl {
+  alignas(16) float ny[GROUPS][BN];  // per group: |y~_j|^2 of the tile's 256 columns
+  uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
+  float tile_min[GROUPS][2][4];  // [group][tile parity][TMEM lane quarter]
+  int ok[GROUPS][2][4];          // per epilogue warp: its wait succeeded (exchanged at the group barrier)
+  uint32_t tmem_base;
+  int abort_flag;
+};
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + sizeof(Ctl) + 1024;  // + 1024-byte alignment slack
+
+// Tiles (bi, bj) of one instance: 128-row blocks bi < nrow16, 256-column blocks bj with
+// bj >= bi / 2 (every such tile holds a pair i < j).  Rows 2k and 2k + 1 have nbj - k tiles, so
+// the tiles before row 2k number 2k nbj - k (k - 1); k is found by bisection.
+__device__ __forceinline__ void decode16(int64_t t, int64_t nbj, int64_t nrow, int64_t* bi, int64_t* bj) {
+  auto P = [&](int64_t k) { return 2 * k * nbj - k * (k - 1); };
+  int64_t lo = 0, hi = (nrow + 1) / 2;  // largest k with P(k) <= t
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (P(mid) <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  const int64_t k = lo, r = t - P(k), c = nbj - k;
+  if (r < c) {
+    *bi = 2 * k;
+    *bj = k + r;
+  } else {
+    *bi = 2 * k + 1;
+    *bj = k + (r - c);
+  }
+}
+
+// Follows one role's increasing tile sequence: the instance by a forward cursor over the tile
+// offsets (binary search after a long jump), (bi, bj) by stepping along the rows of the instance
+// (bisection on entering an instance or after a long step).
+struct TileWalker {
+  const int64_t* offs;
+  const BatchInst* insts;
+  int count, q;
+  int64_t lo, hi, cur, bi, bj;
+  BatchInst in;
+
+  __device__ __forceinline__ void init(const int64_t* o, const BatchInst* is, int c) {
+    offs = o;
+    insts = is;
+    count = c;
+    q = -1;
+    lo = hi = 0;
+  }
+  __device__ __forceinline__ void go(int64_t t) {
+    if (t >= hi) {
+      int qq = q + 1, steps = 0;
+      while (qq < count - 1 && offs[qq + 1] <= t && steps < 8) {
+        ++qq;
+        ++steps;
+      }
+      if (qq < count - 1 && offs[qq + 1] <= t) qq = find_inst(offs, count, t);
+      q = qq;
+      in = insts[q];
+      lo = offs[q];
+      hi = offs[q + 1];
+      cur = t - lo;
+      decode16(cur, in.nbj16, in.nrow16, &bi, &bj);
+      return;
+    }
+    int64_t r = t - lo - cur;
+    cur += r;
+    if (r > 4 * (in.nbj16 - (bi >> 1))) {
+      decode16(cur, in.nbj16, in.nrow16, &bi, &bj);
+      return;
+    }
+    while (r > 0) {
+      const int64_t rem = in.nbj16 - bj;
+      if (r < rem) {
+        bj += r;
+        break;
+      }
+      r -= rem;
+      ++bi;
+      bj = bi >> 1;
+    }
+  }
+};
+
+__device__ __forceinline__ void load_ny(const float* p, float4 (&v)[8]) {  // shared memory, broadcast reads
+#pragma unroll
+  for (int u = 0; u < 8; ++u) v[u] = reinterpret_cast<const float4*>(p)[u];
+}
+
+// One 32-column chunk of a row: D~ - |x~_i|^2 = |y~_j|^2 - 2 x~.y~, computed in place over the
+// loaded accumulator registers (the register file per SMSP holds three warps of this kernel at 168
+// registers), masked to +inf off the triangle and past n; returns the chunk minimum (a depth-5
+// tree, not a 32-long dependent chain); emits radius candidates.
+__device__ __forceinline__ float chunk_min(uint32_t (&r)[32], const float4 (&ny)[8], bool edge, int64_t i, int64_t j0,
+                                           int64_t n, float nx, float th_r, int q, BatchGlobals* g,
+                                           BatchCand* __restrict__ cand, int64_t cap) {
+  const float INF = __int_as_float(0x7f800000);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    r[4 * u + 0] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * u + 0]), ny[u].x));
+    r[4 * u + 1] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * u + 1]), ny[u].y));
+    r[4 * u + 2] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * u + 2]), ny[u].z));
+    r[4 * u + 3] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * u + 3]), ny[u].w));
+  }
+  if (edge) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const int64_t j = j0 + k;
+      if (!(i < n && j < n && j > i)) r[k] = __float_as_uint(INF);
+    }
+  }
+  float m[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) m[k] = fminf(__uint_as_float(r[k]), __uint_as_float(r[k + 16]));
+#pragma unroll
+  for (int k = 0; k < 8; ++k) m[k] = fminf(m[k], m[k + 8]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) m[k] = fminf(m[k], m[k + 4]);
+  const float cmin = fminf(fminf(m[0], m[2]), fminf(m[1], m[3]));
+  if (nx + cmin <= th_r) {  // rare: collect the hits as a bit mask, then emit them in a rolled loop
+    uint32_t hits = 0u;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {  // masked entries hold +inf
+      const float v = __uint_as_float(r[k]);
+      hits |= (nx + v <= th_r && v < INF ? 1u : 0u) << k;
+    }
+    while (hits) {
+      const int k = __ffs(hits) - 1;
+      hits &= hits - 1u;
+      const unsigned long long slot = atomicAdd(&g->n_cand, 1ull);
+      if ((int64_t)slot < cap) {
+        BatchCand cd;
+        cd.qk = q;  // radius candidate: decided by the FP64 test alone, its FP32 value is not used
+        cd.i = (int32_t)i;
+        cd.j = (int32_t)(j0 + k);
+        cd.d2f = 0.f;
+        cand[slot] = cd;
+      }
+    }
+  }
+  return cmin;
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    batch_tc_kernel(const __grid_constant__ BatchMaps maps, const BatchInst* __restrict__ inst,
+                    const int64_t* __restrict__ tile_offs16, int count, int64_t total, const float* __restrict__ norms16,
+                    BatchState* st, BatchGlobals* g, BatchCand* __restrict__ cand, int64_t cap,
+                    TileRec* __restrict__ trec, int64_t trec_cap) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  Ctl* ctl = (Ctl*)(smem + STAGES * STAGE_BYTES);
+  volatile int* abort_flag = &ctl->abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&ctl->full[s], 1);
+      mbar_init(&ctl->empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&ctl->tfull[a], 1);
+      mbar_init(&ctl->tempty[a], 4);
+    }
+    mbar_init(&ctl->drain, 1);
+    ctl->abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = ctl->tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---------------------------------------------- TMA producer
+      for (int c = 0; c < NCLS; ++c) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.m[c]) : "memory");
+      TileWalker w;
+      w.init(tile_offs16, inst, count);
+      uint32_t stage = 0, phase = 0;
+      int64_t issued = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        w.go(t);
+        const CUtensorMap* map = &maps.m[w.in.cls];
+        const int kch = w.in.cls + 1;
+        const int ya = (int)(w.in.row_off16 + w.bi * BM), yb = (int)(w.in.row_off16 + w.bj * BN);
+        for (int kc = 0; kc < kch; ++kc) {
+          if (!mbar_wait(&ctl->empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
+          uint8_t* sa = smem + stage * STAGE_BYTES;
+          mbar_arrive_expect_tx(&ctl->full[stage], STAGE_BYTES);
+          tma_load_2d(sa, map, &ctl->full[stage], kc * BK, ya);
+          tma_load_2d(sa + A_BYTES, map, &ctl->full[stage], kc * BK, yb);
+          tma_load_2d(sa + A_BYTES + BM * BK * 2, map, &ctl->full[stage], kc * BK, yb + BM);
+          ++issued;
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(&g->status, 4u);
+      }
+      const int64_t last = issued < STAGES ? issued : STAGES;
+      for (int64_t k = 1; k <= last; ++k) {  // drain: every issued copy lands before exit
+        const int64_t u = issued - k;
+        const uint32_t s = (uint32_t)(u % STAGES), par = (uint32_t)((u / STAGES) & 1);
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try_wait(&ctl->full[s], par) && globaltimer() - t0 < WAIT_NS) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---------------------------------------------- MMA issuer
+      const uint32_t idesc = make_idesc(1u, BM, BN);  // BF16 operands
+      TileWalker w;
+      w.init(tile_offs16, inst, count);
+      uint32_t stage = 0, phase = 0;
+      int64_t it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
+        w.go(t);
+        const int kch = w.in.cls + 1;
+        const uint32_t acc = (uint32_t)(it & 1), use = (uint32_t)((it >> 1) & 1);
+        if (!mbar_wait(&ctl->tempty[acc], use ^ 1u, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t dtmem = tmem_base + acc * (uint32_t)BN;
+        for (int kc = 0; kc < kch; ++kc) {
+          if (!mbar_wait(&ctl->full[stage], phase, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
+          const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            mma_f16(dtmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (kc | kk) != 0);
+          mma_commit(&ctl->empty[stage]);
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        mma_commit(&ctl->tfull[acc]);
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(&g->status, 4u);
+      }
+      mma_commit(&ctl->drain);
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(&ctl->drain, 0) && globaltimer() - t0 < WAIT_NS) {
+      }
+    }
+  } else {  // -------------------------------------------------------- epilogue groups
+    // Group grp takes the CTA's tiles it = grp, grp + 2, ... and their accumulator grp; warp
+    // (warp & 3) reads TMEM lanes 32 (warp & 3) .. + 31 (the rows it may access).
+    const int grp = (warp - 2) >> 2;
+    const uint32_t quarter = (uint32_t)(warp & 3);
+    const bool leader = ((warp - 2) & 3) == 0 && lane == 0;
+    const int gt = ((warp - 2) & 3) * 32 + lane;  // 0..127 within the group
+    const int64_t stride = (int64_t)GROUPS * gridDim.x;
+    // The walker runs one tile ahead: the next tile's row norm and its two column norms per
+    // thread are loaded while the current tile is reduced.
+    TileWalker w;
+    w.init(tile_offs16, inst, count);
+    float nx_n = 0.f;
+    float2 ny_n = make_float2(0.f, 0.f);
+    auto prefetch = [&](int64_t tt) {
+      w.go(tt);
+      const float* nrm = norms16 + w.in.grow_off16;
+      nx_n = nrm[w.bi * BM + quarter * 32 + lane];
+      ny_n = __ldg(reinterpret_cast<const float2*>(nrm + w.bj * BN) + gt);
+    };
+    int bq = -1;
+    BoundParams bp;
+    float th_r = 0.f;
+    int64_t k = 0;
+    int64_t t = blockIdx.x + (int64_t)grp * gridDim.x;
+    if (t < total) prefetch(t);
+    for (; t < total; t += stride, ++k) {
+      const int q = w.q;
+      if (q != bq) {  // bound parameters are fixed while the tiles run
+        bq = q;
+        bp = st[q].bp16;
+        th_r = w.in.has_r ? theta_of(w.in.rr32, bp) : __int_as_float(0xff800000);
+      }
+      const float Ug = __uint_as_float(*reinterpret_cast<volatile unsigned int*>(&st[q].U_bits));  // early load
+      const int64_t bi = w.bi, bj = w.bj, n = w.in.n;
+      const int64_t row0 = bi * BM, col0 = bj * BN;
+      const int64_t i = row0 + quarter * 32 + lane;
+      const float nx = nx_n;
+      // The group's four warps share a named barrier, so they leave the loop together: each
+      // warp's bounded wait result is exchanged at the barrier and all continue or all stop.  The
+      // same barrier publishes the column norms (the previous tile's readers all passed the
+      // group's closing barrier before this store).
+      reinterpret_cast<float2*>(ctl->ny[grp])[gt] = ny_n;
+      if (t + stride < total) prefetch(t + stride);
+      const uint32_t par = (uint32_t)(k & 1);
+      const bool got = __all_sync(0xffffffffu, mbar_wait(&ctl->tfull[grp], par, abort_flag)) && !*abort_flag;
+      if (lane == 0) ctl->ok[grp][par][quarter] = got ? 1 : 0;
+      asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");
+      const int* okv = ctl->ok[grp][par];
+      if (!(okv[0] && okv[1] && okv[2] && okv[3])) {
+        if (leader) {
+          *abort_flag = 1;
+          atomicOr(&g->status, 4u);
+        }
+        break;
+      }
+      tc_fence_after();
+      const bool edge = (row0 + BM - 1 >= n) || (col0 + BN - 1 >= n) || (col0 < row0 + BM);
+      const uint32_t tbase = tmem_base + ((quarter * 32u) << 16) + (uint32_t)grp * (uint32_t)BN;
+      float rmin = __int_as_float(0x7f800000);
+      const float* nys = ctl->ny[grp];
+      uint32_t ra[32], rb[32];
+      float4 ny[8];
+      tmem_ld32_nowait(tbase, ra);
+      tmem_wait_ld(ra);
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; c += 2) {  // chunk c + 1 loads from TMEM while chunk c is reduced
+        tmem_ld32_nowait(tbase + (uint32_t)((c + 1) * 32), rb);
+        load_ny(nys + c * 32, ny);
+        rmin = fminf(rmin, nx + chunk_min(ra, ny, edge, i, col0 + c * 32, n, nx, th_r, q, g, cand, cap));
+        tmem_wait_ld(rb);
+        if (c + 2 < BN / 32) tmem_ld32_nowait(tbase + (uint32_t)((c + 2) * 32), ra);
+        load_ny(nys + (c + 1) * 32, ny);
+        rmin = fminf(rmin, nx + chunk_min(rb, ny, edge, i, col0 + (c + 1) * 32, n, nx, th_r, q, g, cand, cap));
+        if (c + 2 < BN / 32) tmem_wait_ld(ra);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl->tempty[grp]);
+      // tile minimum over the group's four warps, then the tile record and the bound update
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+      if (lane == 0) ctl->tile_min[grp][par][quarter] = rmin;
+      asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");
+      if (leader) {
+        const float* tm = ctl->tile_min[grp][par];
+        const float tmin = fminf(fminf(tm[0], tm[1]), fminf(tm[2], tm[3]));
+        if (tmin < __int_as_float(0x7f800000)) {
+          if (tmin <= theta_of(Ug, bp)) {
+            atomic_min_nonneg(&st[q].tmin16_bits, tmin);
+            // record the 128-column halves that hold a pair i < j < n for the FP32 second pass (the
+            // FP32 rows of an instance are padded to 128 only, so a half past n must not be read)
+            for (int64_t h = 2 * bj; h <= 2 * bj + 1; ++h) {
+              if (h < bi || h * BM >= n) continue;
+              const unsigned long long kr = atomicAdd(&g->n_trec, 1ull);
+              if ((int64_t)kr < trec_cap) trec[kr] = TileRec{q | TC_FLAG, (int32_t)bi, (int32_t)h, tmin};
+            }
+          }
+          const float ub = upper_d2(tmin, bp);
+          if (ub < Ug) atomic_min_nonneg(&st[q].U_bits, ub);
+        }
+      }
+    }
+    tc_fence_before();
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+}
+}  // namespace btc
 
 __device__ __forceinline__ double exact_d2(const float* __restrict__ p, int d, int32_t i, int32_t j) {
   const float* x = p + (int64_t)i * d;
@@ -370,7 +895,7 @@ __global__ void batch_finish_kernel(const BatchState* st, int count, const int64
 // ---------------------------------------------------------------- host side
 struct BatchLayout {
   BatchInst* inst;
-  int64_t *row_offs, *tile_offs;
+  int64_t *row_offs, *tile_offs, *grow_offs16, *tile_offs16;
   BatchState* st;
   BatchGlobals* g;
   int32_t* pair_counts;
@@ -378,6 +903,8 @@ struct BatchLayout {
   int64_t* tmp;
   float* X;
   float* norms;
+  __nv_bfloat16* X16[NCLS];
+  float* norms16;
   BatchCand* cand;
   double* d2buf;
   uint8_t* keep;
@@ -387,9 +914,25 @@ struct BatchLayout {
   size_t bytes;
 };
 
+// Path of one instance: 1 = FP32 CUDA-core tiles, 2 = BF16 tensor-core tiles.  0 (default) picks the
+// tensor cores from d >= 16 on, where the 64-column K chunk is at least a quarter used.
+int path_of(const cpp_instance& c) {
+  if (c.path == 1 || c.path == 2) return c.path;
+  return c.d >= 16 ? 2 : 1;
+}
+
 struct Totals {
-  int64_t rows = 0, xfloats = 0, tiles = 0;
+  int64_t rows = 0, xfloats = 0, tiles = 0;         // FP32 layout (all instances) and FP32-path tiles
+  int64_t rows16 = 0, tiles16 = 0, crow16[NCLS] = {0, 0, 0, 0};
 };
+
+int64_t nrow16_of(int64_t n) { return n >= 2 ? (n - 2) / 128 + 1 : 0; }
+int64_t tiles16_of(int64_t n) {
+  const int64_t nbj = (n + 255) / 256, nr = nrow16_of(n);
+  int64_t t = 0;
+  for (int64_t bi = 0; bi < nr; ++bi) t += nbj - (bi >> 1);
+  return t;
+}
 
 Totals totals_of(const cpp_instance* inst, int64_t count) {
   Totals t;
@@ -399,7 +942,14 @@ Totals totals_of(const cpp_instance* inst, int64_t count) {
     const int64_t nb = npad / TILE_BM;
     t.rows += npad;
     t.xfloats += npad * Kp;
-    t.tiles += n >= 2 ? nb * (nb + 1) / 2 : 0;
+    if (path_of(inst[q]) == 2) {
+      const int64_t npad16 = (n + 255) / 256 * 256;
+      t.rows16 += npad16;
+      t.crow16[(inst[q].d + 63) / 64 - 1] += npad16;
+      t.tiles16 += tiles16_of(n);
+    } else {
+      t.tiles += n >= 2 ? nb * (nb + 1) / 2 : 0;
+    }
   }
   return t;
 }
@@ -410,6 +960,8 @@ BatchLayout batch_layout(void* ws, int64_t count, const Totals& t, size_t ws_byt
   L.inst = c.take<BatchInst>(count);
   L.row_offs = c.take<int64_t>(count + 1);
   L.tile_offs = c.take<int64_t>(count + 1);
+  L.grow_offs16 = c.take<int64_t>(count + 1);
+  L.tile_offs16 = c.take<int64_t>(count + 1);
   L.st = c.take<BatchState>(count);
   L.g = c.take<BatchGlobals>(1);
   L.pair_counts = c.take<int32_t>(count + 1);
@@ -418,7 +970,10 @@ BatchLayout batch_layout(void* ws, int64_t count, const Totals& t, size_t ws_byt
   L.res = c.take<cpp_pair_result>(count);
   L.X = c.take<float>(t.xfloats + 16);
   L.norms = c.take<float>(t.rows + 1);
-  L.trec_cap = t.tiles > 0 ? t.tiles : 1;  // at most one record per tile
+  for (int k = 0; k < NCLS; ++k)  // at least 256 rows each, so every class has a valid tensor map
+    L.X16[k] = c.take<__nv_bfloat16>((size_t)(t.crow16[k] > 256 ? t.crow16[k] : 256) * 64 * (k + 1));
+  L.norms16 = c.take<float>(t.rows16 + 1);
+  L.trec_cap = 2 * (t.tiles + t.tiles16) + 2;  // at most one record per 128 x 128 tile
   L.trec = c.take<TileRec>(L.trec_cap);
   int64_t cap = t.rows / 4;
   cap = cap < (1 << 20) ? (1 << 20) : cap;
@@ -441,16 +996,49 @@ float kappa_fp32(int64_t Kp) {
   return (float)((4.0 * g + 8.0 * u) * 1.01);
 }
 
+// tensor cores: exact BF16 products, FP32 accumulation padded to 2 K 2^-22 per dot product, norms
+// from 32-term warp sums, three epilogue roundings (as for the dense stage)
+float kappa_tc(int64_t Kp) {
+  const double K = (double)Kp, u = 0x1p-24;
+  return (float)((2.0 * 2.0 * K * 0x1p-22 + 2.0 * (K / 32.0 + 6.0) * u + 8.0 * u) * 1.01);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int encode_class_map(CUtensorMap* m, void* base, int64_t rows, int64_t Kp) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
+        qr != cudaDriverEntryPointSuccess)
+      return set_error(CPPGB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    fn = (EncodeTiledFn)p;
+  }
+  const cuuint64_t gdim[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  const cuuint64_t gstride[1] = {(cuuint64_t)Kp * 2};
+  const cuuint32_t box[2] = {64, 128};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult cr = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, gdim, gstride, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return set_error(CPPGB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+  return CPPGB_OK;
+}
+
 // Graph cache: one instantiated graph per argument set (all kernel arguments are baked in).
 struct GraphKey {
   void* ws;
   size_t ws_bytes;
-  int64_t count, rows, tiles, cap;
+  int64_t count, rows, tiles, cap, rows16, tiles16, c0, c1, c2, c3;
   int32_t* pairs;
   int64_t pairs_cap;
   bool operator==(const GraphKey& o) const {
     return ws == o.ws && ws_bytes == o.ws_bytes && count == o.count && rows == o.rows && tiles == o.tiles &&
-           cap == o.cap && pairs == o.pairs && pairs_cap == o.pairs_cap;
+           cap == o.cap && rows16 == o.rows16 && tiles16 == o.tiles16 && c0 == o.c0 && c1 == o.c1 && c2 == o.c2 &&
+           c3 == o.c3 && pairs == o.pairs && pairs_cap == o.pairs_cap;
   }
 };
 std::mutex g_graph_mu;
@@ -460,23 +1048,43 @@ int g_dev = -1;
 long long g_graph_kernels = 0;  // kernels in the instantiated graph
 
 int enqueue_batch(const BatchLayout& L, int64_t count, const Totals& t, int32_t* pairs, int64_t pairs_cap, int sms,
-                  cudaStream_t st) {
+                  const BatchMaps& maps, cudaStream_t st) {
   const int ci = (int)count;
   batch_init_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(L.st, ci, L.g);
   CPPGB_LAUNCH_CHECK();
   CPPGB_CUDA_TRY(cudaMemsetAsync(L.pair_counts, 0, sizeof(int32_t) * (count + 1), st));
-  batch_prep_kernel<<<(unsigned)((t.rows + 7) / 8), 256, 0, st>>>(L.inst, L.row_offs, ci, t.rows, L.X, L.norms, L.st,
+  batch_prep_kernel<<<(unsigned)((t.rows + 8 * PREP_RUN - 1) / (8 * PREP_RUN)), 256, 0, st>>>(L.inst, L.row_offs, ci, t.rows, L.X, L.norms, L.st,
                                                                   L.g);
   CPPGB_LAUNCH_CHECK();
+  if (t.rows16 > 0) {
+    batch_prep16_kernel<<<(unsigned)((t.rows16 + 8 * PREP_RUN - 1) / (8 * PREP_RUN)), 256, 0, st>>>(L.inst, L.grow_offs16, ci, t.rows16, L.X16[0],
+                                                                        L.X16[1], L.X16[2], L.X16[3], L.norms16, L.st);
+    CPPGB_LAUNCH_CHECK();
+  }
   batch_bounds_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(L.inst, L.st, ci);
   CPPGB_LAUNCH_CHECK();
+  if (t.tiles16 > 0) {
+    const size_t smem = btc::SMEM_BYTES;
+    const int64_t grid = t.tiles16 < sms ? t.tiles16 : sms;
+    btc::batch_tc_kernel<<<(unsigned)grid, btc::NTHREADS, smem, st>>>(maps, L.inst, L.tile_offs16, ci, t.tiles16,
+                                                                       L.norms16, L.st, L.g, L.cand, L.cap, L.trec,
+                                                                       L.trec_cap);
+    CPPGB_LAUNCH_CHECK();
+  }
   if (t.tiles > 0) {
     const int64_t grid = t.tiles < 2 * sms ? t.tiles : 2 * sms;
     batch_dense_kernel<<<(unsigned)grid, TILE_NT, 0, st>>>(L.inst, L.tile_offs, ci, t.tiles, L.X, L.norms, L.st, L.g,
                                                            L.cand, L.cap, L.trec, L.trec_cap);
     CPPGB_LAUNCH_CHECK();
+  }
+  if (t.tiles16 > 0) {
     batch_tile_recheck_kernel<<<(unsigned)(2 * sms), TILE_NT, 0, st>>>(L.inst, L.X, L.norms, L.st, L.g, L.trec,
-                                                                      L.trec_cap, L.cand, L.cap);
+                                                                      L.trec_cap, L.cand, L.cap, 1);
+    CPPGB_LAUNCH_CHECK();
+  }
+  if (t.tiles + t.tiles16 > 0) {
+    batch_tile_recheck_kernel<<<(unsigned)(2 * sms), TILE_NT, 0, st>>>(L.inst, L.X, L.norms, L.st, L.g, L.trec,
+                                                                      L.trec_cap, L.cand, L.cap, 0);
     CPPGB_LAUNCH_CHECK();
   }
   // candidate kernels are sized for the capacity and read the live count on the device
@@ -520,6 +1128,7 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
     const cpp_instance& c = inst[q];
     if (c.n < 0 || c.n > (1 << 30)) return set_error(CPPGB_ERR_ARG, "instance %lld: n out of range", (long long)q);
     if (c.d < 1 || c.d > 256) return set_error(CPPGB_ERR_ARG, "instance %lld: d must be in [1, 256]", (long long)q);
+    if (c.path < 0 || c.path > 2) return set_error(CPPGB_ERR_ARG, "instance %lld: path must be 0, 1 or 2", (long long)q);
     if (c.n > 0 && !c.pts) return set_error(CPPGB_ERR_ARG, "instance %lld: pts is NULL", (long long)q);
     if (!isfinite(c.R)) return set_error(CPPGB_ERR_ARG, "instance %lld: R must be finite", (long long)q);
   }
@@ -531,8 +1140,8 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
 
   // instance table (host-built, copied before the graph runs)
   std::vector<BatchInst> hi((size_t)count);
-  std::vector<int64_t> hro((size_t)count + 1), hto((size_t)count + 1);
-  int64_t xo = 0, ro = 0, to = 0;
+  std::vector<int64_t> hro((size_t)count + 1), hto((size_t)count + 1), hgo((size_t)count + 1), hto16((size_t)count + 1);
+  int64_t xo = 0, ro = 0, to = 0, go = 0, to16 = 0, co[NCLS] = {0, 0, 0, 0};
   for (int64_t q = 0; q < count; ++q) {
     const cpp_instance& c = inst[q];
     BatchInst b;
@@ -548,25 +1157,57 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
     b.rr32 = c.R >= 0.0 ? (float)(c.R * c.R) * (1.f + 0x1p-20f) : 0.f;
     b.kappa = kappa_fp32(b.Kp);
     const int64_t npad = (c.n + TILE_BM - 1) / TILE_BM * TILE_BM, nb = npad / TILE_BM;
+    b.tc = path_of(c) == 2;
+    b.cls = (c.d + 63) / 64 - 1;
+    b.nbj16 = (int32_t)((c.n + 255) / 256);
+    b.nrow16 = (int32_t)nrow16_of(c.n);
+    b.row_off16 = b.tc ? co[b.cls] : 0;
+    b.grow_off16 = go;
+    b.tile_off16 = to16;
+    b.kappa16 = kappa_tc(64 * (b.cls + 1));
+    b.pad = 0.f;
+    if (b.tc) b.tile_off = to;  // no FP32-path tiles
     hro[(size_t)q] = ro;
     hto[(size_t)q] = to;
+    hgo[(size_t)q] = go;
+    hto16[(size_t)q] = to16;
     xo += npad * b.Kp;
     ro += npad;
-    to += c.n >= 2 ? nb * (nb + 1) / 2 : 0;
+    if (b.tc) {
+      const int64_t npad16 = (c.n + 255) / 256 * 256;
+      co[b.cls] += npad16;
+      go += npad16;
+      to16 += tiles16_of(c.n);
+    } else {
+      to += c.n >= 2 ? nb * (nb + 1) / 2 : 0;
+    }
     hi[(size_t)q] = b;
   }
   hro[(size_t)count] = ro;
   hto[(size_t)count] = to;
+  hgo[(size_t)count] = go;
+  hto16[(size_t)count] = to16;
   CPPGB_CUDA_TRY(cudaMemcpyAsync(L.inst, hi.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, st));
   CPPGB_CUDA_TRY(cudaMemcpyAsync(L.row_offs, hro.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
   CPPGB_CUDA_TRY(cudaMemcpyAsync(L.tile_offs, hto.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(L.grow_offs16, hgo.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(L.tile_offs16, hto16.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
+  BatchMaps maps;
+  for (int k = 0; k < NCLS; ++k) {
+    const int rc = encode_class_map(&maps.m[k], L.X16[k], t.crow16[k] > 256 ? t.crow16[k] : 256, 64 * (k + 1));
+    if (rc) return rc;
+  }
 
   int dev = 0, sms = 0;
   CPPGB_CUDA_TRY(cudaGetDevice(&dev));
   CPPGB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (t.tiles16 > 0)
+    CPPGB_CUDA_TRY(
+        cudaFuncSetAttribute(btc::batch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)btc::SMEM_BYTES));
   {
     std::lock_guard<std::mutex> lock(g_graph_mu);
-    const GraphKey key{ws, ws_bytes, count, t.rows, t.tiles, L.cap, pairs, pairs_cap};
+    const GraphKey key{ws, ws_bytes, count, t.rows, t.tiles, L.cap, t.rows16, t.tiles16, t.crow16[0], t.crow16[1],
+                       t.crow16[2], t.crow16[3], pairs, pairs_cap};
     if (!(g_exec && key == g_key && g_dev == dev)) {
       if (g_exec) {
         cudaGraphExecDestroy(g_exec);
@@ -577,7 +1218,7 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
       cudaGraph_t graph;
       CPPGB_CUDA_TRY(cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal));
       const long long before = (long long)cpp_launch_count();
-      const int rc = enqueue_batch(L, count, t, pairs, pairs_cap, sms, cap_st);
+      const int rc = enqueue_batch(L, count, t, pairs, pairs_cap, sms, maps, cap_st);
       g_graph_kernels = (long long)cpp_launch_count() - before;
       note_launches(-g_graph_kernels);  // captured, not launched
       cudaError_t ce = cudaStreamEndCapture(cap_st, &graph);
@@ -604,6 +1245,7 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
   CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
   for (int64_t q = 0; q < count; ++q) pair_counts[q] = hoff[(size_t)q + 1] - hoff[(size_t)q];
   if (hg.status & 1u) return set_error(CPPGB_ERR_NUMERIC, "non-finite coordinate");
+  if (hg.status & 4u) return set_error(CPPGB_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
   if ((int64_t)hg.n_cand > L.cap)
     return set_error(CPPGB_ERR_CAPACITY, "%llu candidate pairs exceed the workspace's %lld; pass %zu bytes",
                      (unsigned long long)hg.n_cand, (long long)L.cap,

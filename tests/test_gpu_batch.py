@@ -25,12 +25,12 @@ def _oracle_pairs(x, R):
     return out
 
 
-def _check_batch(insts, radii, repeat=1):
+def _check_batch(insts, radii, repeat=1, paths=None):
     capi = _capi()
     dev = device()
     pts = [to_dev(np.ascontiguousarray(x, dtype=np.float32), dev) for x in insts]
     for _ in range(repeat):
-        res, counts, pairs = capi.cpp_batch(pts, radii)
+        res, counts, pairs = capi.cpp_batch(pts, radii, paths=paths)
         pairs = pairs.cpu().numpy()
         off = 0
         for q, (x, R) in enumerate(zip(insts, radii)):
@@ -48,7 +48,7 @@ def _check_batch(insts, radii, repeat=1):
     return res, counts
 
 
-def test_batch_mixed_instances_twice():
+def _mixed_instances():
     g = synth.rng_for(71)
     insts, radii = [], []
     for q, (n, d) in enumerate([(2, 8), (3, 1), (129, 16), (300, 33), (1000, 8), (700, 64), (257, 128), (50, 200),
@@ -58,16 +58,66 @@ def test_batch_mixed_instances_twice():
             x[n - 2] = x[n // 3] + np.float32(1e-3) * g.standard_normal(d).astype(np.float32) / np.sqrt(d)
         insts.append(x)
         radii.append(float([0.05, 0.3, -1.0, 0.6][q % 4]))
-    _check_batch(insts, radii, repeat=2)
+    return insts, radii
 
 
-def test_batch_edge_instances():
+@pytest.mark.parametrize("paths", [None, 1, 2, "alternate"])
+def test_batch_mixed_instances_twice(paths):
+    """Both tile paths (FP32 CUDA cores, BF16 tensor cores), the default choice and a mix give
+    the oracle's answer; the second call replays the captured graph."""
+    insts, radii = _mixed_instances()
+    if paths == "alternate":
+        paths = [1 + (q % 2) for q in range(len(insts))]
+    _check_batch(insts, radii, repeat=2, paths=paths)
+
+
+@pytest.mark.parametrize("paths", [1, 2])
+def test_batch_edge_instances(paths):
     g = synth.rng_for(72)
     ident = np.tile(g.random((1, 6)).astype(np.float32), (40, 1))
     insts = [np.zeros((0, 4), np.float32), g.random((1, 4)).astype(np.float32), ident, g.random((200, 4)).astype(np.float32)]
-    res, counts = _check_batch(insts, [0.1, 0.1, 0.0, -1.0])
+    res, counts = _check_batch(insts, [0.1, 0.1, 0.0, -1.0], paths=paths)
     assert (res[0]["i"], res[1]["i"]) == (-1, -1)
     assert counts[2] == 40 * 39 // 2
+
+
+def test_batch_tensor_core_ties_and_widths():
+    """Tensor-core path on exact ties (integer lattices: many pairs at the same distance, the
+    lexicographically smallest must win), on every padded width (d = 1, 64, 65, 128, 129, 192,
+    193, 256), on sizes around the 128/256 tile edges, and with an R whose square overflows FP32
+    (every pair is within R; masked tile entries must not be emitted)."""
+    g = synth.rng_for(73)
+    insts, radii = [], []
+    lat = np.stack(np.meshgrid(*[np.arange(5, dtype=np.float32)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    insts.append(np.concatenate([lat, np.zeros((125, 29), np.float32)], 1))  # d = 32, min distance 1, ties
+    radii.append(1.0)
+    for d, n in [(1, 300), (64, 255), (65, 256), (128, 257), (129, 383), (192, 129), (193, 128), (256, 511)]:
+        insts.append(g.standard_normal((n, d)).astype(np.float32))
+        radii.append(float(np.sqrt(2 * d) * 0.8))
+    insts.append(g.random((300, 24)).astype(np.float32))
+    radii.append(1e20)
+    res, counts = _check_batch(insts, radii, paths=2)
+    assert counts[-1] == 300 * 299 // 2
+
+
+def test_batch_paths_agree_on_generator_workload():
+    """The 2048-instance workload through each path: identical closest pairs, distances and pair
+    lists (both are exact, so they cannot differ)."""
+    capi = _capi()
+    dev = device()
+    batch = synth.make_batch()
+    pts = [to_dev(b.pts, dev) for b in batch]
+    radii = [b.R for b in batch]
+    r1, c1, p1 = capi.cpp_batch(pts, radii, paths=1)
+    r2, c2, p2 = capi.cpp_batch(pts, radii, paths=2)
+    for a, b in zip(r1, r2):
+        assert (a["i"], a["j"], a["dist2"]) == (b["i"], b["j"], b["dist2"])
+    np.testing.assert_array_equal(c1, c2)
+    assert torch_equal(p1, p2)
+
+
+def torch_equal(a, b):
+    return a.shape == b.shape and bool((a == b).all().item())
 
 
 def test_batch_generator_workload_sampled():
