@@ -60,6 +60,7 @@ struct BatchState {
 constexpr int NCLS = 4;  // tensor-core classes: Kp16 = 64, 128, 192, 256
 struct BatchMaps {
   CUtensorMap m[NCLS];
+  CUtensorMap h;  // [rows16][16] BF16: -|x~|^2 / 2 as three BF16 pieces, then zeros
 };
 
 // candidate pair; the top bit of qk marks a closest-pair candidate (else a radius candidate)
@@ -184,7 +185,8 @@ __global__ void __launch_bounds__(256) batch_prep16_kernel(const BatchInst* __re
                                                            const int64_t* __restrict__ grow_offs, int count,
                                                            int64_t rows16, __nv_bfloat16* X16_0, __nv_bfloat16* X16_1,
                                                            __nv_bfloat16* X16_2, __nv_bfloat16* X16_3,
-                                                           float* __restrict__ norms16, BatchState* st) {
+                                                           float* __restrict__ norms16, __nv_bfloat16* __restrict__ H16,
+                                                           BatchState* st) {
   const int lane = threadIdx.x & 31;
   const int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * PREP_RUN;
   if (r0 >= rows16) return;
@@ -227,6 +229,15 @@ __global__ void __launch_bounds__(256) batch_prep16_kernel(const BatchInst* __re
       dd += __shfl_xor_sync(0xffffffffu, dd, o);
     }
     if (lane == 0) norms16[r] = n2;
+    if (lane < 16) {  // -n2 / 2 = -(h1 + h2 + h3) to 2^-27 relative; each residual is exact in FP32
+      const float v = 0.5f * n2;
+      const float h1 = __bfloat162float(__float2bfloat16_rn(v));
+      const float r1 = v - h1;
+      const float h2 = __bfloat162float(__float2bfloat16_rn(r1));
+      const float h3 = r1 - h2;
+      const float hv = lane == 0 ? h1 : lane == 1 ? h2 : lane == 2 ? h3 : 0.f;
+      H16[r * 16 + lane] = __float2bfloat16_rn(-hv);
+    }
     m2 = fmaxf(m2, n2);
     me = fmaxf(me, sqrtf(dd));
   }
@@ -412,20 +423,37 @@ __global__ void __launch_bounds__(TILE_NT, 2)
 namespace btc {
 using namespace tc;
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2, STAGE_BYTES = A_BYTES + BN * BK * 2;
-constexpr int GROUPS = 2;                    // epilogue groups, one TMEM accumulator each
-constexpr int NTHREADS = 64 + GROUPS * 128;  // producer warp, MMA warp, 2 x 4 epilogue warps
+constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, H_BYTES = BN * 16 * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES + H_BYTES;  // H: the B rows' norm pieces (first K chunk only)
+constexpr int ONES_BYTES = 256;                           // 8 x 32-byte rows of the constant operand
+constexpr int GROUPS = 2;                         // epilogue groups, one TMEM accumulator each
+constexpr int NTHREADS = 64 + GROUPS * 128 + 32;  // producer, MMA, 2 x 4 epilogue warps, tile decoder
+constexpr int DECODER = NTHREADS / 32 - 1;        // the decoder's warp
 constexpr uint32_t TMEM_COLS = 512;
 
+// What the decoder warp publishes about each of the CTA's tiles (ring slot = tile iteration % RING).
+struct TileInfo {
+  int32_t q, bi, bj, n;
+  int64_t grow;      // first BF16 row of the instance (norms, norm pieces)
+  int64_t row16;     // first row of the instance in its class matrix
+  int32_t cls;       // class: K chunks of 64 = cls + 1
+  float th_r;        // radius emission threshold on D~ (-inf: no radius output)
+  BoundParams bp;    // the instance's tensor-core bound parameters
+};
+constexpr int RING = 16;         // tile records in flight
+constexpr int RING_READERS = 6;  // producer, MMA issuer, the four warps of the tile's epilogue group
+
 struct Ctl {
-  alignas(16) float ny[GROUPS][BN];  // per group: |y~_j|^2 of the tile's 256 columns
   uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
-  float tile_min[GROUPS][2][4];  // [group][tile parity][TMEM lane quarter]
-  int ok[GROUPS][2][4];          // per epilogue warp: its wait succeeded (exchanged at the group barrier)
+  uint64_t info_full[RING], info_empty[RING];
+  TileInfo info[RING];
+  unsigned int wmin[GROUPS][2][4];  // per group and tile parity: each warp's minimum (float bits, >= 0)
+  unsigned int arrived[GROUPS][2];  // warps that have stored their minimum
   uint32_t tmem_base;
   int abort_flag;
 };
-constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + sizeof(Ctl) + 1024;  // + 1024-byte alignment slack
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + ONES_BYTES + sizeof(Ctl) + 1024;  // + alignment slack
+static_assert(SMEM_BYTES <= 232448, "dynamic shared memory above the 227 KB opt-in limit");
 
 // Tiles (bi, bj) of one instance: 128-row blocks bi < nrow16, 256-column blocks bj with
 // bj >= bi / 2 (every such tile holds a pair i < j).  Rows 2k and 2k + 1 have nbj - k tiles, so
@@ -500,63 +528,87 @@ struct TileWalker {
   }
 };
 
-__device__ __forceinline__ void load_ny(const float* p, float4 (&v)[8]) {  // shared memory, broadcast reads
-#pragma unroll
-  for (int u = 0; u < 8; ++u) v[u] = reinterpret_cast<const float4*>(p)[u];
-}
 
-// One 32-column chunk of a row: D~ - |x~_i|^2 = |y~_j|^2 - 2 x~.y~, computed in place over the
-// loaded accumulator registers (the register file per SMSP holds three warps of this kernel at 168
-// registers), masked to +inf off the triangle and past n; returns the chunk minimum (a depth-5
-// tree, not a 32-long dependent chain); emits radius candidates.
-__device__ __forceinline__ float chunk_min(uint32_t (&r)[32], const float4 (&ny)[8], bool edge, int64_t i, int64_t j0,
-                                           int64_t n, float nx, float th_r, int q, BatchGlobals* g,
-                                           BatchCand* __restrict__ cand, int64_t cap) {
-  const float INF = __int_as_float(0x7f800000);
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    r[4 * u + 0] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * u + 0]), ny[u].x));
-    r[4 * u + 1] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * u + 1]), ny[u].y));
-    r[4 * u + 2] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * u + 2]), ny[u].z));
-    r[4 * u + 3] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * u + 3]), ny[u].w));
-  }
-  if (edge) {
+// One 32-column chunk of a row.  The accumulator holds a_ij = x~_i.x~_j - |x~_j|^2 / 2 (the norm
+// pieces ride along in the MMA), so D~_ij = |x~_i|^2 - 2 a_ij is decreasing in a_ij and the chunk's
+// smallest D~ comes from its largest a (a depth-5 tree).  EDGE tiles mask entries off the triangle
+// and past n to -inf.
+template <bool EDGE>
+__device__ __forceinline__ float chunk_max(uint32_t (&r)[32], int64_t i, int64_t j0, int64_t n) {
+  if (EDGE) {
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
       const int64_t j = j0 + k;
-      if (!(i < n && j < n && j > i)) r[k] = __float_as_uint(INF);
+      if (!(i < n && j < n && j > i)) r[k] = __float_as_uint(__int_as_float(0xff800000));
     }
   }
   float m[16];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) m[k] = fminf(__uint_as_float(r[k]), __uint_as_float(r[k + 16]));
+  for (int k = 0; k < 16; ++k) m[k] = fmaxf(__uint_as_float(r[k]), __uint_as_float(r[k + 16]));
 #pragma unroll
-  for (int k = 0; k < 8; ++k) m[k] = fminf(m[k], m[k + 8]);
+  for (int k = 0; k < 8; ++k) m[k] = fmaxf(m[k], m[k + 8]);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) m[k] = fminf(m[k], m[k + 4]);
-  const float cmin = fminf(fminf(m[0], m[2]), fminf(m[1], m[3]));
-  if (nx + cmin <= th_r) {  // rare: collect the hits as a bit mask, then emit them in a rolled loop
-    uint32_t hits = 0u;
+  for (int k = 0; k < 4; ++k) m[k] = fmaxf(m[k], m[k + 4]);
+  return fmaxf(fmaxf(m[0], m[2]), fmaxf(m[1], m[3]));
+}
+
+// The 8 chunks of a warp's 32 rows x 256 columns, branch-free within each pair of chunks: chunk
+// c + 1 loads from TMEM while chunk c is reduced.  Returns the rows' largest a; `hits` gets bit c when some entry of
+// chunk c may lie within the radius (D~ <= th_r), for the rare second look after the loop.
+template <bool EDGE>
+__device__ __forceinline__ float tile_rows(uint32_t tbase, int64_t i, int64_t col0, int64_t n, float nx, float th_r,
+                                           uint32_t& hits) {
+  float rmax = __int_as_float(0xff800000);
+  uint32_t ra[32], rb[32];
+  tmem_ld32_nowait(tbase, ra);
+  tmem_wait_ld(ra);
+#pragma unroll 1
+  for (int c = 0; c < BN / 32; c += 2) {
+    tmem_ld32_nowait(tbase + (uint32_t)((c + 1) * 32), rb);
+    float m = chunk_max<EDGE>(ra, i, col0 + c * 32, n);
+    hits |= (fmaf(-2.f, m, nx) <= th_r ? 1u : 0u) << c;
+    rmax = fmaxf(rmax, m);
+    tmem_wait_ld(rb);
+    if (c + 2 < BN / 32) tmem_ld32_nowait(tbase + (uint32_t)((c + 2) * 32), ra);
+    m = chunk_max<EDGE>(rb, i, col0 + (c + 1) * 32, n);
+    hits |= (fmaf(-2.f, m, nx) <= th_r ? 1u : 0u) << (c + 1);
+    rmax = fmaxf(rmax, m);
+    if (c + 2 < BN / 32) tmem_wait_ld(ra);
+  }
+  return rmax;
+}
+
+// Rare: emit this lane's radius candidates of the flagged chunks (re-read from TMEM; the accumulator
+// is still held).  Warp-collective: every lane of the warp calls it with the warp's union of flags.
+__device__ __noinline__ void emit_radius(uint32_t tbase, uint32_t flags, int64_t i, int64_t col0, int64_t n, float nx,
+                                         float th_r, int q, BatchGlobals* g, BatchCand* __restrict__ cand,
+                                         int64_t cap) {
+  for (int c = 0; c < BN / 32; ++c) {
+    if (!((flags >> c) & 1u)) continue;  // warp-uniform
+    uint32_t r[32];
+    tmem_ld32_nowait(tbase + (uint32_t)(c * 32), r);
+    tmem_wait_ld(r);
+    uint32_t bits = 0u;
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {  // masked entries hold +inf
-      const float v = __uint_as_float(r[k]);
-      hits |= (nx + v <= th_r && v < INF ? 1u : 0u) << k;
+    for (int k = 0; k < 32; ++k) {
+      const int64_t j = col0 + c * 32 + k;
+      const float a = __uint_as_float(r[k]);
+      bits |= (i < n && j < n && j > i && fmaf(-2.f, a, nx) <= th_r ? 1u : 0u) << k;
     }
-    while (hits) {
-      const int k = __ffs(hits) - 1;
-      hits &= hits - 1u;
+    while (bits) {
+      const int k = __ffs(bits) - 1;
+      bits &= bits - 1u;
       const unsigned long long slot = atomicAdd(&g->n_cand, 1ull);
       if ((int64_t)slot < cap) {
         BatchCand cd;
         cd.qk = q;  // radius candidate: decided by the FP64 test alone, its FP32 value is not used
         cd.i = (int32_t)i;
-        cd.j = (int32_t)(j0 + k);
+        cd.j = (int32_t)(col0 + c * 32 + k);
         cd.d2f = 0.f;
         cand[slot] = cd;
       }
     }
   }
-  return cmin;
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -566,10 +618,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     TileRec* __restrict__ trec, int64_t trec_cap) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  Ctl* ctl = (Ctl*)(smem + STAGES * STAGE_BYTES);
+  uint8_t* ones = smem + STAGES * STAGE_BYTES;  // 1024-aligned
+  Ctl* ctl = (Ctl*)(ones + ONES_BYTES);
   volatile int* abort_flag = &ctl->abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // this CTA's tiles: t = blockIdx.x + it * gridDim.x, it < ntl
+  const int64_t ntl = (total - blockIdx.x + gridDim.x - 1) / gridDim.x;
 
+  if (threadIdx.x < 64) {
+    // Constant A operand of the norm MMA: every row is (1, 1, 1, 0, ..., 0) in BF16.  In the
+    // 32-byte swizzle the two 16-byte halves of rows 4..7 (of every 8) trade places.
+    const int row = threadIdx.x >> 3, word = threadIdx.x & 7;  // 8 rows x 8 words of 4 bytes
+    const int half = (word >> 2) ^ ((row >> 2) & 1), w4 = word & 3;
+    uint32_t v = 0u;
+    if (half == 0 && w4 == 0) v = 0x3f803f80u;  // elements 0, 1
+    if (half == 0 && w4 == 1) v = 0x00003f80u;  // element 2
+    reinterpret_cast<uint32_t*>(ones)[threadIdx.x] = v;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&ctl->full[s], 1);
@@ -579,7 +645,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&ctl->tfull[a], 1);
       mbar_init(&ctl->tempty[a], 4);
     }
+    for (int r = 0; r < RING; ++r) {
+      mbar_init(&ctl->info_full[r], 1);
+      mbar_init(&ctl->info_empty[r], RING_READERS);
+    }
     mbar_init(&ctl->drain, 1);
+    for (int a = 0; a < GROUPS; ++a)
+      for (int b = 0; b < 2; ++b) ctl->arrived[a][b] = 0u;
     ctl->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -594,26 +666,63 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = ctl->tmem_base;
 
-  if (warp == 0) {
-    if (lane == 0) {  // ---------------------------------------------- TMA producer
-      for (int c = 0; c < NCLS; ++c) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.m[c]) : "memory");
+  if (warp == DECODER) {
+    if (lane == 0) {  // ---------------------------------------------- tile decoder
       TileWalker w;
       w.init(tile_offs16, inst, count);
+      int bq = -1;
+      TileInfo ti;
+      bool ok = true;
+      for (int64_t it = 0; it < ntl; ++it) {
+        const uint32_t slot = (uint32_t)(it % RING);
+        if (it >= RING && !mbar_wait(&ctl->info_empty[slot], (uint32_t)((it / RING - 1) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        w.go(blockIdx.x + it * gridDim.x);
+        if (w.q != bq) {
+          bq = w.q;
+          ti.q = w.q;
+          ti.n = w.in.n;
+          ti.grow = w.in.grow_off16;
+          ti.row16 = w.in.row_off16;
+          ti.cls = w.in.cls;
+          ti.bp = st[w.q].bp16;
+          ti.th_r = w.in.has_r ? theta_of(w.in.rr32, ti.bp) : __int_as_float(0xff800000);
+        }
+        ti.bi = (int32_t)w.bi;
+        ti.bj = (int32_t)w.bj;
+        ctl->info[slot] = ti;
+        mbar_arrive(&ctl->info_full[slot]);  // release: the record is visible to its waiters
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(&g->status, 4u);
+      }
+    }
+  } else if (warp == 0) {
+    if (lane == 0) {  // ---------------------------------------------- TMA producer
+      for (int c = 0; c < NCLS; ++c) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.m[c]) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.h) : "memory");
       uint32_t stage = 0, phase = 0;
       int64_t issued = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
-        w.go(t);
-        const CUtensorMap* map = &maps.m[w.in.cls];
-        const int kch = w.in.cls + 1;
-        const int ya = (int)(w.in.row_off16 + w.bi * BM), yb = (int)(w.in.row_off16 + w.bj * BN);
-        for (int kc = 0; kc < kch; ++kc) {
+      for (int64_t it = 0; it < ntl && ok; ++it) {
+        const uint32_t slot = (uint32_t)(it % RING);
+        if (!mbar_wait(&ctl->info_full[slot], (uint32_t)((it / RING) & 1), abort_flag)) { ok = false; break; }
+        const TileInfo ti = ctl->info[slot];
+        mbar_arrive(&ctl->info_empty[slot]);
+        const CUtensorMap* map = &maps.m[ti.cls];
+        const int ya = (int)(ti.row16 + (int64_t)ti.bi * BM), yb = (int)(ti.row16 + (int64_t)ti.bj * BN);
+        const int yh = (int)(ti.grow + (int64_t)ti.bj * BN);
+        for (int kc = 0; kc <= ti.cls; ++kc) {
           if (!mbar_wait(&ctl->empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
           uint8_t* sa = smem + stage * STAGE_BYTES;
-          mbar_arrive_expect_tx(&ctl->full[stage], STAGE_BYTES);
+          mbar_arrive_expect_tx(&ctl->full[stage], A_BYTES + B_BYTES + (kc == 0 ? H_BYTES : 0));
           tma_load_2d(sa, map, &ctl->full[stage], kc * BK, ya);
           tma_load_2d(sa + A_BYTES, map, &ctl->full[stage], kc * BK, yb);
           tma_load_2d(sa + A_BYTES + BM * BK * 2, map, &ctl->full[stage], kc * BK, yb + BM);
+          if (kc == 0) tma_load_2d(sa + A_BYTES + B_BYTES, &maps.h, &ctl->full[stage], 0, yh);
           ++issued;
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
         }
@@ -634,18 +743,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {  // ---------------------------------------------- MMA issuer
       const uint32_t idesc = make_idesc(1u, BM, BN);  // BF16 operands
-      TileWalker w;
-      w.init(tile_offs16, inst, count);
       uint32_t stage = 0, phase = 0;
-      int64_t it = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
-        w.go(t);
-        const int kch = w.in.cls + 1;
+      for (int64_t it = 0; it < ntl && ok; ++it) {
         const uint32_t acc = (uint32_t)(it & 1), use = (uint32_t)((it >> 1) & 1);
         if (!mbar_wait(&ctl->tempty[acc], use ^ 1u, abort_flag)) { ok = false; break; }
         tc_fence_after();
         const uint32_t dtmem = tmem_base + acc * (uint32_t)BN;
+        const uint32_t slot = (uint32_t)(it % RING);
+        if (!mbar_wait(&ctl->info_full[slot], (uint32_t)((it / RING) & 1), abort_flag)) { ok = false; break; }
+        const int kch = ctl->info[slot].cls + 1;
+        mbar_arrive(&ctl->info_empty[slot]);
         for (int kc = 0; kc < kch; ++kc) {
           if (!mbar_wait(&ctl->full[stage], phase, abort_flag)) { ok = false; break; }
           tc_fence_after();
@@ -654,6 +762,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk)
             mma_f16(dtmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (kc | kk) != 0);
+          if (kc == 0)  // + ones x (B rows' norm pieces): a_ij = x~_i.x~_j - |x~_j|^2 / 2
+            mma_f16(dtmem, sw32_desc(smem_u32(ones), 0), sw32_desc(sa + A_BYTES + B_BYTES, 256), idesc, 1u);
           mma_commit(&ctl->empty[stage]);
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
         }
@@ -671,106 +781,85 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else {  // -------------------------------------------------------- epilogue groups
     // Group grp takes the CTA's tiles it = grp, grp + 2, ... and their accumulator grp; warp
-    // (warp & 3) reads TMEM lanes 32 (warp & 3) .. + 31 (the rows it may access).
+    // (warp & 3) reads TMEM lanes 32 (warp & 3) .. + 31 (the rows it may access).  The warps of a
+    // group never wait for one another: each stores its minimum, and the last to arrive takes the
+    // tile's record decision.
     const int grp = (warp - 2) >> 2;
     const uint32_t quarter = (uint32_t)(warp & 3);
-    const bool leader = ((warp - 2) & 3) == 0 && lane == 0;
-    const int gt = ((warp - 2) & 3) * 32 + lane;  // 0..127 within the group
-    const int64_t stride = (int64_t)GROUPS * gridDim.x;
-    // The walker runs one tile ahead: the next tile's row norm and its two column norms per
-    // thread are loaded while the current tile is reduced.
-    TileWalker w;
-    w.init(tile_offs16, inst, count);
+    const float INF = __int_as_float(0x7f800000);
+    // the record and row norm of the group's next tile are read one tile ahead
+    TileInfo nxt;
     float nx_n = 0.f;
-    float2 ny_n = make_float2(0.f, 0.f);
-    auto prefetch = [&](int64_t tt) {
-      w.go(tt);
-      const float* nrm = norms16 + w.in.grow_off16;
-      nx_n = nrm[w.bi * BM + quarter * 32 + lane];
-      ny_n = __ldg(reinterpret_cast<const float2*>(nrm + w.bj * BN) + gt);
+    bool ok = true;
+    auto fetch = [&](int64_t it) -> bool {
+      const bool got =
+          __all_sync(0xffffffffu, mbar_wait(&ctl->info_full[it % RING], (uint32_t)((it / RING) & 1), abort_flag));
+      if (!got) return false;
+      nxt = ctl->info[it % RING];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl->info_empty[it % RING]);
+      nx_n = norms16[nxt.grow + (int64_t)nxt.bi * BM + quarter * 32 + lane];
+      return true;
     };
-    int bq = -1;
-    BoundParams bp;
-    float th_r = 0.f;
+    if (grp < ntl) ok = fetch(grp);
     int64_t k = 0;
-    int64_t t = blockIdx.x + (int64_t)grp * gridDim.x;
-    if (t < total) prefetch(t);
-    for (; t < total; t += stride, ++k) {
-      const int q = w.q;
-      if (q != bq) {  // bound parameters are fixed while the tiles run
-        bq = q;
-        bp = st[q].bp16;
-        th_r = w.in.has_r ? theta_of(w.in.rr32, bp) : __int_as_float(0xff800000);
-      }
-      const float Ug = __uint_as_float(*reinterpret_cast<volatile unsigned int*>(&st[q].U_bits));  // early load
-      const int64_t bi = w.bi, bj = w.bj, n = w.in.n;
-      const int64_t row0 = bi * BM, col0 = bj * BN;
-      const int64_t i = row0 + quarter * 32 + lane;
+    for (int64_t it = grp; it < ntl && ok; it += GROUPS, ++k) {
+      const TileInfo cur = nxt;
       const float nx = nx_n;
-      // The group's four warps share a named barrier, so they leave the loop together: each
-      // warp's bounded wait result is exchanged at the barrier and all continue or all stop.  The
-      // same barrier publishes the column norms (the previous tile's readers all passed the
-      // group's closing barrier before this store).
-      reinterpret_cast<float2*>(ctl->ny[grp])[gt] = ny_n;
-      if (t + stride < total) prefetch(t + stride);
+      const int q = cur.q;
+      const float Ug = __uint_as_float(*reinterpret_cast<volatile unsigned int*>(&st[q].U_bits));  // early load
+      if (it + GROUPS < ntl && !fetch(it + GROUPS)) { ok = false; break; }
       const uint32_t par = (uint32_t)(k & 1);
-      const bool got = __all_sync(0xffffffffu, mbar_wait(&ctl->tfull[grp], par, abort_flag)) && !*abort_flag;
-      if (lane == 0) ctl->ok[grp][par][quarter] = got ? 1 : 0;
-      asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");
-      const int* okv = ctl->ok[grp][par];
-      if (!(okv[0] && okv[1] && okv[2] && okv[3])) {
-        if (leader) {
-          *abort_flag = 1;
-          atomicOr(&g->status, 4u);
-        }
-        break;
-      }
+      if (!__all_sync(0xffffffffu, mbar_wait(&ctl->tfull[grp], par, abort_flag))) { ok = false; break; }
       tc_fence_after();
+      const int64_t n = cur.n, row0 = (int64_t)cur.bi * BM, col0 = (int64_t)cur.bj * BN;
+      const int64_t i = row0 + quarter * 32 + lane;
       const bool edge = (row0 + BM - 1 >= n) || (col0 + BN - 1 >= n) || (col0 < row0 + BM);
       const uint32_t tbase = tmem_base + ((quarter * 32u) << 16) + (uint32_t)grp * (uint32_t)BN;
-      float rmin = __int_as_float(0x7f800000);
-      const float* nys = ctl->ny[grp];
-      uint32_t ra[32], rb[32];
-      float4 ny[8];
-      tmem_ld32_nowait(tbase, ra);
-      tmem_wait_ld(ra);
-#pragma unroll 1
-      for (int c = 0; c < BN / 32; c += 2) {  // chunk c + 1 loads from TMEM while chunk c is reduced
-        tmem_ld32_nowait(tbase + (uint32_t)((c + 1) * 32), rb);
-        load_ny(nys + c * 32, ny);
-        rmin = fminf(rmin, nx + chunk_min(ra, ny, edge, i, col0 + c * 32, n, nx, th_r, q, g, cand, cap));
-        tmem_wait_ld(rb);
-        if (c + 2 < BN / 32) tmem_ld32_nowait(tbase + (uint32_t)((c + 2) * 32), ra);
-        load_ny(nys + (c + 1) * 32, ny);
-        rmin = fminf(rmin, nx + chunk_min(rb, ny, edge, i, col0 + (c + 1) * 32, n, nx, th_r, q, g, cand, cap));
-        if (c + 2 < BN / 32) tmem_wait_ld(ra);
+      uint32_t hits = 0u;
+      const float rmax = edge ? tile_rows<true>(tbase, i, col0, n, nx, cur.th_r, hits)
+                              : tile_rows<false>(tbase, i, col0, n, nx, cur.th_r, hits);
+      const uint32_t flags = __reduce_or_sync(0xffffffffu, hits);
+      if (flags) emit_radius(tbase, flags, i, col0, n, nx, cur.th_r, q, g, cand, cap);
+      // this warp's smallest D~ (+inf for masked rows), clamped at 0 (a looser but valid bound),
+      // so the float bits order like the values
+      const unsigned int wm = __reduce_min_sync(0xffffffffu, __float_as_uint(fmaxf(fmaf(-2.f, rmax, nx), 0.f)));
+      // Publish it before releasing the accumulator: the slot is reused two tiles later, and that
+      // tile's MMA cannot start before all four warps have released this one.
+      bool last = false;
+      float tmin = INF;
+      if (lane == 0) {
+        ctl->wmin[grp][par][quarter] = wm;
+        __threadfence_block();
+        last = atomicAdd(&ctl->arrived[grp][par], 1u) == 3u;
+        if (last) {
+          __threadfence_block();
+          const volatile unsigned int* v = ctl->wmin[grp][par];
+          tmin = __uint_as_float(min(min(v[0], v[1]), min(v[2], v[3])));
+          ctl->arrived[grp][par] = 0u;
+        }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&ctl->tempty[grp]);
-      // tile minimum over the group's four warps, then the tile record and the bound update
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
-      if (lane == 0) ctl->tile_min[grp][par][quarter] = rmin;
-      asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");
-      if (leader) {
-        const float* tm = ctl->tile_min[grp][par];
-        const float tmin = fminf(fminf(tm[0], tm[1]), fminf(tm[2], tm[3]));
-        if (tmin < __int_as_float(0x7f800000)) {
-          if (tmin <= theta_of(Ug, bp)) {
-            atomic_min_nonneg(&st[q].tmin16_bits, tmin);
-            // record the 128-column halves that hold a pair i < j < n for the FP32 second pass (the
-            // FP32 rows of an instance are padded to 128 only, so a half past n must not be read)
-            for (int64_t h = 2 * bj; h <= 2 * bj + 1; ++h) {
-              if (h < bi || h * BM >= n) continue;
-              const unsigned long long kr = atomicAdd(&g->n_trec, 1ull);
-              if ((int64_t)kr < trec_cap) trec[kr] = TileRec{q | TC_FLAG, (int32_t)bi, (int32_t)h, tmin};
-            }
+      if (last && tmin < INF) {  // the tile record and the bound update
+        if (tmin <= theta_of(Ug, cur.bp)) {
+          atomic_min_nonneg(&st[q].tmin16_bits, tmin);
+          // record the 128-column halves that hold a pair i < j < n for the FP32 second pass (the
+          // FP32 rows of an instance are padded to 128 only, so a half past n must not be read)
+          for (int64_t h = 2 * (int64_t)cur.bj; h <= 2 * (int64_t)cur.bj + 1; ++h) {
+            if (h < cur.bi || h * BM >= n) continue;
+            const unsigned long long kr = atomicAdd(&g->n_trec, 1ull);
+            if ((int64_t)kr < trec_cap) trec[kr] = TileRec{q | TC_FLAG, cur.bi, (int32_t)h, tmin};
           }
-          const float ub = upper_d2(tmin, bp);
-          if (ub < Ug) atomic_min_nonneg(&st[q].U_bits, ub);
         }
+        const float ub = upper_d2(tmin, cur.bp);
+        if (ub < Ug) atomic_min_nonneg(&st[q].U_bits, ub);
       }
+    }
+    if (!ok && lane == 0) {
+      *abort_flag = 1;
+      atomicOr(&g->status, 4u);
     }
     tc_fence_before();
   }
@@ -905,6 +994,7 @@ struct BatchLayout {
   float* norms;
   __nv_bfloat16* X16[NCLS];
   float* norms16;
+  __nv_bfloat16* H16;  // [max(rows16, 256)][16]
   BatchCand* cand;
   double* d2buf;
   uint8_t* keep;
@@ -973,6 +1063,7 @@ BatchLayout batch_layout(void* ws, int64_t count, const Totals& t, size_t ws_byt
   for (int k = 0; k < NCLS; ++k)  // at least 256 rows each, so every class has a valid tensor map
     L.X16[k] = c.take<__nv_bfloat16>((size_t)(t.crow16[k] > 256 ? t.crow16[k] : 256) * 64 * (k + 1));
   L.norms16 = c.take<float>(t.rows16 + 1);
+  L.H16 = c.take<__nv_bfloat16>((size_t)(t.rows16 > 256 ? t.rows16 : 256) * 16);
   L.trec_cap = 2 * (t.tiles + t.tiles16) + 2;  // at most one record per 128 x 128 tile
   L.trec = c.take<TileRec>(L.trec_cap);
   int64_t cap = t.rows / 4;
@@ -996,27 +1087,53 @@ float kappa_fp32(int64_t Kp) {
   return (float)((4.0 * g + 8.0 * u) * 1.01);
 }
 
-// tensor cores: exact BF16 products, FP32 accumulation padded to 2 K 2^-22 per dot product, norms
-// from 32-term warp sums, three epilogue roundings (as for the dense stage)
+// Tensor-core tiles compute a_ij = x~_i.x~_j - h_j (h_j: three BF16 pieces of |x~_j|^2 / 2, within
+// 2^-27 relative) with K' = Kp + 16 exact products whose magnitudes sum to at most
+// |x~_i||x~_j| + 1.01 |x~_j|^2 / 2 <= 1.51 m (m = max |x~|^2); the accumulation error is padded to
+// 2 K' 2^-22 of that sum.  D~ = fma(-2, a, |x~_i|^2) adds the FP32 norm error of both rows
+// (32-lane warp sums: (Kp/32 + 5) u each), the split error and one rounding of |D~| <= 4.03 m.
 float kappa_tc(int64_t Kp) {
-  const double K = (double)Kp, u = 0x1p-24;
-  return (float)((2.0 * 2.0 * K * 0x1p-22 + 2.0 * (K / 32.0 + 6.0) * u + 8.0 * u) * 1.01);
+  const double K = (double)Kp, K2 = K + 16.0, u = 0x1p-24;
+  return (float)((2.0 * 1.51 * 2.0 * K2 * 0x1p-22 + 2.0 * (K / 32.0 + 5.0) * 1.01 * u + 0x1p-27 + 4.03 * u) * 1.01);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-int encode_class_map(CUtensorMap* m, void* base, int64_t rows, int64_t Kp) {
+EncodeTiledFn encode_fn() {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult qr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
-        qr != cudaDriverEntryPointSuccess)
-      return set_error(CPPGB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+        qr != cudaDriverEntryPointSuccess) {
+      set_error(CPPGB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+      return nullptr;
+    }
     fn = (EncodeTiledFn)p;
   }
+  return fn;
+}
+
+// norm pieces: [rows][16] BF16 (32-byte rows), box 16 x 256 (the B rows of one tile), 32-byte swizzle
+int encode_h_map(CUtensorMap* m, void* base, int64_t rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return CPPGB_ERR_CUDA;
+  const cuuint64_t gdim[2] = {16, (cuuint64_t)rows};
+  const cuuint64_t gstride[1] = {32};
+  const cuuint32_t box[2] = {16, 256};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult cr = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, gdim, gstride, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return set_error(CPPGB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+  return CPPGB_OK;
+}
+
+int encode_class_map(CUtensorMap* m, void* base, int64_t rows, int64_t Kp) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return CPPGB_ERR_CUDA;
   const cuuint64_t gdim[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
   const cuuint64_t gstride[1] = {(cuuint64_t)Kp * 2};
   const cuuint32_t box[2] = {64, 128};
@@ -1058,7 +1175,8 @@ int enqueue_batch(const BatchLayout& L, int64_t count, const Totals& t, int32_t*
   CPPGB_LAUNCH_CHECK();
   if (t.rows16 > 0) {
     batch_prep16_kernel<<<(unsigned)((t.rows16 + 8 * PREP_RUN - 1) / (8 * PREP_RUN)), 256, 0, st>>>(L.inst, L.grow_offs16, ci, t.rows16, L.X16[0],
-                                                                        L.X16[1], L.X16[2], L.X16[3], L.norms16, L.st);
+                                                                        L.X16[1], L.X16[2], L.X16[3], L.norms16, L.H16,
+                                                                        L.st);
     CPPGB_LAUNCH_CHECK();
   }
   batch_bounds_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(L.inst, L.st, ci);
@@ -1195,6 +1313,10 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
   BatchMaps maps;
   for (int k = 0; k < NCLS; ++k) {
     const int rc = encode_class_map(&maps.m[k], L.X16[k], t.crow16[k] > 256 ? t.crow16[k] : 256, 64 * (k + 1));
+    if (rc) return rc;
+  }
+  {
+    const int rc = encode_h_map(&maps.h, L.H16, t.rows16 > 256 ? t.rows16 : 256);
     if (rc) return rc;
   }
 
