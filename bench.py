@@ -280,16 +280,33 @@ class Batch:
 
     def setup(self, dev):
         import torch
-        from paper_1407_5609_gb300 import capi
+        from paper_1407_5609_gb300 import autotune, capi
+        # the autotuner's tile choice per (n-bucket, d-class): cached, or measured now (outside the timing)
+        entry = autotune.load_or_tune(dense=False)
+        table = entry["batch_path"]
+        self.tc = [autotune.path_for(table, b.pts.shape[0], b.pts.shape[1]) == 2 for b in self.batch]
+        self.tc_flops = sum(f for f, t in zip(self._flops(), self.tc) if t)
+        self.config["batch_paths"] = table
+        self.config["tensor_core_instances"] = int(sum(self.tc))
         self.pts = [torch.from_numpy(b.pts).to(dev) for b in self.batch]
         self.radii = [b.R for b in self.batch]
         inst = [capi.cpp_instance(p.data_ptr(), p.shape[0], p.shape[1], 0, r) for p, r in zip(self.pts, self.radii)]
         self.ws = torch.empty(capi.cpp_batch_workspace_size(inst), dtype=torch.uint8, device=dev)
         self.pairs = torch.empty((1 << 20, 2), dtype=torch.int32, device=dev)
+        inst1 = [capi.cpp_instance(p.data_ptr(), p.shape[0], p.shape[1], 1, r) for p, r in zip(self.pts, self.radii)]
+        self.ws1 = torch.empty(capi.cpp_batch_workspace_size(inst1), dtype=torch.uint8, device=dev)
+
+    def _flops(self):
+        return [b.pts.shape[0] * (b.pts.shape[0] - 1) // 2 * 2 * b.pts.shape[1] for b in self.batch]
 
     def step(self, capi, mode):
         res, counts, _ = capi.cpp_batch(self.pts, self.radii, ws=self.ws, pairs=self.pairs)
-        return {"instances": len(res), "pairs_within_R": int(counts.sum())}
+        return {"instances": len(res), "pairs_within_R": int(counts.sum()),
+                "answers": [(r["i"], r["j"], r["dist2"]) for r in res], "counts": counts}
+
+    def fp32_step(self, capi):
+        res, counts, _ = capi.cpp_batch(self.pts, self.radii, ws=self.ws1, pairs=self.pairs, paths=1)
+        return {"answers": [(r["i"], r["j"], r["dist2"]) for r in res], "counts": counts}
 
     def per_instance_step(self, capi):
         n = 0
@@ -469,14 +486,31 @@ def run_ours(args):
                            "kernel": "dense all-pairs stage (gram_tc / gram_simt)", "peak_source": src,
                            "launch_ms": avg_ms, "algorithmic_flop_per_launch": flops}
     elif wl.name == "batch":
-        per_step_ms = total_ms / args.steps
-        ach = wl.flops / (per_step_ms / 1e3) / 1e12
-        out["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                           "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": recorded_traffic("batch@batch"),
-                           "kernel": "cpp_batch step (persistent FP32 tile kernel dominates)",
-                           "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
-                           "algorithmic_flop_per_step": wl.flops}
+        # dominant kernel: the persistent tensor-core tile kernel (its time from events captured in
+        # the batch's graph); algorithmic work 2 d flop per pair of the instances it runs
+        tc_ms = statistics.mean(dense_ms) if dense_ms else None
+        if wl.tc_flops and tc_ms:
+            ach = wl.tc_flops / (tc_ms / 1e3) / 1e12
+            out["roofline"] = {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                               "frac": ach / pk["bf16_tflops"], "traffic": recorded_traffic("batch_tc@batch"),
+                               "kernel": "batch_tc_kernel (persistent tcgen05 tiles of all tensor-core instances)",
+                               "peak_source": f"{pk['source']} bf16 burst", "launch_ms": tc_ms,
+                               "algorithmic_flop_per_launch": wl.tc_flops}
+        else:
+            per_step_ms = total_ms / args.steps
+            ach = wl.flops / (per_step_ms / 1e3) / 1e12
+            out["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": recorded_traffic("batch@batch"),
+                               "kernel": "cpp_batch step (persistent FP32 tile kernel)",
+                               "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                               "algorithmic_flop_per_step": wl.flops}
+        out["answer"] = {"instances": res["instances"], "pairs_within_R": res["pairs_within_R"]}
         if not args.no_compare:
+            barrier()
+            fms, fres = timed_steps(lambda: wl.fp32_step(capi), 1, stream, torch, flush)
+            out["plain_fp32"] = {"value": wl.units / (fms / 1e3), "unit": UNIT, "ms_per_step": fms,
+                                 "same_answer": fres["answers"] == res["answers"] and
+                                 bool((fres["counts"] == res["counts"]).all())}
             barrier()
             pms, _ = timed_steps(lambda: wl.per_instance_step(capi), 1, stream, torch, flush)
             out["per_instance_launches"] = {"ms_per_step": pms, "value": wl.units / (pms / 1e3), "unit": UNIT,

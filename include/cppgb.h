@@ -191,8 +191,9 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
  * Diagnostics (no counterpart in the paper; used to measure the library).
  * cpp_set_stage_timing(1) makes the dense searches record CUDA events on their stream around
  * their stages; cpp_stage_times() then copies the last call's stage durations in milliseconds
- * (per calling thread) into ms[0..cap) as [prep, dense all-pairs stage, FP64 recheck] and returns
- * how many it wrote.  cpp_launch_count() returns the number of kernels this library has launched
+ * (per calling thread) into ms[0..cap) and returns how many it wrote: [prep, dense all-pairs stage,
+ * FP64 recheck] after cpp_closest_pair / tsmm_motif, [preparation, tensor-core tiles, FP32 tiles,
+ * second pass + recheck + output] after cpp_batch (events captured in its graph).  cpp_launch_count() returns the number of kernels this library has launched
  * in the process so far.
  */
 void cpp_set_stage_timing(int on);
@@ -201,6 +202,23 @@ int64_t cpp_launch_count(void);
 
 /* 1 when this build carries the tensor-core filter modes (CPPGB_MODE_FILTER_*), else 0. */
 int cpp_filter_available(void);
+
+/*
+ * Tuning policy (process-wide; no counterpart in the paper).  The project's autotuner times the
+ * candidates on the device, caches its choice as JSON and installs it here; every later call reads it.
+ *   CPPGB_TUNE_BATCH_PATH  values = int32 [4 n-buckets][4 d-classes], count 16, each 1 (FP32 128 x 128
+ *                          CUDA-core tiles) or 2 (BF16 128 x 256 tensor-core tiles); used by cpp_batch
+ *                          instances whose path is 0.  n-buckets: n < 1024, < 4096, < 16384, the rest;
+ *                          d-class: ceil(d / 64) - 1.  Default: all 2 when the tensor-core kernels exist.
+ *   CPPGB_TUNE_DENSE_BAND  values = int32 [1]: column blocks per band of the tensor-core dense stage's
+ *                          tile order (1 .. 4096; 0 from cpp_get_tuning means the built-in 16).
+ * Both return CPPGB_ERR_ARG for an unknown kind, a short array or an invalid entry; the choice only
+ * changes speed, never a result.
+ */
+#define CPPGB_TUNE_BATCH_PATH 1
+#define CPPGB_TUNE_DENSE_BAND 2
+int cpp_set_tuning(int kind, const int32_t* values, int count);
+int cpp_get_tuning(int kind, int32_t* values, int count);
 
 /* Message for the last non-OK status returned on the calling thread ("" if none). */
 const char* cpp_last_error(void);

@@ -1,0 +1,211 @@
+"""Autotuner for the library's tile choices.
+
+Each candidate is timed on the current GPU (CUDA events, median of a few calls after a warm-up);
+the fastest is cached as JSON and installed in the library through ``cpp_set_tuning``, which every
+later call reads.  The cache is keyed by the GPU (name and SM count) and the library build (hash
+of ``libcppgb.so``), and inside an entry by kernel, n-bucket and d-class.  The choice changes only
+the speed: every candidate returns the same, exact answer.
+
+Candidates:
+
+* batch tiles per (n-bucket, d-class) -- FP32 CUDA-core 128 x 128 tiles (path 1) or BF16 tcgen05
+  128 x 256 tiles with the norms folded into the MMA (path 2);
+* the tensor-core dense stage (closest pair, motif search) -- column blocks per band of its tile
+  order, which sets how much of the B panel set stays in L2.
+
+The cache lives in ``$CPPGB_TUNE_CACHE`` or else ``$XDG_CACHE_HOME/cppgb/tune.json``
+(``~/.cache/cppgb/tune.json``).
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import time
+
+import numpy as np
+
+from . import capi, synth
+
+# must match the library's buckets (csrc/api.cu: tuned_batch_path)
+N_BUCKETS = ((256, 1023), (1024, 4095), (4096, 16383), (16384, 65536))
+D_CLASSES = ((1, 64), (65, 128), (129, 192), (193, 256))
+D_SAMPLES = ((16, 64), (96, 128), (160, 192), (224, 256))  # dimensions timed per class
+BANDS = (8, 16, 32, 64)
+CACHE_VERSION = 1
+
+
+# ---------------------------------------------------------------- pure selection logic
+def choose_batch_table(ms: dict) -> list:
+    """ms[(nb, dc)] = {1: t_fp32, 2: t_tc} -> 4 x 4 table of the faster path (ties: tensor cores)."""
+    table = [[2] * len(D_CLASSES) for _ in N_BUCKETS]
+    for (nb, dc), t in ms.items():
+        table[nb][dc] = 1 if t[1] < t[2] else 2
+    return table
+
+
+def path_for(table, n: int, d: int) -> int:
+    """The table entry the library uses for an instance of n points in d dimensions (path 0)."""
+    nb = 0 if n < 1024 else 1 if n < 4096 else 2 if n < 16384 else 3
+    dc = min(max((d + 63) // 64 - 1, 0), len(D_CLASSES) - 1)
+    return int(table[nb][dc])
+
+
+def choose_band(ms: dict) -> int:
+    """ms[band] = time -> the fastest band (ties: the smaller band)."""
+    return min(sorted(ms), key=lambda b: ms[b])
+
+
+def cache_path() -> str:
+    p = os.environ.get("CPPGB_TUNE_CACHE")
+    if p:
+        return p
+    base = os.environ.get("XDG_CACHE_HOME") or os.path.join(os.path.expanduser("~"), ".cache")
+    return os.path.join(base, "cppgb", "tune.json")
+
+
+def library_hash() -> str:
+    h = hashlib.sha256()
+    with open(capi.LIB_PATH, "rb") as f:
+        for block in iter(lambda: f.read(1 << 20), b""):
+            h.update(block)
+    return h.hexdigest()[:16]
+
+
+def load_cache(path: str | None = None) -> dict:
+    path = path or cache_path()
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        return {"version": CACHE_VERSION, "entries": {}}
+    if data.get("version") != CACHE_VERSION or not isinstance(data.get("entries"), dict):
+        return {"version": CACHE_VERSION, "entries": {}}
+    return data
+
+
+def save_cache(data: dict, path: str | None = None) -> None:
+    path = path or cache_path()
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def install(entry: dict) -> None:
+    """Hand a cached entry's choices to the library."""
+    if "batch_path" in entry:
+        capi.cpp_set_tuning(capi.TUNE_BATCH_PATH, np.asarray(entry["batch_path"], dtype=np.int32))
+    if "dense_band" in entry:
+        capi.cpp_set_tuning(capi.TUNE_DENSE_BAND, [int(entry["dense_band"])])
+
+
+# ---------------------------------------------------------------- measurements (GPU)
+def device_key() -> str:
+    import torch
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{p.name}|sm{p.multi_processor_count}|{library_hash()}"
+
+
+def _time_ms(fn, reps: int) -> float:
+    import torch
+    fn()  # warm-up (and graph capture)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def _cell_instances(nb: int, dc: int, target_pairs: float, seed: int):
+    """Uniform instances with n log-uniform in the bucket and d alternating over the class's samples,
+    about target_pairs pairs in all."""
+    g = synth.rng_for(seed)
+    lo, hi = N_BUCKETS[nb]
+    out, pairs = [], 0.0
+    while pairs < target_pairs or not out:
+        n = int(np.exp(g.uniform(np.log(lo), np.log(hi + 1))))
+        n = min(max(n, lo), hi)
+        d = D_SAMPLES[dc][len(out) % 2]
+        out.append(g.random((n, d)).astype(np.float32))
+        pairs += n * (n - 1) / 2
+    return out
+
+
+def measure_batch(target_pairs: float = 2e9, reps: int = 3, cells=None) -> dict:
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ms = {}
+    cells = cells or [(nb, dc) for nb in range(len(N_BUCKETS)) for dc in range(len(D_CLASSES))]
+    for nb, dc in cells:
+        xs = _cell_instances(nb, dc, target_pairs, seed=1000 + 10 * nb + dc)
+        pts = [torch.from_numpy(x).to(dev) for x in xs]
+        radii = [-1.0] * len(pts)
+        t = {}
+        for path in (1, 2):
+            inst = [capi.cpp_instance(p.data_ptr(), p.shape[0], p.shape[1], path, -1.0) for p in pts]
+            ws = capi._workspace(capi.cpp_batch_workspace_size(inst), dev)
+            pairs = torch.empty((1, 2), dtype=torch.int32, device=dev)
+            t[path] = _time_ms(lambda: capi.cpp_batch(pts, radii, ws=ws, pairs=pairs, paths=path), reps)
+        ms[(nb, dc)] = t
+        del pts
+    return ms
+
+
+def measure_dense_band(N: int = 131072, l: int = 512, excl: int = 256, reps: int = 3) -> dict:
+    import torch
+    if not capi.filters_available():
+        return {}
+    dev = torch.device("cuda", torch.cuda.current_device())
+    series = torch.from_numpy(synth.make_random_walk(N=N, seed=1100).astype(np.float32)).to(dev)
+    ws = capi._workspace(capi.tsmm_motif_workspace_size(N, l, "filter_bf16"), dev)
+    before = capi.cpp_get_tuning(capi.TUNE_DENSE_BAND)
+    ms = {}
+    try:
+        for band in BANDS:
+            capi.cpp_set_tuning(capi.TUNE_DENSE_BAND, [band])
+            ms[band] = _time_ms(lambda: capi.tsmm_motif(series, l, excl, mode="filter_bf16", ws=ws), reps)
+    finally:
+        if before[0] > 0:
+            capi.cpp_set_tuning(capi.TUNE_DENSE_BAND, before)
+    return ms
+
+
+def tune(batch: bool = True, dense: bool = True, target_pairs: float = 2e9, reps: int = 3) -> dict:
+    entry = {"when": time.strftime("%Y-%m-%dT%H:%M:%S")}
+    if batch:
+        ms = measure_batch(target_pairs=target_pairs, reps=reps)
+        entry["batch_path"] = choose_batch_table(ms)
+        entry["batch_ms"] = {f"{nb},{dc}": {"fp32": t[1], "tc": t[2]} for (nb, dc), t in sorted(ms.items())}
+    if dense:
+        ms = measure_dense_band(reps=reps)
+        if ms:
+            entry["dense_band"] = choose_band(ms)
+            entry["dense_ms"] = {str(b): t for b, t in sorted(ms.items())}
+    return entry
+
+
+def load_or_tune(batch: bool = True, dense: bool = True, force: bool = False, path: str | None = None, **kw) -> dict:
+    """Install the cached choices for this GPU and library build, measuring first the requested
+    parts the cache lacks (all of them with force=True)."""
+    key = device_key()
+    data = load_cache(path)
+    entry = dict(data["entries"].get(key, {}))
+    need_batch = batch and (force or "batch_path" not in entry)
+    need_dense = dense and (force or "dense_band" not in entry)
+    if need_batch or need_dense:
+        entry.update(tune(batch=need_batch, dense=need_dense, **kw))
+        data["entries"][key] = entry
+        try:
+            save_cache(data, path)
+        except OSError:
+            pass  # a read-only cache location only costs a re-measurement next time
+    install(entry)
+    return entry

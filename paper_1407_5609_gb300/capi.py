@@ -77,6 +77,8 @@ SIGNATURES = {
     "cpp_stage_times": (_int, [ctypes.POINTER(ctypes.c_double), _int]),
     "cpp_launch_count": (_i64, []),
     "cpp_filter_available": (_int, []),
+    "cpp_set_tuning": (_int, [_int, ctypes.POINTER(ctypes.c_int32), _int]),
+    "cpp_get_tuning": (_int, [_int, ctypes.POINTER(ctypes.c_int32), _int]),
     "cpp_last_error": (ctypes.c_char_p, []),
 }
 
@@ -129,6 +131,24 @@ def _check_cuda(t: torch.Tensor, name: str):
 # ---------------------------------------------------------------- entry points
 def filters_available() -> bool:
     return bool(lib().cpp_filter_available())
+
+
+TUNE_BATCH_PATH, TUNE_DENSE_BAND = 1, 2
+TUNE_SIZES = {TUNE_BATCH_PATH: 16, TUNE_DENSE_BAND: 1}
+
+
+def cpp_set_tuning(kind: int, values) -> None:
+    """Install a tuning table (see include/cppgb.h): 16 batch paths or one dense band."""
+    vals = [int(v) for v in np.asarray(values).reshape(-1)]
+    arr = (ctypes.c_int32 * max(len(vals), 1))(*vals)
+    _raise(lib().cpp_set_tuning(int(kind), arr, len(vals)))
+
+
+def cpp_get_tuning(kind: int) -> list:
+    n = TUNE_SIZES[int(kind)]
+    arr = (ctypes.c_int32 * n)()
+    _raise(lib().cpp_get_tuning(int(kind), arr, n))
+    return list(arr)
 
 
 def cpp_set_stage_timing(on: bool = True) -> None:

@@ -13,13 +13,42 @@ static thread_local char g_err[512] = "";
 static std::atomic<long long> g_launches{0};
 static std::atomic<int> g_timing{0};
 
+// tuning policy: batch path per (n-bucket, d-class), tensor-core dense band (0: the launcher's default)
+static std::atomic<int> g_batch_path[TUNE_NB * TUNE_DC];
+static std::atomic<int> g_dense_band{0};
+static std::atomic<int> g_tuning_init{0};
+
+static void init_tuning() {
+  int expect = 0;
+  if (g_tuning_init.load() == 2 || !g_tuning_init.compare_exchange_strong(expect, 1)) {
+    while (g_tuning_init.load() != 2) {
+    }
+    return;
+  }
+  // measured default: the tensor-core tiles win at every class and size this library runs
+  const int def = gram_tc_available() ? 2 : 1;
+  for (int k = 0; k < TUNE_NB * TUNE_DC; ++k) g_batch_path[k].store(def);
+  g_tuning_init.store(2);
+}
+
+int tuned_batch_path(int64_t n, int d) {
+  init_tuning();
+  const int nb = n < 1024 ? 0 : n < 4096 ? 1 : n < 16384 ? 2 : 3;
+  int dc = (d + 63) / 64 - 1;
+  dc = dc < 0 ? 0 : dc >= TUNE_DC ? TUNE_DC - 1 : dc;
+  const int p = g_batch_path[nb * TUNE_DC + dc].load();
+  return (p == 2 && !gram_tc_available()) ? 1 : p;
+}
+
+int tuned_dense_band() { return g_dense_band.load(); }
+
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // Per-thread CUDA events for the optional stage timing of the dense searches.
 struct StageTimer {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  double ms[3] = {0, 0, 0};
+  double ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int n = 0;
   bool ready = false;
   bool init() {
@@ -32,6 +61,13 @@ struct StageTimer {
   }
 };
 static thread_local StageTimer g_timer;
+
+bool stage_timing_on() { return g_timing.load() != 0; }
+
+void set_stage_times(const double* ms, int n) {
+  g_timer.n = n < 8 ? n : 8;
+  for (int k = 0; k < g_timer.n; ++k) g_timer.ms[k] = ms[k];
+}
 
 int set_error(int code, const char* fmt, ...) {
   va_list ap;
@@ -226,6 +262,38 @@ extern "C" {
 const char* cpp_last_error(void) { return g_err; }
 
 int cpp_filter_available(void) { return gram_tc_available() ? 1 : 0; }
+
+int cpp_set_tuning(int kind, const int32_t* values, int count) {
+  init_tuning();
+  if (kind == CPPGB_TUNE_BATCH_PATH) {
+    if (!values || count != TUNE_NB * TUNE_DC) return set_error(CPPGB_ERR_ARG, "batch path table needs %d entries", TUNE_NB * TUNE_DC);
+    for (int k = 0; k < count; ++k)
+      if (values[k] != 1 && values[k] != 2) return set_error(CPPGB_ERR_ARG, "batch path entries must be 1 or 2");
+    for (int k = 0; k < count; ++k) g_batch_path[k].store(values[k]);
+    return CPPGB_OK;
+  }
+  if (kind == CPPGB_TUNE_DENSE_BAND) {
+    if (!values || count != 1 || values[0] < 1 || values[0] > 4096) return set_error(CPPGB_ERR_ARG, "dense band must be one value in [1, 4096]");
+    g_dense_band.store(values[0]);
+    return CPPGB_OK;
+  }
+  return set_error(CPPGB_ERR_ARG, "unknown tuning kind %d", kind);
+}
+
+int cpp_get_tuning(int kind, int32_t* values, int count) {
+  init_tuning();
+  if (kind == CPPGB_TUNE_BATCH_PATH) {
+    if (!values || count < TUNE_NB * TUNE_DC) return set_error(CPPGB_ERR_ARG, "batch path table needs %d entries", TUNE_NB * TUNE_DC);
+    for (int k = 0; k < TUNE_NB * TUNE_DC; ++k) values[k] = g_batch_path[k].load();
+    return CPPGB_OK;
+  }
+  if (kind == CPPGB_TUNE_DENSE_BAND) {
+    if (!values || count < 1) return set_error(CPPGB_ERR_ARG, "dense band needs one entry");
+    values[0] = g_dense_band.load();
+    return CPPGB_OK;
+  }
+  return set_error(CPPGB_ERR_ARG, "unknown tuning kind %d", kind);
+}
 
 void cpp_set_stage_timing(int on) { g_timing.store(on ? 1 : 0); }
 

@@ -1004,11 +1004,11 @@ struct BatchLayout {
   size_t bytes;
 };
 
-// Path of one instance: 1 = FP32 CUDA-core tiles, 2 = BF16 tensor-core tiles.  0 (default) picks the
-// tensor cores from d >= 16 on, where the 64-column K chunk is at least a quarter used.
+// Path of one instance: 1 = FP32 CUDA-core tiles, 2 = BF16 tensor-core tiles; 0 takes the tuning
+// policy's entry for the instance's n-bucket and d-class.
 int path_of(const cpp_instance& c) {
   if (c.path == 1 || c.path == 2) return c.path;
-  return c.d >= 16 ? 2 : 1;
+  return tuned_batch_path(c.n, c.d);
 }
 
 struct Totals {
@@ -1152,8 +1152,9 @@ struct GraphKey {
   int64_t count, rows, tiles, cap, rows16, tiles16, c0, c1, c2, c3;
   int32_t* pairs;
   int64_t pairs_cap;
+  bool timing;
   bool operator==(const GraphKey& o) const {
-    return ws == o.ws && ws_bytes == o.ws_bytes && count == o.count && rows == o.rows && tiles == o.tiles &&
+    return timing == o.timing && ws == o.ws && ws_bytes == o.ws_bytes && count == o.count && rows == o.rows && tiles == o.tiles &&
            cap == o.cap && rows16 == o.rows16 && tiles16 == o.tiles16 && c0 == o.c0 && c1 == o.c1 && c2 == o.c2 &&
            c3 == o.c3 && pairs == o.pairs && pairs_cap == o.pairs_cap;
   }
@@ -1164,9 +1165,13 @@ cudaGraphExec_t g_exec = nullptr;
 int g_dev = -1;
 long long g_graph_kernels = 0;  // kernels in the instantiated graph
 
+// events around the batch's stages, recorded inside the captured graph while stage timing is on
+cudaEvent_t g_bev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+
 int enqueue_batch(const BatchLayout& L, int64_t count, const Totals& t, int32_t* pairs, int64_t pairs_cap, int sms,
-                  const BatchMaps& maps, cudaStream_t st) {
+                  const BatchMaps& maps, bool timing, cudaStream_t st) {
   const int ci = (int)count;
+  if (timing) CPPGB_CUDA_TRY(cudaEventRecordWithFlags(g_bev[0], st, cudaEventRecordExternal));
   batch_init_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(L.st, ci, L.g);
   CPPGB_LAUNCH_CHECK();
   CPPGB_CUDA_TRY(cudaMemsetAsync(L.pair_counts, 0, sizeof(int32_t) * (count + 1), st));
@@ -1181,6 +1186,7 @@ int enqueue_batch(const BatchLayout& L, int64_t count, const Totals& t, int32_t*
   }
   batch_bounds_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(L.inst, L.st, ci);
   CPPGB_LAUNCH_CHECK();
+  if (timing) CPPGB_CUDA_TRY(cudaEventRecordWithFlags(g_bev[1], st, cudaEventRecordExternal));
   if (t.tiles16 > 0) {
     const size_t smem = btc::SMEM_BYTES;
     const int64_t grid = t.tiles16 < sms ? t.tiles16 : sms;
@@ -1189,12 +1195,14 @@ int enqueue_batch(const BatchLayout& L, int64_t count, const Totals& t, int32_t*
                                                                        L.trec_cap);
     CPPGB_LAUNCH_CHECK();
   }
+  if (timing) CPPGB_CUDA_TRY(cudaEventRecordWithFlags(g_bev[2], st, cudaEventRecordExternal));
   if (t.tiles > 0) {
     const int64_t grid = t.tiles < 2 * sms ? t.tiles : 2 * sms;
     batch_dense_kernel<<<(unsigned)grid, TILE_NT, 0, st>>>(L.inst, L.tile_offs, ci, t.tiles, L.X, L.norms, L.st, L.g,
                                                            L.cand, L.cap, L.trec, L.trec_cap);
     CPPGB_LAUNCH_CHECK();
   }
+  if (timing) CPPGB_CUDA_TRY(cudaEventRecordWithFlags(g_bev[3], st, cudaEventRecordExternal));
   if (t.tiles16 > 0) {
     batch_tile_recheck_kernel<<<(unsigned)(2 * sms), TILE_NT, 0, st>>>(L.inst, L.X, L.norms, L.st, L.g, L.trec,
                                                                       L.trec_cap, L.cand, L.cap, 1);
@@ -1218,6 +1226,7 @@ int enqueue_batch(const BatchLayout& L, int64_t count, const Totals& t, int32_t*
   batch_finish_kernel<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(L.st, ci, L.pair_offs, pairs, pairs_cap, L.g,
                                                                       L.res);
   CPPGB_LAUNCH_CHECK();
+  if (timing) CPPGB_CUDA_TRY(cudaEventRecordWithFlags(g_bev[4], st, cudaEventRecordExternal));
   return CPPGB_OK;
 }
 
@@ -1326,10 +1335,14 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
   if (t.tiles16 > 0)
     CPPGB_CUDA_TRY(
         cudaFuncSetAttribute(btc::batch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)btc::SMEM_BYTES));
+  bool timing = stage_timing_on();
+  if (timing && !g_bev[0])
+    for (auto& e : g_bev)
+      if (cudaEventCreate(&e) != cudaSuccess) timing = false;
   {
     std::lock_guard<std::mutex> lock(g_graph_mu);
     const GraphKey key{ws, ws_bytes, count, t.rows, t.tiles, L.cap, t.rows16, t.tiles16, t.crow16[0], t.crow16[1],
-                       t.crow16[2], t.crow16[3], pairs, pairs_cap};
+                       t.crow16[2], t.crow16[3], pairs, pairs_cap, timing};
     if (!(g_exec && key == g_key && g_dev == dev)) {
       if (g_exec) {
         cudaGraphExecDestroy(g_exec);
@@ -1340,7 +1353,7 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
       cudaGraph_t graph;
       CPPGB_CUDA_TRY(cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal));
       const long long before = (long long)cpp_launch_count();
-      const int rc = enqueue_batch(L, count, t, pairs, pairs_cap, sms, maps, cap_st);
+      const int rc = enqueue_batch(L, count, t, pairs, pairs_cap, sms, maps, timing, cap_st);
       g_graph_kernels = (long long)cpp_launch_count() - before;
       note_launches(-g_graph_kernels);  // captured, not launched
       cudaError_t ce = cudaStreamEndCapture(cap_st, &graph);
@@ -1365,6 +1378,15 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
   CPPGB_CUDA_TRY(cudaMemcpyAsync(hoff.data(), L.pair_offs, sizeof(int64_t) * (count + 1), cudaMemcpyDeviceToHost, st));
   CPPGB_CUDA_TRY(cudaMemcpyAsync(&hg, L.g, sizeof hg, cudaMemcpyDeviceToHost, st));
   CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
+  if (timing) {  // [preparation, tensor-core tiles, FP32 tiles, second pass + recheck + output]
+    double ms[4];
+    for (int k = 0; k < 4; ++k) {
+      float v = 0.f;
+      CPPGB_CUDA_TRY(cudaEventElapsedTime(&v, g_bev[k], g_bev[k + 1]));
+      ms[k] = v;
+    }
+    set_stage_times(ms, 4);
+  }
   for (int64_t q = 0; q < count; ++q) pair_counts[q] = hoff[(size_t)q + 1] - hoff[(size_t)q];
   if (hg.status & 1u) return set_error(CPPGB_ERR_NUMERIC, "non-finite coordinate");
   if (hg.status & 4u) return set_error(CPPGB_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");

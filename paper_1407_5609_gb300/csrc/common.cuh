@@ -133,6 +133,15 @@ int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp
                    int64_t shard = 0, int64_t nshards = 1);
 bool gram_tc_available();
 
+// Tuning policy, process-wide (set through cpp_set_tuning, normally from the autotuner's cache).
+constexpr int TUNE_NB = 4, TUNE_DC = 4;  // batch n-buckets (n < 1024, 4096, 16384, rest) x d-classes ceil(d / 64)
+int tuned_batch_path(int64_t n, int d);   // 1 (FP32 tiles) or 2 (tensor-core tiles)
+int tuned_dense_band();                   // column blocks per band of the tensor-core dense stage
+
+// Stage timing (cpp_set_stage_timing): whether it is on, and the last call's stage durations.
+bool stage_timing_on();
+void set_stage_times(const double* ms, int n);
+
 // FP64 recheck of the surviving candidates and the lexicographic (d^2, i, j) minimum.
 // Source of the exact coordinates: points (dtype F32/F64, [n][ld]) or a series with l-mers.
 // n_live = min(candidates emitted, cap), read back by the host after the dense stage.

@@ -359,7 +359,7 @@ int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp
   ts.excl = excl;
   ts.nbi = (int32_t)(n_pad / BM);
   ts.nbj = (int32_t)(n_pad / BN);
-  int band = BAND;
+  int band = tuned_dense_band() > 0 ? tuned_dense_band() : BAND;
   while ((ts.nbj + band - 1) / band > MAX_BANDS) band *= 2;
   ts.band = band;
   ts.nbands = (int32_t)((ts.nbj + band - 1) / band);

@@ -16,3 +16,10 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="session")
+def libpath():
+    """The in-tree library, built for sm_103a (cross-compiled; loading it needs no GPU)."""
+    from paper_1407_5609_gb300 import build
+    return build.build()

@@ -20,12 +20,6 @@ def _declared_functions():
     return sorted(set(names))
 
 
-@pytest.fixture(scope="module")
-def libpath():
-    from paper_1407_5609_gb300 import build
-    return build.build()
-
-
 def test_header_declares_the_entry_points():
     names = _declared_functions()
     for required in ("cpp_closest_pair", "tsmm_motif", "twolocus_scan", "frnn_query", "cpp_batch",
