@@ -269,6 +269,8 @@ class Batch:
 
     def __init__(self, args):
         from paper_1407_5609_gb300 import synth
+        self.no_tune = args.no_tune
+        self.path = args.batch_path
         self.batch = synth.make_batch(count=args.batch_count)
         self.units = sum(b.pts.shape[0] * (b.pts.shape[0] - 1) // 2 for b in self.batch)
         self.flop_per_unit = None
@@ -279,18 +281,24 @@ class Batch:
                        "l2": "4.8 GB of points per step, > L2"}
 
     def setup(self, dev):
+        import numpy as np
         import torch
         from paper_1407_5609_gb300 import autotune, capi
         # the autotuner's tile choice per (n-bucket, d-class): cached, or measured now (outside the timing)
-        entry = autotune.load_or_tune(dense=False)
-        table = entry["batch_path"]
+        if self.path:
+            table = [[self.path] * 4 for _ in range(4)]
+        elif self.no_tune:
+            table = np.asarray(capi.cpp_get_tuning(capi.TUNE_BATCH_PATH)).reshape(4, 4).tolist()
+        else:
+            table = autotune.load_or_tune(dense=False)["batch_path"]
         self.tc = [autotune.path_for(table, b.pts.shape[0], b.pts.shape[1]) == 2 for b in self.batch]
         self.tc_flops = sum(f for f, t in zip(self._flops(), self.tc) if t)
         self.config["batch_paths"] = table
         self.config["tensor_core_instances"] = int(sum(self.tc))
         self.pts = [torch.from_numpy(b.pts).to(dev) for b in self.batch]
         self.radii = [b.R for b in self.batch]
-        inst = [capi.cpp_instance(p.data_ptr(), p.shape[0], p.shape[1], 0, r) for p, r in zip(self.pts, self.radii)]
+        inst = [capi.cpp_instance(p.data_ptr(), p.shape[0], p.shape[1], self.path, r)
+                for p, r in zip(self.pts, self.radii)]
         self.ws = torch.empty(capi.cpp_batch_workspace_size(inst), dtype=torch.uint8, device=dev)
         self.pairs = torch.empty((1 << 20, 2), dtype=torch.int32, device=dev)
         inst1 = [capi.cpp_instance(p.data_ptr(), p.shape[0], p.shape[1], 1, r) for p, r in zip(self.pts, self.radii)]
@@ -300,7 +308,7 @@ class Batch:
         return [b.pts.shape[0] * (b.pts.shape[0] - 1) // 2 * 2 * b.pts.shape[1] for b in self.batch]
 
     def step(self, capi, mode):
-        res, counts, _ = capi.cpp_batch(self.pts, self.radii, ws=self.ws, pairs=self.pairs)
+        res, counts, _ = capi.cpp_batch(self.pts, self.radii, ws=self.ws, pairs=self.pairs, paths=self.path)
         return {"instances": len(res), "pairs_within_R": int(counts.sum()),
                 "answers": [(r["i"], r["j"], r["dist2"]) for r in res], "counts": counts}
 
@@ -319,7 +327,7 @@ class Batch:
     def e2e_step(self, capi, mode, host, dev_buf):
         for hp, dp in zip(host, dev_buf):
             dp.copy_(hp, non_blocking=True)
-        res, counts, pairs = capi.cpp_batch(dev_buf, self.radii, ws=self.ws, pairs=self.pairs)
+        res, counts, pairs = capi.cpp_batch(dev_buf, self.radii, ws=self.ws, pairs=self.pairs, paths=self.path)
         pairs[:int(counts.sum())].cpu()
         return {"instances": len(res)}
 
@@ -605,6 +613,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--batch-path", type=int, choices=[0, 1, 2], default=0,
+                    help="batch tiles: 0 the tuned policy, 1 FP32 CUDA-core tiles, 2 tensor-core tiles")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the library's built-in tile policy instead of the autotuner's (e.g. under a profiler)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
