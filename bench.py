@@ -383,6 +383,16 @@ def d2h_bytes(wl, capi):
     return ctypes.sizeof(capi.twolocus_result)
 
 
+def calibrate_rows(wl, oracle, target_s):
+    """Rows of the oracle sample that take about target_s: a fixed cost plus a per-row cost, from two
+    short probes."""
+    _, t2, _ = wl.oracle_sample(oracle, 2)
+    _, t8, _ = wl.oracle_sample(oracle, 8)
+    per_row = max((t8 - t2) / 6.0, 1e-4)
+    fixed = max(t2 - 2 * per_row, 0.0)
+    return max(2, int((target_s - fixed) / per_row))
+
+
 def cpu_baseline(wl, target_s=12.0):
     import oracle
     rows = calibrate_rows(wl, oracle, target_s)
