@@ -162,6 +162,10 @@ class TwoLocus:
     def step(self, capi, mode):
         return capi.twolocus_scan(self.dev_planes, 4096, 4096)
 
+    def shard_step(self, capi, mode, rank, world):
+        from paper_1407_5609_gb300 import shards
+        return shards.allreduce_twolocus(capi.twolocus_scan_shard(self.dev_planes, 4096, 4096, rank, world))
+
     def e2e_step(self, capi, mode, host, dev_buf):
         dev_buf.copy_(host, non_blocking=True)
         return capi.twolocus_scan(dev_buf, 4096, 4096)
@@ -240,6 +244,12 @@ class FRNN:
             self.cap = int(cols.shape[0]) + 1024
         self.nnz = int(cols.shape[0])
         return {"n_pairs_directed": self.nnz}
+
+    def shard_step(self, capi, mode, rank, world):
+        from paper_1407_5609_gb300 import shards
+        rp, cols = capi.frnn_query_shard(self.dev_x, self.R, rank, world)
+        rp, cols = shards.allgather_frnn(rp.cpu().numpy(), cols.cpu().numpy())
+        return {"n_pairs_directed": int(cols.shape[0])}
 
     def e2e_step(self, capi, mode, host, dev_buf):
         dev_buf.copy_(host, non_blocking=True)
@@ -440,8 +450,9 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # N > 1: the motif / closest-pair searches are split into shards of one search (strong scaling,
-    # one all-gather of the 24-byte result per step); the other workloads run as replicas.
+    # N > 1: the motif, closest-pair, two-locus and FRNN workloads are split into shards of one search
+    # (strong scaling; one exchange per step: an all-gather of the shard results, min- or max-reduced,
+    # or of the FRNN slabs' CSR pieces); the batch runs as replicas.
     sharded = world > 1 and hasattr(wl, "shard_step")
     step_fn = (lambda: wl.shard_step(capi, mode, rank, world)) if sharded else (lambda: wl.step(capi, mode))
 
@@ -482,7 +493,7 @@ def run_ours(args):
                      if wl.name in ("tsmm", "cpp") else {"frnn": "f32", "twolocus": "u64", "batch": "f32"}[wl.name]),
            "data": "synthetic", "config": dict(wl.config, mode=mode if wl.name in ("tsmm", "cpp") else None,
                                                flush_l2_between_steps=bool(flush),
-                                               parallelism=(f"{world} shards of one search + all-gather of the result"
+                                               parallelism=(f"{world} shards of one search + one exchange of the results"
                                                             if sharded else f"replicas x{world}" if world > 1
                                                             else "single GPU")),
            "answer": {k: res[k] for k in ("i", "j", "dist2", "score") if k in res},

@@ -146,6 +146,17 @@ int twolocus_scan_noalloc(const uint64_t* planes, int64_t S, int64_t W, int64_t 
                           twolocus_result* out, void* stream);
 
 /*
+ * twolocus_scan_shard -- shard s of nshards of the two-locus scan: evaluates only the SNP-pair tiles
+ * (64 x 128 SNPs) whose index is s mod nshards and returns the best pair among them with its tables
+ * (i = j = -1, score = -1 when the shard has none).  The answer of the whole scan is the shard
+ * result with the largest score, then the smallest (i, j): one max-reduce across the shards.
+ * Arguments and workspace as for twolocus_scan; CPPGB_ERR_ARG also for a bad shard.
+ */
+int twolocus_scan_shard(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls,
+                        int64_t shard, int64_t nshards, twolocus_result* out, void* ws, size_t ws_bytes,
+                        void* stream);
+
+/*
  * frnn_query -- fixed-radius near neighbours (Sec. 3.5): for every point p_i its R-neighbourhood
  * N(i) = { j != i : d(p_i, p_j) <= R }, with j in N(i) iff i in N(j).  The decision is the FP64
  * test sum_k (x_ik - x_jk)^2 <= R*R (coordinate order).
@@ -160,6 +171,19 @@ int twolocus_scan_noalloc(const uint64_t* planes, int64_t S, int64_t W, int64_t 
 size_t frnn_query_workspace_size(int64_t n, int d);
 int frnn_query(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t* row_ptr, int32_t* cols,
                int64_t cols_cap, int64_t* n_pairs_out, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * frnn_query_shard -- shard s of nshards of frnn_query on the grid path (1 <= d <= 4): the points
+ * are split into nshards slabs of equal width in x-cells (cells of side >= R over the bounding box)
+ * and only the points of slab s get their neighbour lists; every other row is empty (row_ptr has
+ * n + 1 entries as usual).  Each shard still builds the grid over all points, so the neighbours of
+ * a slab's points in the adjacent slabs (the halo) are found.  Concatenating, point by point, the
+ * rows of the point's own shard gives exactly the CSR of frnn_query.  Arguments, workspace and
+ * errors as for frnn_query; CPPGB_ERR_ARG for d > 4 or a bad shard.
+ */
+int frnn_query_shard(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t shard, int64_t nshards,
+                     int64_t* row_ptr, int32_t* cols, int64_t cols_cap, int64_t* n_pairs_out, void* ws,
+                     size_t ws_bytes, void* stream);
 
 /* One instance of a batch. */
 typedef struct {

@@ -67,9 +67,13 @@ SIGNATURES = {
     "twolocus_scan_workspace_size": (_sz, [_i64, _i64]),
     "twolocus_scan": (_int, [_vp, _i64, _i64, _i64, _i64, ctypes.POINTER(twolocus_result), _vp, _sz, _vp]),
     "twolocus_scan_noalloc": (_int, [_vp, _i64, _i64, _i64, _i64, ctypes.POINTER(twolocus_result), _vp]),
+    "twolocus_scan_shard": (_int, [_vp, _i64, _i64, _i64, _i64, _i64, _i64, ctypes.POINTER(twolocus_result), _vp,
+                                    _sz, _vp]),
     "frnn_query_workspace_size": (_sz, [_i64, _int]),
     "frnn_query": (_int, [_vp, _i64, _int, _i64, ctypes.c_double, _vp, _vp, _i64, ctypes.POINTER(_i64), _vp, _sz,
                           _vp]),
+    "frnn_query_shard": (_int, [_vp, _i64, _int, _i64, ctypes.c_double, _i64, _i64, _vp, _vp, _i64,
+                                ctypes.POINTER(_i64), _vp, _sz, _vp]),
     "cpp_batch_workspace_size": (_sz, [ctypes.POINTER(cpp_instance), _i64]),
     "cpp_batch": (_int, [ctypes.POINTER(cpp_instance), _i64, ctypes.POINTER(cpp_pair_result), ctypes.POINTER(_i64),
                          _vp, _i64, _vp, _sz, _vp]),
@@ -268,6 +272,21 @@ def twolocus_scan(planes: torch.Tensor, m_cases: int, m_controls: int, ws: torch
     return out.as_dict()
 
 
+def twolocus_scan_shard(planes: torch.Tensor, m_cases: int, m_controls: int, shard: int, nshards: int,
+                        ws: torch.Tensor | None = None, stream=None) -> dict:
+    """Shard `shard` of `nshards` of the two-locus scan (see include/cppgb.h)."""
+    _check_cuda(planes, "planes")
+    if planes.dim() != 4 or planes.shape[1:3] != (2, 2) or planes.element_size() != 8 or not planes.is_contiguous():
+        raise ValueError("planes must be a contiguous 64-bit tensor [S][2][2][W]")
+    S, W = planes.shape[0], planes.shape[3]
+    if ws is None:
+        ws = _workspace(twolocus_scan_workspace_size(S, W), planes.device)
+    out = twolocus_result()
+    _raise(lib().twolocus_scan_shard(planes.data_ptr() if S else None, S, W, m_cases, m_controls, shard, nshards,
+                                     ctypes.byref(out), ws.data_ptr(), ws.numel(), _stream(stream)))
+    return out.as_dict()
+
+
 def twolocus_scan_noalloc(planes: torch.Tensor, m_cases: int, m_controls: int, stream=None) -> dict:
     """As :func:`twolocus_scan`, through the entry point that uses the library's fixed scratch
     instead of a workspace (for callers that cannot allocate device memory)."""
@@ -288,6 +307,16 @@ def frnn_query_workspace_size(n: int, d: int) -> int:
 def frnn_query(pts: torch.Tensor, R: float, cols_cap: int | None = None, ws: torch.Tensor | None = None,
                stream=None):
     """R-neighbourhoods of the rows of float32 ``pts`` [n][d]: returns (row_ptr int64, cols int32)."""
+    return _frnn(pts, R, cols_cap, ws, stream, None)
+
+
+def frnn_query_shard(pts: torch.Tensor, R: float, shard: int, nshards: int, cols_cap: int | None = None,
+                     ws: torch.Tensor | None = None, stream=None):
+    """Slab `shard` of `nshards` of frnn_query (d <= 4): (row_ptr, cols) with only that slab's rows."""
+    return _frnn(pts, R, cols_cap, ws, stream, (int(shard), int(nshards)))
+
+
+def _frnn(pts, R, cols_cap, ws, stream, shard):
     _check_cuda(pts, "pts")
     if pts.dim() != 2 or pts.dtype != torch.float32 or pts.stride(1) != 1:
         raise ValueError("pts must be float32 [n][d] with unit column stride")
@@ -299,9 +328,10 @@ def frnn_query(pts: torch.Tensor, R: float, cols_cap: int | None = None, ws: tor
     cap = int(cols_cap) if cols_cap is not None else max(16 * n, 1024)
     while True:
         cols = torch.empty(max(cap, 1), dtype=torch.int32, device=pts.device)
-        st = lib().frnn_query(pts.data_ptr() if n else None, n, d, pts.stride(0) if n else d, float(R),
-                              row_ptr.data_ptr(), cols.data_ptr(), cap, ctypes.byref(total), ws.data_ptr(),
-                              ws.numel(), _stream(stream))
+        args = (pts.data_ptr() if n else None, n, d, pts.stride(0) if n else d, float(R))
+        tail = (row_ptr.data_ptr(), cols.data_ptr(), cap, ctypes.byref(total), ws.data_ptr(), ws.numel(),
+                _stream(stream))
+        st = lib().frnn_query(*args, *tail) if shard is None else lib().frnn_query_shard(*args, *shard, *tail)
         if st == ERR_CAPACITY and cols_cap is None and total.value > cap:
             cap = total.value
             continue

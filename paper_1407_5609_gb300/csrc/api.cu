@@ -400,8 +400,9 @@ size_t twolocus_scan_workspace_size(int64_t S, int64_t W) {
   return c.bytes();
 }
 
-int twolocus_scan(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls,
-                  twolocus_result* out, void* ws, size_t ws_bytes, void* stream) {
+static int twolocus_common(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls,
+                           int64_t shard, int64_t nshards, twolocus_result* out, void* ws, size_t ws_bytes,
+                           void* stream) {
   g_err[0] = 0;
   if (!out) return set_error(CPPGB_ERR_ARG, "out is NULL");
   if (S < 0 || S > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "S out of range");
@@ -422,12 +423,27 @@ int twolocus_scan(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases,
   twolocus_result* dres = c.take<twolocus_result>(1);
   const int64_t np = twolocus_num_partials(S);
   void* partials = c.take<char>((size_t)16 * (size_t)(np > 0 ? np : 1));
-  if ((rc = launch_twolocus(planes, S, W, m_cases, m_controls, partials, np, dres, st))) return rc;
+  if ((rc = launch_twolocus(planes, S, W, m_cases, m_controls, partials, np, dres, st, shard, nshards))) return rc;
   twolocus_result h;
   CPPGB_CUDA_TRY(cudaMemcpyAsync(&h, dres, sizeof h, cudaMemcpyDeviceToHost, st));
   CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
   *out = h;
   return CPPGB_OK;
+}
+
+int twolocus_scan(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls,
+                  twolocus_result* out, void* ws, size_t ws_bytes, void* stream) {
+  return twolocus_common(planes, S, W, m_cases, m_controls, 0, 1, out, ws, ws_bytes, stream);
+}
+
+int twolocus_scan_shard(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls,
+                        int64_t shard, int64_t nshards, twolocus_result* out, void* ws, size_t ws_bytes,
+                        void* stream) {
+  if (nshards < 1 || nshards > 65536 || shard < 0 || shard >= nshards) {
+    g_err[0] = 0;
+    return set_error(CPPGB_ERR_ARG, "need 0 <= shard < nshards <= 65536");
+  }
+  return twolocus_common(planes, S, W, m_cases, m_controls, shard, nshards, out, ws, ws_bytes, stream);
 }
 
 }  // extern "C"

@@ -162,7 +162,7 @@ int launch_exclusive_scan_i64(const int64_t* in, int64_t n, int64_t* out, int64_
 
 // Two-locus scan.
 int launch_twolocus(const uint64_t* planes, int64_t S, int64_t W, int64_t m1, int64_t m2, void* partials,
-                    int64_t n_partials, twolocus_result* dev_out, cudaStream_t st);
+                    int64_t n_partials, twolocus_result* dev_out, cudaStream_t st, int64_t shard = 0, int64_t nshards = 1);
 int64_t twolocus_num_partials(int64_t S);
 
 }  // namespace cppgb

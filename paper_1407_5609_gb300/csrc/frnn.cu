@@ -26,6 +26,7 @@ struct GridParams {
   float rr_lo, rr_hi;  // FP32 band around R^2: below -> inside, above -> outside, else FP64
   int32_t use64;    // 1: decide every pair in FP64
   int32_t pad;
+  int64_t ncx;      // cells along x that hold points (slabs of a sharded query split them evenly)
 };
 
 struct FrnnState {
@@ -115,6 +116,7 @@ __global__ void grid_params_kernel(FrnnState* fs, int d, double R) {
   gp.rr_lo = rf * (1.f - 0x1p-16f);
   gp.rr_hi = rf * (1.f + 0x1p-16f);
   gp.pad = 0;
+  gp.ncx = (int64_t)floorf(__fmul_rn(__fsub_rn(ord_val(fs->mm[4]), gp.o[0]), gp.inv_s)) + 1;
   fs->gp = gp;
 }
 
@@ -229,6 +231,8 @@ __device__ void sort_segment(int32_t* a, int64_t m) {
 }
 
 // FILL = false: counts[q] = |N(q)|.  FILL = true: writes N(q) at cols[row_ptr[q] ..], sorted.
+// With nshards > 1 only the points of slab `shard` (x cells [shard, shard + 1) * ncx / nshards) are
+// answered; the others get empty rows.  The grid holds every point, so no neighbour is missed.
 // The neighbour loop uses 32-bit indices (n < 2^31) and a branch-free FP32 test with the FP64 test
 // only inside the band: an earlier form with 64-bit indices and an early-return test produced wrong
 // counts for a few warps whose lanes spanned several cells (nvcc 13.0, sm_103a); this form matches
@@ -238,7 +242,7 @@ __global__ void grid_query_kernel(int n, const FrnnState* fs, const uint64_t* __
                                   const int32_t* __restrict__ cnt, const int64_t* __restrict__ start,
                                   const int32_t* __restrict__ sorted_idx, const float4* __restrict__ sorted_pts,
                                   int32_t* __restrict__ counts, const int64_t* __restrict__ row_ptr,
-                                  int32_t* __restrict__ cols) {
+                                  int32_t* __restrict__ cols, int shard, int nshards) {
   const int k = (int)(blockIdx.x * blockDim.x + threadIdx.x);
   if (k >= n) return;
   const GridParams gp = fs->gp;
@@ -247,6 +251,14 @@ __global__ void grid_query_kernel(int n, const FrnnState* fs, const uint64_t* __
   const float x[4] = {xv.x, xv.y, xv.z, xv.w};
   int64_t c[4];
   cell_of<D>(gp, x, c);
+  if (nshards > 1) {
+    int64_t slab = c[0] * nshards / gp.ncx;
+    slab = slab < 0 ? 0 : slab >= nshards ? nshards - 1 : slab;
+    if (slab != shard) {
+      if (!FILL) counts[q] = 0;
+      return;
+    }
+  }
   constexpr int stencil = D == 1 ? 3 : D == 2 ? 9 : D == 3 ? 27 : 81;
   int found = 0;
   int32_t* out = FILL ? cols + row_ptr[q] : nullptr;
@@ -404,7 +416,8 @@ RadiusLayout radius_layout(void* ws, int64_t n, int64_t d, size_t ws_bytes) {
 
 template <int D>
 int grid_path(const float* pts, int64_t n, int64_t ld, double R, int64_t* row_ptr, int32_t* cols,
-              int64_t cols_cap, int64_t* n_pairs_out, void* ws, size_t ws_bytes, cudaStream_t st) {
+              int64_t cols_cap, int64_t* n_pairs_out, void* ws, size_t ws_bytes, cudaStream_t st, int shard = 0,
+              int nshards = 1) {
   const int d = D;
   GridLayout L = grid_layout(ws, n);
   if (ws_bytes < L.bytes)
@@ -426,7 +439,7 @@ int grid_path(const float* pts, int64_t n, int64_t ld, double R, int64_t* row_pt
   CPPGB_LAUNCH_CHECK();
   const unsigned nq = (unsigned)((n + 127) / 128);
   grid_query_kernel<D, false><<<nq, 128, 0, st>>>((int)n, L.fs, L.keys, L.T, L.cnt, L.start, L.sorted_idx, L.sorted_pts,
-                                                L.counts, nullptr, nullptr);
+                                                L.counts, nullptr, nullptr, shard, nshards);
   CPPGB_LAUNCH_CHECK();
   if ((rc = launch_exclusive_scan_i32(L.counts, n, row_ptr, L.tmp, st))) return rc;
   int64_t total = 0;
@@ -442,7 +455,7 @@ int grid_path(const float* pts, int64_t n, int64_t ld, double R, int64_t* row_pt
                      (long long)cols_cap, (long long)total);
   if (total > 0) {
     grid_query_kernel<D, true><<<nq, 128, 0, st>>>((int)n, L.fs, L.keys, L.T, L.cnt, L.start, L.sorted_idx, L.sorted_pts,
-                                                 nullptr, row_ptr, cols);
+                                                 nullptr, row_ptr, cols, shard, nshards);
     CPPGB_LAUNCH_CHECK();
   }
   CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
@@ -504,16 +517,9 @@ int dense_path(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t
 
 using namespace cppgb;
 
-extern "C" {
-
-size_t frnn_query_workspace_size(int64_t n, int d) {
-  if (n < 0 || d < 1 || d > 4096) return 0;
-  if (d <= 4) return grid_layout(nullptr, n).bytes;
-  return radius_layout(nullptr, n, d, 0).bytes;
-}
-
-int frnn_query(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t* row_ptr, int32_t* cols,
-               int64_t cols_cap, int64_t* n_pairs_out, void* ws, size_t ws_bytes, void* stream) {
+static int frnn_common(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t* row_ptr, int32_t* cols,
+                int64_t cols_cap, int64_t* n_pairs_out, void* ws, size_t ws_bytes, void* stream, int64_t shard,
+                int64_t nshards) {
   if (!n_pairs_out) return set_error(CPPGB_ERR_ARG, "n_pairs_out is NULL");
   *n_pairs_out = 0;
   if (n < 0 || n > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "n out of range");
@@ -529,13 +535,38 @@ int frnn_query(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t
     CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
     return CPPGB_OK;
   }
+  const int sh = (int)shard, ns = (int)nshards;
   switch (d) {
-    case 1: return grid_path<1>(pts, n, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, st);
-    case 2: return grid_path<2>(pts, n, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, st);
-    case 3: return grid_path<3>(pts, n, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, st);
-    case 4: return grid_path<4>(pts, n, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, st);
+    case 1: return grid_path<1>(pts, n, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, st, sh, ns);
+    case 2: return grid_path<2>(pts, n, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, st, sh, ns);
+    case 3: return grid_path<3>(pts, n, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, st, sh, ns);
+    case 4: return grid_path<4>(pts, n, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, st, sh, ns);
   }
   return dense_path(pts, n, d, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, st);
+}
+
+extern "C" {
+
+size_t frnn_query_workspace_size(int64_t n, int d) {
+  if (n < 0 || d < 1 || d > 4096) return 0;
+  if (d <= 4) return grid_layout(nullptr, n).bytes;
+  return radius_layout(nullptr, n, d, 0).bytes;
+}
+
+
+int frnn_query(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t* row_ptr, int32_t* cols,
+               int64_t cols_cap, int64_t* n_pairs_out, void* ws, size_t ws_bytes, void* stream) {
+  return frnn_common(pts, n, d, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, stream, 0, 1);
+}
+
+int frnn_query_shard(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t shard, int64_t nshards,
+                     int64_t* row_ptr, int32_t* cols, int64_t cols_cap, int64_t* n_pairs_out, void* ws,
+                     size_t ws_bytes, void* stream) {
+  if (n_pairs_out) *n_pairs_out = 0;
+  if (d < 1 || d > 4) return set_error(CPPGB_ERR_ARG, "frnn_query_shard needs 1 <= d <= 4 (the grid path)");
+  if (nshards < 1 || nshards > 65536 || shard < 0 || shard >= nshards)
+    return set_error(CPPGB_ERR_ARG, "need 0 <= shard < nshards <= 65536");
+  return frnn_common(pts, n, d, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, stream, shard, nshards);
 }
 
 }  // extern "C"

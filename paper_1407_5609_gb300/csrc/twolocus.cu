@@ -32,7 +32,7 @@ __device__ __forceinline__ bool better(long long s, int i, int j, long long bs, 
 
 __global__ void __launch_bounds__(NT, 2)
     twolocus_scan_kernel(const uint64_t* __restrict__ planes, int64_t S, int64_t W, int64_t m1, int64_t m2,
-                         Partial* __restrict__ partials) {
+                         Partial* __restrict__ partials, int64_t shard, int64_t nshards) {
   __shared__ __align__(16) uint32_t Si[2 * WC][2][TI];
   __shared__ __align__(16) uint32_t Sj[2 * WC][2][TJ];
   __shared__ Partial red[NT / 32];
@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(NT, 2)
   const int64_t i0 = (int64_t)blockIdx.y * TI, j0 = (int64_t)blockIdx.x * TJ;
   const int64_t pid = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  if (j0 + TJ - 1 <= i0 || i0 >= S) {  // no pair i < j in this tile (uniform exit)
+  // no pair i < j in this tile, or the tile belongs to another shard (uniform exit)
+  if (j0 + TJ - 1 <= i0 || i0 >= S || pid % nshards != shard) {
     if (tid == 0) partials[pid] = Partial{-1, -1, -1};
     return;
   }
@@ -201,12 +202,13 @@ int64_t twolocus_num_partials(int64_t S) {
 }
 
 int launch_twolocus(const uint64_t* planes, int64_t S, int64_t W, int64_t m1, int64_t m2, void* partials,
-                    int64_t n_partials, twolocus_result* dev_out, cudaStream_t st) {
+                    int64_t n_partials, twolocus_result* dev_out, cudaStream_t st, int64_t shard, int64_t nshards) {
   const int64_t gx = (S + TJ - 1) / TJ, gy = (S + TI - 1) / TI;
   if (gx * gy > n_partials) return set_error(CPPGB_ERR_CAPACITY, "internal: partials too small");
   if (gx > 0 && gy > 0) {
     if (gy > 65535) return set_error(CPPGB_ERR_ARG, "S too large for the tile grid");
-    twolocus_scan_kernel<<<dim3((unsigned)gx, (unsigned)gy), NT, 0, st>>>(planes, S, W, m1, m2, (Partial*)partials);
+    twolocus_scan_kernel<<<dim3((unsigned)gx, (unsigned)gy), NT, 0, st>>>(planes, S, W, m1, m2, (Partial*)partials,
+                                                                       shard, nshards);
     CPPGB_LAUNCH_CHECK();
   }
   twolocus_finish_kernel<<<1, NT, 0, st>>>(planes, W, m1, m2, (const Partial*)partials, gx * gy, dev_out);

@@ -1,14 +1,20 @@
-"""Combining the results of shards of one closest-pair / motif search.
+"""Combining the results of the shards of one search (the single exchange step of each row).
 
-A search split with ``tsmm_motif_shard`` / ``cpp_closest_pair_shard`` yields one exact result per
-shard; the answer of the whole search is the lexicographically smallest (dist2, i, j) among them
-(shards with no pair report i = j = -1).  ``reduce_results`` does that on one host;
-``allreduce_result`` is the exchange step across the ranks of a torch.distributed group (each rank
-contributes its shard's 24-byte key; every rank receives the combined answer).
+* Closest pair / motif (``tsmm_motif_shard``, ``cpp_closest_pair_shard``): every shard returns the
+  exact best pair of its tiles; the answer is the lexicographically smallest (dist2, i, j)
+  (``reduce_results``; ``allreduce_result`` across the ranks of a torch.distributed group).
+* Two-locus (``twolocus_scan_shard``): the answer is the shard result with the largest score, then
+  the smallest (i, j) (``reduce_twolocus`` / ``allreduce_twolocus``).
+* FRNN on the grid (``frnn_query_shard``): each shard answers the points of its x-slab; the CSR of
+  the whole query takes each point's row from its own shard (``merge_frnn`` / ``allgather_frnn``).
+
+Shards with no pair report i = j = -1.
 """
 from __future__ import annotations
 
 import math
+
+import numpy as np
 
 
 def _key(r: dict):
@@ -37,3 +43,64 @@ def allreduce_result(result: dict, group=None) -> dict:
     dist.all_gather_object(gathered, {k: result[k] for k in ("i", "j", "dist2", "dist", "n_emitted",
                                                               "n_rechecked") if k in result}, group=group)
     return reduce_results(gathered)
+
+
+def _tl_key(r: dict):
+    if r["i"] < 0:
+        return (1, 0, 0, 0)  # after every real pair
+    return (0, -int(r["score"]), int(r["i"]), int(r["j"]))
+
+
+def reduce_twolocus(results: list) -> dict:
+    """The two-locus shard result with the largest score, ties to the smallest (i, j)."""
+    best = None
+    for r in results:
+        if best is None or _tl_key(r) < _tl_key(best):
+            best = r
+    if best is None:
+        return {"i": -1, "j": -1, "score": -1, "countsA": np.zeros(9, np.int32), "countsB": np.zeros(9, np.int32)}
+    return dict(best)
+
+
+def allreduce_twolocus(result: dict, group=None) -> dict:
+    """Exchange step of a sharded two-locus scan: gather every rank's result and max-reduce."""
+    import torch.distributed as dist
+    gathered = [None] * dist.get_world_size(group)
+    local = {"i": int(result["i"]), "j": int(result["j"]), "score": int(result["score"]),
+             "countsA": np.asarray(result["countsA"]).tolist(), "countsB": np.asarray(result["countsB"]).tolist()}
+    dist.all_gather_object(gathered, local, group=group)
+    out = reduce_twolocus(gathered)
+    out["countsA"] = np.asarray(out["countsA"], dtype=np.int32)
+    out["countsB"] = np.asarray(out["countsB"], dtype=np.int32)
+    return out
+
+
+def merge_frnn(parts: list):
+    """CSR of the whole query from the shards' (row_ptr, cols) pieces (numpy); each point's row is
+    non-empty in at most one piece (its own slab's)."""
+    if not parts:
+        raise ValueError("no shard pieces")
+    n = len(parts[0][0]) - 1
+    deg = np.zeros(n, dtype=np.int64)
+    for rp, _ in parts:
+        deg += np.diff(np.asarray(rp, dtype=np.int64))
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(deg, out=row_ptr[1:])
+    cols = np.empty(int(row_ptr[-1]), dtype=np.int32)
+    for rp, c in parts:
+        rp = np.asarray(rp, dtype=np.int64)
+        c = np.asarray(c, dtype=np.int32)
+        m = int(rp[-1])
+        if m == 0:
+            continue
+        r = np.repeat(np.arange(n), np.diff(rp))            # the row of every entry of this piece
+        cols[row_ptr[r] + (np.arange(m) - rp[r])] = c[:m]
+    return row_ptr, cols
+
+
+def allgather_frnn(row_ptr, cols, group=None):
+    """Exchange step of a sharded FRNN query: every rank receives every slab's piece and merges."""
+    import torch.distributed as dist
+    gathered = [None] * dist.get_world_size(group)
+    dist.all_gather_object(gathered, (np.asarray(row_ptr), np.asarray(cols)), group=group)
+    return merge_frnn(gathered)

@@ -45,3 +45,54 @@ def test_shard_argument_errors():
         with pytest.raises(capi.CppgbError) as e:
             capi.tsmm_motif_shard(s, 32, 16, k, m)
         assert e.value.status == capi.ERR_ARG
+
+
+@pytest.mark.parametrize("nshards", [1, 3, 7])
+def test_twolocus_shards_combine_exactly(nshards):
+    """Max-reduce of the shard results = the unsharded scan = the oracle (score, pair and tables)."""
+    from paper_1407_5609_gb300 import capi
+    g, _ = synth.make_genotypes(S=700, m1=300, m2=260, seed=94)
+    planes = to_dev(synth.pack_planes(g, 300, 260).view(np.int64), device())
+    parts = [capi.twolocus_scan_shard(planes, 300, 260, k, nshards) for k in range(nshards)]
+    r = shards.reduce_twolocus(parts)
+    full = capi.twolocus_scan(planes, 300, 260)
+    oi, oj, osc, ca, cb = oracle.twolocus(g, 300, 260)
+    assert (r["i"], r["j"], r["score"]) == (full["i"], full["j"], full["score"]) == (oi, oj, osc)
+    assert (np.asarray(r["countsA"]) == ca).all() and (np.asarray(r["countsB"]) == cb).all()
+
+
+@pytest.mark.parametrize("d,nshards", [(3, 1), (3, 2), (3, 5), (2, 4), (1, 3)])
+def test_frnn_slabs_concatenate_exactly(d, nshards):
+    """The x-slab shards' CSR pieces concatenate to the unsharded CSR and the oracle's."""
+    from paper_1407_5609_gb300 import capi
+    x = synth.make_frnn_mixture(n=6000, d=d, k=8, sigma=0.05, seed=95)
+    R = {1: 2e-4, 2: 0.004, 3: 0.02}[d]
+    t = to_dev(x, device())
+    parts = []
+    for k in range(nshards):
+        rp, cols = capi.frnn_query_shard(t, R, k, nshards)
+        parts.append((rp.cpu().numpy(), cols.cpu().numpy()))
+    rp, cols = shards.merge_frnn(parts)
+    frp, fcols = capi.frnn_query(t, R)
+    orp, ocols = oracle.frnn(x.astype(np.float64), R)
+    np.testing.assert_array_equal(rp, frp.cpu().numpy())
+    np.testing.assert_array_equal(cols, fcols.cpu().numpy())
+    np.testing.assert_array_equal(rp, orp)
+    np.testing.assert_array_equal(cols, ocols)
+    if nshards > 1:  # every slab answers some points and no point is answered twice
+        owned = [np.diff(p[0]) > 0 for p in parts]
+        assert sum(o.astype(int) for o in owned).max() <= 1
+
+
+def test_new_shard_argument_errors():
+    from paper_1407_5609_gb300 import capi
+    dev = device()
+    x = to_dev(synth.rng_for(96).random((100, 6)).astype(np.float32), dev)
+    with pytest.raises(capi.CppgbError) as e:
+        capi.frnn_query_shard(x, 0.1, 0, 2)          # d > 4 has no slab form
+    assert e.value.status == capi.ERR_ARG
+    g, _ = synth.make_genotypes(S=50, m1=64, m2=64, seed=97)
+    planes = to_dev(synth.pack_planes(g, 64, 64).view(np.int64), dev)
+    with pytest.raises(capi.CppgbError) as e:
+        capi.twolocus_scan_shard(planes, 64, 64, 3, 3)
+    assert e.value.status == capi.ERR_ARG

@@ -57,3 +57,58 @@ def test_reduce_results_lexicographic_and_empty():
     assert (r["i"], r["j"]) == (3, 11)
     assert shards.reduce_results([none, none])["i"] == -1
     assert shards.reduce_results([])["i"] == -1
+
+
+def _rank_main_twolocus_frnn(rank, world, port, out_path):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # two-locus: each rank's part = the best pair (by the oracle) among SNP pairs (i, j) with
+    # i % world == rank; the max-reduce must give the whole scan's answer
+    g, _ = synth.make_genotypes(S=120, m1=90, m2=70, seed=98)
+    best = {"i": -1, "j": -1, "score": -1, "countsA": np.zeros(9, np.int32), "countsB": np.zeros(9, np.int32)}
+    for i in range(rank, 120, world):
+        for j in range(i + 1, 120):
+            ua = int(np.sum(g[i, :90] == g[j, :90]))
+            ub = int(np.sum(g[i, 90:] == g[j, 90:]))
+            sc = abs(ua * 70 - ub * 90)
+            if sc > best["score"]:
+                best = {"i": i, "j": j, "score": sc, "countsA": np.zeros(9, np.int32), "countsB": np.zeros(9, np.int32)}
+    tl = shards.allreduce_twolocus(best)
+    # FRNN: each rank's piece = the oracle's rows of the points in its half of x
+    x = synth.make_frnn_mixture(n=800, d=3, k=4, sigma=0.05, seed=99).astype(np.float64)
+    rp, cols = oracle.frnn(x, 0.03)
+    own = (x[:, 0] >= np.median(x[:, 0])).astype(int) == rank
+    deg = np.where(own, np.diff(rp), 0)
+    prp = np.concatenate([[0], np.cumsum(deg)])
+    pcols = np.concatenate([cols[rp[i]:rp[i + 1]] for i in range(800) if own[i]] or [np.zeros(0, np.int32)])
+    mrp, mcols = shards.allgather_frnn(prp, pcols)
+    if rank == 0:
+        np.savez(out_path, tl=np.array([tl["i"], tl["j"], tl["score"]]), rp=mrp, cols=mcols)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_twolocus_and_frnn_exchange_two_gloo_ranks(tmp_path):
+    out = str(tmp_path / "res.npz")
+    mp.start_processes(_rank_main_twolocus_frnn, args=(2, _free_port(), out), nprocs=2, join=True,
+                       start_method="spawn")
+    z = np.load(out)
+    g, _ = synth.make_genotypes(S=120, m1=90, m2=70, seed=98)
+    oi, oj, osc, _, _ = oracle.twolocus(g, 90, 70)
+    assert tuple(int(v) for v in z["tl"]) == (oi, oj, osc)
+    x = synth.make_frnn_mixture(n=800, d=3, k=4, sigma=0.05, seed=99).astype(np.float64)
+    rp, cols = oracle.frnn(x, 0.03)
+    np.testing.assert_array_equal(z["rp"], rp)
+    np.testing.assert_array_equal(z["cols"], cols)
+
+
+def test_reduce_twolocus_order():
+    none = {"i": -1, "j": -1, "score": -1, "countsA": np.zeros(9), "countsB": np.zeros(9)}
+    a = {"i": 4, "j": 9, "score": 50, "countsA": np.zeros(9), "countsB": np.zeros(9)}
+    b = {"i": 2, "j": 30, "score": 50, "countsA": np.zeros(9), "countsB": np.zeros(9)}
+    c = {"i": 0, "j": 1, "score": 49, "countsA": np.zeros(9), "countsB": np.zeros(9)}
+    r = shards.reduce_twolocus([none, a, c, b])
+    assert (r["i"], r["j"], r["score"]) == (2, 30, 50)
+    assert shards.reduce_twolocus([none])["i"] == -1 and shards.reduce_twolocus([])["i"] == -1
