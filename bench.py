@@ -569,6 +569,29 @@ def run_ours(args):
                              "ms_per_step": pms / max(1, min(args.steps, 3)),
                              "same_answer": (pres["i"], pres["j"], pres["dist2"]) == (res["i"], res["j"], res["dist2"])}
 
+    # the same search with reference pruning of tiles (MK / MPR bound): same answer, fewer tiles
+    if wl.name in ("tsmm", "cpp") and mode != "plain_fp32" and not args.no_compare:
+        barrier()
+        pmode = mode + "_prune"
+        wl.step(capi, pmode)                               # warm-up
+        capi.cpp_set_stage_timing(True)
+        psteps = max(1, min(args.steps, 5))
+        dense = []
+
+        def pruned():
+            r = wl.step(capi, pmode)
+            st = capi.cpp_stage_times()
+            if len(st) >= 2:
+                dense.append(st[1])
+            return r
+        pms, pres = timed_steps(pruned, psteps, stream, torch, flush)
+        capi.cpp_set_stage_timing(False)
+        kept, total = capi.cpp_prune_stats()
+        out["pruned"] = {"mode": pmode, "value": wl.units * psteps / (pms / 1e3), "unit": UNIT,
+                         "ms_per_step": pms / psteps, "dense_stage_ms": statistics.mean(dense) if dense else None,
+                         "tiles_kept": kept, "tiles_total": total,
+                         "same_answer": (pres["i"], pres["j"], pres["dist2"]) == (res["i"], res["j"], res["dist2"])}
+
     # end to end through the public API from pinned host memory
     if not args.no_e2e:
         host_np, nbytes = wl.host_input()

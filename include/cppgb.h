@@ -50,6 +50,13 @@ extern "C" {
 #define CPPGB_MODE_PLAIN_FP32 0  /* FP32 CUDA-core Gram tiles, rigorous bound, FP64 recheck */
 #define CPPGB_MODE_FILTER_BF16 1 /* BF16 tensor-core Gram tiles (tcgen05), bound, FP64 recheck */
 #define CPPGB_MODE_FILTER_FP16 2 /* FP16 tensor-core Gram tiles (tcgen05), bound, FP64 recheck */
+/* OR'd into a FILTER mode: reference pruning of whole tiles (the reference-point bound of
+ * Algorithms MK / MPR, Sec. 3.1-3.3).  Ten reference rows give every row an interval holding its
+ * exact distance to each reference; a 128 x 256 tile whose row and column intervals are, for some
+ * reference, further apart than sqrt(U0) is skipped, U0 being the exact best d^2 of seed pairs
+ * (rows adjacent in the order of their distance to the first reference, as in Algorithm MK).  The
+ * answer is the same as without pruning. */
+#define CPPGB_MODE_PRUNE 0x100
 
 /* Result of a closest-pair style search. */
 typedef struct {
@@ -223,6 +230,9 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
 void cpp_set_stage_timing(int on);
 int cpp_stage_times(double* ms, int cap);
 int64_t cpp_launch_count(void);
+/* Tiles the last pruned dense search on the calling thread evaluated, of all its tiles (-1, -1
+ * when the last search did not prune). */
+int cpp_prune_stats(int64_t* tiles_kept, int64_t* tiles_total);
 
 /* 1 when this build carries the tensor-core filter modes (CPPGB_MODE_FILTER_*), else 0. */
 int cpp_filter_available(void);

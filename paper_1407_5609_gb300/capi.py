@@ -19,7 +19,9 @@ LIB_PATH = os.path.join(_HERE, "libcppgb.so")
 
 OK, ERR_ARG, ERR_CAPACITY, ERR_TIMEOUT, ERR_CUDA, ERR_NUMERIC = 0, 1, 2, 3, 4, 5
 F32, F64 = 0, 1
-MODES = {"plain_fp32": 0, "filter_bf16": 1, "filter_fp16": 2}
+MODE_PRUNE = 0x100
+MODES = {"plain_fp32": 0, "filter_bf16": 1, "filter_fp16": 2,
+         "filter_bf16_prune": 1 | MODE_PRUNE, "filter_fp16_prune": 2 | MODE_PRUNE}
 
 
 class CppgbError(RuntimeError):
@@ -80,6 +82,7 @@ SIGNATURES = {
     "cpp_set_stage_timing": (None, [_int]),
     "cpp_stage_times": (_int, [ctypes.POINTER(ctypes.c_double), _int]),
     "cpp_launch_count": (_i64, []),
+    "cpp_prune_stats": (_int, [ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "cpp_filter_available": (_int, []),
     "cpp_set_tuning": (_int, [_int, ctypes.POINTER(ctypes.c_int32), _int]),
     "cpp_get_tuning": (_int, [_int, ctypes.POINTER(ctypes.c_int32), _int]),
@@ -167,6 +170,13 @@ def cpp_stage_times() -> list:
 
 def cpp_launch_count() -> int:
     return int(lib().cpp_launch_count())
+
+
+def cpp_prune_stats() -> tuple:
+    """(tiles kept, tiles in all) of the last pruned search on this thread; (-1, -1) if none."""
+    kept, total = _i64(0), _i64(0)
+    _raise(lib().cpp_prune_stats(ctypes.byref(kept), ctypes.byref(total)))
+    return kept.value, total.value
 
 
 def cpp_closest_pair_workspace_size(n: int, d: int, mode="plain_fp32") -> int:

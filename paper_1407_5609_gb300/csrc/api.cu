@@ -61,6 +61,7 @@ struct StageTimer {
   }
 };
 static thread_local StageTimer g_timer;
+static thread_local int64_t g_prune_kept = -1, g_prune_total = -1;  // the last pruned search's tiles
 
 bool stage_timing_on() { return g_timing.load() != 0; }
 
@@ -93,8 +94,14 @@ int check_device() {
   return CPPGB_OK;
 }
 
-bool is_filter(int mode) { return mode == CPPGB_MODE_FILTER_BF16 || mode == CPPGB_MODE_FILTER_FP16; }
-bool mode_ok(int mode) { return mode == CPPGB_MODE_PLAIN_FP32 || is_filter(mode); }
+// mode = one base mode, optionally | CPPGB_MODE_PRUNE (tensor-core filter modes only)
+int base_mode(int mode) { return mode & ~CPPGB_MODE_PRUNE; }
+bool is_prune(int mode) { return (mode & CPPGB_MODE_PRUNE) != 0; }
+bool is_filter(int mode) {
+  const int b = base_mode(mode);
+  return b == CPPGB_MODE_FILTER_BF16 || b == CPPGB_MODE_FILTER_FP16;
+}
+bool mode_ok(int mode) { return base_mode(mode) == CPPGB_MODE_PLAIN_FP32 ? !is_prune(mode) : is_filter(mode); }
 
 // ---------------------------------------------------------------- dense search layout
 struct DenseLayout {
@@ -104,6 +111,10 @@ struct DenseLayout {
   float* norms;
   float* eps;
   void* X;
+  // reference pruning (CPPGB_MODE_PRUNE)
+  float *plo, *phi, *pblo, *pbhi;
+  int32_t *hist, *cursor, *perm, *flags, *list;
+  int64_t *start, *pos, *ptmp;
   Candidate* cand;
   double* d2buf;
   size_t bytes;
@@ -124,6 +135,21 @@ DenseLayout dense_layout(void* ws, int64_t n, int64_t d, int mode, size_t ws_byt
   L.norms = c.take<float>(L.n_pad);
   L.eps = c.take<float>(L.n_pad);
   L.X = c.take<char>((size_t)L.n_pad * L.Kp * L.elem);
+  if (is_prune(mode)) {
+    const int64_t nbi = L.n_pad / 128, tiles = nbi * (L.n_pad / 256);  // all tiles: an upper bound
+    L.plo = c.take<float>((size_t)PRUNE_REFS * L.n_pad);
+    L.phi = c.take<float>((size_t)PRUNE_REFS * L.n_pad);
+    L.pblo = c.take<float>((size_t)PRUNE_REFS * nbi);
+    L.pbhi = c.take<float>((size_t)PRUNE_REFS * nbi);
+    L.hist = c.take<int32_t>(65536);
+    L.cursor = c.take<int32_t>(65536);
+    L.start = c.take<int64_t>(65537);
+    L.perm = c.take<int32_t>(L.n_pad);
+    L.flags = c.take<int32_t>(tiles);
+    L.pos = c.take<int64_t>(tiles + 1);
+    L.list = c.take<int32_t>(tiles);
+    L.ptmp = c.take<int64_t>(scan_temp_elems(tiles > 65536 ? tiles : 65536));
+  }
   const size_t fixed = c.bytes() + 512;
   if (ws_bytes > fixed) {
     int64_t fit = (int64_t)((ws_bytes - fixed) / (sizeof(Candidate) + sizeof(double)));
@@ -143,6 +169,7 @@ DenseLayout dense_layout(void* ws, int64_t n, int64_t d, int mode, size_t ws_byt
 //               specified to be round-to-nearest): the dot term padded to 2 * K * 2^-22 |x||y|,
 //               norms from the prep's two-level sums (22u each) and the same epilogue terms.
 float kappa_for(int mode, int64_t Kp) {
+  mode = base_mode(mode);
   double K = (double)Kp;
   if (!is_filter(mode)) {
     double g = K * kU32 / (1.0 - K * kU32);
@@ -170,7 +197,10 @@ int dense_search(const Source& src, int64_t n, int64_t d, int64_t excl, int mode
     return set_error(CPPGB_ERR_ARG, "tensor-core filter modes are not available in this build");
 
   const bool timing = g_timing.load() != 0 && g_timer.init();
+  const bool prune = is_prune(mode);
+  mode = base_mode(mode);
   g_timer.n = 0;
+  g_prune_kept = g_prune_total = -1;
   if (timing) CPPGB_CUDA_TRY(cudaEventRecord(g_timer.ev[0], st));
   int rc;
   if ((rc = launch_init_scalars(L.sc, st))) return rc;
@@ -180,12 +210,37 @@ int dense_search(const Source& src, int64_t n, int64_t d, int64_t excl, int mode
     rc = launch_prep_points(src.pts, src.dtype, n, d, src.ld, mode, L.X, L.n_pad, L.Kp, L.norms, L.eps, L.sc, st);
   if (rc) return rc;
   if ((rc = launch_bounds(L.sc, kappa_for(mode, L.Kp), st))) return rc;
+
+  // Reference pruning: distance intervals to the references, a seed bound U0 from pairs that are
+  // neighbours in the order of reference 0, then the list of tiles the intervals cannot exclude.
+  const int32_t* tlist = nullptr;
+  const int64_t* tcount = nullptr;
+  if (prune && n >= 2) {
+    if ((rc = launch_prune_intervals(L.X, mode, n, L.n_pad, L.Kp, L.norms, L.eps, L.sc, L.plo, L.phi, L.pblo, L.pbhi,
+                                     st)))
+      return rc;
+    if ((rc = launch_prune_seeds(L.X, mode, L.Kp, L.norms, L.eps, L.plo, L.phi, n, excl, L.sc, L.hist, L.cursor,
+                                 L.start, L.ptmp, L.perm, st)))
+      return rc;
+    const int64_t total = gram_tc_tile_count(n, L.n_pad, excl, shard, nshards);
+    if ((rc = launch_gram_tc_prune_list(n, L.n_pad, excl, L.pblo, L.pbhi, L.sc, L.flags, L.pos, L.ptmp, L.list, st,
+                                        shard, nshards)))
+      return rc;
+    tlist = L.list;
+    tcount = L.pos + total;
+    int64_t kept = 0;
+    CPPGB_CUDA_TRY(cudaMemcpyAsync(&kept, tcount, sizeof kept, cudaMemcpyDeviceToHost, st));
+    CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
+    g_prune_kept = kept;
+    g_prune_total = total;
+  }
   if (timing) CPPGB_CUDA_TRY(cudaEventRecord(g_timer.ev[1], st));
 
   DenseScalars h;
   for (int pass = 0; pass < 2; ++pass) {
     if (is_filter(mode))
-      rc = launch_gram_tc(L.X, mode, n, L.n_pad, L.Kp, excl, L.norms, L.sc, L.cand, L.cap, st, shard, nshards);
+      rc = launch_gram_tc(L.X, mode, n, L.n_pad, L.Kp, excl, L.norms, L.sc, L.cand, L.cap, st, shard, nshards, tlist,
+                          tcount);
     else
       rc = launch_gram_simt((const float*)L.X, n, L.Kp, excl, L.norms, L.sc, L.cand, L.cap, st, shard, nshards);
     if (rc) return rc;
@@ -204,7 +259,7 @@ int dense_search(const Source& src, int64_t n, int64_t d, int64_t excl, int mode
                        "candidate buffer overflow (%llu > %lld) at the final bound: many pairs tie within the "
                        "filter's error; pass a workspace of %zu bytes",
                        (unsigned long long)h.n_cand, (long long)L.cap,
-                       dense_layout(nullptr, n, d, mode).bytes +
+                       dense_layout(nullptr, n, d, mode | (prune ? CPPGB_MODE_PRUNE : 0)).bytes +
                            (size_t)(h.n_cand - L.cap) * (sizeof(Candidate) + sizeof(double)) + 4096);
     }
     // The bound U is final now; a second pass emits only pairs whose lower bound meets it.
@@ -304,6 +359,13 @@ int cpp_stage_times(double* ms, int cap) {
 }
 
 int64_t cpp_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int cpp_prune_stats(int64_t* tiles_kept, int64_t* tiles_total) {
+  if (!tiles_kept || !tiles_total) return set_error(CPPGB_ERR_ARG, "NULL argument");
+  *tiles_kept = g_prune_kept;
+  *tiles_total = g_prune_total;
+  return CPPGB_OK;
+}
 
 // ------------------------------------------------------------------ closest pair
 size_t cpp_closest_pair_workspace_size(int64_t n, int64_t d, int mode) {

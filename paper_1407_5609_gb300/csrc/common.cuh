@@ -130,7 +130,8 @@ int launch_gram_simt_radius(const float* X, int64_t n, int64_t Kp, const float* 
 // Dense all-pairs stage on tcgen05 tensor cores (FP16 or BF16 operands).
 int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp, int64_t excl,
                    const float* norms, DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st,
-                   int64_t shard = 0, int64_t nshards = 1);
+                   int64_t shard = 0, int64_t nshards = 1,
+                   const int32_t* tlist = nullptr, const int64_t* tcount = nullptr);
 bool gram_tc_available();
 
 // Tuning policy, process-wide (set through cpp_set_tuning, normally from the autotuner's cache).
@@ -159,6 +160,28 @@ int launch_bounds(DenseScalars* sc, float kappa, cudaStream_t st);
 size_t scan_temp_elems(int64_t n);
 int launch_exclusive_scan_i32(const int32_t* in, int64_t n, int64_t* out, int64_t* tmp, cudaStream_t st);
 int launch_exclusive_scan_i64(const int64_t* in, int64_t n, int64_t* out, int64_t* tmp, cudaStream_t st);
+
+// Reference pruning of the tensor-core dense stage's tiles (prune.cu, gram_tc.cu).
+constexpr int PRUNE_REFS = 10;  // reference rows
+constexpr int PRUNE_SEEDS = 3;  // partners per row in the reference order that seed U0
+struct PruneRefs {
+  int64_t row[PRUNE_REFS];
+};
+// lo / hi [PRUNE_REFS][n_pad]: intervals of each row's exact distance to each reference;
+// blo / bhi [PRUNE_REFS][n_pad / 128]: their hulls per 128-row block.
+int launch_prune_intervals(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp, const float* norms,
+                           const float* eps, const DenseScalars* sc, float* lo, float* hi, float* blo, float* bhi,
+                           cudaStream_t st);
+// Sort by reference 0 and lower U with the seed pairs' bounded distances (U0).
+int launch_prune_seeds(const void* X, int mode, int64_t Kp, const float* norms, const float* eps, const float* lo,
+                       const float* hi, int64_t n, int64_t excl, DenseScalars* sc, int32_t* hist, int32_t* cursor,
+                       int64_t* start, int64_t* tmp, int32_t* perm, cudaStream_t st);
+// Tiles of the tensor-core schedule (this shard's) that the block intervals cannot exclude at the
+// current bound U: flags, compacted list (increasing) and its count at list_count[0].
+int64_t gram_tc_tile_count(int64_t n, int64_t n_pad, int64_t excl, int64_t shard, int64_t nshards);
+int launch_gram_tc_prune_list(int64_t n, int64_t n_pad, int64_t excl, const float* blo, const float* bhi,
+                              const DenseScalars* sc, int32_t* flags, int64_t* pos, int64_t* tmp, int32_t* list,
+                              cudaStream_t st, int64_t shard, int64_t nshards);
 
 // Two-locus scan.
 int launch_twolocus(const uint64_t* planes, int64_t S, int64_t W, int64_t m1, int64_t m2, void* partials,

@@ -175,6 +175,45 @@ __device__ __forceinline__ void epi_publish(int lane, const BoundParams& bp, Den
   }
 }
 
+// ------------------------------------------------------------------ reference pruning of tiles
+// A tile (row block bi, column block bj = row blocks 2bj, 2bj + 1) is kept unless, for some
+// reference, the gap between the row block's and the column block's distance intervals exceeds
+// sqrt(U): then no pair of the tile is within sqrt(U) of the other (triangle inequality).
+__global__ void prune_flags_kernel(const __grid_constant__ TileSched ts, int64_t total, int64_t shard,
+                                   int64_t nshards, const float* __restrict__ blo, const float* __restrict__ bhi,
+                                   int64_t nbi, const DenseScalars* sc, int32_t* __restrict__ flags) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  int band = 0;
+  int64_t lo_b = 0, hi_b = ts.nbands;  // band of tile id g: largest b with off[b] <= g
+  const int64_t g = t * nshards + shard;
+  while (lo_b + 1 < hi_b) {
+    const int64_t mid = (lo_b + hi_b) >> 1;
+    if (ts.off[mid] <= g) lo_b = mid;
+    else hi_b = mid;
+  }
+  band = (int)lo_b;
+  int64_t bi, bj;
+  decode_tile(ts, g, &band, &bi, &bj);
+  const float U = __uint_as_float(sc->U_bits);
+  const float th = sqrtf(U) * (1.f + 0x1p-20f) + 1e-30f;
+  const int64_t c0 = 2 * bj, c1 = 2 * bj + 1 < nbi ? 2 * bj + 1 : 2 * bj;
+  float lb = 0.f;
+#pragma unroll
+  for (int q = 0; q < PRUNE_REFS; ++q) {
+    const float ilo = blo[q * nbi + bi], ihi = bhi[q * nbi + bi];
+    const float jlo = fminf(blo[q * nbi + c0], blo[q * nbi + c1]), jhi = fmaxf(bhi[q * nbi + c0], bhi[q * nbi + c1]);
+    lb = fmaxf(lb, fmaxf(__fsub_rd(jlo, ihi), __fsub_rd(ilo, jhi)));
+  }
+  flags[t] = (U < __int_as_float(0x7f800000) && lb > th) ? 0 : 1;
+}
+
+__global__ void prune_compact_kernel(int64_t total, int64_t shard, int64_t nshards, const int32_t* __restrict__ flags,
+                                     const int64_t* __restrict__ pos, int32_t* __restrict__ list) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < total && flags[t]) list[pos[t]] = (int32_t)(t * nshards + shard);
+}
+
 struct SmemCtl {
   uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
   uint32_t tmem_base;
@@ -182,9 +221,12 @@ struct SmemCtl {
 };
 
 __global__ void __launch_bounds__(NTHREADS, 1)
-    gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TileSched ts, int64_t total,
+    gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TileSched ts, int64_t total_arg,
                    uint32_t ab_fmt, const float* __restrict__ norms, DenseScalars* sc, Candidate* __restrict__ cand,
-                   int64_t cap, int64_t kchunks, int64_t shard, int64_t nshards) {
+                   int64_t cap, int64_t kchunks, int64_t shard, int64_t nshards, const int32_t* __restrict__ tlist,
+                   const int64_t* __restrict__ tcount) {
+  // the tiles: k < total of this shard (t = k * nshards + shard), or the entries of a pruned list
+  const int64_t total = tcount ? *tcount : total_arg;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   SmemCtl* ctl = (SmemCtl*)(smem + STAGES * STAGE_BYTES);
@@ -225,7 +267,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
         int64_t bi, bj;
-        decode_tile(ts, t * nshards + shard, &band, &bi, &bj);
+        decode_tile(ts, tlist ? (int64_t)tlist[t] : t * nshards + shard, &band, &bi, &bj);
         for (int64_t kc = 0; kc < kchunks; ++kc) {
           if (!mbar_wait(&ctl->empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
           uint8_t* sa = smem + stage * STAGE_BYTES;
@@ -297,7 +339,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int band = 0;
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++it) {
       int64_t bi, bj;
-      decode_tile(ts, t * nshards + shard, &band, &bi, &bj);
+      decode_tile(ts, tlist ? (int64_t)tlist[t] : t * nshards + shard, &band, &bi, &bj);
       const uint32_t acc = (uint32_t)(it & 1), use = (uint32_t)((it >> 1) & 1);
       const bool got = __all_sync(0xffffffffu, mbar_wait(&ctl->tfull[acc], use, abort_flag));
       if (!got) {
@@ -349,12 +391,9 @@ EncodeTiledFn encode_fn() {
 
 bool gram_tc_available() { return true; }
 
-int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp, int64_t excl, const float* norms,
-                   DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st, int64_t shard, int64_t nshards) {
-  if (Kp % BK || n_pad % BN) return set_error(CPPGB_ERR_ARG, "internal: tensor-core stage needs Kp %% 64 == 0");
-  if (((uintptr_t)X & 15) != 0) return set_error(CPPGB_ERR_ARG, "internal: row matrix must be 16-byte aligned");
-  if (n_pad > 0x7fffffffLL || Kp > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "problem too large for TMA coordinates");
-  TileSched ts;  // kernel parameter (copied at launch)
+namespace {
+// The band schedule of all tiles; returns their number.
+int64_t build_sched(int64_t n, int64_t n_pad, int64_t excl, TileSched& ts) {
   ts.n = n;
   ts.excl = excl;
   ts.nbi = (int32_t)(n_pad / BM);
@@ -379,9 +418,47 @@ int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp
     ts.nfull[b] = nf;
   }
   ts.off[ts.nbands] = total;
-  // this shard's tiles are t = k * nshards + shard; the kernel walks k
-  const int64_t all_tiles = total;
-  total = all_tiles > shard ? (all_tiles - shard + nshards - 1) / nshards : 0;
+  return total;
+}
+}  // namespace
+
+int64_t gram_tc_tile_count(int64_t n, int64_t n_pad, int64_t excl, int64_t shard, int64_t nshards) {
+  TileSched ts;
+  const int64_t all_tiles = build_sched(n, n_pad, excl, ts);
+  return all_tiles > shard ? (all_tiles - shard + nshards - 1) / nshards : 0;
+}
+
+int launch_gram_tc_prune_list(int64_t n, int64_t n_pad, int64_t excl, const float* blo, const float* bhi,
+                              const DenseScalars* sc, int32_t* flags, int64_t* pos, int64_t* tmp, int32_t* list,
+                              cudaStream_t st, int64_t shard, int64_t nshards) {
+  TileSched ts;
+  const int64_t all_tiles = build_sched(n, n_pad, excl, ts);
+  const int64_t total = all_tiles > shard ? (all_tiles - shard + nshards - 1) / nshards : 0;
+  if (total > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "too many tiles for the pruned list");
+  if (total == 0) {
+    CPPGB_CUDA_TRY(cudaMemsetAsync(pos, 0, sizeof(int64_t), st));
+    return CPPGB_OK;
+  }
+  const unsigned nb = (unsigned)((total + 255) / 256);
+  prune_flags_kernel<<<nb, 256, 0, st>>>(ts, total, shard, nshards, blo, bhi, n_pad / BM, sc, flags);
+  CPPGB_LAUNCH_CHECK();
+  int rc = launch_exclusive_scan_i32(flags, total, pos, tmp, st);  // pos[total] = kept tiles
+  if (rc) return rc;
+  prune_compact_kernel<<<nb, 256, 0, st>>>(total, shard, nshards, flags, pos, list);
+  CPPGB_LAUNCH_CHECK();
+  return CPPGB_OK;
+}
+
+int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp, int64_t excl, const float* norms,
+                   DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st, int64_t shard, int64_t nshards,
+                   const int32_t* tlist, const int64_t* tcount) {
+  if (Kp % BK || n_pad % BN) return set_error(CPPGB_ERR_ARG, "internal: tensor-core stage needs Kp %% 64 == 0");
+  if (((uintptr_t)X & 15) != 0) return set_error(CPPGB_ERR_ARG, "internal: row matrix must be 16-byte aligned");
+  if (n_pad > 0x7fffffffLL || Kp > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "problem too large for TMA coordinates");
+  TileSched ts;  // kernel parameter (copied at launch)
+  const int64_t all_tiles = build_sched(n, n_pad, excl, ts);
+  // this shard's tiles are t = k * nshards + shard; the kernel walks k (or the pruned list's entries)
+  const int64_t total = all_tiles > shard ? (all_tiles - shard + nshards - 1) / nshards : 0;
   if (total == 0) return CPPGB_OK;
 
   EncodeTiledFn enc = encode_fn();
@@ -404,8 +481,8 @@ int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp
   const size_t smem = (size_t)STAGES * STAGE_BYTES + sizeof(SmemCtl) + 1024;
   CPPGB_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t grid = total < sms ? total : sms;
-  gram_tc_kernel<<<(unsigned)grid, NTHREADS, smem, st>>>(tmap, ts, total, ab,
-                                                         norms, sc, cand, cap, Kp / BK, shard, nshards);
+  gram_tc_kernel<<<(unsigned)grid, NTHREADS, smem, st>>>(tmap, ts, total, ab, norms, sc, cand, cap, Kp / BK, shard,
+                                                         nshards, tlist, tcount);
   CPPGB_LAUNCH_CHECK();
   return CPPGB_OK;
 }

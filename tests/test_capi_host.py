@@ -53,6 +53,11 @@ def test_workspace_queries(libpath):
     assert capi.tsmm_motif_workspace_size(10, 20, 0) == 0
     assert capi.twolocus_scan_workspace_size(4096, 64) > 0
     assert capi.twolocus_scan_workspace_size(4096, 0) == 0
+    # reference pruning: only with a tensor-core filter mode, and it needs its own buffers
+    assert capi.tsmm_motif_workspace_size(262144, 512, "filter_bf16_prune") > \
+        capi.tsmm_motif_workspace_size(262144, 512, "filter_bf16")
+    assert capi.cpp_closest_pair_workspace_size(4096, 32, capi.MODE_PRUNE) == 0
+    assert capi.cpp_closest_pair_workspace_size(4096, 32, 3 | capi.MODE_PRUNE) == 0
 
 
 def test_argument_errors_need_no_gpu(libpath):
