@@ -489,7 +489,7 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "strong" if sharded else "weak", "vs_baseline": None,
-           "dtype": ({"plain_fp32": "f32", "filter_fp16": "f16", "filter_bf16": "bf16"}.get(mode)
+           "dtype": ({"plain_fp32": "f32", "filter_fp16": "f16", "filter_bf16": "bf16"}.get(mode.replace("_prune", ""))
                      if wl.name in ("tsmm", "cpp") else {"frnn": "f32", "twolocus": "u64", "batch": "f32"}[wl.name]),
            "data": "synthetic", "config": dict(wl.config, mode=mode if wl.name in ("tsmm", "cpp") else None,
                                                flush_l2_between_steps=bool(flush),
@@ -508,6 +508,10 @@ def run_ours(args):
             peak, bound, unit, src = FP32_ALU_PEAK_TFLOPS, "alu", "TFLOP/s", "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"
         else:
             peak, bound, unit, src = pk["bf16_tflops"], "tensor", "TFLOP/s", f"{pk['source']} bf16 burst"
+        if mode.endswith("_prune"):  # only the kept tiles are evaluated
+            kept, total = capi.cpp_prune_stats()
+            if total > 0:
+                flops = flops * kept / total
         ach = flops / (avg_ms / 1e3) / 1e12 if avg_ms else None
         key = f"dense_{mode}@{wl.name}"
         out["roofline"] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
@@ -570,7 +574,7 @@ def run_ours(args):
                              "same_answer": (pres["i"], pres["j"], pres["dist2"]) == (res["i"], res["j"], res["dist2"])}
 
     # the same search with reference pruning of tiles (MK / MPR bound): same answer, fewer tiles
-    if wl.name in ("tsmm", "cpp") and mode != "plain_fp32" and not args.no_compare:
+    if wl.name in ("tsmm", "cpp") and mode != "plain_fp32" and not mode.endswith("_prune") and not args.no_compare:
         barrier()
         pmode = mode + "_prune"
         wl.step(capi, pmode)                               # warm-up
@@ -647,7 +651,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tsmm")
-    ap.add_argument("--mode", choices=["plain_fp32", "filter_fp16", "filter_bf16"], default=None)
+    ap.add_argument("--mode", choices=["plain_fp32", "filter_fp16", "filter_bf16", "filter_fp16_prune",
+                                       "filter_bf16_prune"], default=None)
     ap.add_argument("--batch-count", type=int, default=2048,
                     help="instances of the batch workload (smaller values only for profiler captures)")
     ap.add_argument("--series-len", type=int, default=262144,

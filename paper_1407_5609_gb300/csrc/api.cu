@@ -111,8 +111,9 @@ struct DenseLayout {
   float* norms;
   float* eps;
   void* X;
-  // reference pruning (CPPGB_MODE_PRUNE)
-  float *plo, *phi, *pblo, *pbhi;
+  // reference pruning (CPPGB_MODE_PRUNE): intervals, sort, and the rows in the sorted order
+  float *plo, *phi, *pblo, *pbhi, *norms_s;
+  void* Xs;
   int32_t *hist, *cursor, *perm, *flags, *list;
   int64_t *start, *pos, *ptmp;
   Candidate* cand;
@@ -149,6 +150,8 @@ DenseLayout dense_layout(void* ws, int64_t n, int64_t d, int mode, size_t ws_byt
     L.pos = c.take<int64_t>(tiles + 1);
     L.list = c.take<int32_t>(tiles);
     L.ptmp = c.take<int64_t>(scan_temp_elems(tiles > 65536 ? tiles : 65536));
+    L.Xs = c.take<char>((size_t)L.n_pad * L.Kp * L.elem);
+    L.norms_s = c.take<float>(L.n_pad);
   }
   const size_t fixed = c.bytes() + 512;
   if (ws_bytes > fixed) {
@@ -215,6 +218,10 @@ int dense_search(const Source& src, int64_t n, int64_t d, int64_t excl, int mode
   // neighbours in the order of reference 0, then the list of tiles the intervals cannot exclude.
   const int32_t* tlist = nullptr;
   const int64_t* tcount = nullptr;
+  const void* Xd = L.X;          // the dense stage's rows, norms, original-index map and schedule exclusion
+  const float* normsd = L.norms;
+  const int32_t* permd = nullptr;
+  int64_t excl_sched = excl;
   if (prune && n >= 2) {
     if ((rc = launch_prune_intervals(L.X, mode, n, L.n_pad, L.Kp, L.norms, L.eps, L.sc, L.plo, L.phi, L.pblo, L.pbhi,
                                      st)))
@@ -222,9 +229,21 @@ int dense_search(const Source& src, int64_t n, int64_t d, int64_t excl, int mode
     if ((rc = launch_prune_seeds(L.X, mode, L.Kp, L.norms, L.eps, L.plo, L.phi, n, excl, L.sc, L.hist, L.cursor,
                                  L.start, L.ptmp, L.perm, st)))
       return rc;
-    const int64_t total = gram_tc_tile_count(n, L.n_pad, excl, shard, nshards);
-    if ((rc = launch_gram_tc_prune_list(n, L.n_pad, excl, L.pblo, L.pbhi, L.sc, L.flags, L.pos, L.ptmp, L.list, st,
-                                        shard, nshards)))
+    // One search: the rows go into the order of their distance to reference 0 (as in Algorithm MK),
+    // which makes the blocks' intervals narrow.  The counting sort's order inside a bucket is not
+    // reproducible, so shards of a search (which must partition the same pairs) keep the original order.
+    if (nshards == 1) {
+      if ((rc = launch_prune_permute(L.X, n, L.n_pad, L.Kp, L.norms, L.perm, L.plo, L.phi, L.Xs, L.norms_s, L.pblo,
+                                     L.pbhi, st)))
+        return rc;
+      Xd = L.Xs;
+      normsd = L.norms_s;
+      permd = L.perm;
+      excl_sched = 1;
+    }
+    const int64_t total = gram_tc_tile_count(n, L.n_pad, excl_sched, shard, nshards);
+    if ((rc = launch_gram_tc_prune_list(n, L.n_pad, excl_sched, L.pblo, L.pbhi, L.sc, L.flags, L.pos, L.ptmp, L.list,
+                                        st, shard, nshards)))
       return rc;
     tlist = L.list;
     tcount = L.pos + total;
@@ -239,8 +258,8 @@ int dense_search(const Source& src, int64_t n, int64_t d, int64_t excl, int mode
   DenseScalars h;
   for (int pass = 0; pass < 2; ++pass) {
     if (is_filter(mode))
-      rc = launch_gram_tc(L.X, mode, n, L.n_pad, L.Kp, excl, L.norms, L.sc, L.cand, L.cap, st, shard, nshards, tlist,
-                          tcount);
+      rc = launch_gram_tc(Xd, mode, n, L.n_pad, L.Kp, excl_sched, normsd, L.sc, L.cand, L.cap, st, shard, nshards,
+                          tlist, tcount, permd, excl);
     else
       rc = launch_gram_simt((const float*)L.X, n, L.Kp, excl, L.norms, L.sc, L.cand, L.cap, st, shard, nshards);
     if (rc) return rc;

@@ -131,7 +131,8 @@ int launch_gram_simt_radius(const float* X, int64_t n, int64_t Kp, const float* 
 int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp, int64_t excl,
                    const float* norms, DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st,
                    int64_t shard = 0, int64_t nshards = 1,
-                   const int32_t* tlist = nullptr, const int64_t* tcount = nullptr);
+                   const int32_t* tlist = nullptr, const int64_t* tcount = nullptr,
+                   const int32_t* perm = nullptr, int64_t excl_orig = 1);
 bool gram_tc_available();
 
 // Tuning policy, process-wide (set through cpp_set_tuning, normally from the autotuner's cache).
@@ -172,6 +173,11 @@ struct PruneRefs {
 int launch_prune_intervals(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp, const float* norms,
                            const float* eps, const DenseScalars* sc, float* lo, float* hi, float* blo, float* bhi,
                            cudaStream_t st);
+// Rows (16-bit), norms and block intervals in the order `perm` (sorted position -> original row);
+// rows past n are zero.
+int launch_prune_permute(const void* X, int64_t n, int64_t n_pad, int64_t Kp, const float* norms,
+                         const int32_t* perm, const float* lo, const float* hi, void* Xs, float* norms_s, float* blo,
+                         float* bhi, cudaStream_t st);
 // Sort by reference 0 and lower U with the seed pairs' bounded distances (U0).
 int launch_prune_seeds(const void* X, int mode, int64_t Kp, const float* norms, const float* eps, const float* lo,
                        const float* hi, int64_t n, int64_t excl, DenseScalars* sc, int32_t* hist, int32_t* cursor,

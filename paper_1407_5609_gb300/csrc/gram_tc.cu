@@ -100,12 +100,22 @@ __device__ __forceinline__ void epi_init(EpiState& es, DenseScalars* sc, const B
 
 // One thread = one accumulator row (TMEM lane) of a 128 x 256 tile: D~ = nx + (ny - 2 S) for its 256
 // columns in 32-column chunks, running minimum, threshold test per chunk, rare candidate emission.
+// With `perm` the rows are a permutation of the original ones (row p is original row perm[p]): the
+// schedule covers the pairs p < q of positions, a pair is excluded when its original indices are
+// closer than excl_orig, and candidates carry original indices (smaller first).
+template <bool PERM>
 __device__ __forceinline__ void epi_tile(int64_t row0, int64_t col0, uint32_t tbase, int lane, uint32_t quarter,
                                          int64_t n, int64_t excl, const float* __restrict__ norms,
                                          const BoundParams& bp, DenseScalars* sc, Candidate* __restrict__ cand,
-                                         int64_t cap, EpiState& es) {
+                                         int64_t cap, EpiState& es, const int32_t* __restrict__ perm,
+                                         int64_t excl_orig) {
   const int64_t i = row0 + quarter * 32 + lane;
   const float nx = norms[i];
+  const bool pmask = PERM && excl_orig > 1;
+  const int32_t oi = PERM && i < n ? perm[i] : (int32_t)i;
+  // |oi - oj| < excl_orig  <=>  (unsigned)(oi - oj + excl_orig - 1) < 2 excl_orig - 1
+  const int32_t xoff = (int32_t)excl_orig - 1;
+  const uint32_t xspan = 2u * (uint32_t)excl_orig - 1u;
   const bool edge = (row0 + BM - 1 >= n) || (col0 + BN - 1 >= n) || (col0 - (row0 + BM - 1) < excl);
 #pragma unroll 1
   for (int c = 0; c < BN / 32; ++c) {
@@ -130,6 +140,17 @@ __device__ __forceinline__ void epi_tile(int64_t row0, int64_t col0, uint32_t tb
         if (!(i < n && j < n && j - i >= excl)) dp[k] = __int_as_float(0x7f800000);
       }
     }
+    if (PERM && pmask) {  // original indices of the chunk's columns (the same for every lane: broadcast loads)
+      const int4* pj4 = reinterpret_cast<const int4*>(perm + col0 + c * 32);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int4 o = __ldg(pj4 + q);
+        const int32_t oj[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if ((uint32_t)(oi - oj[e] + xoff) < xspan) dp[4 * q + e] = __int_as_float(0x7f800000);
+      }
+    }
 #pragma unroll
     for (int k = 0; k < 32; ++k) cmin = fminf(cmin, dp[k]);
     const float cD = nx + cmin;
@@ -145,8 +166,13 @@ __device__ __forceinline__ void epi_tile(int64_t row0, int64_t col0, uint32_t tb
           const unsigned long long slot = atomicAdd(&sc->n_cand, 1ull);
           if ((int64_t)slot < cap) {
             Candidate cd;
-            cd.i = (int32_t)i;
-            cd.j = (int32_t)(col0 + c * 32 + k);
+            int32_t a = (int32_t)i, b = (int32_t)(col0 + c * 32 + k);
+            if (PERM) {
+              a = oi;
+              b = perm[col0 + c * 32 + k];
+            }
+            cd.i = a < b ? a : b;
+            cd.j = a < b ? b : a;
             cd.d2f = D;
             cd.pad = 0.f;
             cand[slot] = cd;
@@ -220,11 +246,12 @@ struct SmemCtl {
   int abort_flag;
 };
 
+template <bool PERM>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TileSched ts, int64_t total_arg,
                    uint32_t ab_fmt, const float* __restrict__ norms, DenseScalars* sc, Candidate* __restrict__ cand,
                    int64_t cap, int64_t kchunks, int64_t shard, int64_t nshards, const int32_t* __restrict__ tlist,
-                   const int64_t* __restrict__ tcount) {
+                   const int64_t* __restrict__ tcount, const int32_t* __restrict__ perm, int64_t excl_orig) {
   // the tiles: k < total of this shard (t = k * nshards + shard), or the entries of a pruned list
   const int64_t total = tcount ? *tcount : total_arg;
   extern __shared__ uint8_t smem_raw[];
@@ -351,7 +378,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       tc_fence_after();
       const uint32_t tbase = tmem_base + ((quarter * 32u) << 16) + acc * (uint32_t)BN;
-      epi_tile(bi * BM, bj * BN, tbase, lane, quarter, ts.n, ts.excl, norms, bp, sc, cand, cap, es);
+      epi_tile<PERM>(bi * BM, bj * BN, tbase, lane, quarter, ts.n, ts.excl, norms, bp, sc, cand, cap, es, perm,
+                     excl_orig);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&ctl->tempty[acc]);
@@ -451,7 +479,7 @@ int launch_gram_tc_prune_list(int64_t n, int64_t n_pad, int64_t excl, const floa
 
 int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp, int64_t excl, const float* norms,
                    DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st, int64_t shard, int64_t nshards,
-                   const int32_t* tlist, const int64_t* tcount) {
+                   const int32_t* tlist, const int64_t* tcount, const int32_t* perm, int64_t excl_orig) {
   if (Kp % BK || n_pad % BN) return set_error(CPPGB_ERR_ARG, "internal: tensor-core stage needs Kp %% 64 == 0");
   if (((uintptr_t)X & 15) != 0) return set_error(CPPGB_ERR_ARG, "internal: row matrix must be 16-byte aligned");
   if (n_pad > 0x7fffffffLL || Kp > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "problem too large for TMA coordinates");
@@ -479,10 +507,16 @@ int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp
   CPPGB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const uint32_t ab = mode == CPPGB_MODE_FILTER_BF16 ? 1u : 0u;
   const size_t smem = (size_t)STAGES * STAGE_BYTES + sizeof(SmemCtl) + 1024;
-  CPPGB_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t grid = total < sms ? total : sms;
-  gram_tc_kernel<<<(unsigned)grid, NTHREADS, smem, st>>>(tmap, ts, total, ab, norms, sc, cand, cap, Kp / BK, shard,
-                                                         nshards, tlist, tcount);
+  if (perm) {
+    CPPGB_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    gram_tc_kernel<true><<<(unsigned)grid, NTHREADS, smem, st>>>(tmap, ts, total, ab, norms, sc, cand, cap, Kp / BK,
+                                                                 shard, nshards, tlist, tcount, perm, excl_orig);
+  } else {
+    CPPGB_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    gram_tc_kernel<false><<<(unsigned)grid, NTHREADS, smem, st>>>(tmap, ts, total, ab, norms, sc, cand, cap, Kp / BK,
+                                                                  shard, nshards, tlist, tcount, nullptr, 1);
+  }
   CPPGB_LAUNCH_CHECK();
   return CPPGB_OK;
 }

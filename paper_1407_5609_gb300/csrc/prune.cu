@@ -80,19 +80,36 @@ __global__ void __launch_bounds__(256) ref_interval_kernel(const T* __restrict__
 }
 
 // Hull of the rows' intervals per 128-row block and reference (rows < n only; an empty block gets
-// the empty interval [+inf, -inf], which no gap test can prune against).
+// the empty interval [+inf, -inf], which excludes every tile it takes part in -- it holds no pair).
+// With `perm`, block b holds the rows perm[128 b ..] (sorted positions).
 __global__ void block_interval_kernel(const float* __restrict__ lo, const float* __restrict__ hi, int64_t n,
-                                      int64_t n_pad, int64_t nbi, float* __restrict__ blo, float* __restrict__ bhi) {
+                                      int64_t n_pad, int64_t nbi, const int32_t* __restrict__ perm,
+                                      float* __restrict__ blo, float* __restrict__ bhi) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)PRUNE_REFS * nbi) return;
   const int64_t q = e / nbi, b = e % nbi;
   float a = __int_as_float(0x7f800000), z = __int_as_float(0xff800000);
-  for (int64_t i = b * 128; i < b * 128 + 128 && i < n; ++i) {
+  for (int64_t p = b * 128; p < b * 128 + 128 && p < n; ++p) {
+    const int64_t i = perm ? (int64_t)perm[p] : p;
     a = fminf(a, lo[q * n_pad + i]);
     z = fmaxf(z, hi[q * n_pad + i]);
   }
   blo[e] = a;
   bhi[e] = z;
+}
+
+// Xs[p] = X[perm[p]] (16-byte words), norms_s[p] = norms[perm[p]]; zero rows past n.
+__global__ void permute_rows_kernel(const uint4* __restrict__ X, int64_t n, int64_t n_pad, int64_t words,
+                                    const float* __restrict__ norms, const int32_t* __restrict__ perm,
+                                    uint4* __restrict__ Xs, float* __restrict__ norms_s) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t p = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); p < n_pad; p += (int64_t)gridDim.x * wpb) {
+    const int64_t src = p < n ? (int64_t)perm[p] : -1;
+    for (int64_t w = lane; w < words; w += 32)
+      Xs[p * words + w] = src >= 0 ? X[src * words + w] : make_uint4(0u, 0u, 0u, 0u);
+    if (lane == 0) norms_s[p] = src >= 0 ? norms[src] : 0.f;
+  }
 }
 
 // Counting sort of the rows by their distance to reference 0 (65536 buckets over [0, vmax]); the
@@ -186,7 +203,24 @@ int launch_prune_intervals(const void* X, int mode, int64_t n, int64_t n_pad, in
   }
   CPPGB_LAUNCH_CHECK();
   const int64_t nbi = n_pad / 128;
-  block_interval_kernel<<<(unsigned)((PRUNE_REFS * nbi + 255) / 256), 256, 0, st>>>(lo, hi, n, n_pad, nbi, blo, bhi);
+  block_interval_kernel<<<(unsigned)((PRUNE_REFS * nbi + 255) / 256), 256, 0, st>>>(lo, hi, n, n_pad, nbi, nullptr,
+                                                                                   blo, bhi);
+  CPPGB_LAUNCH_CHECK();
+  return CPPGB_OK;
+}
+
+int launch_prune_permute(const void* X, int64_t n, int64_t n_pad, int64_t Kp, const float* norms,
+                         const int32_t* perm, const float* lo, const float* hi, void* Xs, float* norms_s, float* blo,
+                         float* bhi, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  CPPGB_CUDA_TRY(cudaGetDevice(&dev));
+  CPPGB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  permute_rows_kernel<<<(unsigned)(8 * sms), 256, 0, st>>>((const uint4*)X, n, n_pad, Kp * 2 / 16, norms, perm,
+                                                           (uint4*)Xs, norms_s);
+  CPPGB_LAUNCH_CHECK();
+  const int64_t nbi = n_pad / 128;
+  block_interval_kernel<<<(unsigned)((PRUNE_REFS * nbi + 255) / 256), 256, 0, st>>>(lo, hi, n, n_pad, nbi, perm, blo,
+                                                                                   bhi);
   CPPGB_LAUNCH_CHECK();
   return CPPGB_OK;
 }
