@@ -43,6 +43,7 @@ _i64p = ctypes.POINTER(ctypes.c_int64)
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _f64p = ctypes.POINTER(ctypes.c_double)
 _i8p = ctypes.POINTER(ctypes.c_int8)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
 
 
 class OracleError(RuntimeError):
@@ -87,6 +88,10 @@ def _load():
                                                           _i64p, _i64p, ctypes.c_int64, _i32p, _i32p, _i64p]),
                 "oracle_twolocus_rows": (ctypes.c_int, [_i8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                                         _i64p, ctypes.c_int64, _i64p, _i64p]),
+                "oracle_twolocus_pearson": (ctypes.c_int, [_i8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                                           _i64p, _i64p, _f64p]),
+                "oracle_hamming": (ctypes.c_int, [_u8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                                  _i64p, _i64p, _i64p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -229,3 +234,23 @@ def twolocus_rows(g, m1: int, m2: int, rows):
     _check(_load().oracle_twolocus_rows(_p(g, _i8p), g.shape[0], m1, m2, _p(rows, _i64p), rows.shape[0],
                                         _p(bj, _i64p), _p(bs, _i64p)), "twolocus_rows")
     return bj, bs
+
+
+def twolocus_pearson(g, m1: int, m2: int):
+    """Returns (i, j, score); score = |r_A - r_B| with Pearson's r of the genotype values per group."""
+    g = np.ascontiguousarray(g, dtype=np.int8)
+    assert g.shape[1] == m1 + m2
+    bi, bj, sc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    _check(_load().oracle_twolocus_pearson(_p(g, _i8p), g.shape[0], m1, m2, ctypes.byref(bi), ctypes.byref(bj),
+                                           ctypes.byref(sc)), "twolocus_pearson")
+    return bi.value, bj.value, sc.value
+
+
+def hamming(strings, sigma: int, least: bool = False):
+    """Closest (least=False) or least correlated (least=True) pair of the rows of a uint8 [n][t]
+    symbol matrix; returns (i, j, mismatches)."""
+    s = np.ascontiguousarray(strings, dtype=np.uint8)
+    bi, bj, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_load().oracle_hamming(_p(s, _u8p), s.shape[0], s.shape[1], sigma, 1 if least else 0, ctypes.byref(bi),
+                                  ctypes.byref(bj), ctypes.byref(d)), "hamming")
+    return bi.value, bj.value, d.value

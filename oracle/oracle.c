@@ -21,12 +21,23 @@
  *                     match-count correlation of Sec. 2 / Sec. 5.3
  *   oracle_twolocus_tables / oracle_twolocus_rows   3x3 tables for chosen
  *                     pairs, best partner for chosen rows
+ *   oracle_twolocus_pearson   the same argmax with Pearson's correlation of the
+ *                     genotype values within each group (the measure Sec. 5 and
+ *                     Sec. 6 attribute to the light-bulb/LSH method they compare
+ *                     with)
+ *   oracle_hamming    closest (or least correlated) pair of strings over an
+ *                     alphabet of sigma symbols under the Hamming distance, Sec. 4
+ *                     (and Sec. 5 for the least correlated pair)
  *
  * Readings taken where the paper is silent (each also listed in the design
  * notes): ties go to the lexicographically smallest (d^2, i, j) with i < j;
  * z-normalisation uses the population standard deviation; a motif pair needs
  * j - i >= excl; FRNN uses "<= R" and excludes the point itself; two-locus
- * compares |u_A*m2 - u_B*m1| exactly in integers (u = matches).
+ * compares |u_A*m2 - u_B*m1| exactly in integers (u = matches); Pearson's r is
+ * (m Sxy - Sx Sy) / sqrt(vx vy) with vx = m Sxx - Sx^2 (exact integers, one FP64
+ * product, square root and division), 0 when a variance is 0, and the score
+ * |r_A - r_B| is compared as a double (ties to the smallest (i, j)); Hamming
+ * pairs are ranked by their number of mismatches (ties to the smallest (i, j)).
  *
  * Build: plain C99, -O2 -ffp-contract=off (no FMA contraction, so every sum is
  * a rounded add of a rounded product, in index order), OpenMP over the outer
@@ -392,5 +403,95 @@ int oracle_twolocus_rows(const int8_t* g, int64_t S, int64_t m1, int64_t m2, con
     best_j[p] = bjj;
     best_score[p] = bs;
   }
+  return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------ Pearson two-locus */
+/* Pearson's r of the genotype values (0, 1, 2) of SNPs i and j over the subjects [lo, hi):
+ * r = (m Sxy - Sx Sy) / sqrt(vx vy), vx = m Sxx - Sx^2, vy = m Syy - Sy^2, all sums exact in
+ * integers; vx vy is exact in FP64 (below 2^53 for m < 2^20); 0 when vx or vy is 0. */
+static double pearson_of(const int8_t* gi, const int8_t* gj, int64_t lo, int64_t hi) {
+  int64_t sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0, m = hi - lo;
+  for (int64_t t = lo; t < hi; ++t) {
+    int64_t x = gi[t], y = gj[t];
+    sx += x; sy += y; sxx += x * x; syy += y * y; sxy += x * y;
+  }
+  int64_t vx = m * sxx - sx * sx, vy = m * syy - sy * sy;
+  if (vx == 0 || vy == 0) return 0.0;
+  double num = (double)(m * sxy - sx * sy);
+  double den = sqrt((double)vx * (double)vy);
+  return num / den;
+}
+
+static int pearson_better(double s, int64_t i, int64_t j, double bs, int64_t bi, int64_t bj) {
+  if (s != bs) return s > bs;
+  if (i != bi) return i < bi;
+  return j < bj;
+}
+
+/* argmax over i < j of |r_A(i,j) - r_B(i,j)| (cases [0, m1), controls [m1, m1 + m2)). */
+int oracle_twolocus_pearson(const int8_t* g, int64_t S, int64_t m1, int64_t m2, int64_t* bi, int64_t* bj,
+                            double* score) {
+  if (!g || S < 0 || m1 < 1 || m2 < 1 || m1 >= (1 << 20) || m2 >= (1 << 20) || !bi || !bj || !score)
+    return ORACLE_ERR_ARG;
+  int64_t m = m1 + m2;
+  if (!geno_ok(g, S, m)) return ORACLE_ERR_ARG;
+  double best = -1.0;
+  int64_t best_i = -1, best_j = -1;
+#pragma omp parallel
+  {
+    double ls = -1.0;
+    int64_t li = -1, lj = -1;
+#pragma omp for schedule(dynamic, 8)
+    for (int64_t i = 0; i < S; ++i) {
+      for (int64_t j = i + 1; j < S; ++j) {
+        double ra = pearson_of(g + i * m, g + j * m, 0, m1);
+        double rb = pearson_of(g + i * m, g + j * m, m1, m);
+        double s = fabs(ra - rb);
+        if (li < 0 || pearson_better(s, i, j, ls, li, lj)) { ls = s; li = i; lj = j; }
+      }
+    }
+#pragma omp critical
+    {
+      if (li >= 0 && (best_i < 0 || pearson_better(ls, li, lj, best, best_i, best_j))) {
+        best = ls; best_i = li; best_j = lj;
+      }
+    }
+  }
+  *bi = best_i; *bj = best_j; *score = best;
+  return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------ Hamming strings */
+/* Closest pair (least = 0: fewest mismatches) or least correlated pair (least = 1: most
+ * mismatches) of n strings s[i][0..t) over symbols 0 .. sigma-1; ties to the smallest (i, j). */
+int oracle_hamming(const uint8_t* s, int64_t n, int64_t t, int64_t sigma, int least, int64_t* bi, int64_t* bj,
+                   int64_t* dist) {
+  if (!s || n < 0 || t < 1 || sigma < 2 || sigma > 256 || !bi || !bj || !dist) return ORACLE_ERR_ARG;
+  for (int64_t e = 0; e < n * t; ++e)
+    if ((int64_t)s[e] >= sigma) return ORACLE_ERR_ARG;
+  int64_t best = -1, best_i = -1, best_j = -1;
+#pragma omp parallel
+  {
+    int64_t ld = -1, li = -1, lj = -1;
+#pragma omp for schedule(dynamic, 8)
+    for (int64_t i = 0; i < n; ++i) {
+      for (int64_t j = i + 1; j < n; ++j) {
+        int64_t h = 0;
+        for (int64_t k = 0; k < t; ++k) h += s[i * t + k] != s[j * t + k];
+        int better = li < 0 || (least ? h > ld : h < ld) || (h == ld && (i < li || (i == li && j < lj)));
+        if (better) { ld = h; li = i; lj = j; }
+      }
+    }
+#pragma omp critical
+    {
+      if (li >= 0) {
+        int better = best_i < 0 || (least ? ld > best : ld < best) ||
+                     (ld == best && (li < best_i || (li == best_i && lj < best_j)));
+        if (better) { best = ld; best_i = li; best_j = lj; }
+      }
+    }
+  }
+  *bi = best_i; *bj = best_j; *dist = best;
   return ORACLE_OK;
 }
