@@ -274,6 +274,54 @@ class FRNN:
         return pairs, dt, f"N(i) of {rows} points evenly spaced over the {self.n} ({pairs} pairs)"
 
 
+class Hamming:
+    """Closest pair of strings under the Hamming distance (Sec. 4): 65,536 strings of 64 symbols over
+    {0, 1, 2, 3} (the four-letter discretisation of Sec. 4's experiment), uniform, with one pair
+    planted at 2 mismatches."""
+    name = "hamming"
+
+    def __init__(self, args):
+        import numpy as np
+        from paper_1407_5609_gb300 import synth
+        g = synth.rng_for(synth.SEED_BASE + 5)
+        self.n, self.t, self.sigma = 65536, 64, 4
+        s = g.integers(0, self.sigma, (self.n, self.t)).astype(np.uint8)
+        a, b = 12345, 54321
+        s[b] = s[a]
+        s[b, [7, 40]] = (s[b, [7, 40]] + 1) % self.sigma
+        self.s = np.ascontiguousarray(s)
+        self.units = self.n * (self.n - 1) // 2
+        self.K = (self.t * self.sigma + 63) // 64 * 64
+        self.flop_per_unit = 2 * self.K               # the one-hot GEMM per pair
+        self.config = {"workload": "hamming closest pair: 65536 strings x 64 symbols, sigma=4, uniform, planted pair "
+                                   "at 2 mismatches", "pairs_per_step": self.units,
+                       "l2": "32 MB of one-hot rows per step"}
+
+    def setup(self, dev):
+        import torch
+        from paper_1407_5609_gb300 import capi
+        self.dev_s = torch.from_numpy(self.s).to(dev)
+        self.ws = torch.empty(capi.hamming_pair_workspace_size(self.n, self.t, self.sigma), dtype=torch.uint8,
+                              device=dev)
+
+    def step(self, capi, mode):
+        return capi.hamming_pair(self.dev_s, self.sigma, ws=self.ws)
+
+    def e2e_step(self, capi, mode, host, dev_buf):
+        dev_buf.copy_(host, non_blocking=True)
+        return capi.hamming_pair(dev_buf, self.sigma, ws=self.ws)
+
+    def host_input(self):
+        return self.s, self.s.nbytes
+
+    def oracle_sample(self, oracle, rows):
+        import numpy as np
+        rows = max(2, min(rows, self.n))
+        t = time.perf_counter()
+        oracle.hamming(self.s[:rows], self.sigma)
+        return rows * (rows - 1) // 2, time.perf_counter() - t, f"closest pair of the first {rows} strings"
+
+
 class Batch:
     name = "batch"
 
@@ -356,7 +404,7 @@ class Batch:
         return pairs, time.perf_counter() - t, f"closest pair + R-pairs of the first {rows} instances ({pairs} pairs)"
 
 
-WORKLOADS = {"tsmm": TSMM, "twolocus": TwoLocus, "cpp": CPP, "frnn": FRNN, "batch": Batch}
+WORKLOADS = {"tsmm": TSMM, "twolocus": TwoLocus, "cpp": CPP, "frnn": FRNN, "batch": Batch, "hamming": Hamming}
 
 
 # ------------------------------------------------------------------ helpers
@@ -390,6 +438,8 @@ def d2h_bytes(wl, capi):
         return 4 * (wl.nnz or 0) + 16                   # the column list plus two status words
     if wl.name == "batch":
         return len(wl.batch) * (64 + 8) + 24            # per-instance results and pair offsets
+    if wl.name == "hamming":
+        return 32 + 4                                   # the best partial and the status word
     return ctypes.sizeof(capi.twolocus_result)
 
 
@@ -490,13 +540,14 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "strong" if sharded else "weak", "vs_baseline": None,
            "dtype": ({"plain_fp32": "f32", "filter_fp16": "f16", "filter_bf16": "bf16"}.get(mode.replace("_prune", ""))
-                     if wl.name in ("tsmm", "cpp") else {"frnn": "f32", "twolocus": "u64", "batch": "f32"}[wl.name]),
+                     if wl.name in ("tsmm", "cpp") else {"frnn": "f32", "twolocus": "u64", "batch": "f32",
+                                                         "hamming": "bf16"}[wl.name]),
            "data": "synthetic", "config": dict(wl.config, mode=mode if wl.name in ("tsmm", "cpp") else None,
                                                flush_l2_between_steps=bool(flush),
                                                parallelism=(f"{world} shards of one search + one exchange of the results"
                                                             if sharded else f"replicas x{world}" if world > 1
                                                             else "single GPU")),
-           "answer": {k: res[k] for k in ("i", "j", "dist2", "score") if k in res},
+           "answer": {k: res[k] for k in ("i", "j", "dist2", "score", "mismatches") if k in res},
            "gpu_launches": launches}
 
     # roofline of the dominant kernel
@@ -563,6 +614,30 @@ def run_ours(args):
                            "frac": ach / POPC_PEAK_TOPS, "traffic": recorded_traffic("twolocus_scan@twolocus"),
                            "kernel": "twolocus_scan_kernel (step time)",
                            "peak_source": "derived: 152 SM x 16 POPC/clk x 2070 MHz"}
+        if not args.no_compare and capi.filters_available():
+            # the same scan on the tensor cores (exact integer GEMMs of one-hot rows), both measures
+            ws = torch.empty(capi.twolocus_scan_tc_workspace_size(4096, wl.planes.shape[3]), dtype=torch.uint8,
+                             device=dev)
+            for meas in ("matches", "pearson"):
+                capi.twolocus_scan_tc(wl.dev_planes, 4096, 4096, measure=meas, ws=ws)
+                barrier()
+                tms, tres = timed_steps(lambda: capi.twolocus_scan_tc(wl.dev_planes, 4096, 4096, measure=meas, ws=ws),
+                                        max(1, min(args.steps, 10)), stream, torch, flush)
+                tms /= max(1, min(args.steps, 10))
+                k = 2 * 128 * wl.planes.shape[3]       # two groups x K per group
+                out[f"tensor_core_{meas}"] = {
+                    "ms_per_step": tms, "value": wl.units / (tms / 1e3), "unit": UNIT,
+                    "gemm_tflops": wl.units * 2 * k / (tms / 1e3) / 1e12,
+                    "answer": {"i": tres["i"], "j": tres["j"], "score": tres["score"], "score_real": tres["score_real"]},
+                    **({"same_answer": (tres["i"], tres["j"], tres["score"]) == (res["i"], res["j"], res["score"])}
+                       if meas == "matches" else {})}
+    elif wl.name == "hamming":
+        per_step_ms = total_ms / args.steps
+        ach = wl.units * wl.flop_per_unit / (per_step_ms / 1e3) / 1e12
+        out["roofline"] = {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                           "frac": ach / pk["bf16_tflops"], "traffic": recorded_traffic("match_tc@hamming"),
+                           "kernel": "match_tc_kernel (step time; one-hot GEMM, 2 K flop per pair)",
+                           "peak_source": f"{pk['source']} bf16 burst"}
     out["clocks"] = clk
 
     # the same answer from the plain FP32 path, and its throughput

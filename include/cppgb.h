@@ -119,6 +119,7 @@ typedef struct {
   int64_t score;       /* |u_A * m_controls - u_B * m_cases| = |P_A - P_B| * m_cases * m_controls */
   int32_t countsA[9];  /* cases: countsA[3a+b] = #subjects with g_i = a, g_j = b */
   int32_t countsB[9];  /* controls, same layout */
+  double score_real;   /* the score as a real number: |P_A - P_B| (matches), |r_A - r_B| (Pearson) */
 } twolocus_result;
 
 /*
@@ -162,6 +163,46 @@ int twolocus_scan_noalloc(const uint64_t* planes, int64_t S, int64_t W, int64_t 
 int twolocus_scan_shard(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls,
                         int64_t shard, int64_t nshards, twolocus_result* out, void* ws, size_t ws_bytes,
                         void* stream);
+
+/*
+ * twolocus_scan_tc -- the two-locus scan of Sec. 6 on the tensor cores, with either measure:
+ *   CPPGB_TL_MATCHES  the match fraction of Sec. 5.3 (the result equals twolocus_scan's);
+ *   CPPGB_TL_PEARSON  Pearson's correlation of the genotype values 0, 1, 2 within each group (the
+ *                     measure Sec. 5 and Sec. 6 attribute to the method they compare with):
+ *                     r = (m Sxy - Sx Sy) / sqrt(vx vy), vx = m Sxx - Sx^2 (0 when vx or vy is 0),
+ *                     score |r_A - r_B| in score_real (score = -1), ties to the smallest (i, j).
+ * The per-pair counts are exact integer GEMMs: one-hot planes a = [g = 1], b = [g = 2] become BF16
+ * rows [a, b] (left) and [2c + d, c + 2d] or [c + 2d, 2c + 4d] (right); every partial sum is an
+ * integer below 2^24, so the FP32 tensor-core accumulation is exact.  Arguments as for
+ * twolocus_scan (W <= 4096, groups < 2^20 subjects); the workspace holds the four BF16 matrices,
+ * 4 S W 128 x 2 bytes (256 MB at 4096 SNPs x 4096 + 4096 subjects).
+ * Errors: CPPGB_ERR_ARG, CPPGB_ERR_CAPACITY (ws), CPPGB_ERR_TIMEOUT, CPPGB_ERR_CUDA.
+ */
+#define CPPGB_TL_MATCHES 0
+#define CPPGB_TL_PEARSON 1
+size_t twolocus_scan_tc_workspace_size(int64_t S, int64_t W);
+int twolocus_scan_tc(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls, int measure,
+                     twolocus_result* out, void* ws, size_t ws_bytes, void* stream);
+
+/* Result of a string-pair search. */
+typedef struct {
+  int64_t i, j;        /* the pair, i < j; -1 when n < 2 */
+  int64_t mismatches;  /* its Hamming distance */
+} hamming_result;
+
+/*
+ * hamming_pair -- closest pair (least = 0: fewest mismatches, the CPP of Sec. 4) or least
+ * correlated pair (least = 1: most mismatches, Sec. 5) of n strings of t symbols from
+ * {0, .., sigma - 1}, ties to the smallest (i, j).  Each string becomes a one-hot BF16 row of
+ * t sigma entries (the mapping of Sec. 5.5, one 1 per position); the dot product of two rows,
+ * accumulated exactly on the tensor cores, is the number of agreeing positions.
+ *   strs  device uint8 [n][ld], ld >= t.   2 <= sigma <= 256, t <= 2^23.
+ * Errors: CPPGB_ERR_ARG (also for a symbol >= sigma), CPPGB_ERR_CAPACITY (ws), CPPGB_ERR_TIMEOUT,
+ * CPPGB_ERR_CUDA.
+ */
+size_t hamming_pair_workspace_size(int64_t n, int64_t t, int sigma);
+int hamming_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, int least, hamming_result* out,
+                 void* ws, size_t ws_bytes, void* stream);
 
 /*
  * frnn_query -- fixed-radius near neighbours (Sec. 3.5): for every point p_i its R-neighbourhood

@@ -41,12 +41,19 @@ class cpp_pair_result(ctypes.Structure):
 
 class twolocus_result(ctypes.Structure):
     _fields_ = [("i", ctypes.c_int64), ("j", ctypes.c_int64), ("score", ctypes.c_int64),
-                ("countsA", ctypes.c_int32 * 9), ("countsB", ctypes.c_int32 * 9)]
+                ("countsA", ctypes.c_int32 * 9), ("countsB", ctypes.c_int32 * 9), ("score_real", ctypes.c_double)]
 
     def as_dict(self):
-        return {"i": self.i, "j": self.j, "score": self.score,
+        return {"i": self.i, "j": self.j, "score": self.score, "score_real": self.score_real,
                 "countsA": np.array(list(self.countsA), dtype=np.int32),
                 "countsB": np.array(list(self.countsB), dtype=np.int32)}
+
+
+class hamming_result(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_int64), ("j", ctypes.c_int64), ("mismatches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {"i": self.i, "j": self.j, "mismatches": self.mismatches}
 
 
 class cpp_instance(ctypes.Structure):
@@ -69,6 +76,10 @@ SIGNATURES = {
     "twolocus_scan_workspace_size": (_sz, [_i64, _i64]),
     "twolocus_scan": (_int, [_vp, _i64, _i64, _i64, _i64, ctypes.POINTER(twolocus_result), _vp, _sz, _vp]),
     "twolocus_scan_noalloc": (_int, [_vp, _i64, _i64, _i64, _i64, ctypes.POINTER(twolocus_result), _vp]),
+    "twolocus_scan_tc_workspace_size": (_sz, [_i64, _i64]),
+    "twolocus_scan_tc": (_int, [_vp, _i64, _i64, _i64, _i64, _int, ctypes.POINTER(twolocus_result), _vp, _sz, _vp]),
+    "hamming_pair_workspace_size": (_sz, [_i64, _i64, _int]),
+    "hamming_pair": (_int, [_vp, _i64, _i64, _i64, _int, _int, ctypes.POINTER(hamming_result), _vp, _sz, _vp]),
     "twolocus_scan_shard": (_int, [_vp, _i64, _i64, _i64, _i64, _i64, _i64, ctypes.POINTER(twolocus_result), _vp,
                                     _sz, _vp]),
     "frnn_query_workspace_size": (_sz, [_i64, _int]),
@@ -294,6 +305,48 @@ def twolocus_scan_shard(planes: torch.Tensor, m_cases: int, m_controls: int, sha
     out = twolocus_result()
     _raise(lib().twolocus_scan_shard(planes.data_ptr() if S else None, S, W, m_cases, m_controls, shard, nshards,
                                      ctypes.byref(out), ws.data_ptr(), ws.numel(), _stream(stream)))
+    return out.as_dict()
+
+
+TL_MATCHES, TL_PEARSON = 0, 1
+
+
+def twolocus_scan_tc_workspace_size(S: int, W: int) -> int:
+    return int(lib().twolocus_scan_tc_workspace_size(S, W))
+
+
+def hamming_pair_workspace_size(n: int, t: int, sigma: int) -> int:
+    return int(lib().hamming_pair_workspace_size(n, t, sigma))
+
+
+def twolocus_scan_tc(planes: torch.Tensor, m_cases: int, m_controls: int, measure=TL_MATCHES,
+                     ws: torch.Tensor | None = None, stream=None) -> dict:
+    """Two-locus scan on the tensor cores with the match or the Pearson measure (include/cppgb.h)."""
+    _check_cuda(planes, "planes")
+    if planes.dim() != 4 or planes.shape[1:3] != (2, 2) or planes.element_size() != 8 or not planes.is_contiguous():
+        raise ValueError("planes must be a contiguous 64-bit tensor [S][2][2][W]")
+    S, W = planes.shape[0], planes.shape[3]
+    if ws is None:
+        ws = _workspace(twolocus_scan_tc_workspace_size(S, W), planes.device)
+    out = twolocus_result()
+    m = {"matches": TL_MATCHES, "pearson": TL_PEARSON}.get(measure, measure)
+    _raise(lib().twolocus_scan_tc(planes.data_ptr() if S else None, S, W, m_cases, m_controls, int(m),
+                                  ctypes.byref(out), ws.data_ptr(), ws.numel(), _stream(stream)))
+    return out.as_dict()
+
+
+def hamming_pair(strings: torch.Tensor, sigma: int, least: bool = False, ws: torch.Tensor | None = None,
+                 stream=None) -> dict:
+    """Closest (or, with least=True, least correlated) pair of the rows of a uint8 [n][t] symbol matrix."""
+    _check_cuda(strings, "strings")
+    if strings.dim() != 2 or strings.dtype != torch.uint8 or strings.stride(1) != 1:
+        raise ValueError("strings must be uint8 [n][t] with unit column stride")
+    n, t = strings.shape
+    if ws is None:
+        ws = _workspace(hamming_pair_workspace_size(n, t, sigma), strings.device)
+    out = hamming_result()
+    _raise(lib().hamming_pair(strings.data_ptr() if n else None, n, t, strings.stride(0) if n else t, int(sigma),
+                              1 if least else 0, ctypes.byref(out), ws.data_ptr(), ws.numel(), _stream(stream)))
     return out.as_dict()
 
 

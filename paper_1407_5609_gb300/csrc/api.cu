@@ -508,6 +508,7 @@ static int twolocus_common(const uint64_t* planes, int64_t S, int64_t W, int64_t
   twolocus_result h;
   CPPGB_CUDA_TRY(cudaMemcpyAsync(&h, dres, sizeof h, cudaMemcpyDeviceToHost, st));
   CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
+  h.score_real = h.i >= 0 ? (double)h.score / ((double)m_cases * (double)m_controls) : -1.0;
   *out = h;
   return CPPGB_OK;
 }

@@ -193,5 +193,14 @@ int launch_gram_tc_prune_list(int64_t n, int64_t n_pad, int64_t excl, const floa
 int launch_twolocus(const uint64_t* planes, int64_t S, int64_t W, int64_t m1, int64_t m2, void* partials,
                     int64_t n_partials, twolocus_result* dev_out, cudaStream_t st, int64_t shard = 0, int64_t nshards = 1);
 int64_t twolocus_num_partials(int64_t S);
+int launch_twolocus_finish(const uint64_t* planes, int64_t W, int64_t m1, int64_t m2, const void* partials,
+                           int64_t np, twolocus_result* dev_out, cudaStream_t st);
+
+// Tensor-core match engine (match_tc.cu): exact integer GEMMs of 0/1/2-valued BF16 rows.
+enum MatchMode { MATCH_TL_COUNT = 0, MATCH_TL_PEARSON = 1, MATCH_HAMMING_MIN = 2, MATCH_HAMMING_MAX = 3 };
+struct MatchPartial {  // one per CTA: the best key (larger wins) and its pair (smaller (i, j) on ties)
+  long long key;
+  int32_t i, j;
+};
 
 }  // namespace cppgb

@@ -1,0 +1,646 @@
+// Exact match counts of categorical rows on the tensor cores.
+//
+// Two rows of symbols are compared through the dot products of 0/1/2-valued encodings (BF16, exact),
+// accumulated in FP32 on tcgen05: every product and every partial sum is an integer below 2^24, so
+// the accumulators hold the exact integer counts.
+//
+//  * Two-locus (Sec. 6) with the one-hot planes of Sec. 5.3 (a = [g_i = 1], b = [g_i = 2],
+//    c = [g_j = 1], d = [g_j = 2] per subject): the number of subjects whose genotypes match is
+//      u = m - s_i - s_j + [a, b] . [2c + d, c + 2d],   s = sum (a + b),
+//    because [g_i = g_j] = (1 - a - b)(1 - c - d) + ac + bd.  The score is |u_A m2 - u_B m1|.
+//  * Pearson's correlation of the genotype values x = a + 2b: sum x_i x_j = [a, b] . [c + 2d, 2c + 4d];
+//    r = (m Sxy - Sx_i Sx_j) / sqrt(vx_i vx_j), vx = m Sxx - Sx^2, and the score |r_A - r_B| is formed
+//    in FP64 with the same operations as the oracle, so it is bit-identical.
+//  * Strings over sigma symbols (Sec. 4), one-hot per position (the mapping of Sec. 5.5): the dot
+//    product of two one-hot rows is the number of positions where the strings agree, so the pair
+//    with the most (fewest) matches is the closest (least correlated) pair under the Hamming distance.
+//
+// Kernel: one persistent CTA per SM over the 128 x 128 tiles (bi <= bj) of the upper triangle; warp
+// 0 loads K-chunks of the left and right rows with TMA (6 stages), warp 1 issues the MMAs into one
+// 128-column TMEM accumulator per group (two tiles in flight), warps 2-5 turn each pair's counts into
+// a 64-bit key (larger is better, ties to the smaller (i, j)) and keep the best per CTA.
+#include <cuda_bf16.h>
+
+#include <cstring>
+
+#include "common.cuh"
+#include "tc_ptx.cuh"
+
+namespace cppgb {
+namespace {
+using namespace tc;
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6;
+constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int NTHREADS = 192;
+constexpr uint32_t TMEM_COLS = 512;  // 2 tiles in flight x up to 2 groups x 128 columns
+
+struct MatchMaps {
+  CUtensorMap L[2], R[2];
+};
+
+struct MatchParams {
+  int64_t S;              // rows
+  int32_t groups, mode;   // 1 or 2 groups; MatchMode
+  int64_t kch[2];         // K chunks of 64 per group
+  int64_t m[2];           // two-locus: group sizes; strings: the length t (m[0])
+  const int32_t* s[2];    // two-locus count: sum (a + b) per row
+  const int64_t* sx[2];   // Pearson: sum x and m sum x^2 - (sum x)^2 per row
+  const int64_t* vx[2];
+};
+
+struct Ctl {
+  uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
+  MatchPartial red[4];
+  uint32_t tmem_base;
+  int abort_flag;
+};
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + sizeof(Ctl) + 1024;
+
+__device__ __forceinline__ void tri_tile(int64_t t, int64_t nb, int64_t* bi, int64_t* bj) {
+  // row k holds nb - k tiles (bj = k .. nb - 1); the tiles before row k number k nb - k (k - 1) / 2
+  int64_t lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (mid * nb - mid * (mid - 1) / 2 <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  *bi = lo;
+  *bj = lo + (t - (lo * nb - lo * (lo - 1) / 2));
+}
+
+__device__ __forceinline__ bool better(unsigned long long k, int i, int j, unsigned long long bk, int bi, int bj) {
+  if (bi < 0) return true;
+  if (k != bk) return k > bk;
+  if (i != bi) return i < bi;
+  return j < bj;
+}
+
+__device__ __forceinline__ double pearson_r(int64_t m, int64_t sxy, int64_t sxi, int64_t sxj, int64_t vxi, int64_t vxj) {
+  if (vxi == 0 || vxj == 0) return 0.0;
+  const double num = (double)(m * sxy - sxi * sxj);
+  const double den = __dsqrt_rn(__dmul_rn((double)vxi, (double)vxj));
+  return __ddiv_rn(num, den);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    match_tc_kernel(const __grid_constant__ MatchMaps maps, const __grid_constant__ MatchParams mp, int64_t total,
+                    int64_t nb, MatchPartial* __restrict__ partials, unsigned int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  Ctl* ctl = (Ctl*)(smem + STAGES * STAGE_BYTES);
+  volatile int* abort_flag = &ctl->abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&ctl->full[s], 1);
+      mbar_init(&ctl->empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&ctl->tfull[a], 1);
+      mbar_init(&ctl->tempty[a], 4);
+    }
+    mbar_init(&ctl->drain, 1);
+    ctl->abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = ctl->tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---------------------------------------------- TMA producer
+      for (int g = 0; g < mp.groups; ++g) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.L[g]) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.R[g]) : "memory");
+      }
+      uint32_t stage = 0, phase = 0;
+      int64_t issued = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        int64_t bi, bj;
+        tri_tile(t, nb, &bi, &bj);
+        for (int g = 0; g < mp.groups && ok; ++g)
+          for (int64_t kc = 0; kc < mp.kch[g]; ++kc) {
+            if (!mbar_wait(&ctl->empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
+            uint8_t* sa = smem + stage * STAGE_BYTES;
+            mbar_arrive_expect_tx(&ctl->full[stage], STAGE_BYTES);
+            tma_load_2d(sa, &maps.L[g], &ctl->full[stage], (int)(kc * BK), (int)(bi * BM));
+            tma_load_2d(sa + A_BYTES, &maps.R[g], &ctl->full[stage], (int)(kc * BK), (int)(bj * BN));
+            ++issued;
+            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+          }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(status, 4u);
+      }
+      const int64_t last = issued < STAGES ? issued : STAGES;
+      for (int64_t k = 1; k <= last; ++k) {  // drain: every issued copy lands before exit
+        const int64_t u = issued - k;
+        const uint32_t s = (uint32_t)(u % STAGES), par = (uint32_t)((u / STAGES) & 1);
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try_wait(&ctl->full[s], par) && globaltimer() - t0 < WAIT_NS) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---------------------------------------------- MMA issuer
+      const uint32_t idesc = make_idesc(1u, BM, BN);  // BF16 operands
+      uint32_t stage = 0, phase = 0;
+      int64_t it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
+        const uint32_t acc = (uint32_t)(it & 1), use = (uint32_t)((it >> 1) & 1);
+        if (!mbar_wait(&ctl->tempty[acc], use ^ 1u, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        for (int g = 0; g < mp.groups && ok; ++g) {
+          const uint32_t dtmem = tmem_base + acc * 256u + (uint32_t)g * (uint32_t)BN;
+          for (int64_t kc = 0; kc < mp.kch[g]; ++kc) {
+            if (!mbar_wait(&ctl->full[stage], phase, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
+            const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+              mma_f16(dtmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (kc | kk) != 0);
+            mma_commit(&ctl->empty[stage]);
+            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+          }
+        }
+        if (!ok) break;
+        mma_commit(&ctl->tfull[acc]);
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(status, 4u);
+      }
+      mma_commit(&ctl->drain);
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(&ctl->drain, 0) && globaltimer() - t0 < WAIT_NS) {
+      }
+    }
+  } else {  // -------------------------------------------------------- epilogue (warps 2..5)
+    const uint32_t quarter = (uint32_t)(warp & 3);
+    unsigned long long bk = 0ull;
+    int bi_best = -1, bj_best = -1;
+    int64_t it = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
+      int64_t bi, bj;
+      tri_tile(t, nb, &bi, &bj);
+      const uint32_t acc = (uint32_t)(it & 1), use = (uint32_t)((it >> 1) & 1);
+      if (!__all_sync(0xffffffffu, mbar_wait(&ctl->tfull[acc], use, abort_flag))) { ok = false; break; }
+      tc_fence_after();
+      const int64_t i = bi * BM + quarter * 32 + lane;
+      const bool row_ok = i < mp.S;
+      const int64_t ii = row_ok ? i : 0;
+      const uint32_t tb = tmem_base + ((quarter * 32u) << 16) + acc * 256u;
+      int32_t sAi = 0, sBi = 0;
+      int64_t sxAi = 0, sxBi = 0, vxAi = 0, vxBi = 0;
+      if (mp.mode == MATCH_TL_COUNT) {
+        sAi = mp.s[0][ii];
+        sBi = mp.s[1][ii];
+      } else if (mp.mode == MATCH_TL_PEARSON) {
+        sxAi = mp.sx[0][ii];
+        sxBi = mp.sx[1][ii];
+        vxAi = mp.vx[0][ii];
+        vxBi = mp.vx[1][ii];
+      }
+      const bool ham = mp.mode == MATCH_HAMMING_MIN || mp.mode == MATCH_HAMMING_MAX;
+      const bool edge = bi == bj || (bi + 1) * BM > mp.S || (bj + 1) * BN > mp.S;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t ra[32], rb[32];
+        tmem_ld32(tb + (uint32_t)(c * 32), ra);
+        if (mp.groups == 2) tmem_ld32(tb + (uint32_t)BN + (uint32_t)(c * 32), rb);
+        if (ham && !edge && bi_best >= 0) {
+          // fast path: the chunk's best count (a 31-op tree) decides whether any entry can reach or
+          // tie the thread's best key; most chunks cannot
+          float m[16];
+          const bool most = mp.mode == MATCH_HAMMING_MIN;
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            m[k] = most ? fmaxf(__uint_as_float(ra[k]), __uint_as_float(ra[k + 16]))
+                        : fminf(__uint_as_float(ra[k]), __uint_as_float(ra[k + 16]));
+#pragma unroll
+          for (int k = 0; k < 8; ++k) m[k] = most ? fmaxf(m[k], m[k + 8]) : fminf(m[k], m[k + 8]);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) m[k] = most ? fmaxf(m[k], m[k + 4]) : fminf(m[k], m[k + 4]);
+          const float cm = most ? fmaxf(fmaxf(m[0], m[2]), fmaxf(m[1], m[3])) : fminf(fminf(m[0], m[2]), fminf(m[1], m[3]));
+          const unsigned long long ck = most ? (unsigned long long)cm : (unsigned long long)(mp.m[0] - (int64_t)cm);
+          if (ck < bk) continue;
+        }
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const int64_t j = bj * BN + c * 32 + k;
+          if (!(row_ok && j < mp.S && j > i)) continue;
+          const int64_t accA = (int64_t)__uint_as_float(ra[k]);
+          unsigned long long key;
+          if (mp.mode == MATCH_TL_COUNT) {
+            const int64_t accB = (int64_t)__uint_as_float(rb[k]);
+            const int64_t uA = mp.m[0] - sAi - mp.s[0][j] + accA;
+            const int64_t uB = mp.m[1] - sBi - mp.s[1][j] + accB;
+            const int64_t sc = uA * mp.m[1] - uB * mp.m[0];
+            key = (unsigned long long)(sc < 0 ? -sc : sc);
+          } else if (mp.mode == MATCH_TL_PEARSON) {
+            const int64_t accB = (int64_t)__uint_as_float(rb[k]);
+            const double rA = pearson_r(mp.m[0], accA, sxAi, mp.sx[0][j], vxAi, mp.vx[0][j]);
+            const double rB = pearson_r(mp.m[1], accB, sxBi, mp.sx[1][j], vxBi, mp.vx[1][j]);
+            key = (unsigned long long)__double_as_longlong(fabs(__dsub_rn(rA, rB)));
+          } else if (mp.mode == MATCH_HAMMING_MIN) {
+            key = (unsigned long long)accA;  // most agreeing positions = fewest mismatches
+          } else {
+            key = (unsigned long long)(mp.m[0] - accA);  // most mismatches
+          }
+          if (better(key, (int)i, (int)j, bk, bi_best, bj_best)) {
+            bk = key;
+            bi_best = (int)i;
+            bj_best = (int)j;
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl->tempty[acc]);
+    }
+    if (!ok && lane == 0) {
+      *abort_flag = 1;
+      atomicOr(status, 4u);
+    }
+    // best of the warp, then of the four epilogue warps
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ok2 = __shfl_xor_sync(0xffffffffu, bk, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi_best, o), oj = __shfl_xor_sync(0xffffffffu, bj_best, o);
+      if (oi >= 0 && better(ok2, oi, oj, bk, bi_best, bj_best)) {
+        bk = ok2;
+        bi_best = oi;
+        bj_best = oj;
+      }
+    }
+    if (lane == 0) ctl->red[warp - 2] = MatchPartial{(long long)bk, bi_best, bj_best};
+    asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps, once, after their loops
+    if (warp == 2 && lane == 0) {
+      MatchPartial b = ctl->red[0];
+      for (int w = 1; w < 4; ++w) {
+        const MatchPartial o = ctl->red[w];
+        if (o.i >= 0 && better((unsigned long long)o.key, o.i, o.j, (unsigned long long)b.key, b.i, b.j)) b = o;
+      }
+      if (b.i < 0) b.key = -1;
+      partials[blockIdx.x] = b;
+    }
+    tc_fence_before();
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- preparation
+__device__ __forceinline__ uint16_t bf16_small(int v) {  // exact BF16 bits of 0 .. 4
+  return v == 0 ? 0x0000 : v == 1 ? 0x3f80 : v == 2 ? 0x4000 : v == 3 ? 0x4040 : 0x4080;
+}
+
+// Two-locus rows: one warp per (row, group).  L = [a bits, b bits] of the group's W words (K = 128 W);
+// R = [2c + d, c + 2d] (count) or [c + 2d, 2c + 4d] (Pearson); rows >= S are zero.  Per-row sums:
+// s = sum (a + b) (count); Sx = sum (a + 2b), vx = m Sxx - Sx^2 with Sxx = sum (a + 4b) (Pearson).
+__global__ void tl_prep_kernel(const uint64_t* __restrict__ planes, int64_t S, int64_t S_pad, int64_t W, int64_t m1,
+                               int64_t m2, int mode, uint16_t* L0, uint16_t* R0, uint16_t* L1, uint16_t* R1,
+                               int32_t* s0, int32_t* s1, int64_t* sx0, int64_t* sx1, int64_t* vx0, int64_t* vx1) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w_id = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w_id >= 2 * S_pad) return;
+  const int64_t row = w_id >> 1;
+  const int g = (int)(w_id & 1);
+  const int64_t K = 128 * W;
+  uint16_t* L = (g == 0 ? L0 : L1) + row * K;
+  uint16_t* R = (g == 0 ? R0 : R1) + row * K;
+  long long sa = 0, sb = 0;
+  for (int64_t w = lane; w < W; w += 32) {
+    uint64_t a = 0, b = 0;
+    if (row < S) {
+      a = planes[((row * 2 + g) * 2 + 0) * W + w];
+      b = planes[((row * 2 + g) * 2 + 1) * W + w];
+    }
+    sa += __popcll(a);
+    sb += __popcll(b);
+    for (int q = 0; q < 64; q += 8) {  // 8 subjects per 16-byte store
+      uint16_t la[8], lb[8], r1[8], r2[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int ab = (int)((a >> (q + e)) & 1), bb = (int)((b >> (q + e)) & 1);
+        la[e] = bf16_small(ab);
+        lb[e] = bf16_small(bb);
+        if (mode == MATCH_TL_COUNT) {
+          r1[e] = bf16_small(2 * ab + bb);
+          r2[e] = bf16_small(ab + 2 * bb);
+        } else {
+          r1[e] = bf16_small(ab + 2 * bb);
+          r2[e] = bf16_small(2 * ab + 4 * bb);
+        }
+      }
+      *reinterpret_cast<uint4*>(L + 64 * w + q) = *reinterpret_cast<const uint4*>(la);
+      *reinterpret_cast<uint4*>(L + 64 * W + 64 * w + q) = *reinterpret_cast<const uint4*>(lb);
+      *reinterpret_cast<uint4*>(R + 64 * w + q) = *reinterpret_cast<const uint4*>(r1);
+      *reinterpret_cast<uint4*>(R + 64 * W + 64 * w + q) = *reinterpret_cast<const uint4*>(r2);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+  }
+  if (lane == 0) {
+    if (mode == MATCH_TL_COUNT) {
+      (g == 0 ? s0 : s1)[row] = (int32_t)(sa + sb);
+    } else {
+      const int64_t m = g == 0 ? m1 : m2;
+      const int64_t sx = sa + 2 * sb, sxx = sa + 4 * sb;
+      (g == 0 ? sx0 : sx1)[row] = sx;
+      (g == 0 ? vx0 : vx1)[row] = m * sxx - sx * sx;
+    }
+  }
+}
+
+// One-hot rows of strings: X[row][p sigma + v] = 1 where s[row][p] = v (X zeroed before); one warp per row.
+__global__ void ham_prep_kernel(const uint8_t* __restrict__ strs, int64_t n, int64_t t, int64_t ld, int sigma,
+                                uint16_t* __restrict__ X, int64_t K, unsigned int* status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  bool bad = false;
+  for (int64_t p = lane; p < t; p += 32) {
+    const int v = strs[row * ld + p];
+    if (v >= sigma) {
+      bad = true;
+      continue;
+    }
+    X[row * K + p * sigma + v] = 0x3f80;
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, 1u);
+}
+
+// Best of the per-CTA partials (one block).
+__global__ void match_finish_kernel(const MatchPartial* __restrict__ partials, int64_t np, MatchPartial* out) {
+  __shared__ MatchPartial red[256];
+  MatchPartial b{-1, -1, -1};
+  for (int64_t q = threadIdx.x; q < np; q += blockDim.x) {
+    const MatchPartial o = partials[q];
+    if (o.i >= 0 && better((unsigned long long)o.key, o.i, o.j, (unsigned long long)b.key, b.i, b.j)) b = o;
+  }
+  red[threadIdx.x] = b;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      const MatchPartial o = red[threadIdx.x + s], c = red[threadIdx.x];
+      if (o.i >= 0 && better((unsigned long long)o.key, o.i, o.j, (unsigned long long)c.key, c.i, c.j))
+        red[threadIdx.x] = o;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int encode_rows(CUtensorMap* m, void* base, int64_t rows, int64_t K) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
+        qr != cudaDriverEntryPointSuccess)
+      return set_error(CPPGB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    fn = (EncodeTiledFn)p;
+  }
+  const cuuint64_t gdim[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t gstride[1] = {(cuuint64_t)K * 2};
+  const cuuint32_t box[2] = {64, 128};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult cr = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, gdim, gstride, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return set_error(CPPGB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+  return CPPGB_OK;
+}
+
+int launch_match(const MatchMaps& maps, const MatchParams& mp, MatchPartial* partials, int64_t* np_out,
+                 unsigned int* status, cudaStream_t st) {
+  const int64_t nb = (mp.S + BM - 1) / BM;
+  const int64_t total = nb * (nb + 1) / 2;
+  int dev = 0, sms = 0;
+  CPPGB_CUDA_TRY(cudaGetDevice(&dev));
+  CPPGB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t grid = total < sms ? total : sms;
+  *np_out = grid;
+  if (grid == 0) return CPPGB_OK;
+  CPPGB_CUDA_TRY(cudaFuncSetAttribute(match_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+  match_tc_kernel<<<(unsigned)grid, NTHREADS, SMEM_BYTES, st>>>(maps, mp, total, nb, partials, status);
+  CPPGB_LAUNCH_CHECK();
+  return CPPGB_OK;
+}
+
+struct TLLayout {
+  uint16_t *L[2], *R[2];
+  int32_t* s[2];
+  int64_t *sx[2], *vx[2];
+  MatchPartial* partials;
+  twolocus_result* dres;
+  unsigned int* status;
+  size_t bytes;
+};
+
+TLLayout tl_layout(void* ws, int64_t S, int64_t W) {
+  TLLayout L;
+  Carver c(ws);
+  const int64_t S_pad = (S + BM - 1) / BM * BM, K = 128 * W;
+  for (int g = 0; g < 2; ++g) {
+    L.L[g] = c.take<uint16_t>((size_t)(S_pad > 0 ? S_pad : BM) * K);
+    L.R[g] = c.take<uint16_t>((size_t)(S_pad > 0 ? S_pad : BM) * K);
+    L.s[g] = c.take<int32_t>(S_pad + 1);
+    L.sx[g] = c.take<int64_t>(S_pad + 1);
+    L.vx[g] = c.take<int64_t>(S_pad + 1);
+  }
+  L.partials = c.take<MatchPartial>(1024);
+  L.dres = c.take<twolocus_result>(1);
+  L.status = c.take<unsigned int>(1);
+  L.bytes = c.bytes();
+  return L;
+}
+
+struct HamLayout {
+  uint16_t* X;
+  MatchPartial *partials, *best;
+  unsigned int* status;
+  size_t bytes;
+};
+
+HamLayout ham_layout(void* ws, int64_t n, int64_t K) {
+  HamLayout L;
+  Carver c(ws);
+  const int64_t n_pad = (n + BM - 1) / BM * BM;
+  L.X = c.take<uint16_t>((size_t)(n_pad > 0 ? n_pad : BM) * K);
+  L.partials = c.take<MatchPartial>(1024);
+  L.best = c.take<MatchPartial>(1);
+  L.status = c.take<unsigned int>(1);
+  L.bytes = c.bytes();
+  return L;
+}
+
+}  // namespace
+}  // namespace cppgb
+
+using namespace cppgb;
+
+extern "C" {
+
+size_t twolocus_scan_tc_workspace_size(int64_t S, int64_t W) {
+  if (S < 0 || W < 1) return 0;
+  return tl_layout(nullptr, S, W).bytes;
+}
+
+int twolocus_scan_tc(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls, int measure,
+                     twolocus_result* out, void* ws, size_t ws_bytes, void* stream) {
+  if (!out) return set_error(CPPGB_ERR_ARG, "out is NULL");
+  if (measure != CPPGB_TL_MATCHES && measure != CPPGB_TL_PEARSON) return set_error(CPPGB_ERR_ARG, "unknown measure");
+  if (S < 0 || S > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "S out of range");
+  if (m_cases < 1 || m_controls < 1) return set_error(CPPGB_ERR_ARG, "group sizes must be >= 1");
+  if (W < (m_cases + 63) / 64 || W < (m_controls + 63) / 64 || W > 4096)
+    return set_error(CPPGB_ERR_ARG, "W = %lld words cannot hold the groups (or exceeds 4096)", (long long)W);
+  if (m_cases >= (1 << 20) || m_controls >= (1 << 20)) return set_error(CPPGB_ERR_ARG, "groups must hold < 2^20 subjects");
+  if (S > 0 && !planes) return set_error(CPPGB_ERR_ARG, "planes is NULL");
+  if (!ws || ((uintptr_t)ws & 255)) return set_error(CPPGB_ERR_ARG, "workspace must be non-NULL and 256-byte aligned");
+  TLLayout L = tl_layout(ws, S, W);
+  if (ws_bytes < L.bytes) return set_error(CPPGB_ERR_CAPACITY, "workspace too small: %zu given, %zu needed", ws_bytes, L.bytes);
+  if (!gram_tc_available()) return set_error(CPPGB_ERR_ARG, "tensor-core kernels are not available in this build");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (S < 2) {
+    memset(out, 0, sizeof *out);
+    out->i = out->j = -1;
+    out->score = -1;
+    out->score_real = -1.0;
+    return CPPGB_OK;
+  }
+  const int mode = measure == CPPGB_TL_PEARSON ? MATCH_TL_PEARSON : MATCH_TL_COUNT;
+  const int64_t S_pad = (S + BM - 1) / BM * BM, K = 128 * W;
+  CPPGB_CUDA_TRY(cudaMemsetAsync(L.status, 0, sizeof(unsigned int), st));
+  const int64_t warps = 2 * S_pad;
+  tl_prep_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(planes, S, S_pad, W, m_cases, m_controls, mode, L.L[0],
+                                                             L.R[0], L.L[1], L.R[1], L.s[0], L.s[1], L.sx[0], L.sx[1],
+                                                             L.vx[0], L.vx[1]);
+  CPPGB_LAUNCH_CHECK();
+  MatchMaps maps;
+  int rc;
+  for (int g = 0; g < 2; ++g) {
+    if ((rc = encode_rows(&maps.L[g], L.L[g], S_pad, K))) return rc;
+    if ((rc = encode_rows(&maps.R[g], L.R[g], S_pad, K))) return rc;
+  }
+  MatchParams mp;
+  mp.S = S;
+  mp.groups = 2;
+  mp.mode = mode;
+  mp.kch[0] = mp.kch[1] = K / BK;
+  mp.m[0] = m_cases;
+  mp.m[1] = m_controls;
+  for (int g = 0; g < 2; ++g) {
+    mp.s[g] = L.s[g];
+    mp.sx[g] = L.sx[g];
+    mp.vx[g] = L.vx[g];
+  }
+  int64_t np = 0;
+  if ((rc = launch_match(maps, mp, L.partials, &np, L.status, st))) return rc;
+  if ((rc = launch_twolocus_finish(planes, W, m_cases, m_controls, L.partials, np, L.dres, st))) return rc;
+  twolocus_result h;
+  unsigned int status = 0;
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(&h, L.dres, sizeof h, cudaMemcpyDeviceToHost, st));
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(&status, L.status, sizeof status, cudaMemcpyDeviceToHost, st));
+  CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
+  if (status & 4u) return set_error(CPPGB_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
+  if (mode == MATCH_TL_PEARSON && h.i >= 0) {
+    long long bits = h.score;
+    double v;
+    memcpy(&v, &bits, sizeof v);
+    h.score = -1;  // the Pearson measure has no integer score
+    h.score_real = v;
+  } else {
+    h.score_real = h.i >= 0 ? (double)h.score / ((double)m_cases * (double)m_controls) : -1.0;
+  }
+  *out = h;
+  return CPPGB_OK;
+}
+
+size_t hamming_pair_workspace_size(int64_t n, int64_t t, int sigma) {
+  if (n < 0 || t < 1 || sigma < 2 || sigma > 256) return 0;
+  const int64_t K = (t * sigma + 63) / 64 * 64;
+  return ham_layout(nullptr, n, K).bytes;
+}
+
+int hamming_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, int least, hamming_result* out,
+                 void* ws, size_t ws_bytes, void* stream) {
+  if (!out) return set_error(CPPGB_ERR_ARG, "out is NULL");
+  out->i = out->j = -1;
+  out->mismatches = -1;
+  if (n < 0 || n > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "n out of range");
+  if (t < 1 || sigma < 2 || sigma > 256 || ld < t) return set_error(CPPGB_ERR_ARG, "need t >= 1, 2 <= sigma <= 256, ld >= t");
+  if (t > (1 << 23)) return set_error(CPPGB_ERR_ARG, "strings longer than 2^23 symbols are not supported");
+  const int64_t K = (t * sigma + 63) / 64 * 64;
+  if (K > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "t * sigma too large");
+  if (n > 0 && !strs) return set_error(CPPGB_ERR_ARG, "strings is NULL");
+  if (!ws || ((uintptr_t)ws & 255)) return set_error(CPPGB_ERR_ARG, "workspace must be non-NULL and 256-byte aligned");
+  HamLayout L = ham_layout(ws, n, K);
+  if (ws_bytes < L.bytes) return set_error(CPPGB_ERR_CAPACITY, "workspace too small: %zu given, %zu needed", ws_bytes, L.bytes);
+  if (!gram_tc_available()) return set_error(CPPGB_ERR_ARG, "tensor-core kernels are not available in this build");
+  if (n < 2) return CPPGB_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n_pad = (n + BM - 1) / BM * BM;
+  CPPGB_CUDA_TRY(cudaMemsetAsync(L.X, 0, sizeof(uint16_t) * (size_t)n_pad * K, st));
+  CPPGB_CUDA_TRY(cudaMemsetAsync(L.status, 0, sizeof(unsigned int), st));
+  ham_prep_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(strs, n, t, ld, sigma, L.X, K, L.status);
+  CPPGB_LAUNCH_CHECK();
+  MatchMaps maps;
+  int rc;
+  if ((rc = encode_rows(&maps.L[0], L.X, n_pad, K))) return rc;
+  maps.R[0] = maps.L[0];
+  maps.L[1] = maps.R[1] = maps.L[0];
+  MatchParams mp;
+  memset(&mp, 0, sizeof mp);
+  mp.S = n;
+  mp.groups = 1;
+  mp.mode = least ? MATCH_HAMMING_MAX : MATCH_HAMMING_MIN;
+  mp.kch[0] = K / BK;
+  mp.m[0] = t;
+  int64_t np = 0;
+  if ((rc = launch_match(maps, mp, L.partials, &np, L.status, st))) return rc;
+  match_finish_kernel<<<1, 256, 0, st>>>(L.partials, np, L.best);
+  CPPGB_LAUNCH_CHECK();
+  MatchPartial b;
+  unsigned int status = 0;
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(&b, L.best, sizeof b, cudaMemcpyDeviceToHost, st));
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(&status, L.status, sizeof status, cudaMemcpyDeviceToHost, st));
+  CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
+  if (status & 1u) return set_error(CPPGB_ERR_ARG, "a symbol is >= sigma");
+  if (status & 4u) return set_error(CPPGB_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
+  if (b.i >= 0) {
+    out->i = b.i;
+    out->j = b.j;
+    out->mismatches = least ? b.key : t - b.key;
+  }
+  return CPPGB_OK;
+}
+
+}  // extern "C"

@@ -196,6 +196,15 @@ __global__ void __launch_bounds__(NT)
 
 }  // namespace
 
+// Reduce per-block partials {score, i, j} (largest score, then smallest (i, j)) and count the
+// winner's tables; the tensor-core scan writes the same partials.
+int launch_twolocus_finish(const uint64_t* planes, int64_t W, int64_t m1, int64_t m2, const void* partials,
+                           int64_t np, twolocus_result* dev_out, cudaStream_t st) {
+  twolocus_finish_kernel<<<1, NT, 0, st>>>(planes, W, m1, m2, (const Partial*)partials, np, dev_out);
+  CPPGB_LAUNCH_CHECK();
+  return CPPGB_OK;
+}
+
 int64_t twolocus_num_partials(int64_t S) {
   const int64_t gx = (S + TJ - 1) / TJ, gy = (S + TI - 1) / TI;
   return gx * gy;
@@ -288,6 +297,7 @@ extern "C" int twolocus_scan_noalloc(const uint64_t* planes, int64_t S, int64_t 
   twolocus_result h;
   CPPGB_CUDA_TRY(cudaMemcpyAsync(&h, dres, sizeof h, cudaMemcpyDeviceToHost, st));
   CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
+  h.score_real = h.i >= 0 ? (double)h.score / ((double)m_cases * (double)m_controls) : -1.0;
   *out = h;
   return CPPGB_OK;
 }
