@@ -19,6 +19,10 @@ Applications"):
   twolocus(g, m1, m2)              argmax |P_A - P_B|, Sec. 6 (matches of Sec. 2 / 5.3)
   twolocus_tables(g, m1, m2, I, J) 3x3 tables and scores of chosen pairs
   twolocus_rows(g, m1, m2, rows)   best partner of chosen SNPs
+  twolocus_pearson(g, m1, m2)      the same argmax with Pearson's r per group
+  hamming(strings, sigma, least)   closest / least correlated pair of strings, Sec. 4 / Sec. 5
+  mlba(strings, sigma, cols, least) the light-bulb algorithm of Sec. 4 on given sampled columns,
+                                   least correlated form over the one-hot complements of Sec. 5
 
 All functions follow plain definitions, so the parity of each is pinned by the
 tests in ``tests/test_oracle_*.py`` against library routines, closed forms,
@@ -92,6 +96,8 @@ def _load():
                                                            _i64p, _i64p, _f64p]),
                 "oracle_hamming": (ctypes.c_int, [_u8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                                   _i64p, _i64p, _i64p]),
+                "oracle_mlba": (ctypes.c_int, [_u8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                               _i32p, ctypes.c_int64, ctypes.c_int64, _i64p, _i64p, _i64p, _i64p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -254,3 +260,19 @@ def hamming(strings, sigma: int, least: bool = False):
     _check(_load().oracle_hamming(_p(s, _u8p), s.shape[0], s.shape[1], sigma, 1 if least else 0, ctypes.byref(bi),
                                   ctypes.byref(bj), ctypes.byref(d)), "hamming")
     return bi.value, bj.value, d.value
+
+
+def mlba(strings, sigma: int, cols, least: bool = False):
+    """The modified light-bulb algorithm (Sec. 4; Sec. 5.4-5.5 for least=True) with the sampled
+    columns given: cols is int32 [iters][L], columns of the strings (least=False) or of the one-hot
+    strings, 0 .. sigma*t - 1 (least=True).  Returns (i, j, mismatches, candidates); i = j = -1
+    when no pair shared a bucket."""
+    s = np.ascontiguousarray(strings, dtype=np.uint8)
+    c = np.ascontiguousarray(cols, dtype=np.int32)
+    if c.ndim != 2:
+        raise ValueError("cols must be [iters][L]")
+    bi, bj, d, nc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_load().oracle_mlba(_p(s, _u8p), s.shape[0], s.shape[1], sigma, 1 if least else 0, _p(c, _i32p),
+                               c.shape[0], c.shape[1], ctypes.byref(bi), ctypes.byref(bj), ctypes.byref(d),
+                               ctypes.byref(nc)), "mlba")
+    return bi.value, bj.value, d.value, nc.value

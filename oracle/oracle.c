@@ -28,6 +28,10 @@
  *   oracle_hamming    closest (or least correlated) pair of strings over an
  *                     alphabet of sigma symbols under the Hamming distance, Sec. 4
  *                     (and Sec. 5 for the least correlated pair)
+ *   oracle_mlba       the modified light-bulb algorithm of Sec. 4 (sampled columns,
+ *                     sort, buckets, candidate pairs, verification), and its least
+ *                     correlated form over the one-hot strings and their complements
+ *                     of Sec. 5.4-5.5; the columns each iteration samples are inputs
  *
  * Readings taken where the paper is silent (each also listed in the design
  * notes): ties go to the lexicographically smallest (d^2, i, j) with i < j;
@@ -493,5 +497,121 @@ int oracle_hamming(const uint8_t* s, int64_t n, int64_t t, int64_t sigma, int le
     }
   }
   *bi = best_i; *bj = best_j; *dist = best;
+  return ORACLE_OK;
+}
+
+/* ---- MLBA, Sec. 4 (closest pair) and Sec. 5.4-5.5 (least correlated pair) ---------------------
+ *
+ * The rows the algorithm sorts:
+ *   least = 0: the n strings themselves, columns 0 .. t-1 (Sec. 4 sorts the strings over the
+ *              alphabet directly; no mapping);
+ *   least = 1: the 2n columns of the matrix D of Sec. 5.4: row r < n is A'_r, the one-hot string of
+ *              string r (symbol a at position p sets bit p*sigma + a, the mapping of Sec. 5.5), and
+ *              row n + r is its bitwise complement; columns 0 .. sigma*t - 1.
+ * Iteration `it` looks only at the L columns cols[it*L .. it*L + L - 1] (the random draw is made by
+ * the caller).  The rows are sorted by their characters in those columns, taken in the given
+ * order (ties by row number), so rows with equal characters form runs: the buckets.  Every pair
+ * of rows in a bucket is a candidate; for least = 1 only a row A'_i with a complement row of A'_j,
+ * i != j.  The pair {i, j} shares a bucket as (A'_i, comp A'_j) exactly when it shares one as
+ * (A'_j, comp A'_i) (complementing all characters maps one bucket onto the other), so the oracle
+ * counts the representative with i < j: each unordered pair at most once per iteration.
+ * Candidates are counted with repetition across iterations.  Verification (the last step of the
+ * algorithm) computes the Hamming distance of every candidate on the original strings; the answer
+ * is the candidate with the fewest (least = 0) or most (least = 1) mismatches, ties to the smallest
+ * (i, j).  No candidate: i = j = -1, mismatches = -1. */
+
+typedef struct {
+  const uint8_t* s;
+  int64_t n, t, sigma;
+  int least;
+  const int32_t* cols;  // this iteration's L columns
+  int64_t L;
+} mlba_ctx;
+
+/* character of row r in column c of the matrix being sorted */
+static int mlba_char(const mlba_ctx* q, int64_t r, int64_t c) {
+  if (!q->least) return q->s[r * q->t + c];
+  const int64_t i = r < q->n ? r : r - q->n;
+  const int bit = q->s[i * q->t + c / q->sigma] == (uint8_t)(c % q->sigma);
+  return r < q->n ? bit : 1 - bit;
+}
+
+/* -1, 0, 1: the rows' characters in the sampled columns, compared in column order */
+static int mlba_cmp_key(const mlba_ctx* q, int64_t a, int64_t b) {
+  for (int64_t k = 0; k < q->L; ++k) {
+    const int ca = mlba_char(q, a, q->cols[k]), cb = mlba_char(q, b, q->cols[k]);
+    if (ca != cb) return ca < cb ? -1 : 1;
+  }
+  return 0;
+}
+
+/* bottom-up merge sort of idx[0..m) by (key, row) */
+static void mlba_sort(const mlba_ctx* q, int64_t* idx, int64_t* tmp, int64_t m) {
+  for (int64_t w = 1; w < m; w *= 2) {
+    for (int64_t lo = 0; lo < m; lo += 2 * w) {
+      const int64_t mid = lo + w < m ? lo + w : m, hi = lo + 2 * w < m ? lo + 2 * w : m;
+      int64_t a = lo, b = mid, o = lo;
+      while (a < mid && b < hi) {
+        const int c = mlba_cmp_key(q, idx[a], idx[b]);
+        if (c < 0 || (c == 0 && idx[a] < idx[b])) tmp[o++] = idx[a++];
+        else tmp[o++] = idx[b++];
+      }
+      while (a < mid) tmp[o++] = idx[a++];
+      while (b < hi) tmp[o++] = idx[b++];
+    }
+    memcpy(idx, tmp, (size_t)m * sizeof(int64_t));
+  }
+}
+
+int oracle_mlba(const uint8_t* s, int64_t n, int64_t t, int64_t sigma, int least, const int32_t* cols, int64_t iters,
+                int64_t L, int64_t* bi, int64_t* bj, int64_t* dist, int64_t* ncand) {
+  if (!s || n < 0 || t < 1 || sigma < 2 || sigma > 256 || iters < 0 || L < (least ? 1 : 0) || !bi || !bj || !dist ||
+      !ncand || (iters > 0 && L > 0 && !cols))
+    return ORACLE_ERR_ARG;
+  for (int64_t e = 0; e < n * t; ++e)
+    if ((int64_t)s[e] >= sigma) return ORACLE_ERR_ARG;
+  const int64_t width = least ? sigma * t : t;
+  for (int64_t e = 0; e < iters * L; ++e)
+    if (cols[e] < 0 || cols[e] >= width) return ORACLE_ERR_ARG;
+  const int64_t m = least ? 2 * n : n;
+  int64_t* idx = (int64_t*)malloc((size_t)(m + 1) * sizeof(int64_t));
+  int64_t* tmp = (int64_t*)malloc((size_t)(m + 1) * sizeof(int64_t));
+  if (!idx || !tmp) { free(idx); free(tmp); return ORACLE_ERR_CAPACITY; }
+  int64_t best = -1, best_i = -1, best_j = -1, cand = 0;
+  for (int64_t it = 0; it < iters; ++it) {
+    mlba_ctx q = {s, n, t, sigma, least, cols ? cols + it * L : NULL, L};
+    for (int64_t r = 0; r < m; ++r) idx[r] = r;
+    mlba_sort(&q, idx, tmp, m);
+    for (int64_t a = 0; a < m;) {
+      int64_t b = a + 1;
+      while (b < m && mlba_cmp_key(&q, idx[a], idx[b]) == 0) ++b;
+      /* bucket idx[a .. b) */
+      for (int64_t x = a; x < b; ++x) {
+        for (int64_t y = x + 1; y < b; ++y) {
+          int64_t i, j;
+          if (!least) {
+            i = idx[x] < idx[y] ? idx[x] : idx[y];
+            j = idx[x] < idx[y] ? idx[y] : idx[x];
+          } else {
+            const int64_t rx = idx[x], ry = idx[y];
+            if ((rx < n) == (ry < n)) continue;  /* two originals or two complements */
+            i = rx < n ? rx : ry;                /* the original row */
+            j = rx < n ? ry - n : rx - n;        /* the string whose complement it met */
+            if (i >= j) continue;                /* the pair is counted as (A'_j, comp A'_i) instead */
+          }
+          ++cand;
+          int64_t h = 0;
+          for (int64_t k = 0; k < t; ++k) h += s[i * t + k] != s[j * t + k];
+          const int better = best_i < 0 || (least ? h > best : h < best) ||
+                             (h == best && (i < best_i || (i == best_i && j < best_j)));
+          if (better) { best = h; best_i = i; best_j = j; }
+        }
+      }
+      a = b;
+    }
+  }
+  free(idx);
+  free(tmp);
+  *bi = best_i; *bj = best_j; *dist = best; *ncand = cand;
   return ORACLE_OK;
 }
