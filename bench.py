@@ -283,13 +283,8 @@ class Hamming:
     def __init__(self, args):
         import numpy as np
         from paper_1407_5609_gb300 import synth
-        g = synth.rng_for(synth.SEED_BASE + 5)
         self.n, self.t, self.sigma = 65536, 64, 4
-        s = g.integers(0, self.sigma, (self.n, self.t)).astype(np.uint8)
-        a, b = 12345, 54321
-        s[b] = s[a]
-        s[b, [7, 40]] = (s[b, [7, 40]] + 1) % self.sigma
-        self.s = np.ascontiguousarray(s)
+        self.s = synth.make_strings(self.n, self.t, self.sigma)
         self.units = self.n * (self.n - 1) // 2
         self.K = (self.t * self.sigma + 63) // 64 * 64
         self.flop_per_unit = 2 * self.K               # the one-hot GEMM per pair
@@ -320,6 +315,52 @@ class Hamming:
         t = time.perf_counter()
         oracle.hamming(self.s[:rows], self.sigma)
         return rows * (rows - 1) // 2, time.perf_counter() - t, f"closest pair of the first {rows} strings"
+
+
+class MLBA:
+    """The light-bulb candidate search of Sec. 4 (MLBA) on the strings of the hamming workload
+    (65,536 strings x 64 symbols over {0, 1, 2, 3}, one pair planted at 2 mismatches): 8 iterations
+    of 16 sampled columns (c log n columns with c = 1).  Throughput is counted in brute-force-equivalent
+    pairs, n (n - 1) / 2 per step, as in the paper's comparison with the exact search."""
+    name = "mlba"
+
+    def __init__(self, args):
+        from paper_1407_5609_gb300 import synth
+        self.n, self.t, self.sigma, self.iters, self.L = 65536, 64, 4, 8, 16
+        self.s = synth.make_strings(self.n, self.t, self.sigma)
+        self.cols = synth.sample_columns(self.iters, self.L, self.t, seed=synth.SEED_BASE + 6)
+        self.units = self.n * (self.n - 1) // 2
+        self.passes = (self.L * 2 + 7) // 8                 # 8-bit digits of the 2-bit symbols' keys
+        self.config = {"workload": "MLBA closest pair: 65536 strings x 64 symbols, sigma=4, planted pair at 2 "
+                                   "mismatches; 8 iterations x 16 sampled columns",
+                       "pairs_per_step": self.units, "units": "brute-force-equivalent pairs",
+                       "l2": "every buffer (about 14 MB) stays in L2"}
+
+    def setup(self, dev):
+        import torch
+        from paper_1407_5609_gb300 import capi
+        self.dev_s = torch.from_numpy(self.s).to(dev)
+        self.dev_cols = torch.from_numpy(self.cols).to(dev)
+        self.ws = torch.empty(capi.mlba_pair_workspace_size(self.n, self.t, self.sigma, False, self.iters),
+                              dtype=torch.uint8, device=dev)
+
+    def step(self, capi, mode):
+        return capi.mlba_pair(self.dev_s, self.sigma, self.dev_cols, ws=self.ws)
+
+    def e2e_step(self, capi, mode, host, dev_buf):
+        for hp, dp in zip(host, dev_buf):
+            dp.copy_(hp, non_blocking=True)
+        return capi.mlba_pair(dev_buf[0], self.sigma, dev_buf[1], ws=self.ws)
+
+    def host_input(self):
+        return [self.s, self.cols], self.s.nbytes + self.cols.nbytes
+
+    def oracle_sample(self, oracle, rows):
+        rows = max(2, min(rows, self.n))
+        t = time.perf_counter()
+        oracle.mlba(self.s[:rows], self.sigma, self.cols)
+        return (rows * (rows - 1) // 2, time.perf_counter() - t,
+                f"MLBA on the first {rows} strings with the same sampled columns")
 
 
 class Batch:
@@ -404,7 +445,8 @@ class Batch:
         return pairs, time.perf_counter() - t, f"closest pair + R-pairs of the first {rows} instances ({pairs} pairs)"
 
 
-WORKLOADS = {"tsmm": TSMM, "twolocus": TwoLocus, "cpp": CPP, "frnn": FRNN, "batch": Batch, "hamming": Hamming}
+WORKLOADS = {"tsmm": TSMM, "twolocus": TwoLocus, "cpp": CPP, "frnn": FRNN, "batch": Batch, "hamming": Hamming,
+             "mlba": MLBA}
 
 
 # ------------------------------------------------------------------ helpers
@@ -440,6 +482,8 @@ def d2h_bytes(wl, capi):
         return len(wl.batch) * (64 + 8) + 24            # per-instance results and pair offsets
     if wl.name == "hamming":
         return 32 + 4                                   # the best partial and the status word
+    if wl.name == "mlba":
+        return 32 + 4                                   # the result block and the status word
     return ctypes.sizeof(capi.twolocus_result)
 
 
@@ -513,7 +557,7 @@ def run_ours(args):
 
     # timed region (device-resident inputs)
     capi.cpp_set_stage_timing(True)
-    dense_ms = []
+    dense_ms, stages = [], []
     launches0 = capi.cpp_launch_count()
     clocks = ClockSampler(local)
     clocks.start()
@@ -523,6 +567,7 @@ def run_ours(args):
         st = capi.cpp_stage_times()
         if len(st) >= 2:
             dense_ms.append(st[1])
+            stages.append(list(st))
         return r
     barrier()
     total_ms, res = timed_steps(one, args.steps, stream, torch, flush)
@@ -541,7 +586,7 @@ def run_ours(args):
            "scaling": "strong" if sharded else "weak", "vs_baseline": None,
            "dtype": ({"plain_fp32": "f32", "filter_fp16": "f16", "filter_bf16": "bf16"}.get(mode.replace("_prune", ""))
                      if wl.name in ("tsmm", "cpp") else {"frnn": "f32", "twolocus": "u64", "batch": "f32",
-                                                         "hamming": "bf16"}[wl.name]),
+                                                         "hamming": "bf16", "mlba": "u64"}[wl.name]),
            "data": "synthetic", "config": dict(wl.config, mode=mode if wl.name in ("tsmm", "cpp") else None,
                                                flush_l2_between_steps=bool(flush),
                                                parallelism=(f"{world} shards of one search + one exchange of the results"
@@ -638,6 +683,23 @@ def run_ours(args):
                            "frac": ach / pk["bf16_tflops"], "traffic": recorded_traffic("match_tc@hamming"),
                            "kernel": "match_tc_kernel (step time; one-hot GEMM, 2 K flop per pair)",
                            "peak_source": f"{pk['source']} bf16 burst"}
+    elif wl.name == "mlba" and stages:
+        # per stage [pack + keys, radix sort, buckets + pair offsets, verification], CUDA events inside the call
+        st_ms = [statistics.mean(x[k] for x in stages) for k in range(4)]
+        out["stages_ms"] = dict(zip(("pack_keys", "radix_sort", "buckets", "verify"), st_ms))
+        E = wl.iters * wl.n
+        # algorithmic bytes of the sort: per 8-bit pass the histogram reads the keys (8 B) and the scatter
+        # reads and writes key + row (12 + 12 B) of every element
+        sort_bytes = wl.passes * E * (8 + 24)
+        ach = sort_bytes / (st_ms[1] / 1e3) / 1e9
+        out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                           "frac": ach / pk["hbm_gbs"], "traffic": recorded_traffic("mlba_sort@mlba"),
+                           "kernel": f"radix sort stage ({wl.passes} passes x hist + scan + scatter; L2-resident)",
+                           "peak_source": f"{pk['source']} HBM copy"}
+        if not args.no_compare and capi.filters_available():
+            ex = capi.hamming_pair(wl.dev_s, wl.sigma)      # the exact all-pairs answer, untimed
+            out["same_answer_as_exact"] = (ex["i"], ex["j"], ex["mismatches"]) == (res["i"], res["j"], res["mismatches"])
+        out["candidates_per_step"] = res["candidates"]
     out["clocks"] = clk
 
     # the same answer from the plain FP32 path, and its throughput

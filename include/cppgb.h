@@ -204,6 +204,40 @@ size_t hamming_pair_workspace_size(int64_t n, int64_t t, int sigma);
 int hamming_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, int least, hamming_result* out,
                  void* ws, size_t ws_bytes, void* stream);
 
+/* Result of a light-bulb candidate search. */
+typedef struct {
+  int64_t i, j;        /* the best candidate pair, i < j; -1 when no pair shared a bucket */
+  int64_t mismatches;  /* its Hamming distance; -1 when there is no candidate */
+  int64_t candidates;  /* candidate pairs verified, each counted once per iteration it was found in */
+} mlba_result;
+
+/*
+ * mlba_pair -- the modified light-bulb algorithm (MLBA) of Sec. 4: a randomised search for the
+ * closest pair of strings (least = 0) that looks only at the pairs sharing a bucket in some
+ * iteration, and its least correlated form (least = 1) over the one-hot strings and their
+ * complements of Sec. 5.4-5.5.  The random choice of columns is the caller's: cols holds, for each
+ * of the iters iterations, L sampled columns (the paper samples c log n of them), which are
+ *   least = 0: symbol positions 0 .. t-1;
+ *   least = 1: one-hot columns 0 .. sigma*t - 1, column c being the bit [s_{c / sigma} = c % sigma]
+ *              of a string and its negation for a complement.
+ * In each iteration the rows are grouped by their characters in the sampled columns (a radix sort);
+ * every two strings in a group are a candidate (least = 1: a string and the complement of another;
+ * each unordered pair at most once per iteration), and every candidate is verified by its Hamming
+ * distance.  The answer is the candidate with the fewest (least = 0) or most (least = 1)
+ * mismatches, ties to the smallest (i, j); it is the exact answer when the best pair met in some
+ * iteration (L = 0 makes every pair a candidate: the brute force).
+ *   strs  device uint8 [n][ld], ld >= t, symbols < sigma, 2 <= sigma <= 256.
+ *   cols  device int32 [iters][L] (not read when L = 0).  The sampled characters fill one 64-bit
+ *         key: L * ceil(log2 sigma) <= 64 (least = 0), 1 <= L <= 64 (least = 1); iters x rows
+ *         (n, or 2n for least = 1) below 2^31.
+ * The call synchronises the stream before it returns.
+ * Errors: CPPGB_ERR_ARG (also for a symbol >= sigma or a column out of range), CPPGB_ERR_CAPACITY
+ * (ws), CPPGB_ERR_CUDA.
+ */
+size_t mlba_pair_workspace_size(int64_t n, int64_t t, int sigma, int least, int64_t iters);
+int mlba_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, int least, const int32_t* cols,
+              int64_t iters, int64_t L, mlba_result* out, void* ws, size_t ws_bytes, void* stream);
+
 /*
  * frnn_query -- fixed-radius near neighbours (Sec. 3.5): for every point p_i its R-neighbourhood
  * N(i) = { j != i : d(p_i, p_j) <= R }, with j in N(i) iff i in N(j).  The decision is the FP64
@@ -265,7 +299,8 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
  * their stages; cpp_stage_times() then copies the last call's stage durations in milliseconds
  * (per calling thread) into ms[0..cap) and returns how many it wrote: [prep, dense all-pairs stage,
  * FP64 recheck] after cpp_closest_pair / tsmm_motif, [preparation, tensor-core tiles, FP32 tiles,
- * second pass + recheck + output] after cpp_batch (events captured in its graph).  cpp_launch_count() returns the number of kernels this library has launched
+ * second pass + recheck + output] after cpp_batch (events captured in its graph), [pack + keys,
+ * radix sort, buckets + pair offsets, verification] after mlba_pair.  cpp_launch_count() returns the number of kernels this library has launched
  * in the process so far.
  */
 void cpp_set_stage_timing(int on);

@@ -56,6 +56,14 @@ class hamming_result(ctypes.Structure):
         return {"i": self.i, "j": self.j, "mismatches": self.mismatches}
 
 
+class mlba_result(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_int64), ("j", ctypes.c_int64), ("mismatches", ctypes.c_int64),
+                ("candidates", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {"i": self.i, "j": self.j, "mismatches": self.mismatches, "candidates": self.candidates}
+
+
 class cpp_instance(ctypes.Structure):
     _fields_ = [("pts", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("R", ctypes.c_double)]
@@ -80,6 +88,9 @@ SIGNATURES = {
     "twolocus_scan_tc": (_int, [_vp, _i64, _i64, _i64, _i64, _int, ctypes.POINTER(twolocus_result), _vp, _sz, _vp]),
     "hamming_pair_workspace_size": (_sz, [_i64, _i64, _int]),
     "hamming_pair": (_int, [_vp, _i64, _i64, _i64, _int, _int, ctypes.POINTER(hamming_result), _vp, _sz, _vp]),
+    "mlba_pair_workspace_size": (_sz, [_i64, _i64, _int, _int, _i64]),
+    "mlba_pair": (_int, [_vp, _i64, _i64, _i64, _int, _int, _vp, _i64, _i64, ctypes.POINTER(mlba_result), _vp, _sz,
+                         _vp]),
     "twolocus_scan_shard": (_int, [_vp, _i64, _i64, _i64, _i64, _i64, _i64, ctypes.POINTER(twolocus_result), _vp,
                                     _sz, _vp]),
     "frnn_query_workspace_size": (_sz, [_i64, _int]),
@@ -347,6 +358,31 @@ def hamming_pair(strings: torch.Tensor, sigma: int, least: bool = False, ws: tor
     out = hamming_result()
     _raise(lib().hamming_pair(strings.data_ptr() if n else None, n, t, strings.stride(0) if n else t, int(sigma),
                               1 if least else 0, ctypes.byref(out), ws.data_ptr(), ws.numel(), _stream(stream)))
+    return out.as_dict()
+
+
+def mlba_pair_workspace_size(n: int, t: int, sigma: int, least: bool, iters: int) -> int:
+    return int(lib().mlba_pair_workspace_size(n, t, sigma, 1 if least else 0, iters))
+
+
+def mlba_pair(strings: torch.Tensor, sigma: int, cols: torch.Tensor, least: bool = False,
+              ws: torch.Tensor | None = None, stream=None) -> dict:
+    """Light-bulb candidate search (include/cppgb.h, mlba_pair) over the rows of a uint8 [n][t]
+    symbol matrix with the sampled columns cols, int32 [iters][L] on the device."""
+    _check_cuda(strings, "strings")
+    _check_cuda(cols, "cols")
+    if strings.dim() != 2 or strings.dtype != torch.uint8 or strings.stride(1) != 1:
+        raise ValueError("strings must be uint8 [n][t] with unit column stride")
+    if cols.dim() != 2 or cols.dtype != torch.int32 or not cols.is_contiguous():
+        raise ValueError("cols must be a contiguous int32 tensor [iters][L]")
+    n, t = strings.shape
+    iters, L = cols.shape
+    if ws is None:
+        ws = _workspace(mlba_pair_workspace_size(n, t, sigma, least, iters), strings.device)
+    out = mlba_result()
+    _raise(lib().mlba_pair(strings.data_ptr() if n else None, n, t, strings.stride(0) if n else t, int(sigma),
+                           1 if least else 0, cols.data_ptr() if cols.numel() else None, iters, L,
+                           ctypes.byref(out), ws.data_ptr(), ws.numel(), _stream(stream)))
     return out.as_dict()
 
 

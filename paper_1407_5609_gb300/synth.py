@@ -194,3 +194,25 @@ def make_batch(count: int = 2048, seed: int = SEED_BASE + 4, n_lo: int = 256, n_
         out.append(BatchInstance(np.ascontiguousarray(pts.astype(np.float32)), (a, b),
                                  plant_dist, 2.0 * plant_dist))
     return out
+
+
+def make_strings(n: int = 65536, t: int = 64, sigma: int = 4, seed: int = SEED_BASE + 5,
+                 plant: tuple | None = (12345, 54321), at: tuple = (7, 40)) -> np.ndarray:
+    """Uniform strings uint8 [n][t] over {0, .., sigma-1} (Sec. 4's strings; four letters is the
+    discretisation of its experiment).  With ``plant = (a, b)`` string b copies string a except at
+    the positions ``at``, where its symbol is shifted by one: a pair at len(at) mismatches."""
+    s = rng_for(seed).integers(0, sigma, (n, t)).astype(np.uint8)
+    if plant is not None:
+        a, b = plant
+        s[b] = s[a]
+        idx = list(at)
+        s[b, idx] = ((s[b, idx].astype(np.int64) + 1) % sigma).astype(np.uint8)
+    return np.ascontiguousarray(s)
+
+
+def sample_columns(iters: int, L: int, width: int, seed: int) -> np.ndarray:
+    """The columns the light-bulb algorithm samples (Sec. 4): int32 [iters][L], each drawn
+    uniformly from [0, width) with replacement."""
+    if L == 0 or width == 0:
+        return np.zeros((iters, L), np.int32)
+    return rng_for(seed).integers(0, width, (iters, L)).astype(np.int32)

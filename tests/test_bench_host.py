@@ -21,7 +21,7 @@ def bench_mod():
     return bench
 
 
-@pytest.mark.parametrize("name", ["tsmm", "cpp", "twolocus", "frnn", "batch", "hamming"])
+@pytest.mark.parametrize("name", ["tsmm", "cpp", "twolocus", "frnn", "batch", "hamming", "mlba"])
 def test_workload_and_cpu_baseline(bench_mod, name):
     args = argparse.Namespace(series_len=262144, batch_count=4, no_tune=True, batch_path=0)
     wl = bench_mod.WORKLOADS[name](args)
