@@ -341,7 +341,7 @@ class MLBA:
         from paper_1407_5609_gb300 import capi
         self.dev_s = torch.from_numpy(self.s).to(dev)
         self.dev_cols = torch.from_numpy(self.cols).to(dev)
-        self.ws = torch.empty(capi.mlba_pair_workspace_size(self.n, self.t, self.sigma, False, self.iters),
+        self.ws = torch.empty(capi.mlba_pair_workspace_size(self.n, self.t, self.sigma, False, self.iters, self.L),
                               dtype=torch.uint8, device=dev)
 
     def step(self, capi, mode):

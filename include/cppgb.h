@@ -234,7 +234,7 @@ typedef struct {
  * Errors: CPPGB_ERR_ARG (also for a symbol >= sigma or a column out of range), CPPGB_ERR_CAPACITY
  * (ws), CPPGB_ERR_CUDA.
  */
-size_t mlba_pair_workspace_size(int64_t n, int64_t t, int sigma, int least, int64_t iters);
+size_t mlba_pair_workspace_size(int64_t n, int64_t t, int sigma, int least, int64_t iters, int64_t L);
 int mlba_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, int least, const int32_t* cols,
               int64_t iters, int64_t L, mlba_result* out, void* ws, size_t ws_bytes, void* stream);
 

@@ -88,7 +88,7 @@ SIGNATURES = {
     "twolocus_scan_tc": (_int, [_vp, _i64, _i64, _i64, _i64, _int, ctypes.POINTER(twolocus_result), _vp, _sz, _vp]),
     "hamming_pair_workspace_size": (_sz, [_i64, _i64, _int]),
     "hamming_pair": (_int, [_vp, _i64, _i64, _i64, _int, _int, ctypes.POINTER(hamming_result), _vp, _sz, _vp]),
-    "mlba_pair_workspace_size": (_sz, [_i64, _i64, _int, _int, _i64]),
+    "mlba_pair_workspace_size": (_sz, [_i64, _i64, _int, _int, _i64, _i64]),
     "mlba_pair": (_int, [_vp, _i64, _i64, _i64, _int, _int, _vp, _i64, _i64, ctypes.POINTER(mlba_result), _vp, _sz,
                          _vp]),
     "twolocus_scan_shard": (_int, [_vp, _i64, _i64, _i64, _i64, _i64, _i64, ctypes.POINTER(twolocus_result), _vp,
@@ -361,8 +361,8 @@ def hamming_pair(strings: torch.Tensor, sigma: int, least: bool = False, ws: tor
     return out.as_dict()
 
 
-def mlba_pair_workspace_size(n: int, t: int, sigma: int, least: bool, iters: int) -> int:
-    return int(lib().mlba_pair_workspace_size(n, t, sigma, 1 if least else 0, iters))
+def mlba_pair_workspace_size(n: int, t: int, sigma: int, least: bool, iters: int, L: int) -> int:
+    return int(lib().mlba_pair_workspace_size(n, t, sigma, 1 if least else 0, iters, L))
 
 
 def mlba_pair(strings: torch.Tensor, sigma: int, cols: torch.Tensor, least: bool = False,
@@ -378,7 +378,7 @@ def mlba_pair(strings: torch.Tensor, sigma: int, cols: torch.Tensor, least: bool
     n, t = strings.shape
     iters, L = cols.shape
     if ws is None:
-        ws = _workspace(mlba_pair_workspace_size(n, t, sigma, least, iters), strings.device)
+        ws = _workspace(mlba_pair_workspace_size(n, t, sigma, least, iters, L), strings.device)
     out = mlba_result()
     _raise(lib().mlba_pair(strings.data_ptr() if n else None, n, t, strings.stride(0) if n else t, int(sigma),
                            1 if least else 0, cols.data_ptr() if cols.numel() else None, iters, L,

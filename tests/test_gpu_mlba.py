@@ -29,7 +29,7 @@ def _run(s, sigma, cols, least):
 # long strings, every packing width (1, 2, 3, 5, 8 bits per symbol), few and many sort passes
 CLOSEST = [(2, 1, 2, 1, 1), (3, 7, 3, 2, 2), (1000, 37, 4, 3, 5), (5000, 64, 4, 4, 8), (4099, 100, 5, 2, 6),
            (2500, 33, 17, 3, 3), (3000, 20, 256, 2, 2), (6000, 130, 2, 5, 16), (4097, 64, 4, 2, 32),
-           (3000, 64, 2, 1, 64)]
+           (3000, 64, 2, 1, 64), (140000, 16, 4, 2, 8)]       # the last: 69 sort tiles, the unfused scan
 
 
 @pytest.mark.parametrize("n,t,sigma,iters,L", CLOSEST)
@@ -40,7 +40,7 @@ def test_closest_matches_oracle(n, t, sigma, iters, L):
 
 
 LEAST = [(2, 3, 2, 1, 1), (700, 9, 3, 4, 3), (3000, 16, 4, 3, 6), (4099, 40, 3, 2, 10), (2500, 12, 5, 3, 4),
-         (1500, 8, 2, 6, 5), (5000, 64, 4, 2, 20), (2000, 30, 7, 2, 64)]
+         (1500, 8, 2, 6, 5), (5000, 64, 4, 2, 20), (2000, 30, 7, 2, 64), (70000, 10, 3, 2, 12)]
 
 
 @pytest.mark.parametrize("n,t,sigma,iters,L", LEAST)
@@ -109,7 +109,7 @@ def test_empty_and_errors():
             capi.mlba_pair(to_dev(bad_s, dev), 4, to_dev(cols, dev), least=least)
         assert e.value.status == capi.ERR_ARG
     cols = to_dev(np.zeros((2, 3), np.int32), dev)
-    need = capi.mlba_pair_workspace_size(100, 8, 4, False, 2)
+    need = capi.mlba_pair_workspace_size(100, 8, 4, False, 2, 3)
     import torch
     small = torch.empty(need - 256, dtype=torch.uint8, device=dev)
     with pytest.raises(capi.CppgbError) as e:
