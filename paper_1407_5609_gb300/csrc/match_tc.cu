@@ -32,8 +32,10 @@ using namespace tc;
 
 constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6;
 constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int NTHREADS = 192;
-constexpr uint32_t TMEM_COLS = 512;  // 2 tiles in flight x up to 2 groups x 128 columns
+constexpr int EPI_WARPS = 8;                  // two per TMEM lane quarter, each on half the tile's columns
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;  // producer, MMA issuer, epilogue
+constexpr uint32_t TMEM_COLS = 512;            // 4 tiles in flight (one group) or 2 (two groups) x 128 columns
+constexpr int MAX_ACC = 4;
 
 struct MatchMaps {
   CUtensorMap L[2], R[2];
@@ -50,8 +52,8 @@ struct MatchParams {
 };
 
 struct Ctl {
-  uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
-  MatchPartial red[4];
+  uint64_t full[STAGES], empty[STAGES], tfull[MAX_ACC], tempty[MAX_ACC], drain;
+  MatchPartial red[EPI_WARPS];
   uint32_t tmem_base;
   int abort_flag;
 };
@@ -76,6 +78,22 @@ __device__ __forceinline__ bool better(unsigned long long k, int i, int j, unsig
   return j < bj;
 }
 
+// the best key a 32-column chunk of string matches can give: most agreeing positions (most) or
+// most mismatches (t - fewest agreeing), from a max / min tree over the FP32 counts
+template <bool MOST>
+__device__ __forceinline__ unsigned long long chunk_key(const uint32_t (&r)[32], int64_t t) {
+  float m[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+    m[k] = MOST ? fmaxf(__uint_as_float(r[k]), __uint_as_float(r[k + 16]))
+                : fminf(__uint_as_float(r[k]), __uint_as_float(r[k + 16]));
+#pragma unroll
+  for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+    for (int k = 0; k < w; ++k) m[k] = MOST ? fmaxf(m[k], m[k + w]) : fminf(m[k], m[k + w]);
+  return MOST ? (unsigned long long)m[0] : (unsigned long long)(t - (int64_t)m[0]);
+}
+
 __device__ __forceinline__ double pearson_r(int64_t m, int64_t sxy, int64_t sxi, int64_t sxj, int64_t vxi, int64_t vxj) {
   if (vxi == 0 || vxj == 0) return 0.0;
   const double num = (double)(m * sxy - sxi * sxj);
@@ -83,6 +101,8 @@ __device__ __forceinline__ double pearson_r(int64_t m, int64_t sxy, int64_t sxi,
   return __ddiv_rn(num, den);
 }
 
+// One instantiation per measure (MatchMode): each carries only its own epilogue arithmetic.
+template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     match_tc_kernel(const __grid_constant__ MatchMaps maps, const __grid_constant__ MatchParams mp, int64_t total,
                     int64_t nb, MatchPartial* __restrict__ partials, unsigned int* status) {
@@ -97,9 +117,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&ctl->full[s], 1);
       mbar_init(&ctl->empty[s], 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < MAX_ACC; ++a) {
       mbar_init(&ctl->tfull[a], 1);
-      mbar_init(&ctl->tempty[a], 4);
+      mbar_init(&ctl->tempty[a], EPI_WARPS);
     }
     mbar_init(&ctl->drain, 1);
     ctl->abort_flag = 0;
@@ -115,6 +135,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = ctl->tmem_base;
+  // accumulators in flight: TMEM holds 512 columns, a tile needs 128 per group
+  const uint32_t nacc = mp.groups == 1 ? 4u : 2u, acc_cols = (uint32_t)mp.groups * (uint32_t)BN;
 
   if (warp == 0) {
     if (lane == 0) {  // ---------------------------------------------- TMA producer
@@ -159,11 +181,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int64_t it = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
-        const uint32_t acc = (uint32_t)(it & 1), use = (uint32_t)((it >> 1) & 1);
+        const uint32_t acc = (uint32_t)(it % nacc), use = (uint32_t)((it / nacc) & 1);
         if (!mbar_wait(&ctl->tempty[acc], use ^ 1u, abort_flag)) { ok = false; break; }
         tc_fence_after();
         for (int g = 0; g < mp.groups && ok; ++g) {
-          const uint32_t dtmem = tmem_base + acc * 256u + (uint32_t)g * (uint32_t)BN;
+          const uint32_t dtmem = tmem_base + acc * acc_cols + (uint32_t)g * (uint32_t)BN;
           for (int64_t kc = 0; kc < mp.kch[g]; ++kc) {
             if (!mbar_wait(&ctl->full[stage], phase, abort_flag)) { ok = false; break; }
             tc_fence_after();
@@ -188,84 +210,94 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       while (!mbar_try_wait(&ctl->drain, 0) && globaltimer() - t0 < WAIT_NS) {
       }
     }
-  } else {  // -------------------------------------------------------- epilogue (warps 2..5)
+  } else {  // -------------------------------------------------------- epilogue (warps 2 .. 2 + EPI_WARPS - 1)
+    // warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31 (its lane quarter) and the half (w - 2) / 4
+    // of the tile's columns
     const uint32_t quarter = (uint32_t)(warp & 3);
+    const int half = (warp - 2) / 4;
     unsigned long long bk = 0ull;
     int bi_best = -1, bj_best = -1;
     int64_t it = 0;
     bool ok = true;
+    constexpr bool ham = MODE == MATCH_HAMMING_MIN || MODE == MATCH_HAMMING_MAX;
+    constexpr bool most = MODE == MATCH_HAMMING_MIN;
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
       int64_t bi, bj;
       tri_tile(t, nb, &bi, &bj);
-      const uint32_t acc = (uint32_t)(it & 1), use = (uint32_t)((it >> 1) & 1);
+      const uint32_t acc = (uint32_t)(it % nacc), use = (uint32_t)((it / nacc) & 1);
       if (!__all_sync(0xffffffffu, mbar_wait(&ctl->tfull[acc], use, abort_flag))) { ok = false; break; }
       tc_fence_after();
       const int64_t i = bi * BM + quarter * 32 + lane;
       const bool row_ok = i < mp.S;
       const int64_t ii = row_ok ? i : 0;
-      const uint32_t tb = tmem_base + ((quarter * 32u) << 16) + acc * 256u;
+      const uint32_t tb = tmem_base + ((quarter * 32u) << 16) + acc * acc_cols;
       int32_t sAi = 0, sBi = 0;
       int64_t sxAi = 0, sxBi = 0, vxAi = 0, vxBi = 0;
-      if (mp.mode == MATCH_TL_COUNT) {
+      if (MODE == MATCH_TL_COUNT) {
         sAi = mp.s[0][ii];
         sBi = mp.s[1][ii];
-      } else if (mp.mode == MATCH_TL_PEARSON) {
+      } else if (MODE == MATCH_TL_PEARSON) {
         sxAi = mp.sx[0][ii];
         sxBi = mp.sx[1][ii];
         vxAi = mp.vx[0][ii];
         vxBi = mp.vx[1][ii];
       }
-      const bool ham = mp.mode == MATCH_HAMMING_MIN || mp.mode == MATCH_HAMMING_MAX;
       const bool edge = bi == bj || (bi + 1) * BM > mp.S || (bj + 1) * BN > mp.S;
-#pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
-        uint32_t ra[32], rb[32];
-        tmem_ld32(tb + (uint32_t)(c * 32), ra);
-        if (mp.groups == 2) tmem_ld32(tb + (uint32_t)BN + (uint32_t)(c * 32), rb);
-        if (ham && !edge && bi_best >= 0) {
-          // fast path: the chunk's best count (a 31-op tree) decides whether any entry can reach or
-          // tie the thread's best key; most chunks cannot
-          float m[16];
-          const bool most = mp.mode == MATCH_HAMMING_MIN;
-#pragma unroll
-          for (int k = 0; k < 16; ++k)
-            m[k] = most ? fmaxf(__uint_as_float(ra[k]), __uint_as_float(ra[k + 16]))
-                        : fminf(__uint_as_float(ra[k]), __uint_as_float(ra[k + 16]));
-#pragma unroll
-          for (int k = 0; k < 8; ++k) m[k] = most ? fmaxf(m[k], m[k + 8]) : fminf(m[k], m[k + 8]);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) m[k] = most ? fmaxf(m[k], m[k + 4]) : fminf(m[k], m[k + 4]);
-          const float cm = most ? fmaxf(fmaxf(m[0], m[2]), fmaxf(m[1], m[3])) : fminf(fminf(m[0], m[2]), fminf(m[1], m[3]));
-          const unsigned long long ck = most ? (unsigned long long)cm : (unsigned long long)(mp.m[0] - (int64_t)cm);
-          if (ck < bk) continue;
+      // the pair (i, j) with the accumulators a (group A / strings) and b (group B) as FP32 bits
+      auto consider = [&](int64_t j, uint32_t a, uint32_t b) {
+        if (!(row_ok && j < mp.S && j > i)) return;
+        const int64_t accA = (int64_t)__uint_as_float(a);
+        unsigned long long key;
+        if (MODE == MATCH_TL_COUNT) {
+          const int64_t accB = (int64_t)__uint_as_float(b);
+          const int64_t uA = mp.m[0] - sAi - mp.s[0][j] + accA;
+          const int64_t uB = mp.m[1] - sBi - mp.s[1][j] + accB;
+          const int64_t sc = uA * mp.m[1] - uB * mp.m[0];
+          key = (unsigned long long)(sc < 0 ? -sc : sc);
+        } else if (MODE == MATCH_TL_PEARSON) {
+          const int64_t accB = (int64_t)__uint_as_float(b);
+          const double rA = pearson_r(mp.m[0], accA, sxAi, mp.sx[0][j], vxAi, mp.vx[0][j]);
+          const double rB = pearson_r(mp.m[1], accB, sxBi, mp.sx[1][j], vxBi, mp.vx[1][j]);
+          key = (unsigned long long)__double_as_longlong(fabs(__dsub_rn(rA, rB)));
+        } else if (MODE == MATCH_HAMMING_MIN) {
+          key = (unsigned long long)accA;  // most agreeing positions = fewest mismatches
+        } else {
+          key = (unsigned long long)(mp.m[0] - accA);  // most mismatches
         }
+        if (better(key, (int)i, (int)j, bk, bi_best, bj_best)) {
+          bk = key;
+          bi_best = (int)i;
+          bj_best = (int)j;
+        }
+      };
+      if (ham) {
+        // both 32-column chunks of this half in flight at once, one wait
+        uint32_t ra[32], rb[32];
+        const uint32_t c0 = (uint32_t)(half * 64);
+        tmem_ld32_nowait(tb + c0, ra);
+        tmem_ld32_nowait(tb + c0 + 32u, rb);
+        tmem_wait_ld(ra);
+        tmem_wait_ld(rb);
+        const int64_t j0 = bj * BN + c0;
+        // per chunk, its best count (a 31-op tree) decides whether any entry can reach or tie the
+        // thread's best key; most chunks cannot
+        const bool fast = !edge && bi_best >= 0;
+        if (!fast || chunk_key<most>(ra, mp.m[0]) >= bk) {
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const int64_t j = bj * BN + c * 32 + k;
-          if (!(row_ok && j < mp.S && j > i)) continue;
-          const int64_t accA = (int64_t)__uint_as_float(ra[k]);
-          unsigned long long key;
-          if (mp.mode == MATCH_TL_COUNT) {
-            const int64_t accB = (int64_t)__uint_as_float(rb[k]);
-            const int64_t uA = mp.m[0] - sAi - mp.s[0][j] + accA;
-            const int64_t uB = mp.m[1] - sBi - mp.s[1][j] + accB;
-            const int64_t sc = uA * mp.m[1] - uB * mp.m[0];
-            key = (unsigned long long)(sc < 0 ? -sc : sc);
-          } else if (mp.mode == MATCH_TL_PEARSON) {
-            const int64_t accB = (int64_t)__uint_as_float(rb[k]);
-            const double rA = pearson_r(mp.m[0], accA, sxAi, mp.sx[0][j], vxAi, mp.vx[0][j]);
-            const double rB = pearson_r(mp.m[1], accB, sxBi, mp.sx[1][j], vxBi, mp.vx[1][j]);
-            key = (unsigned long long)__double_as_longlong(fabs(__dsub_rn(rA, rB)));
-          } else if (mp.mode == MATCH_HAMMING_MIN) {
-            key = (unsigned long long)accA;  // most agreeing positions = fewest mismatches
-          } else {
-            key = (unsigned long long)(mp.m[0] - accA);  // most mismatches
-          }
-          if (better(key, (int)i, (int)j, bk, bi_best, bj_best)) {
-            bk = key;
-            bi_best = (int)i;
-            bj_best = (int)j;
-          }
+          for (int k = 0; k < 32; ++k) consider(j0 + k, ra[k], 0u);
+        }
+        if (!fast || chunk_key<most>(rb, mp.m[0]) >= bk) {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) consider(j0 + 32 + k, rb[k], 0u);
+        }
+      } else {
+#pragma unroll 1
+        for (int c = 2 * half; c < 2 * half + 2; ++c) {
+          uint32_t ra[32], rb[32];
+          tmem_ld32(tb + (uint32_t)(c * 32), ra);
+          if (mp.groups == 2) tmem_ld32(tb + (uint32_t)BN + (uint32_t)(c * 32), rb);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) consider(bj * BN + c * 32 + k, ra[k], mp.groups == 2 ? rb[k] : 0u);
         }
       }
       tc_fence_before();
@@ -276,7 +308,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       *abort_flag = 1;
       atomicOr(status, 4u);
     }
-    // best of the warp, then of the four epilogue warps
+    // best of the warp, then of the epilogue warps
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned long long ok2 = __shfl_xor_sync(0xffffffffu, bk, o);
@@ -288,10 +320,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
     if (lane == 0) ctl->red[warp - 2] = MatchPartial{(long long)bk, bi_best, bj_best};
-    asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps, once, after their loops
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");  // the epilogue warps, once, after their loops
     if (warp == 2 && lane == 0) {
       MatchPartial b = ctl->red[0];
-      for (int w = 1; w < 4; ++w) {
+      for (int w = 1; w < EPI_WARPS; ++w) {
         const MatchPartial o = ctl->red[w];
         if (o.i >= 0 && better((unsigned long long)o.key, o.i, o.j, (unsigned long long)b.key, b.i, b.j)) b = o;
       }
@@ -449,8 +481,12 @@ int launch_match(const MatchMaps& maps, const MatchParams& mp, MatchPartial* par
   const int64_t grid = total < sms ? total : sms;
   *np_out = grid;
   if (grid == 0) return CPPGB_OK;
-  CPPGB_CUDA_TRY(cudaFuncSetAttribute(match_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-  match_tc_kernel<<<(unsigned)grid, NTHREADS, SMEM_BYTES, st>>>(maps, mp, total, nb, partials, status);
+  auto kern = mp.mode == MATCH_TL_COUNT      ? match_tc_kernel<MATCH_TL_COUNT>
+              : mp.mode == MATCH_TL_PEARSON  ? match_tc_kernel<MATCH_TL_PEARSON>
+              : mp.mode == MATCH_HAMMING_MIN ? match_tc_kernel<MATCH_HAMMING_MIN>
+                                             : match_tc_kernel<MATCH_HAMMING_MAX>;
+  CPPGB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+  kern<<<(unsigned)grid, NTHREADS, SMEM_BYTES, st>>>(maps, mp, total, nb, partials, status);
   CPPGB_LAUNCH_CHECK();
   return CPPGB_OK;
 }
