@@ -171,11 +171,12 @@ int twolocus_scan_shard(const uint64_t* planes, int64_t S, int64_t W, int64_t m_
  *                     measure Sec. 5 and Sec. 6 attribute to the method they compare with):
  *                     r = (m Sxy - Sx Sy) / sqrt(vx vy), vx = m Sxx - Sx^2 (0 when vx or vy is 0),
  *                     score |r_A - r_B| in score_real (score = -1), ties to the smallest (i, j).
- * The per-pair counts are exact integer GEMMs: one-hot planes a = [g = 1], b = [g = 2] become BF16
- * rows [a, b] (left) and [2c + d, c + 2d] or [c + 2d, 2c + 4d] (right); every partial sum is an
- * integer below 2^24, so the FP32 tensor-core accumulation is exact.  Arguments as for
- * twolocus_scan (W <= 4096, groups < 2^20 subjects); the workspace holds the four BF16 matrices,
- * 4 S W 128 x 2 bytes (256 MB at 4096 SNPs x 4096 + 4096 subjects).
+ * The per-pair counts are exact integer GEMMs: one-hot planes a = [g = 1], b = [g = 2] become FP8
+ * (E4M3) rows [a, b] (left) and [2c + d, c + 2d] or [c + 2d, 2c + 4d] (right) -- every value is
+ * 0, 1, 2 or 4, exact in E4M3 -- and every partial sum is an integer below 2^24, so the FP32
+ * tensor-core accumulation is exact.  Arguments as for twolocus_scan (W <= 4096, groups < 2^20
+ * subjects); the workspace holds the four FP8 matrices, 4 S W 128 bytes (128 MB at 4096 SNPs x
+ * 4096 + 4096 subjects).
  * Errors: CPPGB_ERR_ARG, CPPGB_ERR_CAPACITY (ws), CPPGB_ERR_TIMEOUT, CPPGB_ERR_CUDA.
  */
 #define CPPGB_TL_MATCHES 0
@@ -193,9 +194,9 @@ typedef struct {
 /*
  * hamming_pair -- closest pair (least = 0: fewest mismatches, the CPP of Sec. 4) or least
  * correlated pair (least = 1: most mismatches, Sec. 5) of n strings of t symbols from
- * {0, .., sigma - 1}, ties to the smallest (i, j).  Each string becomes a one-hot BF16 row of
- * t sigma entries (the mapping of Sec. 5.5, one 1 per position); the dot product of two rows,
- * accumulated exactly on the tensor cores, is the number of agreeing positions.
+ * {0, .., sigma - 1}, ties to the smallest (i, j).  Each string becomes a one-hot FP8 (E4M3) row
+ * of t sigma entries (the mapping of Sec. 5.5, one 1 per position); the dot product of two rows,
+ * accumulated exactly in FP32 on the tensor cores, is the number of agreeing positions.
  *   strs  device uint8 [n][ld], ld >= t.   2 <= sigma <= 256, t <= 2^23.
  * Errors: CPPGB_ERR_ARG (also for a symbol >= sigma), CPPGB_ERR_CAPACITY (ws), CPPGB_ERR_TIMEOUT,
  * CPPGB_ERR_CUDA.

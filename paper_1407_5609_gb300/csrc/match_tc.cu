@@ -30,8 +30,10 @@ namespace cppgb {
 namespace {
 using namespace tc;
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6;
-constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+// Operands are FP8 E4M3 (one byte; 0, 1, 2 and 4 are exact), so a stage holds 128 K values per row
+// (one 128-byte swizzle atom) and one MMA covers K = 32.
+constexpr int BM = 128, BN = 128, BK = 128, STAGES = 6;
+constexpr int A_BYTES = BM * BK, B_BYTES = BN * BK, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int EPI_WARPS = 8;                  // two per TMEM lane quarter, each on half the tile's columns
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;  // producer, MMA issuer, epilogue
 constexpr uint32_t TMEM_COLS = 512;            // 4 tiles in flight (one group) or 2 (two groups) x 128 columns
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---------------------------------------------- MMA issuer
-      const uint32_t idesc = make_idesc(1u, BM, BN);  // BF16 operands
+      const uint32_t idesc = make_idesc_f8(BM, BN);  // E4M3 operands, FP32 accumulator
       uint32_t stage = 0, phase = 0;
       int64_t it = 0;
       bool ok = true;
@@ -192,8 +194,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
             const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-              mma_f16(dtmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (kc | kk) != 0);
+            for (int kk = 0; kk < BK / 32; ++kk)  // K = 32 bytes per MMA: +2 in 16-byte descriptor units
+              mma_f8(dtmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (kc | kk) != 0);
             mma_commit(&ctl->empty[stage]);
             if (++stage == STAGES) { stage = 0; phase ^= 1u; }
           }
@@ -342,15 +344,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ---------------------------------------------------------------- preparation
-__device__ __forceinline__ uint16_t bf16_small(int v) {  // exact BF16 bits of 0 .. 4
-  return v == 0 ? 0x0000 : v == 1 ? 0x3f80 : v == 2 ? 0x4000 : v == 3 ? 0x4040 : 0x4080;
+__device__ __forceinline__ uint8_t e4m3_small(int v) {  // exact E4M3 bits of 0 .. 4 (exponent bias 7)
+  return v == 0 ? 0x00 : v == 1 ? 0x38 : v == 2 ? 0x40 : v == 3 ? 0x44 : 0x48;
 }
 
 // Two-locus rows: one warp per (row, group).  L = [a bits, b bits] of the group's W words (K = 128 W);
 // R = [2c + d, c + 2d] (count) or [c + 2d, 2c + 4d] (Pearson); rows >= S are zero.  Per-row sums:
 // s = sum (a + b) (count); Sx = sum (a + 2b), vx = m Sxx - Sx^2 with Sxx = sum (a + 4b) (Pearson).
 __global__ void tl_prep_kernel(const uint64_t* __restrict__ planes, int64_t S, int64_t S_pad, int64_t W, int64_t m1,
-                               int64_t m2, int mode, uint16_t* L0, uint16_t* R0, uint16_t* L1, uint16_t* R1,
+                               int64_t m2, int mode, uint8_t* L0, uint8_t* R0, uint8_t* L1, uint8_t* R1,
                                int32_t* s0, int32_t* s1, int64_t* sx0, int64_t* sx1, int64_t* vx0, int64_t* vx1) {
   const int lane = threadIdx.x & 31;
   const int64_t w_id = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -358,8 +360,8 @@ __global__ void tl_prep_kernel(const uint64_t* __restrict__ planes, int64_t S, i
   const int64_t row = w_id >> 1;
   const int g = (int)(w_id & 1);
   const int64_t K = 128 * W;
-  uint16_t* L = (g == 0 ? L0 : L1) + row * K;
-  uint16_t* R = (g == 0 ? R0 : R1) + row * K;
+  uint8_t* L = (g == 0 ? L0 : L1) + row * K;
+  uint8_t* R = (g == 0 ? R0 : R1) + row * K;
   long long sa = 0, sb = 0;
   for (int64_t w = lane; w < W; w += 32) {
     uint64_t a = 0, b = 0;
@@ -369,19 +371,19 @@ __global__ void tl_prep_kernel(const uint64_t* __restrict__ planes, int64_t S, i
     }
     sa += __popcll(a);
     sb += __popcll(b);
-    for (int q = 0; q < 64; q += 8) {  // 8 subjects per 16-byte store
-      uint16_t la[8], lb[8], r1[8], r2[8];
+    for (int q = 0; q < 64; q += 16) {  // 16 subjects per 16-byte store
+      uint8_t la[16], lb[16], r1[16], r2[16];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
+      for (int e = 0; e < 16; ++e) {
         const int ab = (int)((a >> (q + e)) & 1), bb = (int)((b >> (q + e)) & 1);
-        la[e] = bf16_small(ab);
-        lb[e] = bf16_small(bb);
+        la[e] = e4m3_small(ab);
+        lb[e] = e4m3_small(bb);
         if (mode == MATCH_TL_COUNT) {
-          r1[e] = bf16_small(2 * ab + bb);
-          r2[e] = bf16_small(ab + 2 * bb);
+          r1[e] = e4m3_small(2 * ab + bb);
+          r2[e] = e4m3_small(ab + 2 * bb);
         } else {
-          r1[e] = bf16_small(ab + 2 * bb);
-          r2[e] = bf16_small(2 * ab + 4 * bb);
+          r1[e] = e4m3_small(ab + 2 * bb);
+          r2[e] = e4m3_small(2 * ab + 4 * bb);
         }
       }
       *reinterpret_cast<uint4*>(L + 64 * w + q) = *reinterpret_cast<const uint4*>(la);
@@ -409,7 +411,7 @@ __global__ void tl_prep_kernel(const uint64_t* __restrict__ planes, int64_t S, i
 
 // One-hot rows of strings: X[row][p sigma + v] = 1 where s[row][p] = v (X zeroed before); one warp per row.
 __global__ void ham_prep_kernel(const uint8_t* __restrict__ strs, int64_t n, int64_t t, int64_t ld, int sigma,
-                                uint16_t* __restrict__ X, int64_t K, unsigned int* status) {
+                                uint8_t* __restrict__ X, int64_t K, unsigned int* status) {
   const int lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= n) return;
@@ -420,7 +422,7 @@ __global__ void ham_prep_kernel(const uint8_t* __restrict__ strs, int64_t n, int
       bad = true;
       continue;
     }
-    X[row * K + p * sigma + v] = 0x3f80;
+    X[row * K + p * sigma + v] = 0x38;  // E4M3 1.0
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, 1u);
 }
@@ -461,10 +463,10 @@ int encode_rows(CUtensorMap* m, void* base, int64_t rows, int64_t K) {
     fn = (EncodeTiledFn)p;
   }
   const cuuint64_t gdim[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-  const cuuint64_t gstride[1] = {(cuuint64_t)K * 2};
-  const cuuint32_t box[2] = {64, 128};
+  const cuuint64_t gstride[1] = {(cuuint64_t)K};  // one byte per value; K is a multiple of 128
+  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult cr = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, gdim, gstride, box, estr,
+  const CUresult cr = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, gdim, gstride, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return set_error(CPPGB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
@@ -492,7 +494,7 @@ int launch_match(const MatchMaps& maps, const MatchParams& mp, MatchPartial* par
 }
 
 struct TLLayout {
-  uint16_t *L[2], *R[2];
+  uint8_t *L[2], *R[2];
   int32_t* s[2];
   int64_t *sx[2], *vx[2];
   MatchPartial* partials;
@@ -506,8 +508,8 @@ TLLayout tl_layout(void* ws, int64_t S, int64_t W) {
   Carver c(ws);
   const int64_t S_pad = (S + BM - 1) / BM * BM, K = 128 * W;
   for (int g = 0; g < 2; ++g) {
-    L.L[g] = c.take<uint16_t>((size_t)(S_pad > 0 ? S_pad : BM) * K);
-    L.R[g] = c.take<uint16_t>((size_t)(S_pad > 0 ? S_pad : BM) * K);
+    L.L[g] = c.take<uint8_t>((size_t)(S_pad > 0 ? S_pad : BM) * K);
+    L.R[g] = c.take<uint8_t>((size_t)(S_pad > 0 ? S_pad : BM) * K);
     L.s[g] = c.take<int32_t>(S_pad + 1);
     L.sx[g] = c.take<int64_t>(S_pad + 1);
     L.vx[g] = c.take<int64_t>(S_pad + 1);
@@ -520,7 +522,7 @@ TLLayout tl_layout(void* ws, int64_t S, int64_t W) {
 }
 
 struct HamLayout {
-  uint16_t* X;
+  uint8_t* X;
   MatchPartial *partials, *best;
   unsigned int* status;
   size_t bytes;
@@ -530,7 +532,7 @@ HamLayout ham_layout(void* ws, int64_t n, int64_t K) {
   HamLayout L;
   Carver c(ws);
   const int64_t n_pad = (n + BM - 1) / BM * BM;
-  L.X = c.take<uint16_t>((size_t)(n_pad > 0 ? n_pad : BM) * K);
+  L.X = c.take<uint8_t>((size_t)(n_pad > 0 ? n_pad : BM) * K);
   L.partials = c.take<MatchPartial>(1024);
   L.best = c.take<MatchPartial>(1);
   L.status = c.take<unsigned int>(1);
@@ -622,7 +624,7 @@ int twolocus_scan_tc(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cas
 
 size_t hamming_pair_workspace_size(int64_t n, int64_t t, int sigma) {
   if (n < 0 || t < 1 || sigma < 2 || sigma > 256) return 0;
-  const int64_t K = (t * sigma + 63) / 64 * 64;
+  const int64_t K = (t * sigma + BK - 1) / BK * BK;
   return ham_layout(nullptr, n, K).bytes;
 }
 
@@ -634,7 +636,7 @@ int hamming_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigm
   if (n < 0 || n > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "n out of range");
   if (t < 1 || sigma < 2 || sigma > 256 || ld < t) return set_error(CPPGB_ERR_ARG, "need t >= 1, 2 <= sigma <= 256, ld >= t");
   if (t > (1 << 23)) return set_error(CPPGB_ERR_ARG, "strings longer than 2^23 symbols are not supported");
-  const int64_t K = (t * sigma + 63) / 64 * 64;
+  const int64_t K = (t * sigma + BK - 1) / BK * BK;
   if (K > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "t * sigma too large");
   if (n > 0 && !strs) return set_error(CPPGB_ERR_ARG, "strings is NULL");
   if (!ws || ((uintptr_t)ws & 255)) return set_error(CPPGB_ERR_ARG, "workspace must be non-NULL and 256-byte aligned");
@@ -644,7 +646,7 @@ int hamming_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigm
   if (n < 2) return CPPGB_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n_pad = (n + BM - 1) / BM * BM;
-  CPPGB_CUDA_TRY(cudaMemsetAsync(L.X, 0, sizeof(uint16_t) * (size_t)n_pad * K, st));
+  CPPGB_CUDA_TRY(cudaMemsetAsync(L.X, 0, (size_t)n_pad * K, st));
   CPPGB_CUDA_TRY(cudaMemsetAsync(L.status, 0, sizeof(unsigned int), st));
   ham_prep_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(strs, n, t, ld, sigma, L.X, K, L.status);
   CPPGB_LAUNCH_CHECK();

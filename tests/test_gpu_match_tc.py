@@ -86,3 +86,26 @@ def test_hamming_ties_and_small_inputs():
     with pytest.raises(capi.CppgbError) as e:
         capi.hamming_pair(to_dev(np.full((5, 3), 9, np.uint8), device()), 4)  # symbol >= sigma
     assert e.value.status == capi.ERR_ARG
+
+
+def test_large_sums_stay_exact():
+    """Counts far beyond 2^14 (where a reduced-precision accumulation of 8-bit products would lose
+    units): long strings and large genotype groups, against the oracle."""
+    capi = _capi()
+    dev = device()
+    s = synth.rng_for(150).integers(0, 2, (160, 100000)).astype(np.uint8)
+    s[101] = s[7]                                     # 100,000 agreeing positions
+    s[150] = 1 - s[20]                                 # none
+    d = to_dev(s, dev)
+    for least in (False, True):
+        r = capi.hamming_pair(d, 2, least=least)
+        assert (r["i"], r["j"], r["mismatches"]) == oracle.hamming(s, 2, least=least)
+    m1, m2 = 200000, 150001
+    g, _ = synth.make_genotypes(S=64, m1=m1, m2=m2, seed=151)
+    pl = _planes(g, m1, m2)
+    r = capi.twolocus_scan_tc(pl, m1, m2, measure="matches")
+    oi, oj, osc, ca, cb = oracle.twolocus(g, m1, m2)
+    assert (r["i"], r["j"], r["score"]) == (oi, oj, osc)
+    r = capi.twolocus_scan_tc(pl, m1, m2, measure="pearson")
+    pi, pj, psc = oracle.twolocus_pearson(g, m1, m2)
+    assert (r["i"], r["j"]) == (pi, pj) and r["score_real"] == psc
