@@ -56,6 +56,7 @@ struct MatchParams {
 struct Ctl {
   uint64_t full[STAGES], empty[STAGES], tfull[MAX_ACC], tempty[MAX_ACC], drain;
   MatchPartial red[EPI_WARPS];
+  unsigned long long cta_best;  // strings: the best key any thread of the CTA has found
   uint32_t tmem_base;
   int abort_flag;
 };
@@ -71,6 +72,17 @@ __device__ __forceinline__ void tri_tile(int64_t t, int64_t nb, int64_t* bi, int
   }
   *bi = lo;
   *bj = lo + (t - (lo * nb - lo * (lo - 1) / 2));
+}
+
+// the tile G further on in the same order (callers make sure it exists, so the loop ends inside the
+// triangle): rows shrink as bi grows, so the position wraps row by row
+__device__ __forceinline__ void tri_next(int64_t G, int64_t nb, int64_t& bi, int64_t& bj) {
+  int64_t pos = bj - bi + G;
+  while (pos >= nb - bi) {
+    pos -= nb - bi;
+    ++bi;
+  }
+  bj = bi + pos;
 }
 
 __device__ __forceinline__ bool better(unsigned long long k, int i, int j, unsigned long long bk, int bi, int bj) {
@@ -125,6 +137,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     mbar_init(&ctl->drain, 1);
     ctl->abort_flag = 0;
+    ctl->cta_best = 0ull;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -149,9 +162,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t stage = 0, phase = 0;
       int64_t issued = 0;
       bool ok = true;
+      int64_t bi = 0, bj = 0;
+      if ((int64_t)blockIdx.x < total) tri_tile(blockIdx.x, nb, &bi, &bj);
       for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
-        int64_t bi, bj;
-        tri_tile(t, nb, &bi, &bj);
+        if (t != (int64_t)blockIdx.x) tri_next(gridDim.x, nb, bi, bj);
         for (int g = 0; g < mp.groups && ok; ++g)
           for (int64_t kc = 0; kc < mp.kch[g]; ++kc) {
             if (!mbar_wait(&ctl->empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
@@ -182,8 +196,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t stage = 0, phase = 0;
       int64_t it = 0;
       bool ok = true;
+      uint32_t acc = 0, use = 0;
       for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
-        const uint32_t acc = (uint32_t)(it % nacc), use = (uint32_t)((it / nacc) & 1);
+        if (t != (int64_t)blockIdx.x && ++acc == nacc) {
+          acc = 0;
+          use ^= 1u;
+        }
         if (!mbar_wait(&ctl->tempty[acc], use ^ 1u, abort_flag)) { ok = false; break; }
         tc_fence_after();
         for (int g = 0; g < mp.groups && ok; ++g) {
@@ -223,10 +241,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     bool ok = true;
     constexpr bool ham = MODE == MATCH_HAMMING_MIN || MODE == MATCH_HAMMING_MAX;
     constexpr bool most = MODE == MATCH_HAMMING_MIN;
+    int64_t bi = 0, bj = 0;
+    if ((int64_t)blockIdx.x < total) tri_tile(blockIdx.x, nb, &bi, &bj);
+    uint32_t acc = 0, use = 0;
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
-      int64_t bi, bj;
-      tri_tile(t, nb, &bi, &bj);
-      const uint32_t acc = (uint32_t)(it % nacc), use = (uint32_t)((it / nacc) & 1);
+      if (t != (int64_t)blockIdx.x) {
+        tri_next(gridDim.x, nb, bi, bj);
+        if (++acc == nacc) {
+          acc = 0;
+          use ^= 1u;
+        }
+      }
       if (!__all_sync(0xffffffffu, mbar_wait(&ctl->tfull[acc], use, abort_flag))) { ok = false; break; }
       tc_fence_after();
       const int64_t i = bi * BM + quarter * 32 + lane;
@@ -244,7 +269,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         vxAi = mp.vx[0][ii];
         vxBi = mp.vx[1][ii];
       }
-      const bool edge = bi == bj || (bi + 1) * BM > mp.S || (bj + 1) * BN > mp.S;
       // the pair (i, j) with the accumulators a (group A / strings) and b (group B) as FP32 bits
       auto consider = [&](int64_t j, uint32_t a, uint32_t b) {
         if (!(row_ok && j < mp.S && j > i)) return;
@@ -270,6 +294,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           bk = key;
           bi_best = (int)i;
           bj_best = (int)j;
+          if (ham) atomicMax(&ctl->cta_best, key);
         }
       };
       if (ham) {
@@ -282,13 +307,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tmem_wait_ld(rb);
         const int64_t j0 = bj * BN + c0;
         // per chunk, its best count (a 31-op tree) decides whether any entry can reach or tie the
-        // thread's best key; most chunks cannot
-        const bool fast = !edge && bi_best >= 0;
-        if (!fast || chunk_key<most>(ra, mp.m[0]) >= bk) {
+        // best key found so far in the CTA (a key some pair has, so a smaller one cannot win); the
+        // tree also counts the masked entries of edge tiles, which can only raise it.  Most chunks
+        // are skipped.
+        const unsigned long long cb = *(volatile unsigned long long*)&ctl->cta_best;
+        const unsigned long long bar = cb > bk ? cb : bk;
+        if (chunk_key<most>(ra, mp.m[0]) >= bar) {
 #pragma unroll
           for (int k = 0; k < 32; ++k) consider(j0 + k, ra[k], 0u);
         }
-        if (!fast || chunk_key<most>(rb, mp.m[0]) >= bk) {
+        if (chunk_key<most>(rb, mp.m[0]) >= bar) {
 #pragma unroll
           for (int k = 0; k < 32; ++k) consider(j0 + 32 + k, rb[k], 0u);
         }
