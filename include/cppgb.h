@@ -184,6 +184,13 @@ int twolocus_scan_shard(const uint64_t* planes, int64_t S, int64_t W, int64_t m_
 size_t twolocus_scan_tc_workspace_size(int64_t S, int64_t W);
 int twolocus_scan_tc(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls, int measure,
                      twolocus_result* out, void* ws, size_t ws_bytes, void* stream);
+/* Shard `shard` of `nshards` of twolocus_scan_tc: the 128 x 128 tiles t (in the scan's order of the
+ * SNP-pair triangle) with t mod nshards == shard; the best pair of those tiles (i = j = -1 when they
+ * hold none).  The answer of the whole scan is the shard result with the largest score (score_real
+ * for Pearson), ties to the smallest (i, j).  Same workspace as twolocus_scan_tc. */
+int twolocus_scan_tc_shard(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls,
+                           int measure, int64_t shard, int64_t nshards, twolocus_result* out, void* ws, size_t ws_bytes,
+                           void* stream);
 
 /* Result of a string-pair search. */
 typedef struct {
@@ -204,6 +211,11 @@ typedef struct {
 size_t hamming_pair_workspace_size(int64_t n, int64_t t, int sigma);
 int hamming_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, int least, hamming_result* out,
                  void* ws, size_t ws_bytes, void* stream);
+/* Shard `shard` of `nshards` of hamming_pair: the 128 x 128 tiles t with t mod nshards == shard; the
+ * answer of the whole search is the shard result with the fewest (least = 0) or most (least = 1)
+ * mismatches, ties to the smallest (i, j).  Same workspace as hamming_pair. */
+int hamming_pair_shard(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, int least, int64_t shard,
+                       int64_t nshards, hamming_result* out, void* ws, size_t ws_bytes, void* stream);
 
 /* Result of a light-bulb candidate search. */
 typedef struct {

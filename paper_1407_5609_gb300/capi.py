@@ -88,6 +88,10 @@ SIGNATURES = {
     "twolocus_scan_tc": (_int, [_vp, _i64, _i64, _i64, _i64, _int, ctypes.POINTER(twolocus_result), _vp, _sz, _vp]),
     "hamming_pair_workspace_size": (_sz, [_i64, _i64, _int]),
     "hamming_pair": (_int, [_vp, _i64, _i64, _i64, _int, _int, ctypes.POINTER(hamming_result), _vp, _sz, _vp]),
+    "twolocus_scan_tc_shard": (_int, [_vp, _i64, _i64, _i64, _i64, _int, _i64, _i64, ctypes.POINTER(twolocus_result),
+                                       _vp, _sz, _vp]),
+    "hamming_pair_shard": (_int, [_vp, _i64, _i64, _i64, _int, _int, _i64, _i64, ctypes.POINTER(hamming_result), _vp,
+                                   _sz, _vp]),
     "mlba_pair_workspace_size": (_sz, [_i64, _i64, _int, _int, _i64, _i64]),
     "mlba_pair": (_int, [_vp, _i64, _i64, _i64, _int, _int, _vp, _i64, _i64, ctypes.POINTER(mlba_result), _vp, _sz,
                          _vp]),
@@ -343,6 +347,38 @@ def twolocus_scan_tc(planes: torch.Tensor, m_cases: int, m_controls: int, measur
     m = {"matches": TL_MATCHES, "pearson": TL_PEARSON}.get(measure, measure)
     _raise(lib().twolocus_scan_tc(planes.data_ptr() if S else None, S, W, m_cases, m_controls, int(m),
                                   ctypes.byref(out), ws.data_ptr(), ws.numel(), _stream(stream)))
+    return out.as_dict()
+
+
+def twolocus_scan_tc_shard(planes: torch.Tensor, m_cases: int, m_controls: int, shard: int, nshards: int,
+                           measure=TL_MATCHES, ws: torch.Tensor | None = None, stream=None) -> dict:
+    """Shard `shard` of `nshards` of :func:`twolocus_scan_tc` (include/cppgb.h)."""
+    _check_cuda(planes, "planes")
+    if planes.dim() != 4 or planes.shape[1:3] != (2, 2) or planes.element_size() != 8 or not planes.is_contiguous():
+        raise ValueError("planes must be a contiguous 64-bit tensor [S][2][2][W]")
+    S, W = planes.shape[0], planes.shape[3]
+    if ws is None:
+        ws = _workspace(twolocus_scan_tc_workspace_size(S, W), planes.device)
+    out = twolocus_result()
+    m = {"matches": TL_MATCHES, "pearson": TL_PEARSON}.get(measure, measure)
+    _raise(lib().twolocus_scan_tc_shard(planes.data_ptr() if S else None, S, W, m_cases, m_controls, int(m), shard,
+                                        nshards, ctypes.byref(out), ws.data_ptr(), ws.numel(), _stream(stream)))
+    return out.as_dict()
+
+
+def hamming_pair_shard(strings: torch.Tensor, sigma: int, shard: int, nshards: int, least: bool = False,
+                       ws: torch.Tensor | None = None, stream=None) -> dict:
+    """Shard `shard` of `nshards` of :func:`hamming_pair` (include/cppgb.h)."""
+    _check_cuda(strings, "strings")
+    if strings.dim() != 2 or strings.dtype != torch.uint8 or strings.stride(1) != 1:
+        raise ValueError("strings must be uint8 [n][t] with unit column stride")
+    n, t = strings.shape
+    if ws is None:
+        ws = _workspace(hamming_pair_workspace_size(n, t, sigma), strings.device)
+    out = hamming_result()
+    _raise(lib().hamming_pair_shard(strings.data_ptr() if n else None, n, t, strings.stride(0) if n else t, int(sigma),
+                                    1 if least else 0, shard, nshards, ctypes.byref(out), ws.data_ptr(), ws.numel(),
+                                    _stream(stream)))
     return out.as_dict()
 
 

@@ -46,7 +46,8 @@ struct MatchMaps {
 struct MatchParams {
   int64_t S;              // rows
   int32_t groups, mode;   // 1 or 2 groups; MatchMode
-  int64_t kch[2];         // K chunks of 64 per group
+  int64_t kch[2];         // K chunks of BK per group
+  int64_t t0, tstride;    // shard: the tiles t = t0 + k tstride of the triangle's order (0, 1: all)
   int64_t m[2];           // two-locus: group sizes; strings: the length t (m[0])
   const int32_t* s[2];    // two-locus count: sum (a + b) per row
   const int64_t* sx[2];   // Pearson: sum x and m sum x^2 - (sum x)^2 per row
@@ -118,7 +119,7 @@ __device__ __forceinline__ double pearson_r(int64_t m, int64_t sxy, int64_t sxi,
 // One instantiation per measure (MatchMode): each carries only its own epilogue arithmetic.
 template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    match_tc_kernel(const __grid_constant__ MatchMaps maps, const __grid_constant__ MatchParams mp, int64_t total,
+    match_tc_kernel(const __grid_constant__ MatchMaps maps, const __grid_constant__ MatchParams mp, int64_t total,  // tiles of the shard
                     int64_t nb, MatchPartial* __restrict__ partials, unsigned int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -163,9 +164,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int64_t issued = 0;
       bool ok = true;
       int64_t bi = 0, bj = 0;
-      if ((int64_t)blockIdx.x < total) tri_tile(blockIdx.x, nb, &bi, &bj);
+      if ((int64_t)blockIdx.x < total) tri_tile(mp.t0 + (int64_t)blockIdx.x * mp.tstride, nb, &bi, &bj);
       for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
-        if (t != (int64_t)blockIdx.x) tri_next(gridDim.x, nb, bi, bj);
+        if (t != (int64_t)blockIdx.x) tri_next((int64_t)gridDim.x * mp.tstride, nb, bi, bj);
         for (int g = 0; g < mp.groups && ok; ++g)
           for (int64_t kc = 0; kc < mp.kch[g]; ++kc) {
             if (!mbar_wait(&ctl->empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
@@ -242,11 +243,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     constexpr bool ham = MODE == MATCH_HAMMING_MIN || MODE == MATCH_HAMMING_MAX;
     constexpr bool most = MODE == MATCH_HAMMING_MIN;
     int64_t bi = 0, bj = 0;
-    if ((int64_t)blockIdx.x < total) tri_tile(blockIdx.x, nb, &bi, &bj);
+    if ((int64_t)blockIdx.x < total) tri_tile(mp.t0 + (int64_t)blockIdx.x * mp.tstride, nb, &bi, &bj);
     uint32_t acc = 0, use = 0;
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
       if (t != (int64_t)blockIdx.x) {
-        tri_next(gridDim.x, nb, bi, bj);
+        tri_next((int64_t)gridDim.x * mp.tstride, nb, bi, bj);
         if (++acc == nacc) {
           acc = 0;
           use ^= 1u;
@@ -504,7 +505,8 @@ int encode_rows(CUtensorMap* m, void* base, int64_t rows, int64_t K) {
 int launch_match(const MatchMaps& maps, const MatchParams& mp, MatchPartial* partials, int64_t* np_out,
                  unsigned int* status, cudaStream_t st) {
   const int64_t nb = (mp.S + BM - 1) / BM;
-  const int64_t total = nb * (nb + 1) / 2;
+  const int64_t all = nb * (nb + 1) / 2;
+  const int64_t total = mp.t0 < all ? (all - mp.t0 + mp.tstride - 1) / mp.tstride : 0;  // this shard's tiles
   int dev = 0, sms = 0;
   CPPGB_CUDA_TRY(cudaGetDevice(&dev));
   CPPGB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -580,9 +582,11 @@ size_t twolocus_scan_tc_workspace_size(int64_t S, int64_t W) {
   return tl_layout(nullptr, S, W).bytes;
 }
 
-int twolocus_scan_tc(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls, int measure,
-                     twolocus_result* out, void* ws, size_t ws_bytes, void* stream) {
+int twolocus_scan_tc_shard(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls,
+                           int measure, int64_t shard, int64_t nshards, twolocus_result* out, void* ws, size_t ws_bytes,
+                           void* stream) {
   if (!out) return set_error(CPPGB_ERR_ARG, "out is NULL");
+  if (nshards < 1 || shard < 0 || shard >= nshards) return set_error(CPPGB_ERR_ARG, "need 0 <= shard < nshards");
   if (measure != CPPGB_TL_MATCHES && measure != CPPGB_TL_PEARSON) return set_error(CPPGB_ERR_ARG, "unknown measure");
   if (S < 0 || S > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "S out of range");
   if (m_cases < 1 || m_controls < 1) return set_error(CPPGB_ERR_ARG, "group sizes must be >= 1");
@@ -621,6 +625,8 @@ int twolocus_scan_tc(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cas
   mp.groups = 2;
   mp.mode = mode;
   mp.kch[0] = mp.kch[1] = K / BK;
+  mp.t0 = shard;
+  mp.tstride = nshards;
   mp.m[0] = m_cases;
   mp.m[1] = m_controls;
   for (int g = 0; g < 2; ++g) {
@@ -650,15 +656,21 @@ int twolocus_scan_tc(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cas
   return CPPGB_OK;
 }
 
+int twolocus_scan_tc(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls, int measure,
+                     twolocus_result* out, void* ws, size_t ws_bytes, void* stream) {
+  return twolocus_scan_tc_shard(planes, S, W, m_cases, m_controls, measure, 0, 1, out, ws, ws_bytes, stream);
+}
+
 size_t hamming_pair_workspace_size(int64_t n, int64_t t, int sigma) {
   if (n < 0 || t < 1 || sigma < 2 || sigma > 256) return 0;
   const int64_t K = (t * sigma + BK - 1) / BK * BK;
   return ham_layout(nullptr, n, K).bytes;
 }
 
-int hamming_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, int least, hamming_result* out,
-                 void* ws, size_t ws_bytes, void* stream) {
+int hamming_pair_shard(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, int least, int64_t shard,
+                       int64_t nshards, hamming_result* out, void* ws, size_t ws_bytes, void* stream) {
   if (!out) return set_error(CPPGB_ERR_ARG, "out is NULL");
+  if (nshards < 1 || shard < 0 || shard >= nshards) return set_error(CPPGB_ERR_ARG, "need 0 <= shard < nshards");
   out->i = out->j = -1;
   out->mismatches = -1;
   if (n < 0 || n > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "n out of range");
@@ -689,6 +701,8 @@ int hamming_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigm
   mp.groups = 1;
   mp.mode = least ? MATCH_HAMMING_MAX : MATCH_HAMMING_MIN;
   mp.kch[0] = K / BK;
+  mp.t0 = shard;
+  mp.tstride = nshards;
   mp.m[0] = t;
   int64_t np = 0;
   if ((rc = launch_match(maps, mp, L.partials, &np, L.status, st))) return rc;
@@ -707,6 +721,11 @@ int hamming_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigm
     out->mismatches = least ? b.key : t - b.key;
   }
   return CPPGB_OK;
+}
+
+int hamming_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, int least, hamming_result* out,
+                 void* ws, size_t ws_bytes, void* stream) {
+  return hamming_pair_shard(strs, n, t, ld, sigma, least, 0, 1, out, ws, ws_bytes, stream);
 }
 
 }  // extern "C"

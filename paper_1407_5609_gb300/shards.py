@@ -7,6 +7,12 @@
   the smallest (i, j) (``reduce_twolocus`` / ``allreduce_twolocus``).
 * FRNN on the grid (``frnn_query_shard``): each shard answers the points of its x-slab; the CSR of
   the whole query takes each point's row from its own shard (``merge_frnn`` / ``allgather_frnn``).
+* Two-locus on the tensor cores (``twolocus_scan_tc_shard``): as two-locus, with Pearson's results
+  ranked by ``score_real`` (``reduce_twolocus``).
+* Strings (``hamming_pair_shard``): the fewest (closest) or most (least correlated) mismatches, then
+  the smallest (i, j) (``reduce_hamming`` / ``allreduce_hamming``).
+* Light-bulb search (``mlba_pair`` on a subset of the iterations, i.e. of the rows of ``cols``): the
+  same ranking as strings; the candidate counts add up (``reduce_mlba`` / ``allreduce_mlba``).
 
 Shards with no pair report i = j = -1.
 """
@@ -48,6 +54,8 @@ def allreduce_result(result: dict, group=None) -> dict:
 def _tl_key(r: dict):
     if r["i"] < 0:
         return (1, 0, 0, 0)  # after every real pair
+    if int(r["score"]) < 0:  # Pearson: the score is score_real
+        return (0, -float(r["score_real"]), int(r["i"]), int(r["j"]))
     return (0, -int(r["score"]), int(r["i"]), int(r["j"]))
 
 
@@ -67,12 +75,57 @@ def allreduce_twolocus(result: dict, group=None) -> dict:
     import torch.distributed as dist
     gathered = [None] * dist.get_world_size(group)
     local = {"i": int(result["i"]), "j": int(result["j"]), "score": int(result["score"]),
+             "score_real": float(result.get("score_real", -1.0)),
              "countsA": np.asarray(result["countsA"]).tolist(), "countsB": np.asarray(result["countsB"]).tolist()}
     dist.all_gather_object(gathered, local, group=group)
     out = reduce_twolocus(gathered)
     out["countsA"] = np.asarray(out["countsA"], dtype=np.int32)
     out["countsB"] = np.asarray(out["countsB"], dtype=np.int32)
     return out
+
+
+def _ham_key(r: dict, least: bool):
+    if r["i"] < 0:
+        return (1, 0, 0, 0)
+    m = int(r["mismatches"])
+    return (0, -m if least else m, int(r["i"]), int(r["j"]))
+
+
+def reduce_hamming(results: list, least: bool = False) -> dict:
+    """The string-pair shard result with the fewest (least=False) or most (least=True) mismatches,
+    ties to the smallest (i, j); i = j = -1 when no shard has a pair."""
+    best = None
+    for r in results:
+        if best is None or _ham_key(r, least) < _ham_key(best, least):
+            best = r
+    return dict(best) if best is not None else {"i": -1, "j": -1, "mismatches": -1}
+
+
+def reduce_mlba(results: list, least: bool = False) -> dict:
+    """Light-bulb searches over disjoint sets of iterations: the best candidate as in
+    :func:`reduce_hamming`; the candidate counts add up."""
+    out = reduce_hamming(results, least)
+    out["candidates"] = sum(int(r.get("candidates", 0)) for r in results)
+    return out
+
+
+def _allgather(obj, group=None):
+    import torch.distributed as dist
+    gathered = [None] * dist.get_world_size(group)
+    dist.all_gather_object(gathered, obj, group=group)
+    return gathered
+
+
+def allreduce_hamming(result: dict, least: bool = False, group=None) -> dict:
+    """Exchange step of a sharded string-pair search across the ranks of a process group."""
+    local = {k: int(result[k]) for k in ("i", "j", "mismatches")}
+    return reduce_hamming(_allgather(local, group), least)
+
+
+def allreduce_mlba(result: dict, least: bool = False, group=None) -> dict:
+    """Exchange step of a light-bulb search whose iterations are split across the ranks."""
+    local = {k: int(result[k]) for k in ("i", "j", "mismatches", "candidates")}
+    return reduce_mlba(_allgather(local, group), least)
 
 
 def merge_frnn(parts: list):

@@ -96,3 +96,48 @@ def test_new_shard_argument_errors():
     with pytest.raises(capi.CppgbError) as e:
         capi.twolocus_scan_shard(planes, 64, 64, 3, 3)
     assert e.value.status == capi.ERR_ARG
+
+
+@pytest.mark.parametrize("nshards", [1, 3, 8])
+def test_match_engine_shards_combine_exactly(nshards):
+    """Tensor-core two-locus (both measures) and string pairs: the shards' reduce = the whole search =
+    the oracle."""
+    from paper_1407_5609_gb300 import capi
+    dev = device()
+    g, _ = synth.make_genotypes(S=600, m1=200, m2=170, seed=95)
+    planes = to_dev(synth.pack_planes(g, 200, 170).view(np.int64), dev)
+    for meas in ("matches", "pearson"):
+        parts = [capi.twolocus_scan_tc_shard(planes, 200, 170, k, nshards, measure=meas) for k in range(nshards)]
+        r = shards.reduce_twolocus(parts)
+        full = capi.twolocus_scan_tc(planes, 200, 170, measure=meas)
+        assert (r["i"], r["j"], r["score"], r["score_real"]) == (full["i"], full["j"], full["score"], full["score_real"])
+    oi, oj, osc, _, _ = oracle.twolocus(g, 200, 170)
+    assert (full["i"], full["j"]) == oracle.twolocus_pearson(g, 200, 170)[:2]
+    s = synth.make_strings(3000, 40, 4, seed=96, plant=(11, 2900), at=(1, 2))
+    d = to_dev(s, dev)
+    for least in (False, True):
+        parts = [capi.hamming_pair_shard(d, 4, k, nshards, least=least) for k in range(nshards)]
+        r = shards.reduce_hamming(parts, least=least)
+        assert (r["i"], r["j"], r["mismatches"]) == oracle.hamming(s, 4, least=least)
+
+
+def test_mlba_iterations_shard_exactly():
+    """The light-bulb search split by iterations: the reduce of the parts = the whole search."""
+    from paper_1407_5609_gb300 import capi
+    dev = device()
+    s = synth.make_strings(5000, 32, 4, seed=97, plant=(5, 4000), at=(3, 9))
+    cols = synth.sample_columns(9, 7, 32, seed=98)
+    d = to_dev(s, dev)
+    parts = [capi.mlba_pair(d, 4, to_dev(np.ascontiguousarray(cols[k::3]), dev)) for k in range(3)]
+    r = shards.reduce_mlba(parts)
+    assert (r["i"], r["j"], r["mismatches"], r["candidates"]) == oracle.mlba(s, 4, cols)
+
+
+def test_match_shard_argument_errors():
+    from paper_1407_5609_gb300 import capi
+    dev = device()
+    d = to_dev(synth.make_strings(300, 8, 4, seed=99, plant=None), dev)
+    for k, m in [(2, 2), (-1, 3), (0, 0)]:
+        with pytest.raises(capi.CppgbError) as e:
+            capi.hamming_pair_shard(d, 4, k, m)
+        assert e.value.status == capi.ERR_ARG

@@ -112,3 +112,51 @@ def test_reduce_twolocus_order():
     r = shards.reduce_twolocus([none, a, c, b])
     assert (r["i"], r["j"], r["score"]) == (2, 30, 50)
     assert shards.reduce_twolocus([none])["i"] == -1 and shards.reduce_twolocus([])["i"] == -1
+
+
+def _rank_main_strings(rank, world, port, out_path):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    s = synth.make_strings(700, 20, 4, seed=120, plant=(3, 650), at=(0,))
+    # light-bulb search: this rank runs every world-th iteration (the oracle stands in for the GPU)
+    cols = synth.sample_columns(6, 5, 20, seed=121)
+    i, j, h, c = oracle.mlba(s, 4, cols[rank::world])
+    ml = shards.allreduce_mlba({"i": i, "j": j, "mismatches": h, "candidates": c})
+    # strings: this rank's part = the pairs (i, j) with i % world == rank, searched by brute force
+    best = {"i": -1, "j": -1, "mismatches": -1}
+    for a in range(rank, 700, world):
+        hd = (s[a + 1:] != s[a]).sum(axis=1)
+        if hd.size:
+            k = int(np.argmax(hd))
+            if best["i"] < 0 or hd[k] > best["mismatches"]:
+                best = {"i": a, "j": a + 1 + k, "mismatches": int(hd[k])}
+    hm = shards.allreduce_hamming(best, least=True)
+    if rank == 0:
+        np.save(out_path, np.array([ml["i"], ml["j"], ml["mismatches"], ml["candidates"], hm["i"], hm["j"],
+                                    hm["mismatches"]]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_strings_and_mlba_exchange_two_gloo_ranks(tmp_path):
+    out = str(tmp_path / "res.npy")
+    mp.start_processes(_rank_main_strings, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+    z = [int(v) for v in np.load(out)]
+    s = synth.make_strings(700, 20, 4, seed=120, plant=(3, 650), at=(0,))
+    cols = synth.sample_columns(6, 5, 20, seed=121)
+    assert tuple(z[:4]) == oracle.mlba(s, 4, cols)
+    assert tuple(z[4:]) == oracle.hamming(s, 4, least=True)
+
+
+def test_reduce_hamming_and_mlba_order():
+    none = {"i": -1, "j": -1, "mismatches": -1, "candidates": 0}
+    a = {"i": 4, "j": 9, "mismatches": 3, "candidates": 10}
+    b = {"i": 2, "j": 30, "mismatches": 3, "candidates": 1}
+    c = {"i": 0, "j": 1, "mismatches": 5, "candidates": 2}
+    assert (shards.reduce_hamming([none, a, c, b])["i"], shards.reduce_hamming([a, b])["j"]) == (2, 30)
+    assert shards.reduce_hamming([a, b, c], least=True)["i"] == 0
+    r = shards.reduce_mlba([none, a, b, c])
+    assert (r["i"], r["j"], r["candidates"]) == (2, 30, 13)
+    assert shards.reduce_mlba([none])["i"] == -1 and shards.reduce_hamming([])["i"] == -1
