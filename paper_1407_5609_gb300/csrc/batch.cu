@@ -821,11 +821,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                               : tile_rows<false>(tbase, i, col0, n, nx, cur.th_r, hits);
       const uint32_t flags = __reduce_or_sync(0xffffffffu, hits);
       if (flags) emit_radius(tbase, flags, i, col0, n, nx, cur.th_r, q, g, cand, cap);
+      // The accumulator has been read for the last time: release it now, so that the MMA of the
+      // group's next tile overlaps the reductions and the record decision below.
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl->tempty[grp]);
       // this warp's smallest D~ (+inf for masked rows), clamped at 0 (a looser but valid bound),
       // so the float bits order like the values
       const unsigned int wm = __reduce_min_sync(0xffffffffu, __float_as_uint(fmaxf(fmaf(-2.f, rmax, nx), 0.f)));
-      // Publish it before releasing the accumulator: the slot is reused two tiles later, and that
-      // tile's MMA cannot start before all four warps have released this one.
+      // The minimum slots [grp][par] are reused two tiles later.  That tile's MMA needs every warp's
+      // release of the tile in between, which each warp gives only after this publication (and the
+      // last warp after its reset below), so no warp can overwrite a slot still being read.
       bool last = false;
       float tmin = INF;
       if (lane == 0) {
@@ -839,9 +845,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           ctl->arrived[grp][par] = 0u;
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&ctl->tempty[grp]);
       if (last && tmin < INF) {  // the tile record and the bound update
         if (tmin <= theta_of(Ug, cur.bp)) {
           atomic_min_nonneg(&st[q].tmin16_bits, tmin);
