@@ -118,6 +118,7 @@ struct DenseLayout {
   int64_t *start, *pos, *ptmp;
   Candidate* cand;
   double* d2buf;
+  int32_t* surv;  // the candidates that pass the final screen (l-mer recheck)
   size_t bytes;
 };
 
@@ -153,14 +154,15 @@ DenseLayout dense_layout(void* ws, int64_t n, int64_t d, int mode, size_t ws_byt
     L.Xs = c.take<char>((size_t)L.n_pad * L.Kp * L.elem);
     L.norms_s = c.take<float>(L.n_pad);
   }
-  const size_t fixed = c.bytes() + 512;
+  const size_t fixed = c.bytes() + 1024;  // room for the 256-byte rounding of the three arrays below
   if (ws_bytes > fixed) {
-    int64_t fit = (int64_t)((ws_bytes - fixed) / (sizeof(Candidate) + sizeof(double)));
+    int64_t fit = (int64_t)((ws_bytes - fixed) / (sizeof(Candidate) + sizeof(double) + sizeof(int32_t)));
     if (fit > cap) cap = fit;
   }
   L.cap = cap;
   L.cand = c.take<Candidate>(L.cap);
   L.d2buf = c.take<double>(L.cap);
+  L.surv = c.take<int32_t>(L.cap);
   L.bytes = c.bytes();
   return L;
 }
@@ -279,14 +281,14 @@ int dense_search(const Source& src, int64_t n, int64_t d, int64_t excl, int mode
                        "filter's error; pass a workspace of %zu bytes",
                        (unsigned long long)h.n_cand, (long long)L.cap,
                        dense_layout(nullptr, n, d, mode | (prune ? CPPGB_MODE_PRUNE : 0)).bytes +
-                           (size_t)(h.n_cand - L.cap) * (sizeof(Candidate) + sizeof(double)) + 4096);
+                           (size_t)(h.n_cand - L.cap) * (sizeof(Candidate) + sizeof(double) + sizeof(int32_t)) + 4096);
     }
     // The bound U is final now; a second pass emits only pairs whose lower bound meets it.
     CPPGB_CUDA_TRY(cudaMemsetAsync(&L.sc->n_cand, 0, sizeof(L.sc->n_cand), st));
   }
   const int64_t n_live = (int64_t)h.n_cand;
   if (src.lmers)
-    rc = launch_recheck_lmers(src.series, src.l, L.sc, L.cand, L.cap, L.d2buf, n_live, st);
+    rc = launch_recheck_lmers(src.series, src.l, L.sc, L.surv, L.cand, L.cap, L.d2buf, n_live, st);
   else
     rc = launch_recheck_points(src.pts, src.dtype, d, src.ld, L.sc, L.cand, L.cap, L.d2buf, n_live, st);
   if (rc) return rc;

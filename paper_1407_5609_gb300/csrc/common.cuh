@@ -72,7 +72,7 @@ struct DenseScalars {
   unsigned long long best_bits; // FP64 bits of the best rechecked d^2
   unsigned long long best_ij;   // (i << 32) | j of the best pair among equal d^2
   unsigned int ferr_bits;       // max |d2_fp64 - D~| over rechecked candidates (float bits)
-  unsigned int pad[1];
+  unsigned int n_surv;          // l-mer recheck: candidates that pass the final screen (listed)
 };
 
 // True distance d of a pair with filtered value D~ satisfies
@@ -149,7 +149,7 @@ void set_stage_times(const double* ms, int n);
 // n_live = min(candidates emitted, cap), read back by the host after the dense stage.
 int launch_recheck_points(const void* pts, int dtype, int64_t d, int64_t ld, DenseScalars* sc, const Candidate* cand, int64_t cap, double* d2buf,
                           int64_t n_live, cudaStream_t st);
-int launch_recheck_lmers(const float* series, int64_t l, DenseScalars* sc,
+int launch_recheck_lmers(const float* series, int64_t l, DenseScalars* sc, int32_t* surv,
                          const Candidate* cand, int64_t cap, double* d2buf, int64_t n_live,
                          cudaStream_t st);
 

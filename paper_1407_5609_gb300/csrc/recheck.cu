@@ -23,32 +23,6 @@ __device__ double exact_d2_points(const Src* __restrict__ pts, int64_t d, int64_
   return s;
 }
 
-// mean and population standard deviation of one window, two sequential passes
-__device__ void window_stats(const float* __restrict__ w, int64_t l, double* mu, double* sd) {
-  double s = 0.0;
-  for (int64_t k = 0; k < l; ++k) s = __dadd_rn(s, (double)w[k]);
-  double m = __ddiv_rn(s, (double)l);
-  double v = 0.0;
-  for (int64_t k = 0; k < l; ++k) v = __dadd_rn(v, sq_rn(__dsub_rn((double)w[k], m)));
-  *mu = m;
-  *sd = __dsqrt_rn(__ddiv_rn(v, (double)l));
-}
-
-__device__ double exact_d2_lmers(const float* __restrict__ a, int64_t l, int64_t i, int64_t j) {
-  double mi, si, mj, sj;
-  window_stats(a + i, l, &mi, &si);
-  window_stats(a + j, l, &mj, &sj);
-  const float* wi = a + i;
-  const float* wj = a + j;
-  double s = 0.0;
-  for (int64_t k = 0; k < l; ++k) {
-    double zi = __ddiv_rn(__dsub_rn((double)wi[k], mi), si);
-    double zj = __ddiv_rn(__dsub_rn((double)wj[k], mj), sj);
-    s = __dadd_rn(s, sq_rn(__dsub_rn(zi, zj)));
-  }
-  return s;
-}
-
 __device__ __forceinline__ int64_t live_count(const DenseScalars* sc, int64_t cap) {
   int64_t c = (int64_t)sc->n_cand;
   return c < cap ? c : cap;
@@ -79,9 +53,84 @@ __global__ void recheck_points_kernel(const Src* __restrict__ pts, int64_t d, in
   recheck_body([&](int64_t i, int64_t j) { return exact_d2_points(pts, d, ld, i, j); }, sc, cand, cap, d2buf);
 }
 
-__global__ void recheck_lmers_kernel(const float* __restrict__ a, int64_t l, DenseScalars* sc,
-                                     const Candidate* __restrict__ cand, int64_t cap, double* __restrict__ d2buf) {
-  recheck_body([&](int64_t i, int64_t j) { return exact_d2_lmers(a, l, i, j); }, sc, cand, cap, d2buf);
+// l-mers, in two kernels.  The screen lists the candidates whose D~ can still reach the final bound
+// (most emitted candidates were written before the bound settled: the survivors are a few per
+// thousand, and they cluster, since one tile emits many).  Then one warp takes each survivor.
+// Each window w is z-normalised with its mean m = (sum_k w_k) / l and population standard deviation
+// sd = sqrt((sum_k (w_k - m)^2) / l), z_k = (w_k - m) / sd, and d^2 = sum_k (z_ik - z_jk)^2, every
+// operation rounded (no contraction) and every sum in index order.  The sums keep that order -- one
+// lane adds each -- while their terms (the converted values, the deviations, the divisions of the
+// z-values) are computed by all lanes at once into shared memory, RCH at a time.
+constexpr int RW = 4, RCH = 512, RGRID = 152 * 16;
+
+__global__ void screen_lmers_kernel(DenseScalars* sc, const Candidate* __restrict__ cand, int64_t cap,
+                                    double* __restrict__ d2buf, int32_t* __restrict__ surv) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= live_count(sc, cap)) return;
+  const float th = theta_of(__uint_as_float(sc->U_bits), sc->bp);
+  const float d2f = cand[c].d2f;
+  if (d2f <= th && d2f < __int_as_float(0x7f800000)) surv[atomicAdd(&sc->n_surv, 1u)] = (int32_t)c;
+  else d2buf[c] = -1.0;
+}
+
+// sum_k t_k in index order, the terms written by `term` (all lanes) into buf[q], RCH at a time;
+// lane q (q < nsums) keeps sum q
+template <class Term>
+__device__ __forceinline__ double ordered_sum(int64_t l, int lane, int nsums, double (&buf)[2][RCH], Term term) {
+  double v = 0.0;
+  for (int64_t k0 = 0; k0 < l; k0 += RCH) {
+    const int cnt = (int)(l - k0 < RCH ? l - k0 : RCH);
+#pragma unroll 4
+    for (int k = lane; k < cnt; k += 32) term(k0 + k, k);
+    __syncwarp();
+    if (lane < nsums)
+      for (int k = 0; k < cnt; ++k) v = __dadd_rn(v, buf[lane][k]);
+    __syncwarp();
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(32 * RW) recheck_lmers_kernel(const float* __restrict__ a, int64_t l,
+                                                                DenseScalars* sc, const Candidate* __restrict__ cand,
+                                                                const int32_t* __restrict__ surv,
+                                                                double* __restrict__ d2buf) {
+  __shared__ double sbuf[RW][2][RCH];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double (&buf)[2][RCH] = sbuf[w];
+  const int64_t ns = (int64_t)sc->n_surv;
+  const double dl = (double)l;
+  for (int64_t k = (int64_t)blockIdx.x * RW + w; k < ns; k += (int64_t)gridDim.x * RW) {
+    const int32_t c = surv[k];
+    const Candidate cd = cand[c];
+    const float* wi = a + cd.i;
+    const float* wj = a + cd.j;
+    // means (lane 0: window i, lane 1: window j)
+    const double sm = ordered_sum(l, lane, 2, buf, [&](int64_t g, int k2) {
+      buf[0][k2] = (double)wi[g];
+      buf[1][k2] = (double)wj[g];
+    });
+    const double m = lane < 2 ? __ddiv_rn(sm, dl) : 0.0;
+    const double mi = __shfl_sync(0xffffffffu, m, 0), mj = __shfl_sync(0xffffffffu, m, 1);
+    // population variances
+    const double sv = ordered_sum(l, lane, 2, buf, [&](int64_t g, int k2) {
+      buf[0][k2] = sq_rn(__dsub_rn((double)wi[g], mi));
+      buf[1][k2] = sq_rn(__dsub_rn((double)wj[g], mj));
+    });
+    const double sd = lane < 2 ? __dsqrt_rn(__ddiv_rn(sv, dl)) : 1.0;
+    const double si = __shfl_sync(0xffffffffu, sd, 0), sj = __shfl_sync(0xffffffffu, sd, 1);
+    // the distance (lane 0)
+    const double s = ordered_sum(l, lane, 1, buf, [&](int64_t g, int k2) {
+      const double zi = __ddiv_rn(__dsub_rn((double)wi[g], mi), si);
+      const double zj = __ddiv_rn(__dsub_rn((double)wj[g], mj), sj);
+      buf[0][k2] = sq_rn(__dsub_rn(zi, zj));
+    });
+    if (lane == 0) {
+      d2buf[c] = s;
+      atomicMin(&sc->best_bits, (unsigned long long)__double_as_longlong(s));
+      atomicAdd(&sc->n_rech, 1ull);
+      atomic_max_nonneg(&sc->ferr_bits, (float)fabs(__dsub_rn(s, (double)cd.d2f)));
+    }
+  }
 }
 
 // Pass B: among the survivors at the minimal d^2, the lexicographically smallest (i, j).
@@ -110,7 +159,7 @@ __global__ void init_scalars_kernel(DenseScalars* sc) {
   z.best_bits = 0x7ff0000000000000ull;  // +inf
   z.best_ij = ~0ull;
   z.ferr_bits = 0u;
-  z.pad[0] = 0u;
+  z.n_surv = 0u;
   *sc = z;
 }
 
@@ -153,11 +202,14 @@ int launch_recheck_points(const void* pts, int dtype, int64_t d, int64_t ld, Den
   return finish(sc, cand, cap, d2buf, blocks, st);
 }
 
-int launch_recheck_lmers(const float* series, int64_t l, DenseScalars* sc, const Candidate* cand,
+int launch_recheck_lmers(const float* series, int64_t l, DenseScalars* sc, int32_t* surv, const Candidate* cand,
                          int64_t cap, double* d2buf, int64_t n_live, cudaStream_t st) {
+  if (n_live <= 0) return CPPGB_OK;
   const int64_t blocks = (n_live + 127) / 128;
-  if (blocks == 0) return CPPGB_OK;
-  recheck_lmers_kernel<<<(unsigned)blocks, 128, 0, st>>>(series, l, sc, cand, cap, d2buf);
+  screen_lmers_kernel<<<(unsigned)blocks, 128, 0, st>>>(sc, cand, cap, d2buf, surv);
+  CPPGB_LAUNCH_CHECK();
+  const int64_t want = (n_live + RW - 1) / RW;  // at most one survivor per warp is ever needed
+  recheck_lmers_kernel<<<(unsigned)(want < RGRID ? want : RGRID), 32 * RW, 0, st>>>(series, l, sc, cand, surv, d2buf);
   CPPGB_LAUNCH_CHECK();
   return finish(sc, cand, cap, d2buf, blocks, st);
 }
