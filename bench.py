@@ -43,6 +43,15 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
+def alu_peaks(capi):
+    """The ALU rates measured on this device (FFMA and POPC microbenchmarks), reported beside the
+    derived peaks the ALU rooflines use."""
+    try:
+        return capi.cpp_measure_alu_peaks()
+    except Exception as e:  # diagnostics only: never fail the bench line for it
+        return {"error": str(e)}
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -602,6 +611,7 @@ def run_ours(args):
         flops = wl.units * wl.flop_per_unit
         if mode == "plain_fp32":
             peak, bound, unit, src = FP32_ALU_PEAK_TFLOPS, "alu", "TFLOP/s", "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"
+            out["alu_peak_microbenchmark"] = alu_peaks(capi)
         else:
             peak, bound, unit, src = pk["bf16_tflops"], "tensor", "TFLOP/s", f"{pk['source']} bf16 burst"
         if mode.endswith("_prune"):  # only the kept tiles are evaluated
@@ -628,6 +638,7 @@ def run_ours(args):
         else:
             per_step_ms = total_ms / args.steps
             ach = wl.flops / (per_step_ms / 1e3) / 1e12
+            out["alu_peak_microbenchmark"] = alu_peaks(capi)
             out["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                                "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": recorded_traffic("batch@batch"),
                                "kernel": "cpp_batch step (persistent FP32 tile kernel)",
@@ -655,6 +666,7 @@ def run_ours(args):
         per_step_ms = total_ms / args.steps
         pops = wl.units * wl.flop_per_unit
         ach = pops / (per_step_ms / 1e3) / 1e12
+        out["alu_peak_microbenchmark"] = alu_peaks(capi)
         out["roofline"] = {"bound": "alu", "achieved": ach, "peak": POPC_PEAK_TOPS, "unit": "Tpopc/s",
                            "frac": ach / POPC_PEAK_TOPS, "traffic": recorded_traffic("twolocus_scan@twolocus"),
                            "kernel": "twolocus_scan_kernel (step time)",

@@ -317,6 +317,11 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
  * in the process so far.
  */
 void cpp_set_stage_timing(int on);
+/* Measures the CUDA-core rates the ALU rooflines are checked against (diagnostics): FP32 FFMA in
+ * TFLOP/s (2 flop per FMA) and POPC in Tpopc/s, each from independent chains on a full grid of the
+ * current device, timed with CUDA events on the legacy default stream (about 0.1 s; allocates and
+ * frees 1.2 MB of device memory).  Errors: CPPGB_ERR_ARG, CPPGB_ERR_CUDA. */
+int cpp_measure_alu_peaks(double* ffma_tflops, double* popc_tops);
 int cpp_stage_times(double* ms, int cap);
 int64_t cpp_launch_count(void);
 /* Tiles the last pruned dense search on the calling thread evaluated, of all its tiles (-1, -1

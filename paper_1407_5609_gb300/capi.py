@@ -92,6 +92,7 @@ SIGNATURES = {
                                        _vp, _sz, _vp]),
     "hamming_pair_shard": (_int, [_vp, _i64, _i64, _i64, _int, _int, _i64, _i64, ctypes.POINTER(hamming_result), _vp,
                                    _sz, _vp]),
+    "cpp_measure_alu_peaks": (_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "mlba_pair_workspace_size": (_sz, [_i64, _i64, _int, _int, _i64, _i64]),
     "mlba_pair": (_int, [_vp, _i64, _i64, _i64, _int, _int, _vp, _i64, _i64, ctypes.POINTER(mlba_result), _vp, _sz,
                          _vp]),
@@ -395,6 +396,13 @@ def hamming_pair(strings: torch.Tensor, sigma: int, least: bool = False, ws: tor
     _raise(lib().hamming_pair(strings.data_ptr() if n else None, n, t, strings.stride(0) if n else t, int(sigma),
                               1 if least else 0, ctypes.byref(out), ws.data_ptr(), ws.numel(), _stream(stream)))
     return out.as_dict()
+
+
+def cpp_measure_alu_peaks() -> dict:
+    """Measured FP32 FFMA (TFLOP/s) and POPC (Tpopc/s) rates of the current device (diagnostics)."""
+    f, p = ctypes.c_double(), ctypes.c_double()
+    _raise(lib().cpp_measure_alu_peaks(ctypes.byref(f), ctypes.byref(p)))
+    return {"ffma_tflops": f.value, "popc_tops": p.value}
 
 
 def mlba_pair_workspace_size(n: int, t: int, sigma: int, least: bool, iters: int, L: int) -> int:
