@@ -1353,7 +1353,7 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
       }
       cudaStream_t cap_st;
       CPPGB_CUDA_TRY(cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking));
-      cudaGraph_t graph;
+      cudaGraph_t graph = nullptr;
       CPPGB_CUDA_TRY(cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal));
       const long long before = (long long)cpp_launch_count();
       const int rc = enqueue_batch(L, count, t, pairs, pairs_cap, sms, maps, timing, cap_st);
@@ -1361,7 +1361,10 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
       note_launches(-g_graph_kernels);  // captured, not launched
       cudaError_t ce = cudaStreamEndCapture(cap_st, &graph);
       cudaStreamDestroy(cap_st);
-      if (rc) return rc;
+      if (rc) {  // a failed enqueue: drop whatever the capture recorded
+        if (ce == cudaSuccess && graph) cudaGraphDestroy(graph);
+        return rc;
+      }
       if (ce != cudaSuccess) return set_error(CPPGB_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
       ce = cudaGraphInstantiate(&g_exec, graph, 0);
       cudaGraphDestroy(graph);

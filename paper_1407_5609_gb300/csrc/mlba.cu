@@ -670,7 +670,7 @@ int mlba_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, 
     }
     cudaStream_t cap_st;
     CPPGB_CUDA_TRY(cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking));
-    cudaGraph_t graph;
+    cudaGraph_t graph = nullptr;
     CPPGB_CUDA_TRY(cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal));
     const long long before = (long long)cpp_launch_count();
     const int rc = enqueue_mlba(args, Lo, timing, cap_st);
@@ -678,7 +678,10 @@ int mlba_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, 
     note_launches(-g_mgraph_kernels);  // captured, not launched
     cudaError_t ce = cudaStreamEndCapture(cap_st, &graph);
     cudaStreamDestroy(cap_st);
-    if (rc) return rc;
+    if (rc) {  // a failed enqueue: drop whatever the capture recorded
+      if (ce == cudaSuccess && graph) cudaGraphDestroy(graph);
+      return rc;
+    }
     if (ce != cudaSuccess) return set_error(CPPGB_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
     ce = cudaGraphInstantiate(&g_mexec, graph, 0);
     cudaGraphDestroy(graph);
