@@ -12,7 +12,7 @@
 namespace cppgb {
 namespace {
 
-constexpr int BM = 128, BK = 16, PAD = 4, NT = 256;
+constexpr int BM = 128, BK = 16, NT = 256;
 
 // RADIUS = false: closest-pair epilogue (tile minimum, bound update, emission against the bound).
 // RADIUS = true:  fixed-radius epilogue (Sec. 3.5): emit every pair whose lower bound on d is <= R,
