@@ -243,7 +243,10 @@ typedef struct {
  *   cols  device int32 [iters][L] (not read when L = 0).  The sampled characters fill one 64-bit
  *         key: L * ceil(log2 sigma) <= 64 (least = 0), 1 <= L <= 64 (least = 1); iters x rows
  *         (n, or 2n for least = 1) below 2^31.
- * The call synchronises the stream before it returns.
+ * The call synchronises the stream before it returns.  Its kernels are captured once into a CUDA
+ * graph per argument set (pointers and sizes) and replayed while the arguments stay the same; calls
+ * from several threads are serialised by a library-wide lock (so the call cannot itself be captured
+ * into a caller's graph).
  * Errors: CPPGB_ERR_ARG (also for a symbol >= sigma or a column out of range), CPPGB_ERR_CAPACITY
  * (ws), CPPGB_ERR_CUDA.
  */
