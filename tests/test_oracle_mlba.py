@@ -10,7 +10,10 @@ What fixes it, independently of its own code:
     complement of another in 2(t - u) columns (u = matches), and over all t columns two strings
     agree in u columns;
   * for a binary alphabet a string and its complement collide in every iteration (Sec. 5.2);
-  * a planted close pair is found with the brute-force answer when the iterations are many enough.
+  * a planted close pair is found with the brute-force answer when the iterations are many enough;
+  * on uniform random strings the candidate rate is sigma^-L per pair and iteration (and
+    (2 (sigma - 1) / sigma^2)^L in the least correlated form), the collision probabilities behind
+    Theorem 1's run-time analysis.
 """
 import itertools
 
@@ -132,3 +135,25 @@ def test_argument_errors():
         oracle.mlba(s, 2, np.zeros((1, 0), np.int32), least=True)  # least needs a column
     with pytest.raises(oracle.OracleError):
         oracle.mlba(s + 2, 2, np.array([[0]], np.int32))       # symbol >= sigma
+
+
+@pytest.mark.parametrize("sigma,L", [(2, 8), (4, 4), (3, 5)])
+def test_collision_rate_matches_sigma_power(sigma, L):
+    """Uniform random strings and L distinct sampled columns: two strings share a bucket with
+    probability sigma^-L (least=False), so the candidates per iteration average C(n, 2) sigma^-L; in
+    the least correlated form a string meets a complement with probability (2 (sigma-1) / sigma^2)^L
+    per column set.  A dropped, repeated or mis-mapped character in the keys moves these rates by a
+    factor of sigma (or more)."""
+    rng = np.random.default_rng(40 + sigma + L)
+    n, t, iters = 1500, 40, 12
+    s = rng.integers(0, sigma, size=(n, t), dtype=np.uint8)
+    cols = np.stack([rng.choice(t, L, replace=False) for _ in range(iters)]).astype(np.int32)
+    nc = oracle.mlba(s, sigma, cols)[3]
+    expect = iters * n * (n - 1) / 2 * sigma ** -L
+    assert abs(nc - expect) < 0.08 * expect, (nc, expect)
+    # one-hot columns at distinct positions: bit_i != bit_j with probability 2 (1/sigma)(1 - 1/sigma)
+    colsl = np.stack([np.array([sigma * p + rng.integers(0, sigma) for p in rng.choice(t, L, replace=False)])
+                      for _ in range(iters)]).astype(np.int32)
+    ncl = oracle.mlba(s, sigma, colsl, least=True)[3]
+    expl = iters * n * (n - 1) / 2 * (2 * (sigma - 1) / sigma ** 2) ** L
+    assert abs(ncl - expl) < 0.08 * expl, (ncl, expl)
