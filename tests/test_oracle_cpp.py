@@ -114,3 +114,16 @@ def test_cpp_index_gap():
 @pytest.mark.parametrize("n", [0, 1])
 def test_cpp_degenerate_sizes(n):
     assert oracle.cpp(np.zeros((n, 3))) == (-1, -1, math.inf)
+
+
+def test_workload_has_no_near_tie():
+    """The 4096 x 32 closest-pair workload is not a near tie: the best and the second-best squared
+    distance (scipy, a library routine) differ by far more than 1e-12 relative, so its answer cannot
+    hinge on the last bits of the arithmetic (a seed whose two best pairs came that close would be
+    replaced, not passed)."""
+    x, plant = synth.make_cpp()
+    d2 = pdist(x.astype(np.float64), "sqeuclidean")
+    two = np.partition(d2, 1)[:2]
+    assert (two[1] - two[0]) > 1e-12 * two[1]
+    i, j, best = oracle.cpp(x)
+    assert (i, j) == plant and best == pytest.approx(two[0], rel=1e-12)
