@@ -16,6 +16,7 @@ Applications"):
   tsmm_rows(a, l, excl, rows)      best partner of chosen rows
   frnn(x, R)                       R-neighbourhoods, Sec. 3.5, as CSR
   frnn_rows(x, R, rows)            N(r) of chosen rows
+  radius_pairs(x, R)               the pairs i < j with d <= R, Sec. 3.5, in increasing (i, j)
   twolocus(g, m1, m2)              argmax |P_A - P_B|, Sec. 6 (matches of Sec. 2 / 5.3)
   twolocus_tables(g, m1, m2, I, J) 3x3 tables and scores of chosen pairs
   twolocus_rows(g, m1, m2, rows)   best partner of chosen SNPs
@@ -86,6 +87,8 @@ def _load():
                                                _i64p, _i32p, ctypes.c_int64, _i64p]),
                 "oracle_frnn_rows": (ctypes.c_int, [_f64p, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                                                     _i64p, ctypes.c_int64, _i64p, _i32p, ctypes.c_int64]),
+                "oracle_radius_pairs": (ctypes.c_int, [_f64p, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                                       _i32p, ctypes.c_int64, _i64p]),
                 "oracle_twolocus": (ctypes.c_int, [_i8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                                    _i64p, _i64p, _i64p, _i32p, _i32p]),
                 "oracle_twolocus_tables": (ctypes.c_int, [_i8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
@@ -206,6 +209,23 @@ def frnn_rows(x, R: float, rows):
     _check(lib.oracle_frnn_rows(_p(x, _f64p), n, d, float(R), _p(rows, _i64p), rows.shape[0], _p(offs, _i64p),
                                 _p(cols, _i32p), cols.shape[0]), "frnn_rows")
     return offs, cols[:offs[-1]]
+
+
+def radius_pairs(x, R: float):
+    """Pairs i < j with d(x_i, x_j) <= R (Sec. 3.5), each once: int32 [m][2] in increasing (i, j)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n, d = x.shape
+    lib = _load()
+    cap = 1 << 16
+    while True:
+        out = np.empty((cap, 2), dtype=np.int32)
+        total = ctypes.c_int64()
+        rc = lib.oracle_radius_pairs(_p(x, _f64p), n, d, float(R), _p(out, _i32p), cap, ctypes.byref(total))
+        if rc == 2:
+            cap = int(total.value)
+            continue
+        _check(rc, "radius_pairs")
+        return out[:total.value].copy()
 
 
 def twolocus(g, m1: int, m2: int):

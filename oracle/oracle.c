@@ -17,6 +17,8 @@
  *   oracle_frnn       R-neighbourhoods N(i) for all i, Sec. 3.5 (d <= R,
  *                     symmetric insertion into N(i) and N(j))
  *   oracle_frnn_rows  N(i) for chosen rows
+ *   oracle_radius_pairs  the same neighbourhoods as a list of pairs i < j, each
+ *                     once, in increasing (i, j)
  *   oracle_twolocus   argmax |P_A(i,j) - P_B(i,j)|, Sec. 6, with the
  *                     match-count correlation of Sec. 2 / Sec. 5.3
  *   oracle_twolocus_tables / oracle_twolocus_rows   3x3 tables for chosen
@@ -299,6 +301,71 @@ int oracle_frnn_rows(const double* x, int64_t n, int64_t d, double R, const int6
       if (j != rows[p] && frnn_pred(x + rows[p] * d, x + j * d, d, rr)) cols[o++] = (int32_t)j;
   }
   return ORACLE_OK;
+}
+
+/*
+ * The pairs of an R-neighbourhood query (Sec. 3.5) counted once each: every i < j with
+ * sum_k (x_ik - x_jk)^2 <= R*R in FP64 (k order), listed in increasing (i, j) as int32
+ * pairs[2p], pairs[2p+1].  One pass over the pairs; each thread collects its rows' pairs, and the
+ * collected list is sorted at the end.  *total = number of pairs; ERR_CAPACITY when cap < total.
+ */
+static int pair_cmp(const void* a, const void* b) {
+  const int32_t* p = (const int32_t*)a;
+  const int32_t* q = (const int32_t*)b;
+  if (p[0] != q[0]) return p[0] < q[0] ? -1 : 1;
+  if (p[1] != q[1]) return p[1] < q[1] ? -1 : 1;
+  return 0;
+}
+
+int oracle_radius_pairs(const double* x, int64_t n, int64_t d, double R, int32_t* pairs, int64_t cap,
+                        int64_t* total) {
+  if (!x || n < 0 || d <= 0 || !(R >= 0.0) || !total || n > INT32_MAX) return ORACLE_ERR_ARG;
+  double rr = R * R;
+  int32_t* all = NULL;
+  int64_t nall = 0;
+  int bad = 0;
+#pragma omp parallel reduction(| : bad)
+  {
+    int32_t* mine = NULL;
+    int64_t nm = 0, capm = 0;
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+      for (int64_t j = i + 1; j < n; ++j) {
+        if (!frnn_pred(x + i * d, x + j * d, d, rr)) continue;
+        if (nm == capm) {
+          int64_t nc = capm ? 2 * capm : 64;
+          int32_t* grown = (int32_t*)realloc(mine, (size_t)nc * 2 * sizeof(int32_t));
+          if (!grown) { bad = 1; continue; }
+          mine = grown;
+          capm = nc;
+        }
+        mine[2 * nm] = (int32_t)i;
+        mine[2 * nm + 1] = (int32_t)j;
+        ++nm;
+      }
+    }
+#pragma omp critical
+    {
+      if (nm > 0) {
+        int32_t* grown = (int32_t*)realloc(all, (size_t)(nall + nm) * 2 * sizeof(int32_t));
+        if (!grown) bad = 1;
+        else {
+          all = grown;
+          memcpy(all + 2 * nall, mine, (size_t)nm * 2 * sizeof(int32_t));
+          nall += nm;
+        }
+      }
+    }
+    free(mine);
+  }
+  if (bad) { free(all); return ORACLE_ERR_ARG; }
+  if (nall > 1) qsort(all, (size_t)nall, 2 * sizeof(int32_t), pair_cmp);
+  *total = nall;
+  int rc = ORACLE_OK;
+  if (!pairs || cap < nall) rc = ORACLE_ERR_CAPACITY;
+  else if (nall > 0) memcpy(pairs, all, (size_t)nall * 2 * sizeof(int32_t));
+  free(all);
+  return rc;
 }
 
 /*

@@ -68,3 +68,40 @@ def test_frnn_rows_match_full():
     offs, rc = oracle.frnn_rows(x, 0.006, rows)
     for p, r in enumerate(rows):
         np.testing.assert_array_equal(rc[offs[p]:offs[p + 1]], cols[row_ptr[r]:row_ptr[r + 1]])
+
+
+@pytest.mark.parametrize("n,d,R,seed", [(2500, 3, 0.004, 46), (1200, 8, 0.4, 47), (600, 2, 2e-3, 48)])
+def test_radius_pairs_match_ckdtree(n, d, R, seed):
+    """The once-per-pair list (i < j) against scipy's cKDTree.query_pairs, outside a 1e-12 band of R."""
+    if d == 3:
+        x = synth.make_frnn_mixture(n=n, seed=seed).astype(np.float64)
+    else:
+        x = synth.rng_for(seed).random((n, d))
+    got = oracle.radius_pairs(x, R)
+    assert got.dtype == np.int32 and got.ndim == 2 and got.shape[1] == 2
+    gs = {(int(i), int(j)) for i, j in got}
+    assert len(gs) == got.shape[0] and all(i < j for i, j in gs)
+    ref = {(min(i, j), max(i, j)) for i, j in cKDTree(x).query_pairs(R * (1 + 1e-12))}
+    band = {(i, j) for (i, j) in ref ^ gs if abs(np.sqrt(((x[i] - x[j]) ** 2).sum()) - R) <= 1e-12 * R}
+    assert (gs ^ ref) == band
+    assert len(gs) > 0
+    # increasing (i, j)
+    key = got[:, 0].astype(np.int64) * n + got[:, 1]
+    assert np.all(np.diff(key) > 0)
+
+
+def test_radius_pairs_boundary_and_empty():
+    x = np.array([[0.0, 0.0], [0.5, 0.0], [0.0, 0.75], [2.0, 2.0], [0.5, 0.0]])
+    assert oracle.radius_pairs(x, 0.5).tolist() == [[0, 1], [0, 4], [1, 4]]
+    assert oracle.radius_pairs(x, 0.0).tolist() == [[1, 4]]   # the duplicate point is at distance 0
+    assert oracle.radius_pairs(x[:1], 1.0).shape == (0, 2)
+    assert oracle.radius_pairs(np.zeros((0, 3)), 1.0).shape == (0, 2)
+
+
+def test_radius_pairs_capacity_growth():
+    """More pairs than the first buffer holds: every point of a tight cluster pairs with every other."""
+    x = synth.rng_for(49).random((400, 2)) * 1e-3
+    got = oracle.radius_pairs(x, 1.0)
+    assert got.shape[0] == 400 * 399 // 2
+    iu = np.triu_indices(400, 1)
+    np.testing.assert_array_equal(got, np.stack(iu, axis=1).astype(np.int32))
