@@ -335,6 +335,45 @@ int cpp_prune_stats(int64_t* tiles_kept, int64_t* tiles_total);
 int cpp_filter_available(void);
 
 /*
+ * cpp_gram_tile_dump -- diagnostics (no counterpart in the paper): the raw Gram values that the
+ * tensor-core filter stage of cpp_closest_pair accumulates for chosen tiles, so that their error
+ * can be compared with the accumulation term of the filter's error bound.  The points are prepared
+ * exactly as by cpp_closest_pair in `mode`, and the tiles run through the same TMA / tcgen05.mma
+ * pipeline; only the epilogue differs (it stores the accumulator instead of reducing it).
+ *   pts, dtype, n (>= 1), d, ld  as for cpp_closest_pair.   mode  CPPGB_MODE_FILTER_BF16 or _FP16.
+ *   tiles  host int32 [ntiles][2]: (bi, bj) = rows 128 bi .. 128 bi + 127 against rows
+ *          256 bj .. 256 bj + 255, with 0 <= bi < n_pad / 128, 0 <= bj < n_pad / 256 (n_pad = n
+ *          rounded up to a multiple of 256; rows past n are zero).
+ *   S      device FP32 [ntiles][128][256]: S[t][r][c] = x~_(128 bi + r) . x~_(256 bj + c), the
+ *          FP32 accumulator of the tensor cores (x~ = the stored 16-bit rows).
+ *   rows   device, optional (NULL: not written): the stored 16-bit rows, [n_pad][Kp] with Kp = d
+ *          rounded up to a multiple of 64, zero-padded (2 n_pad Kp bytes).
+ *   ws     a workspace of cpp_closest_pair_workspace_size(n, d, mode) bytes.
+ * The call synchronises the stream.  Errors: CPPGB_ERR_ARG (also a tile out of range, or more
+ * than 131,072 tiles), CPPGB_ERR_CAPACITY (ws), CPPGB_ERR_NUMERIC, CPPGB_ERR_TIMEOUT, CPPGB_ERR_CUDA.
+ */
+int cpp_gram_tile_dump(const void* pts, int dtype, int64_t n, int64_t d, int64_t ld, int mode, const int32_t* tiles,
+                       int64_t ntiles, float* S, void* rows, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Fault injection for tests of the failure path (no counterpart in the paper).  Every wait of the
+ * tensor-core kernels (TMA copies, MMA completion, accumulator hand-over, tile records) is bounded
+ * by about 2 s; when one runs out the kernel stops issuing work, waits (bounded) for what it has in
+ * flight, frees its tensor memory and returns, and the call reports CPPGB_ERR_TIMEOUT.
+ *   CPPGB_FAULT_SKIP_TMA  the TMA producers of the tensor-core kernels (dense filter stage of
+ *                         cpp_closest_pair / tsmm_motif, tensor-core tiles of cpp_batch,
+ *                         twolocus_scan_tc, hamming_pair) issue no copy, so the consumers' waits
+ *                         run out: each such call then takes about 2 s and returns
+ *                         CPPGB_ERR_TIMEOUT; nothing is left in flight and the device stays usable.
+ *   CPPGB_FAULT_NONE      normal operation (the default).
+ * Process-wide, for the current device; a synchronous copy to device memory, so make no call
+ * during stream capture.  Errors: CPPGB_ERR_ARG (unknown kind), CPPGB_ERR_CUDA.
+ */
+#define CPPGB_FAULT_NONE 0
+#define CPPGB_FAULT_SKIP_TMA 1
+int cpp_set_fault_injection(int kind);
+
+/*
  * Tuning policy (process-wide; no counterpart in the paper).  The project's autotuner times the
  * candidates on the device, caches its choice as JSON and installs it here; every later call reads it.
  *   CPPGB_TUNE_BATCH_PATH  values = int32 [4 n-buckets][4 d-classes], count 16, each 1 (FP32 128 x 128

@@ -111,6 +111,9 @@ SIGNATURES = {
     "cpp_launch_count": (_i64, []),
     "cpp_prune_stats": (_int, [ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "cpp_filter_available": (_int, []),
+    "cpp_gram_tile_dump": (_int, [_vp, _int, _i64, _i64, _i64, _int, ctypes.POINTER(ctypes.c_int32), _i64, _vp, _vp,
+                                   _vp, _sz, _vp]),
+    "cpp_set_fault_injection": (_int, [_int]),
     "cpp_set_tuning": (_int, [_int, ctypes.POINTER(ctypes.c_int32), _int]),
     "cpp_get_tuning": (_int, [_int, ctypes.POINTER(ctypes.c_int32), _int]),
     "cpp_last_error": (ctypes.c_char_p, []),
@@ -167,6 +170,15 @@ def filters_available() -> bool:
     return bool(lib().cpp_filter_available())
 
 
+FAULT_NONE, FAULT_SKIP_TMA = 0, 1
+
+
+def cpp_set_fault_injection(kind: int) -> None:
+    """Test-only: make the tensor-core kernels' TMA producers issue nothing (FAULT_SKIP_TMA), so
+    their bounded waits run out, or restore normal operation (FAULT_NONE)."""
+    _raise(lib().cpp_set_fault_injection(int(kind)))
+
+
 TUNE_BATCH_PATH, TUNE_DENSE_BAND = 1, 2
 TUNE_SIZES = {TUNE_BATCH_PATH: 16, TUNE_DENSE_BAND: 1}
 
@@ -204,6 +216,30 @@ def cpp_prune_stats() -> tuple:
     kept, total = _i64(0), _i64(0)
     _raise(lib().cpp_prune_stats(ctypes.byref(kept), ctypes.byref(total)))
     return kept.value, total.value
+
+
+def cpp_gram_tile_dump(pts: torch.Tensor, tiles, mode="filter_bf16", stream=None):
+    """Raw tensor-core Gram values of chosen filter-stage tiles (diagnostics, include/cppgb.h).
+
+    ``tiles`` is a sequence of (bi, bj) block pairs.  Returns (S float32 [ntiles][128][256],
+    rows [n_pad][Kp] in the stored 16-bit type), both on the device."""
+    _check_cuda(pts, "pts")
+    if pts.dim() != 2 or pts.stride(1) != 1:
+        raise ValueError("pts must be 2-D with unit column stride")
+    dtype = {torch.float32: F32, torch.float64: F64}[pts.dtype]
+    n, d = pts.shape
+    m = _mode(mode)
+    tl = np.ascontiguousarray(np.asarray(tiles, dtype=np.int32).reshape(-1, 2))
+    n_pad = (max(n, 1) + 255) // 256 * 256
+    kp = (d + 63) // 64 * 64
+    S = torch.empty((tl.shape[0], 128, 256), dtype=torch.float32, device=pts.device)
+    rows = torch.empty((n_pad, kp), dtype=torch.bfloat16 if m == MODES["filter_bf16"] else torch.float16,
+                       device=pts.device)
+    ws = _workspace(cpp_closest_pair_workspace_size(n, d, m), pts.device)
+    _raise(lib().cpp_gram_tile_dump(pts.data_ptr(), dtype, n, d, pts.stride(0), m,
+                                    tl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), tl.shape[0], S.data_ptr(),
+                                    rows.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)))
+    return S, rows
 
 
 def cpp_closest_pair_workspace_size(n: int, d: int, mode="plain_fp32") -> int:

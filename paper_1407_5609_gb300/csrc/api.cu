@@ -270,6 +270,7 @@ int dense_search(const Source& src, int64_t n, int64_t d, int64_t excl, int mode
     CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
     if (h.status & 1u) return set_error(CPPGB_ERR_NUMERIC, "non-finite input value");
     if (h.status & 2u) return set_error(CPPGB_ERR_NUMERIC, "an l-mer has zero variance");
+    if (h.status & 4u) return set_error(CPPGB_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
     if ((int64_t)h.n_cand <= L.cap) break;
     if (pass == 1) {
       // report the number of candidates a larger workspace would have to hold
@@ -338,6 +339,16 @@ extern "C" {
 const char* cpp_last_error(void) { return g_err; }
 
 int cpp_filter_available(void) { return gram_tc_available() ? 1 : 0; }
+
+int cpp_set_fault_injection(int kind) {
+  g_err[0] = 0;
+  if (kind != CPPGB_FAULT_NONE && kind != CPPGB_FAULT_SKIP_TMA)
+    return set_error(CPPGB_ERR_ARG, "unknown fault kind %d", kind);
+  const int on = kind == CPPGB_FAULT_SKIP_TMA ? 1 : 0;
+  int rc;
+  if ((rc = set_fault_gram_tc(on)) || (rc = set_fault_batch(on)) || (rc = set_fault_match(on))) return rc;
+  return CPPGB_OK;
+}
 
 int cpp_set_tuning(int kind, const int32_t* values, int count) {
   init_tuning();
@@ -408,6 +419,49 @@ int cpp_closest_pair(const void* pts, int dtype, int64_t n, int64_t d, int64_t l
   if (rc) return rc;
   Source src{false, pts, dtype, d, ld, nullptr, 0};
   return dense_search(src, n, d, 1, mode, out, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ tensor-core Gram dump (diagnostics)
+int cpp_gram_tile_dump(const void* pts, int dtype, int64_t n, int64_t d, int64_t ld, int mode, const int32_t* tiles,
+                       int64_t ntiles, float* S, void* rows, void* ws, size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  if (n < 1 || n > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "n out of range (%lld)", (long long)n);
+  if (d < 1 || d > 4096 || ld < d) return set_error(CPPGB_ERR_ARG, "need 1 <= d <= 4096 and ld >= d");
+  if (dtype != CPPGB_F32 && dtype != CPPGB_F64) return set_error(CPPGB_ERR_ARG, "dtype must be CPPGB_F32 or CPPGB_F64");
+  if (mode != CPPGB_MODE_FILTER_BF16 && mode != CPPGB_MODE_FILTER_FP16)
+    return set_error(CPPGB_ERR_ARG, "mode must be CPPGB_MODE_FILTER_BF16 or CPPGB_MODE_FILTER_FP16");
+  if (!pts || !S || !ws || (ntiles > 0 && !tiles)) return set_error(CPPGB_ERR_ARG, "NULL argument");
+  if (!gram_tc_available()) return set_error(CPPGB_ERR_ARG, "tensor-core kernels are not available in this build");
+  DenseLayout L = dense_layout(ws, n, d, mode, ws_bytes);
+  if (ws_bytes < L.bytes)
+    return set_error(CPPGB_ERR_CAPACITY, "workspace too small: %zu bytes given, %zu needed", ws_bytes, L.bytes);
+  if (((uintptr_t)ws & 255) != 0) return set_error(CPPGB_ERR_ARG, "workspace must be 256-byte aligned");
+  if (ntiles < 0 || ntiles * 2 * (int64_t)sizeof(int32_t) > L.cap * (int64_t)sizeof(Candidate))
+    return set_error(CPPGB_ERR_ARG, "ntiles out of range");
+  const int64_t nbi = L.n_pad / 128, nbj = L.n_pad / 256;
+  for (int64_t t = 0; t < ntiles; ++t)
+    if (tiles[2 * t] < 0 || tiles[2 * t] >= nbi || tiles[2 * t + 1] < 0 || tiles[2 * t + 1] >= nbj)
+      return set_error(CPPGB_ERR_ARG, "tile %lld = (%d, %d) outside the %lld x %lld blocks", (long long)t,
+                       tiles[2 * t], tiles[2 * t + 1], (long long)nbi, (long long)nbj);
+  int rc = check_device();
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t* dlist = reinterpret_cast<int32_t*>(L.cand);  // the candidate buffer is unused by a dump
+  if (ntiles > 0)
+    CPPGB_CUDA_TRY(cudaMemcpyAsync(dlist, tiles, (size_t)ntiles * 2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  if ((rc = launch_init_scalars(L.sc, st))) return rc;
+  if ((rc = launch_prep_points(pts, dtype, n, d, ld, mode, L.X, L.n_pad, L.Kp, L.norms, L.eps, L.sc, st))) return rc;
+  if ((rc = launch_bounds(L.sc, kappa_for(mode, L.Kp), st))) return rc;
+  if ((rc = launch_gram_tc(L.X, mode, n, L.n_pad, L.Kp, 1, L.norms, L.sc, L.cand, L.cap, st, 0, 1, dlist, nullptr,
+                           nullptr, 1, S, ntiles)))
+    return rc;
+  if (rows) CPPGB_CUDA_TRY(cudaMemcpyAsync(rows, L.X, (size_t)L.n_pad * L.Kp * L.elem, cudaMemcpyDeviceToDevice, st));
+  DenseScalars h;
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(&h, L.sc, sizeof h, cudaMemcpyDeviceToHost, st));
+  CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h.status & 1u) return set_error(CPPGB_ERR_NUMERIC, "non-finite input value");
+  if (h.status & 4u) return set_error(CPPGB_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
+  return CPPGB_OK;
 }
 
 // ------------------------------------------------------------------ motif pair

@@ -443,6 +443,11 @@ struct TileInfo {
 constexpr int RING = 16;         // tile records in flight
 constexpr int RING_READERS = 6;  // producer, MMA issuer, the four warps of the tile's epilogue group
 
+// Fault injection for the tests of the bounded waits (cpp_set_fault_injection): when non-zero the TMA
+// producer issues no copy (and consumes no tile record), so the MMA issuer's, the epilogue's and the
+// decoder's waits run out and the batch reports CPPGB_ERR_TIMEOUT.  Zero unless a test sets it.
+__device__ int g_fault_skip_tma = 0;
+
 struct Ctl {
   uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
   uint64_t info_full[RING], info_empty[RING];
@@ -707,7 +712,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t stage = 0, phase = 0;
       int64_t issued = 0;
       bool ok = true;
-      for (int64_t it = 0; it < ntl && ok; ++it) {
+      const bool skip = *reinterpret_cast<volatile int*>(&g_fault_skip_tma) != 0;
+      for (int64_t it = 0; it < ntl && ok && !skip; ++it) {
         const uint32_t slot = (uint32_t)(it % RING);
         if (!mbar_wait(&ctl->info_full[slot], (uint32_t)((it / RING) & 1), abort_flag)) { ok = false; break; }
         const TileInfo ti = ctl->info[slot];
@@ -1100,22 +1106,9 @@ float kappa_tc(int64_t Kp) {
   return (float)((2.0 * 1.51 * 2.0 * K2 * 0x1p-22 + 2.0 * (K / 32.0 + 5.0) * 1.01 * u + 0x1p-27 + 4.03 * u) * 1.01);
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult qr;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
-        qr != cudaDriverEntryPointSuccess) {
-      set_error(CPPGB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-      return nullptr;
-    }
-    fn = (EncodeTiledFn)p;
-  }
+  EncodeTiledFn fn = tensor_map_encoder();
+  if (!fn) set_error(CPPGB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   return fn;
 }
 
@@ -1234,6 +1227,11 @@ int enqueue_batch(const BatchLayout& L, int64_t count, const Totals& t, int32_t*
 }
 
 }  // namespace
+
+int set_fault_batch(int on) {
+  CPPGB_CUDA_TRY(cudaMemcpyToSymbol(btc::g_fault_skip_tma, &on, sizeof on));
+  return CPPGB_OK;
+}
 }  // namespace cppgb
 
 using namespace cppgb;

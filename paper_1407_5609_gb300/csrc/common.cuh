@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -66,7 +67,8 @@ struct DenseScalars {
   unsigned int U_bits;          // running upper bound on the best true d^2 (non-negative float bits)
   unsigned int eps_bits;        // max over rows of eps_i (distance from the exact row, float bits)
   unsigned int n2_bits;         // max over rows of |x~_i|^2 (float bits)
-  unsigned int status;          // device-side flags: 1 = non-finite input, 2 = zero-variance l-mer
+  unsigned int status;          // device-side flags: 1 = non-finite input, 2 = zero-variance l-mer,
+                                // 4 = a bounded wait of the tensor-core stage gave up (CPPGB_ERR_TIMEOUT)
   unsigned long long n_cand;    // candidates emitted (may exceed capacity -> overflow)
   unsigned long long n_rech;    // candidates rechecked in FP64
   unsigned long long best_bits; // FP64 bits of the best rechecked d^2
@@ -132,8 +134,23 @@ int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp
                    const float* norms, DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st,
                    int64_t shard = 0, int64_t nshards = 1,
                    const int32_t* tlist = nullptr, const int64_t* tcount = nullptr,
-                   const int32_t* perm = nullptr, int64_t excl_orig = 1);
+                   const int32_t* perm = nullptr, int64_t excl_orig = 1, float* dump = nullptr,
+                   int64_t dump_tiles = 0);
+// (dump != nullptr: tlist holds dump_tiles (bi, bj) pairs and each tile's raw accumulator is written
+// to dump[t][128][256]; nothing else is computed.)
 bool gram_tc_available();
+
+// cuTensorMapEncodeTiled from the driver, looked up once (thread-safe); nullptr when unavailable.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn tensor_map_encoder();
+
+// Test-only fault injection (cpp_set_fault_injection): the TMA producers of the tensor-core kernels
+// of each translation unit issue no copy while `on` is non-zero (current device).
+int set_fault_gram_tc(int on);
+int set_fault_batch(int on);
+int set_fault_match(int on);
 
 // Tuning policy, process-wide (set through cpp_set_tuning, normally from the autotuner's cache).
 constexpr int TUNE_NB = 4, TUNE_DC = 4;  // batch n-buckets (n < 1024, 4096, 16384, rest) x d-classes ceil(d / 64)

@@ -240,18 +240,40 @@ __global__ void prune_compact_kernel(int64_t total, int64_t shard, int64_t nshar
   if (t < total && flags[t]) list[pos[t]] = (int32_t)(t * nshards + shard);
 }
 
+// Fault injection for the tests of the bounded waits (cpp_set_fault_injection): when non-zero the TMA
+// producer issues no copy, so the MMA issuer's and the epilogue's waits run out and the search
+// reports CPPGB_ERR_TIMEOUT.  Nothing is in flight when the CTA exits.  Zero unless a test sets it.
+__device__ int g_fault_skip_tma = 0;
+
 struct SmemCtl {
   uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
   uint32_t tmem_base;
   int abort_flag;
 };
 
-template <bool PERM>
+// Tile t of this launch: the (bi, bj) pairs of a dump list (DUMP), else tile id t * nshards + shard
+// of the band schedule or the entry t of a pruned list.
+template <bool DUMP>
+__device__ __forceinline__ void tile_of(const TileSched& ts, int64_t t, const int32_t* __restrict__ tlist,
+                                        int64_t shard, int64_t nshards, int* band, int64_t* bi, int64_t* bj) {
+  if (DUMP) {
+    *bi = tlist[2 * t];
+    *bj = tlist[2 * t + 1];
+    return;
+  }
+  decode_tile(ts, tlist ? (int64_t)tlist[t] : t * nshards + shard, band, bi, bj);
+}
+
+// DUMP (diagnostics, cpp_gram_tile_dump): the tiles are the (bi, bj) pairs of tlist and the
+// epilogue writes each tile's raw accumulator S~ = x~_i . x~_j (128 x 256 FP32, row-major) to
+// dump[t]; the TMA producer and the MMA issuer are those of the search.
+template <bool PERM, bool DUMP>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TileSched ts, int64_t total_arg,
                    uint32_t ab_fmt, const float* __restrict__ norms, DenseScalars* sc, Candidate* __restrict__ cand,
                    int64_t cap, int64_t kchunks, int64_t shard, int64_t nshards, const int32_t* __restrict__ tlist,
-                   const int64_t* __restrict__ tcount, const int32_t* __restrict__ perm, int64_t excl_orig) {
+                   const int64_t* __restrict__ tcount, const int32_t* __restrict__ perm, int64_t excl_orig,
+                   float* __restrict__ dump) {
   // the tiles: k < total of this shard (t = k * nshards + shard), or the entries of a pruned list
   const int64_t total = tcount ? *tcount : total_arg;
   extern __shared__ uint8_t smem_raw[];
@@ -292,9 +314,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int64_t issued = 0;
       int band = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      const bool skip = *reinterpret_cast<volatile int*>(&g_fault_skip_tma) != 0;
+      for (int64_t t = blockIdx.x; t < total && ok && !skip; t += gridDim.x) {
         int64_t bi, bj;
-        decode_tile(ts, tlist ? (int64_t)tlist[t] : t * nshards + shard, &band, &bi, &bj);
+        tile_of<DUMP>(ts, t, tlist, shard, nshards, &band, &bi, &bj);
         for (int64_t kc = 0; kc < kchunks; ++kc) {
           if (!mbar_wait(&ctl->empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
           uint8_t* sa = smem + stage * STAGE_BYTES;
@@ -366,7 +389,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int band = 0;
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++it) {
       int64_t bi, bj;
-      decode_tile(ts, tlist ? (int64_t)tlist[t] : t * nshards + shard, &band, &bi, &bj);
+      tile_of<DUMP>(ts, t, tlist, shard, nshards, &band, &bi, &bj);
       const uint32_t acc = (uint32_t)(it & 1), use = (uint32_t)((it >> 1) & 1);
       const bool got = __all_sync(0xffffffffu, mbar_wait(&ctl->tfull[acc], use, abort_flag));
       if (!got) {
@@ -378,12 +401,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       tc_fence_after();
       const uint32_t tbase = tmem_base + ((quarter * 32u) << 16) + acc * (uint32_t)BN;
-      epi_tile<PERM>(bi * BM, bj * BN, tbase, lane, quarter, ts.n, ts.excl, norms, bp, sc, cand, cap, es, perm,
-                     excl_orig);
+      if (DUMP) {
+        float4* row = reinterpret_cast<float4*>(dump + ((size_t)t * BM + quarter * 32 + lane) * BN);
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; ++c) {
+          uint32_t r[32];
+          __syncwarp();
+          tmem_ld32(tbase + (uint32_t)(c * 32), r);
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            row[c * 8 + q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                         __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+        }
+      } else {
+        epi_tile<PERM>(bi * BM, bj * BN, tbase, lane, quarter, ts.n, ts.excl, norms, bp, sc, cand, cap, es, perm,
+                       excl_orig);
+      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&ctl->tempty[acc]);
-      epi_publish(lane, bp, sc, es);
+      if (!DUMP) epi_publish(lane, bp, sc, es);
       if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
     }
     tc_fence_before();
@@ -397,27 +434,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+}  // namespace
 
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+bool gram_tc_available() { return true; }
+
+EncodeTiledFn tensor_map_encoder() {
+  // a function-local static is initialised exactly once, even under concurrent first calls
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-  }
+      return (EncodeTiledFn)p;
+    return nullptr;
+  }();
   return fn;
 }
 
-}  // namespace
-
-bool gram_tc_available() { return true; }
+int set_fault_gram_tc(int on) {
+  CPPGB_CUDA_TRY(cudaMemcpyToSymbol(g_fault_skip_tma, &on, sizeof on));
+  return CPPGB_OK;
+}
 
 namespace {
 // The band schedule of all tiles; returns their number.
@@ -479,7 +516,8 @@ int launch_gram_tc_prune_list(int64_t n, int64_t n_pad, int64_t excl, const floa
 
 int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp, int64_t excl, const float* norms,
                    DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st, int64_t shard, int64_t nshards,
-                   const int32_t* tlist, const int64_t* tcount, const int32_t* perm, int64_t excl_orig) {
+                   const int32_t* tlist, const int64_t* tcount, const int32_t* perm, int64_t excl_orig,
+                   float* dump, int64_t dump_tiles) {
   if (Kp % BK || n_pad % BN) return set_error(CPPGB_ERR_ARG, "internal: tensor-core stage needs Kp %% 64 == 0");
   if (((uintptr_t)X & 15) != 0) return set_error(CPPGB_ERR_ARG, "internal: row matrix must be 16-byte aligned");
   if (n_pad > 0x7fffffffLL || Kp > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "problem too large for TMA coordinates");
@@ -487,9 +525,9 @@ int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp
   const int64_t all_tiles = build_sched(n, n_pad, excl, ts);
   // this shard's tiles are t = k * nshards + shard; the kernel walks k (or the pruned list's entries)
   const int64_t total = all_tiles > shard ? (all_tiles - shard + nshards - 1) / nshards : 0;
-  if (total == 0) return CPPGB_OK;
+  if (dump ? dump_tiles == 0 : total == 0) return CPPGB_OK;
 
-  EncodeTiledFn enc = encode_fn();
+  EncodeTiledFn enc = tensor_map_encoder();
   if (!enc) return set_error(CPPGB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   CUtensorMap tmap;
   const cuuint64_t gdim[2] = {(cuuint64_t)Kp, (cuuint64_t)n_pad};
@@ -508,14 +546,22 @@ int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp
   const uint32_t ab = mode == CPPGB_MODE_FILTER_BF16 ? 1u : 0u;
   const size_t smem = (size_t)STAGES * STAGE_BYTES + sizeof(SmemCtl) + 1024;
   const int64_t grid = total < sms ? total : sms;
-  if (perm) {
-    CPPGB_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    gram_tc_kernel<true><<<(unsigned)grid, NTHREADS, smem, st>>>(tmap, ts, total, ab, norms, sc, cand, cap, Kp / BK,
-                                                                 shard, nshards, tlist, tcount, perm, excl_orig);
+  if (dump) {
+    CPPGB_CUDA_TRY(
+        cudaFuncSetAttribute(gram_tc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t g = dump_tiles < sms ? dump_tiles : sms;
+    gram_tc_kernel<false, true><<<(unsigned)g, NTHREADS, smem, st>>>(
+        tmap, ts, dump_tiles, ab, norms, sc, cand, cap, Kp / BK, 0, 1, tlist, nullptr, nullptr, 1, dump);
+  } else if (perm) {
+    CPPGB_CUDA_TRY(
+        cudaFuncSetAttribute(gram_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    gram_tc_kernel<true, false><<<(unsigned)grid, NTHREADS, smem, st>>>(
+        tmap, ts, total, ab, norms, sc, cand, cap, Kp / BK, shard, nshards, tlist, tcount, perm, excl_orig, nullptr);
   } else {
-    CPPGB_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    gram_tc_kernel<false><<<(unsigned)grid, NTHREADS, smem, st>>>(tmap, ts, total, ab, norms, sc, cand, cap, Kp / BK,
-                                                                  shard, nshards, tlist, tcount, nullptr, 1);
+    CPPGB_CUDA_TRY(
+        cudaFuncSetAttribute(gram_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    gram_tc_kernel<false, false><<<(unsigned)grid, NTHREADS, smem, st>>>(
+        tmap, ts, total, ab, norms, sc, cand, cap, Kp / BK, shard, nshards, tlist, tcount, nullptr, 1, nullptr);
   }
   CPPGB_LAUNCH_CHECK();
   return CPPGB_OK;

@@ -54,6 +54,11 @@ struct MatchParams {
   const int64_t* vx[2];
 };
 
+// Fault injection for the tests of the bounded waits (cpp_set_fault_injection): when non-zero the TMA
+// producer issues no copy, so the MMA issuer's and the epilogue's waits run out and the scan reports
+// CPPGB_ERR_TIMEOUT.  Zero unless a test sets it.
+__device__ int g_fault_skip_tma = 0;
+
 struct Ctl {
   uint64_t full[STAGES], empty[STAGES], tfull[MAX_ACC], tempty[MAX_ACC], drain;
   MatchPartial red[EPI_WARPS];
@@ -165,7 +170,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       int64_t bi = 0, bj = 0;
       if ((int64_t)blockIdx.x < total) tri_tile(mp.t0 + (int64_t)blockIdx.x * mp.tstride, nb, &bi, &bj);
-      for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      const bool skip = *reinterpret_cast<volatile int*>(&g_fault_skip_tma) != 0;
+      for (int64_t t = blockIdx.x; t < total && ok && !skip; t += gridDim.x) {
         if (t != (int64_t)blockIdx.x) tri_next((int64_t)gridDim.x * mp.tstride, nb, bi, bj);
         for (int g = 0; g < mp.groups && ok; ++g)
           for (int64_t kc = 0; kc < mp.kch[g]; ++kc) {
@@ -477,20 +483,9 @@ __global__ void match_finish_kernel(const MatchPartial* __restrict__ partials, i
   if (threadIdx.x == 0) *out = red[0];
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 int encode_rows(CUtensorMap* m, void* base, int64_t rows, int64_t K) {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult qr;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
-        qr != cudaDriverEntryPointSuccess)
-      return set_error(CPPGB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    fn = (EncodeTiledFn)p;
-  }
+  const EncodeTiledFn fn = tensor_map_encoder();
+  if (!fn) return set_error(CPPGB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   const cuuint64_t gdim[2] = {(cuuint64_t)K, (cuuint64_t)rows};
   const cuuint64_t gstride[1] = {(cuuint64_t)K};  // one byte per value; K is a multiple of 128
   const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
@@ -571,6 +566,11 @@ HamLayout ham_layout(void* ws, int64_t n, int64_t K) {
 }
 
 }  // namespace
+
+int set_fault_match(int on) {
+  CPPGB_CUDA_TRY(cudaMemcpyToSymbol(g_fault_skip_tma, &on, sizeof on));
+  return CPPGB_OK;
+}
 }  // namespace cppgb
 
 using namespace cppgb;
