@@ -507,11 +507,21 @@ def calibrate_rows(wl, oracle, target_s):
 
 
 def cpu_baseline(wl, target_s=12.0):
+    """The oracle on all host cores (OpenMP threads = cores) on a bounded sample of the workload, and
+    on one thread on a smaller sample."""
     import oracle
     rows = calibrate_rows(wl, oracle, target_s)
     pairs, dt, sample = wl.oracle_sample(oracle, rows)
-    return {"value": pairs / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": sample, "seconds": round(dt, 2)}
+    out = {"value": pairs / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": sample, "seconds": round(dt, 2)}
+    prev = oracle.set_num_threads(1)
+    try:
+        rows1 = calibrate_rows(wl, oracle, target_s / 3.0)
+        p1, dt1, sample1 = wl.oracle_sample(oracle, rows1)
+    finally:
+        oracle.set_num_threads(prev)
+    out["one_thread"] = {"value": p1 / dt1, "unit": UNIT, "cores": 1, "sample": sample1, "seconds": round(dt1, 2)}
+    return out
 
 
 def timed_steps(fn, steps, stream, torch, flush=None):
@@ -528,6 +538,312 @@ def timed_steps(fn, steps, stream, torch, flush=None):
         evs.append((a, b))
     torch.cuda.synchronize()
     return sum(a.elapsed_time(b) for a, b in evs), r
+
+
+# ------------------------------------------------------------------ stored oracle answers
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def golden(name):
+    """A stored oracle answer (tests/golden/, written by the oracle alone); None when absent."""
+    try:
+        with open(os.path.join(GOLDEN, name)) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def sha256_le(a, dtype) -> str:
+    import numpy as np
+    return hashlib.sha256(np.ascontiguousarray(a, dtype=dtype).tobytes()).hexdigest()
+
+
+def same_as_golden(wl, capi, mode):
+    """One untimed call at full size, compared with the workload's stored oracle answer: True /
+    False, or None when no stored answer exists for this workload."""
+    import numpy as np
+    if wl.name == "tsmm":
+        g = golden("tsmm_rw262144_l512_excl256.json")
+        if g is None or wl.N != 262144:
+            return None
+        r = wl.step(capi, mode)
+        return (r["i"], r["j"], r["dist2"]) == (g["i"], g["j"], float.fromhex(g["dist2"]))
+    if wl.name == "cpp":
+        g = golden("cpp_4096x32.json")
+        if g is None:
+            return None
+        r = wl.step(capi, mode)
+        return (r["i"], r["j"], r["dist2"]) == (g["i"], g["j"], float.fromhex(g["dist2"]))
+    if wl.name == "twolocus":
+        g = golden("twolocus_4096snp_4096x4096.json")
+        if g is None:
+            return None
+        r = wl.step(capi, mode)
+        return ((r["i"], r["j"], r["score"]) == (g["i"], g["j"], g["score"]) and
+                list(r["countsA"]) == g["countsA"] and list(r["countsB"]) == g["countsB"])
+    if wl.name == "frnn":
+        g = golden("frnn_mix1048576_d3_r0.002.json")
+        if g is None:
+            return None
+        rp, cols = capi.frnn_query(wl.dev_x, wl.R)
+        return (int(rp[-1].item()) == g["n_pairs"] and sha256_le(rp.cpu().numpy(), "<i8") == g["row_ptr_sha256"]
+                and sha256_le(cols.cpu().numpy(), "<i4") == g["cols_sha256"])
+    if wl.name == "batch":
+        g = golden("batch_2048inst.json")
+        if g is None or len(wl.batch) != len(g["instances"]):
+            return None
+        res, counts, pairs = capi.cpp_batch(wl.pts, wl.radii, ws=wl.ws, pairs=wl.pairs, paths=wl.path)
+        pairs = pairs.cpu().numpy()
+        offs = np.concatenate([[0], np.cumsum(counts)])
+        for q, (r, gi) in enumerate(zip(res, g["instances"])):
+            if (r["i"], r["j"], r["dist2"]) != (gi["i"], gi["j"], float.fromhex(gi["dist2"])):
+                return False
+            if int(counts[q]) != gi["n_pairs"] or sha256_le(pairs[offs[q]:offs[q + 1]], "<i4") != gi["pairs_sha256"]:
+                return False
+        return True
+    return None
+
+
+def roofline_of(wl, capi, mode, pk, dense_ms, stages, total_ms, steps):
+    """The dominant kernel's roofline record for the workload, plus workload-specific extras."""
+    extra = {}
+    if wl.name in ("tsmm", "cpp"):
+        avg_ms = statistics.mean(dense_ms) if dense_ms else None
+        flops = wl.units * wl.flop_per_unit
+        if mode == "plain_fp32":
+            peak, bound, unit, src = FP32_ALU_PEAK_TFLOPS, "alu", "TFLOP/s", "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"
+            extra["alu_peak_microbenchmark"] = alu_peaks(capi)
+        else:
+            peak, bound, unit, src = pk["bf16_tflops"], "tensor", "TFLOP/s", f"{pk['source']} bf16 burst"
+        if mode.endswith("_prune"):  # only the kept tiles are evaluated
+            kept, total = capi.cpp_prune_stats()
+            if total > 0:
+                flops = flops * kept / total
+        ach = flops / (avg_ms / 1e3) / 1e12 if avg_ms else None
+        return {"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                "frac": ach / peak if ach else None, "traffic": recorded_traffic(f"dense_{mode}@{wl.name}"),
+                "kernel": "dense all-pairs stage (gram_tc / gram_simt)", "peak_source": src,
+                "launch_ms": avg_ms, "algorithmic_flop_per_launch": flops}, extra
+    per_step_ms = total_ms / steps
+    if wl.name == "batch":
+        # dominant kernel: the persistent tensor-core tile kernel (its time from events captured in
+        # the batch's graph); algorithmic work 2 d flop per pair of the instances it runs
+        tc_ms = statistics.mean(dense_ms) if dense_ms else None
+        if wl.tc_flops and tc_ms:
+            ach = wl.tc_flops / (tc_ms / 1e3) / 1e12
+            return {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                    "frac": ach / pk["bf16_tflops"], "traffic": recorded_traffic("batch_tc@batch"),
+                    "kernel": "batch_tc_kernel (persistent tcgen05 tiles of all tensor-core instances)",
+                    "peak_source": f"{pk['source']} bf16 burst", "launch_ms": tc_ms,
+                    "algorithmic_flop_per_launch": wl.tc_flops}, extra
+        ach = wl.flops / (per_step_ms / 1e3) / 1e12
+        extra["alu_peak_microbenchmark"] = alu_peaks(capi)
+        return {"bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": recorded_traffic("batch@batch"),
+                "kernel": "cpp_batch step (persistent FP32 tile kernel)",
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                "algorithmic_flop_per_step": wl.flops}, extra
+    if wl.name == "frnn":
+        gbs = wl.algorithmic_bytes() / (per_step_ms / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / pk["hbm_gbs"], "traffic": recorded_traffic("frnn_query@frnn"),
+                "kernel": "frnn_query step (grid build + neighbour-cell scan + CSR)",
+                "peak_source": f"{pk['source']} hbm copy", "algorithmic_bytes_per_step": wl.algorithmic_bytes()}, extra
+    if wl.name == "twolocus":
+        pops = wl.units * wl.flop_per_unit
+        ach = pops / (per_step_ms / 1e3) / 1e12
+        extra["alu_peak_microbenchmark"] = alu_peaks(capi)
+        return {"bound": "alu", "achieved": ach, "peak": POPC_PEAK_TOPS, "unit": "Tpopc/s",
+                "frac": ach / POPC_PEAK_TOPS, "traffic": recorded_traffic("twolocus_scan@twolocus"),
+                "kernel": "twolocus_scan_kernel (step time)",
+                "peak_source": "derived: 152 SM x 16 POPC/clk x 2070 MHz"}, extra
+    if wl.name == "hamming":
+        ach = wl.units * wl.flop_per_unit / (per_step_ms / 1e3) / 1e12
+        peak = 2 * pk["bf16_tflops"]                   # E4M3 operands: the bf16 burst x the nominal 2x
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": recorded_traffic("match_tc@hamming"),
+                "kernel": "match_tc_kernel (step time; one-hot FP8 GEMM, 2 K flop per pair)",
+                "peak_source": f"{pk['source']} bf16 burst x 2 (nominal fp8 / bf16 ratio)"}, extra
+    if wl.name == "mlba" and stages:
+        # per stage [pack + keys, radix sort, buckets + pair offsets, verification], CUDA events inside the call
+        st_ms = [statistics.mean(x[k] for x in stages) for k in range(4)]
+        extra["stages_ms"] = dict(zip(("pack_keys", "radix_sort", "buckets", "verify"), st_ms))
+        E = wl.iters * wl.n
+        # algorithmic bytes of the sort: per 8-bit pass the histogram reads the keys (8 B) and the scatter
+        # reads and writes key + row (12 + 12 B) of every element
+        sort_bytes = wl.passes * E * (8 + 24)
+        ach = sort_bytes / (st_ms[1] / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": recorded_traffic("mlba_sort@mlba"),
+                "kernel": f"radix sort stage ({wl.passes} passes x hist + scan + scatter; L2-resident)",
+                "peak_source": f"{pk['source']} HBM copy"}, extra
+    return None, extra
+
+
+def measure(wl, capi, args, mode, dev, stream, flush, barrier, steps, warmup, rank, world, detail):
+    """Warm-up, then `steps` timed steps of the workload with inputs resident on the device; the
+    roofline of its dominant kernel, the comparisons (with `detail`), the end-to-end figure through
+    the public API from pinned host memory, and the check against the stored oracle answer."""
+    import torch
+    import torch.distributed as dist
+    # N > 1: the motif, closest-pair, two-locus and FRNN workloads are split into shards of one search
+    # (strong scaling; one exchange per step: an all-gather of the shard results, min- or max-reduced,
+    # or of the FRNN slabs' CSR pieces); the batch runs as replicas.
+    sharded = world > 1 and hasattr(wl, "shard_step")
+    step_fn = (lambda: wl.shard_step(capi, mode, rank, world)) if sharded else (lambda: wl.step(capi, mode))
+    for _ in range(warmup):
+        step_fn()
+    barrier()
+
+    # timed region (device-resident inputs)
+    capi.cpp_set_stage_timing(True)
+    dense_ms, stages = [], []
+    launches0 = capi.cpp_launch_count()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+
+    def one():
+        r = step_fn()
+        st = capi.cpp_stage_times()
+        if len(st) >= 2:
+            dense_ms.append(st[1])
+            stages.append(list(st))
+        return r
+    barrier()
+    total_ms, res = timed_steps(one, steps, stream, torch, flush)
+    barrier()
+    clk = clocks.stop()
+    launches = capi.cpp_launch_count() - launches0
+    capi.cpp_set_stage_timing(False)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    rec = {"value": wl.units * steps * (1 if sharded else world) / (total_ms / 1e3), "unit": UNIT,
+           "steps": steps, "warmup": warmup, "ms_per_step": total_ms / steps,
+           "scaling": "strong" if sharded else "weak",
+           "dtype": ({"plain_fp32": "f32", "filter_fp16": "f16", "filter_bf16": "bf16"}.get(mode.replace("_prune", ""))
+                     if wl.name in ("tsmm", "cpp") else {"frnn": "f32", "twolocus": "u64", "batch": "f32",
+                                                         "hamming": "f8e4m3", "mlba": "u64"}[wl.name]),
+           "config": dict(wl.config, mode=mode if wl.name in ("tsmm", "cpp") else None,
+                          flush_l2_between_steps=bool(flush),
+                          parallelism=(f"{world} shards of one search + one exchange of the results"
+                                       if sharded else f"replicas x{world}" if world > 1 else "single GPU")),
+           "answer": {k: res[k] for k in ("i", "j", "dist2", "score", "mismatches") if k in res},
+           "gpu_launches": launches}
+    if wl.name == "batch":
+        rec["answer"] = {"instances": res["instances"], "pairs_within_R": res["pairs_within_R"]}
+    if wl.name == "frnn":
+        rec["answer"] = {"n_pairs_directed": res["n_pairs_directed"]}
+    if wl.name == "mlba":
+        rec["candidates_per_step"] = res["candidates"]
+
+    pk = peaks()
+    rec["roofline"], extra = roofline_of(wl, capi, mode, pk, dense_ms, stages, total_ms, steps)
+    rec.update(extra)
+    rec["clocks"] = clk
+
+    if detail and not args.no_compare:
+        rec.update(compare(wl, capi, args, mode, res, stream, flush, barrier, steps, pk, dev))
+
+    # end to end through the public API from pinned host memory
+    if not args.no_e2e:
+        host_np, nbytes = wl.host_input()
+        if isinstance(host_np, list):
+            host = [torch.from_numpy(h).pin_memory() for h in host_np]
+            dev_buf = [torch.empty_like(h, device=dev) for h in host]
+        else:
+            host = torch.from_numpy(host_np).pin_memory()
+            dev_buf = torch.empty_like(host, device=dev)
+        barrier()
+        ems, _ = timed_steps(lambda: wl.e2e_step(capi, mode, host, dev_buf), steps, stream, torch, flush)
+        rec["e2e"] = {"value": wl.units * steps / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                      "d2h_bytes_per_step": d2h_bytes(wl, capi)}
+        del host, dev_buf
+
+    # the answer against the stored oracle answer (one untimed call)
+    if world == 1:
+        barrier()
+        rec["same_answer_as_oracle"] = same_as_golden(wl, capi, mode)
+    return rec
+
+
+def compare(wl, capi, args, mode, res, stream, flush, barrier, steps, pk, dev):
+    """Comparisons beside a workload's line: the plain FP32 path and reference pruning (motif,
+    closest pair), the FP32 tiles and per-instance calls (batch), the tensor-core scans (two-locus),
+    the exact scan (MLBA)."""
+    import torch
+    out = {}
+    if wl.name in ("tsmm", "cpp") and mode != "plain_fp32":
+        barrier()
+        k = max(1, min(steps, 3))
+        pms, pres = timed_steps(lambda: wl.step(capi, "plain_fp32"), k, stream, torch, flush)
+        out["plain_fp32"] = {"value": wl.units * k / (pms / 1e3), "unit": UNIT, "ms_per_step": pms / k,
+                             "same_answer": (pres["i"], pres["j"], pres["dist2"]) == (res["i"], res["j"], res["dist2"])}
+    if wl.name in ("tsmm", "cpp") and mode != "plain_fp32" and not mode.endswith("_prune"):
+        # the same search with reference pruning of tiles (MK / MPR bound): same answer, fewer tiles
+        barrier()
+        pmode = mode + "_prune"
+        wl.step(capi, pmode)                               # warm-up
+        capi.cpp_set_stage_timing(True)
+        psteps = max(1, min(steps, 5))
+        dense = []
+
+        def pruned():
+            r = wl.step(capi, pmode)
+            st = capi.cpp_stage_times()
+            if len(st) >= 2:
+                dense.append(st[1])
+            return r
+        pms, pres = timed_steps(pruned, psteps, stream, torch, flush)
+        capi.cpp_set_stage_timing(False)
+        kept, total = capi.cpp_prune_stats()
+        sec = pms / psteps / 1e3
+        out["pruned"] = {"mode": pmode, "ms_per_step": pms / psteps,
+                         "dense_stage_ms": statistics.mean(dense) if dense else None,
+                         # every pair's answer is decided; the skipped tiles' pairs are excluded by the bound
+                         "brute_force_equivalent_pairs_per_s": wl.units / sec,
+                         "evaluated_pairs_per_s": wl.units * kept / max(total, 1) / sec,
+                         "unit": UNIT, "tiles_kept": kept, "tiles_total": total,
+                         "same_answer": (pres["i"], pres["j"], pres["dist2"]) == (res["i"], res["j"], res["dist2"])}
+    if wl.name == "batch":
+        barrier()
+        fms, fres = timed_steps(lambda: wl.fp32_step(capi), 1, stream, torch, flush)
+        out["plain_fp32"] = {"value": wl.units / (fms / 1e3), "unit": UNIT, "ms_per_step": fms,
+                             "same_answer": fres["answers"] == res["answers"] and
+                             bool((fres["counts"] == res["counts"]).all())}
+        barrier()
+        pms, _ = timed_steps(lambda: wl.per_instance_step(capi), 1, stream, torch, flush)
+        out["per_instance_launches"] = {"ms_per_step": pms, "value": wl.units / (pms / 1e3), "unit": UNIT,
+                                        "calls_per_step": 2 * len(wl.batch)}
+    if wl.name == "twolocus" and capi.filters_available():
+        # the same scan on the tensor cores (exact integer GEMMs of one-hot rows), both measures
+        ws = torch.empty(capi.twolocus_scan_tc_workspace_size(4096, wl.planes.shape[3]), dtype=torch.uint8,
+                         device=dev)
+        for meas in ("matches", "pearson"):
+            capi.twolocus_scan_tc(wl.dev_planes, 4096, 4096, measure=meas, ws=ws)
+            barrier()
+            k = max(1, min(steps, 10))
+            tms, tres = timed_steps(lambda: capi.twolocus_scan_tc(wl.dev_planes, 4096, 4096, measure=meas, ws=ws),
+                                    k, stream, torch, flush)
+            tms /= k
+            kk = 2 * 128 * wl.planes.shape[3]      # two groups x K per group
+            fp8_peak = 2 * pk["bf16_tflops"]       # E4M3 operands: the bf16 burst x the nominal 2x
+            out[f"tensor_core_{meas}"] = {
+                "ms_per_step": tms, "value": wl.units / (tms / 1e3), "unit": UNIT,
+                "gemm_tflops": wl.units * 2 * kk / (tms / 1e3) / 1e12,
+                "frac_of_fp8_peak": wl.units * 2 * kk / (tms / 1e3) / 1e12 / fp8_peak,
+                "answer": {"i": tres["i"], "j": tres["j"], "score": tres["score"], "score_real": tres["score_real"]},
+                **({"same_answer": (tres["i"], tres["j"], tres["score"]) == (res["i"], res["j"], res["score"])}
+                   if meas == "matches" else {})}
+    if wl.name == "mlba" and capi.filters_available():
+        ex = capi.hamming_pair(wl.dev_s, wl.sigma)      # the exact all-pairs answer, untimed
+        out["same_answer_as_exact"] = (ex["i"], ex["j"], ex["mismatches"]) == (res["i"], res["j"], res["mismatches"])
+    return out
+
+
+# the other scope-table workloads measured beside the motif headline (one GPU)
+EXTRA_WORKLOADS = ("cpp", "frnn", "twolocus", "batch")
 
 
 # ------------------------------------------------------------------ arms
@@ -553,217 +869,33 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # N > 1: the motif, closest-pair, two-locus and FRNN workloads are split into shards of one search
-    # (strong scaling; one exchange per step: an all-gather of the shard results, min- or max-reduced,
-    # or of the FRNN slabs' CSR pieces); the batch runs as replicas.
-    sharded = world > 1 and hasattr(wl, "shard_step")
-    step_fn = (lambda: wl.shard_step(capi, mode, rank, world)) if sharded else (lambda: wl.step(capi, mode))
-
-    # warm-up
-    for _ in range(args.warmup):
-        ref = step_fn()
-    barrier()
-
-    # timed region (device-resident inputs)
-    capi.cpp_set_stage_timing(True)
-    dense_ms, stages = [], []
-    launches0 = capi.cpp_launch_count()
-    clocks = ClockSampler(local)
-    clocks.start()
-
-    def one():
-        r = step_fn()
-        st = capi.cpp_stage_times()
-        if len(st) >= 2:
-            dense_ms.append(st[1])
-            stages.append(list(st))
-        return r
-    barrier()
-    total_ms, res = timed_steps(one, args.steps, stream, torch, flush)
-    barrier()
-    clk = clocks.stop()
-    launches = capi.cpp_launch_count() - launches0
-    capi.cpp_set_stage_timing(False)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = wl.units * args.steps * (1 if sharded else world) / (total_ms / 1e3)
-
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-           "scaling": "strong" if sharded else "weak", "vs_baseline": None,
-           "dtype": ({"plain_fp32": "f32", "filter_fp16": "f16", "filter_bf16": "bf16"}.get(mode.replace("_prune", ""))
-                     if wl.name in ("tsmm", "cpp") else {"frnn": "f32", "twolocus": "u64", "batch": "f32",
-                                                         "hamming": "f8e4m3", "mlba": "u64"}[wl.name]),
-           "data": "synthetic", "config": dict(wl.config, mode=mode if wl.name in ("tsmm", "cpp") else None,
-                                               flush_l2_between_steps=bool(flush),
-                                               parallelism=(f"{world} shards of one search + one exchange of the results"
-                                                            if sharded else f"replicas x{world}" if world > 1
-                                                            else "single GPU")),
-           "answer": {k: res[k] for k in ("i", "j", "dist2", "score", "mismatches") if k in res},
-           "gpu_launches": launches}
-
-    # roofline of the dominant kernel
-    pk = peaks()
-    if wl.name in ("tsmm", "cpp"):
-        avg_ms = statistics.mean(dense_ms) if dense_ms else None
-        flops = wl.units * wl.flop_per_unit
-        if mode == "plain_fp32":
-            peak, bound, unit, src = FP32_ALU_PEAK_TFLOPS, "alu", "TFLOP/s", "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"
-            out["alu_peak_microbenchmark"] = alu_peaks(capi)
-        else:
-            peak, bound, unit, src = pk["bf16_tflops"], "tensor", "TFLOP/s", f"{pk['source']} bf16 burst"
-        if mode.endswith("_prune"):  # only the kept tiles are evaluated
-            kept, total = capi.cpp_prune_stats()
-            if total > 0:
-                flops = flops * kept / total
-        ach = flops / (avg_ms / 1e3) / 1e12 if avg_ms else None
-        key = f"dense_{mode}@{wl.name}"
-        out["roofline"] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-                           "frac": ach / peak if ach else None, "traffic": recorded_traffic(key),
-                           "kernel": "dense all-pairs stage (gram_tc / gram_simt)", "peak_source": src,
-                           "launch_ms": avg_ms, "algorithmic_flop_per_launch": flops}
-    elif wl.name == "batch":
-        # dominant kernel: the persistent tensor-core tile kernel (its time from events captured in
-        # the batch's graph); algorithmic work 2 d flop per pair of the instances it runs
-        tc_ms = statistics.mean(dense_ms) if dense_ms else None
-        if wl.tc_flops and tc_ms:
-            ach = wl.tc_flops / (tc_ms / 1e3) / 1e12
-            out["roofline"] = {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                               "frac": ach / pk["bf16_tflops"], "traffic": recorded_traffic("batch_tc@batch"),
-                               "kernel": "batch_tc_kernel (persistent tcgen05 tiles of all tensor-core instances)",
-                               "peak_source": f"{pk['source']} bf16 burst", "launch_ms": tc_ms,
-                               "algorithmic_flop_per_launch": wl.tc_flops}
-        else:
-            per_step_ms = total_ms / args.steps
-            ach = wl.flops / (per_step_ms / 1e3) / 1e12
-            out["alu_peak_microbenchmark"] = alu_peaks(capi)
-            out["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                               "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": recorded_traffic("batch@batch"),
-                               "kernel": "cpp_batch step (persistent FP32 tile kernel)",
-                               "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
-                               "algorithmic_flop_per_step": wl.flops}
-        out["answer"] = {"instances": res["instances"], "pairs_within_R": res["pairs_within_R"]}
-        if not args.no_compare:
-            barrier()
-            fms, fres = timed_steps(lambda: wl.fp32_step(capi), 1, stream, torch, flush)
-            out["plain_fp32"] = {"value": wl.units / (fms / 1e3), "unit": UNIT, "ms_per_step": fms,
-                                 "same_answer": fres["answers"] == res["answers"] and
-                                 bool((fres["counts"] == res["counts"]).all())}
-            barrier()
-            pms, _ = timed_steps(lambda: wl.per_instance_step(capi), 1, stream, torch, flush)
-            out["per_instance_launches"] = {"ms_per_step": pms, "value": wl.units / (pms / 1e3), "unit": UNIT,
-                                            "calls_per_step": 2 * len(wl.batch)}
-    elif wl.name == "frnn":
-        per_step_ms = total_ms / args.steps
-        gbs = wl.algorithmic_bytes() / (per_step_ms / 1e3) / 1e9
-        out["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                           "frac": gbs / pk["hbm_gbs"], "traffic": recorded_traffic("frnn_query@frnn"),
-                           "kernel": "frnn_query step (grid build + 27-cell count and fill passes)",
-                           "peak_source": f"{pk['source']} hbm copy"}
-    elif wl.name == "twolocus":
-        per_step_ms = total_ms / args.steps
-        pops = wl.units * wl.flop_per_unit
-        ach = pops / (per_step_ms / 1e3) / 1e12
-        out["alu_peak_microbenchmark"] = alu_peaks(capi)
-        out["roofline"] = {"bound": "alu", "achieved": ach, "peak": POPC_PEAK_TOPS, "unit": "Tpopc/s",
-                           "frac": ach / POPC_PEAK_TOPS, "traffic": recorded_traffic("twolocus_scan@twolocus"),
-                           "kernel": "twolocus_scan_kernel (step time)",
-                           "peak_source": "derived: 152 SM x 16 POPC/clk x 2070 MHz"}
-        if not args.no_compare and capi.filters_available():
-            # the same scan on the tensor cores (exact integer GEMMs of one-hot rows), both measures
-            ws = torch.empty(capi.twolocus_scan_tc_workspace_size(4096, wl.planes.shape[3]), dtype=torch.uint8,
-                             device=dev)
-            for meas in ("matches", "pearson"):
-                capi.twolocus_scan_tc(wl.dev_planes, 4096, 4096, measure=meas, ws=ws)
-                barrier()
-                tms, tres = timed_steps(lambda: capi.twolocus_scan_tc(wl.dev_planes, 4096, 4096, measure=meas, ws=ws),
-                                        max(1, min(args.steps, 10)), stream, torch, flush)
-                tms /= max(1, min(args.steps, 10))
-                k = 2 * 128 * wl.planes.shape[3]       # two groups x K per group
-                fp8_peak = 2 * pk["bf16_tflops"]       # E4M3 operands: the bf16 burst x the nominal 2x
-                out[f"tensor_core_{meas}"] = {
-                    "ms_per_step": tms, "value": wl.units / (tms / 1e3), "unit": UNIT,
-                    "gemm_tflops": wl.units * 2 * k / (tms / 1e3) / 1e12,
-                    "frac_of_fp8_peak": wl.units * 2 * k / (tms / 1e3) / 1e12 / fp8_peak,
-                    "answer": {"i": tres["i"], "j": tres["j"], "score": tres["score"], "score_real": tres["score_real"]},
-                    **({"same_answer": (tres["i"], tres["j"], tres["score"]) == (res["i"], res["j"], res["score"])}
-                       if meas == "matches" else {})}
-    elif wl.name == "hamming":
-        per_step_ms = total_ms / args.steps
-        ach = wl.units * wl.flop_per_unit / (per_step_ms / 1e3) / 1e12
-        peak = 2 * pk["bf16_tflops"]                   # E4M3 operands: the bf16 burst x the nominal 2x
-        out["roofline"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                           "frac": ach / peak, "traffic": recorded_traffic("match_tc@hamming"),
-                           "kernel": "match_tc_kernel (step time; one-hot FP8 GEMM, 2 K flop per pair)",
-                           "peak_source": f"{pk['source']} bf16 burst x 2 (nominal fp8 / bf16 ratio)"}
-    elif wl.name == "mlba" and stages:
-        # per stage [pack + keys, radix sort, buckets + pair offsets, verification], CUDA events inside the call
-        st_ms = [statistics.mean(x[k] for x in stages) for k in range(4)]
-        out["stages_ms"] = dict(zip(("pack_keys", "radix_sort", "buckets", "verify"), st_ms))
-        E = wl.iters * wl.n
-        # algorithmic bytes of the sort: per 8-bit pass the histogram reads the keys (8 B) and the scatter
-        # reads and writes key + row (12 + 12 B) of every element
-        sort_bytes = wl.passes * E * (8 + 24)
-        ach = sort_bytes / (st_ms[1] / 1e3) / 1e9
-        out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                           "frac": ach / pk["hbm_gbs"], "traffic": recorded_traffic("mlba_sort@mlba"),
-                           "kernel": f"radix sort stage ({wl.passes} passes x hist + scan + scatter; L2-resident)",
-                           "peak_source": f"{pk['source']} HBM copy"}
-        if not args.no_compare and capi.filters_available():
-            ex = capi.hamming_pair(wl.dev_s, wl.sigma)      # the exact all-pairs answer, untimed
-            out["same_answer_as_exact"] = (ex["i"], ex["j"], ex["mismatches"]) == (res["i"], res["j"], res["mismatches"])
-        out["candidates_per_step"] = res["candidates"]
-    out["clocks"] = clk
-
-    # the same answer from the plain FP32 path, and its throughput
-    if wl.name in ("tsmm", "cpp") and mode != "plain_fp32" and not args.no_compare:
-        barrier()
-        pms, pres = timed_steps(lambda: wl.step(capi, "plain_fp32"), max(1, min(args.steps, 3)), stream, torch, flush)
-        out["plain_fp32"] = {"value": wl.units * max(1, min(args.steps, 3)) / (pms / 1e3), "unit": UNIT,
-                             "ms_per_step": pms / max(1, min(args.steps, 3)),
-                             "same_answer": (pres["i"], pres["j"], pres["dist2"]) == (res["i"], res["j"], res["dist2"])}
-
-    # the same search with reference pruning of tiles (MK / MPR bound): same answer, fewer tiles
-    if wl.name in ("tsmm", "cpp") and mode != "plain_fp32" and not mode.endswith("_prune") and not args.no_compare:
-        barrier()
-        pmode = mode + "_prune"
-        wl.step(capi, pmode)                               # warm-up
-        capi.cpp_set_stage_timing(True)
-        psteps = max(1, min(args.steps, 5))
-        dense = []
-
-        def pruned():
-            r = wl.step(capi, pmode)
-            st = capi.cpp_stage_times()
-            if len(st) >= 2:
-                dense.append(st[1])
-            return r
-        pms, pres = timed_steps(pruned, psteps, stream, torch, flush)
-        capi.cpp_set_stage_timing(False)
-        kept, total = capi.cpp_prune_stats()
-        out["pruned"] = {"mode": pmode, "value": wl.units * psteps / (pms / 1e3), "unit": UNIT,
-                         "ms_per_step": pms / psteps, "dense_stage_ms": statistics.mean(dense) if dense else None,
-                         "tiles_kept": kept, "tiles_total": total,
-                         "same_answer": (pres["i"], pres["j"], pres["dist2"]) == (res["i"], res["j"], res["dist2"])}
-
-    # end to end through the public API from pinned host memory
-    if not args.no_e2e:
-        host_np, nbytes = wl.host_input()
-        if isinstance(host_np, list):
-            host = [torch.from_numpy(h).pin_memory() for h in host_np]
-            dev_buf = [torch.empty_like(h, device=dev) for h in host]
-        else:
-            host = torch.from_numpy(host_np).pin_memory()
-            dev_buf = torch.empty_like(host, device=dev)
-        barrier()
-        ems, _ = timed_steps(lambda: wl.e2e_step(capi, mode, host, dev_buf), args.steps, stream, torch, flush)
-        out["e2e"] = {"value": wl.units * args.steps / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                      "d2h_bytes_per_step": d2h_bytes(wl, capi)}
+    rec = measure(wl, capi, args, mode, dev, stream, flush, barrier, args.steps, args.warmup, rank, world, True)
+    out = {"metric": METRIC, "value": rec.pop("value"), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": rec.pop("ms_per_step"), "higher_is_better": True,
+           "scaling": rec.pop("scaling"), "vs_baseline": None, "dtype": rec.pop("dtype"), "data": "synthetic"}
+    rec.pop("steps")
+    rec.pop("warmup")
+    out.update(rec)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
+
+    # the other workloads of the scope table, each with its own steps, roofline, e2e and answer check
+    if world == 1 and args.workload == "tsmm" and not args.no_extra:
+        del wl
+        torch.cuda.empty_cache()
+        subs = {}
+        for name in EXTRA_WORKLOADS:
+            w = WORKLOADS[name](args)
+            w.setup(dev)
+            wmode = mode if name == "cpp" else None
+            k = max(1, min(args.steps, 10))
+            subs[name] = measure(w, capi, args, wmode or mode, dev, stream, flush, barrier, k,
+                                 max(3, min(args.warmup, 5)), rank, world, name == "batch")
+            del w
+            torch.cuda.empty_cache()
+        out["workloads"] = subs
+
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -814,6 +946,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="time only --workload (by default the motif line also times the closest-pair, FRNN, "
+                         "two-locus and batch workloads)")
     ap.add_argument("--batch-path", type=int, choices=[0, 1, 2], default=0,
                     help="batch tiles: 0 the tuned policy, 1 FP32 CUDA-core tiles, 2 tensor-core tiles")
     ap.add_argument("--no-tune", action="store_true",

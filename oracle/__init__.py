@@ -73,6 +73,7 @@ def _load():
             lib = ctypes.CDLL(_LIB)
             sig = {
                 "oracle_num_threads": (ctypes.c_int, []),
+                "oracle_set_num_threads": (None, [ctypes.c_int]),
                 "oracle_sqdist": (ctypes.c_double, [_f64p, _f64p, ctypes.c_int64]),
                 "oracle_cpp": (ctypes.c_int, [_f64p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                               _i64p, _i64p, _f64p]),
@@ -121,6 +122,13 @@ def _check(rc: int, what: str):
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(k: int) -> int:
+    """Use k OpenMP threads from now on (k >= 1); returns the previous count."""
+    prev = num_threads()
+    _load().oracle_set_num_threads(int(k))
+    return prev
 
 
 def sqdist(x, y) -> float:

@@ -70,6 +70,15 @@ int oracle_num_threads(void) {
 #endif
 }
 
+/* Threads of the following calls (for timing the oracle on one core); k < 1 is ignored. */
+void oracle_set_num_threads(int k) {
+#ifdef _OPENMP
+  if (k >= 1) omp_set_num_threads(k);
+#else
+  (void)k;
+#endif
+}
+
 /* (d2, i, j) is lexicographically smaller than (bd2, bi, bj) */
 static int lex_less(double d2, int64_t i, int64_t j, double bd2, int64_t bi, int64_t bj) {
   if (d2 < bd2) return 1;

@@ -1,10 +1,13 @@
 """Writes the stored expected values under tests/golden/ by calling the oracle only.
 
-    python tests/golden/make_golden.py [twolocus] [tsmm] [frnn] [batch]   (default: all)
+    python tests/golden/make_golden.py [cpp] [twolocus] [tsmm] [frnn] [batch]   (default: all)
 
 Each stored value is the oracle's answer for one full-size seeded workload of
 paper_1407_5609_gb300.synth, too slow to brute-force on every test run:
 
+cpp_4096x32.json                 closest pair (Sec. 3) of make_cpp() (4096 FP64 points in [0,1]^32, one pair
+                                 planted at 1e-3): 8.4e6 pairs; stored so that the benchmark can check
+                                 its answer without running the oracle.
 twolocus_4096snp_4096x4096.json  two-locus (Sec. 6): pair, score, 3x3 tables for make_genotypes()
                                  (4096 SNPs, 4096 cases, 4096 controls); 8.4e6 SNP pairs.
 tsmm_rw262144_l512_excl256.json  motif pair (Sec. 3 over the z-normalised l-mers of Sec. 2) of
@@ -44,6 +47,16 @@ def _write(name, out):
     with open(os.path.join(HERE, name), "w") as f:
         json.dump(out, f, indent=1)
     print(name, {k: v for k, v in out.items() if k != "instances"}, flush=True)
+
+
+def cpp_full():
+    x, plant = synth.make_cpp()
+    t = time.time()
+    i, j, d2 = oracle.cpp(x)
+    out = {"workload": "make_cpp(n=4096, d=32, seed=14075609+0), FP64, pair planted at 1e-3", "i": i, "j": j,
+           "dist2": float(d2).hex(), "dist2_repr": repr(float(d2)), "planted": list(plant),
+           "oracle_seconds": round(time.time() - t, 1), "oracle_threads": oracle.num_threads()}
+    _write("cpp_4096x32.json", out)
 
 
 def twolocus_full():
@@ -95,7 +108,7 @@ def batch_full():
     _write("batch_2048inst.json", out)
 
 
-JOBS = {"twolocus": twolocus_full, "tsmm": tsmm_full, "frnn": frnn_full, "batch": batch_full}
+JOBS = {"cpp": cpp_full, "twolocus": twolocus_full, "tsmm": tsmm_full, "frnn": frnn_full, "batch": batch_full}
 
 if __name__ == "__main__":
     for name in sys.argv[1:] or list(JOBS):

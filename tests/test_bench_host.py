@@ -28,6 +28,7 @@ def test_workload_and_cpu_baseline(bench_mod, name):
     assert wl.units > 0 and wl.config["workload"]
     cb = bench_mod.cpu_baseline(wl, target_s=0.3)
     assert cb["value"] > 0 and cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"]
+    assert cb["one_thread"]["value"] > 0 and cb["one_thread"]["cores"] == 1
 
 
 def test_reference_arm_prints_one_json_line():
@@ -37,3 +38,10 @@ def test_reference_arm_prints_one_json_line():
     line = json.loads(p.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "pairs/s"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_stored_answers_are_read(bench_mod):
+    """The benchmark's answer checks read the oracle's stored answers (tests/golden/)."""
+    g = bench_mod.golden("cpp_4096x32.json")
+    assert g is not None and g["i"] < g["j"] and float.fromhex(g["dist2"]) > 0
+    assert bench_mod.golden("no_such_file.json") is None
