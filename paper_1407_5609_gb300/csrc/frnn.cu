@@ -43,26 +43,38 @@ __device__ __forceinline__ unsigned int ord_key(float f) {
 __device__ __forceinline__ float ord_val(unsigned int k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
-__device__ __forceinline__ uint64_t mix64(uint64_t x) {
-  x ^= x >> 33;
-  x *= 0xff51afd7ed558ccdull;
-  x ^= x >> 33;
-  x *= 0xc4ceb9fe1a85ec53ull;
-  x ^= x >> 33;
-  return x;
+// Slot of a cell key in a table of T = 2^tbits slots: the key folded to 32 bits, then Fibonacci
+// hashing (multiply by 2^32 / golden ratio, keep the top tbits bits).
+__device__ __forceinline__ uint64_t slot_hash(uint64_t key, int tbits) {
+  const uint32_t f = (uint32_t)key ^ ((uint32_t)(key >> 32) * 0x85EBCA6Bu);
+  return (uint64_t)((f * 0x9E3779B1u) >> (32 - tbits));
 }
 
-__global__ void frnn_init_kernel(FrnnState* fs) {
+// A cell of the grid in the hash table: its 64-bit key, and (after the counting sort) its first
+// position in the cell-sorted point arrays and its number of points; one 16-byte load per probe.
+struct __align__(16) CellRec {
+  unsigned long long key;
+  int32_t start, cnt;
+};
+
+__global__ void frnn_init_kernel(FrnnState* fs, uint32_t* counters) {
   for (int k = 0; k < 4; ++k) {
     fs->mm[k] = 0xffffffffu;
     fs->mm[4 + k] = 0u;
   }
   fs->status = 0u;
+  if (counters) counters[0] = counters[1] = 0u;
 }
 
-__global__ void bbox_kernel(const float* __restrict__ pts, int64_t n, int d, int64_t ld, FrnnState* fs) {
+// Bounding box (ordered-float keys) and the non-finite flag: warp, then block reductions, then one
+// atomic per block and bound.
+__global__ void __launch_bounds__(256) bbox_kernel(const float* __restrict__ pts, int64_t n, int d, int64_t ld,
+                                                   FrnnState* fs) {
+  __shared__ unsigned int red[8][8];
+  __shared__ int bad_any;
   unsigned int lo[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[4] = {0u, 0u, 0u, 0u};
   bool bad = false;
+  if (threadIdx.x == 0) bad_any = 0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
     for (int k = 0; k < d; ++k) {
       const float x = pts[p * ld + k];
@@ -72,7 +84,7 @@ __global__ void bbox_kernel(const float* __restrict__ pts, int64_t n, int d, int
       hi[k] = max(hi[k], key);
     }
   }
-  for (int k = 0; k < d; ++k) {
+  for (int k = 0; k < 4; ++k) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
@@ -80,12 +92,25 @@ __global__ void bbox_kernel(const float* __restrict__ pts, int64_t n, int d, int
     }
   }
   bad = __any_sync(0xffffffffu, bad);
-  if ((threadIdx.x & 31) == 0) {
-    for (int k = 0; k < d; ++k) {
-      atomicMin(&fs->mm[k], lo[k]);
-      atomicMax(&fs->mm[4 + k], hi[k]);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) {
+    for (int k = 0; k < 4; ++k) {
+      red[w][k] = lo[k];
+      red[w][4 + k] = hi[k];
     }
-    if (bad) atomicOr(&fs->status, 1u);
+    if (bad) atomicOr(&bad_any, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    const int k = threadIdx.x;
+    unsigned int v = red[0][k];
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) v = k < 4 ? min(v, red[q][k]) : max(v, red[q][k]);
+    if ((k & 3) < d) {
+      if (k < 4) atomicMin(&fs->mm[k], v);
+      else atomicMax(&fs->mm[k], v);
+    }
+    if (k == 0 && bad_any) atomicOr(&fs->status, 1u);
   }
 }
 
@@ -133,43 +158,84 @@ __device__ __forceinline__ uint64_t key_of(const GridParams& gp, const int64_t* 
   return key;
 }
 
+// Every point joins its cell's record (created on first sight) and takes a rank inside the cell;
+// the threads that create cells append them (key and slot) to the list of occupied cells, one
+// atomic per warp.
 template <int D>
-__global__ void hash_insert_kernel(const float* __restrict__ pts, int64_t n, int64_t ld, FrnnState* fs,
-                                   uint64_t* __restrict__ keys, int64_t T, uint32_t* __restrict__ slot_of,
-                                   int32_t* __restrict__ cnt, uint32_t* __restrict__ rank_of) {
+__global__ void __launch_bounds__(256) hash_insert_kernel(const float* __restrict__ pts, int64_t n, int64_t ld,
+                                                          FrnnState* fs, CellRec* __restrict__ tab, int64_t T,
+                                                          uint32_t* __restrict__ slot_of,
+                                                          uint32_t* __restrict__ rank_of,
+                                                          uint32_t* __restrict__ occ_slot,
+                                                          unsigned long long* __restrict__ occ_key,
+                                                          uint32_t* __restrict__ n_occ) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
+  const int lane = threadIdx.x & 31;
+  const bool valid = p < n;
   const GridParams gp = fs->gp;
-  float x[4] = {0.f, 0.f, 0.f, 0.f};
+  uint64_t key = 0;
+  int64_t h = -1;
+  bool created = false;
+  if (valid) {
+    float x[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int k = 0; k < D; ++k) x[k] = pts[p * ld + k];
-  int64_t c[4];
-  cell_of<D>(gp, x, c);
-  const uint64_t key = key_of<D>(gp, c);
-  uint64_t h = mix64(key) & (uint64_t)(T - 1);
-  for (int64_t probe = 0; probe < T; ++probe) {
-    const unsigned long long prev = atomicCAS((unsigned long long*)&keys[h], EMPTY_KEY, key);
-    if (prev == EMPTY_KEY || prev == key) {
-      slot_of[p] = (uint32_t)h;
-      rank_of[p] = (uint32_t)atomicAdd(&cnt[h], 1);
-      return;
+    for (int k = 0; k < D; ++k) x[k] = pts[p * ld + k];
+    int64_t c[4];
+    cell_of<D>(gp, x, c);
+    key = key_of<D>(gp, c);
+    uint64_t g = slot_hash(key, __ffsll(T) - 1);
+    for (int64_t probe = 0; probe < T; ++probe) {
+      const unsigned long long prev = atomicCAS(&tab[g].key, EMPTY_KEY, key);
+      if (prev == EMPTY_KEY || prev == key) {
+        created = prev == EMPTY_KEY;
+        h = (int64_t)g;
+        break;
+      }
+      g = (g + 1) & (uint64_t)(T - 1);
     }
-    h = (h + 1) & (uint64_t)(T - 1);
+    if (h >= 0) {
+      slot_of[p] = (uint32_t)h;
+      rank_of[p] = (uint32_t)atomicAdd(&tab[h].cnt, 1);
+    } else {
+      atomicOr(&fs->status, 8u);
+      slot_of[p] = 0xffffffffu;
+    }
   }
-  atomicOr(&fs->status, 8u);
-  slot_of[p] = 0xffffffffu;
+  const uint32_t mask = __ballot_sync(0xffffffffu, created);
+  if (mask) {
+    uint32_t base = 0;
+    if (lane == __ffs(mask) - 1) base = atomicAdd(n_occ, (uint32_t)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
+    if (created) {
+      const uint32_t idx = base + (uint32_t)__popc(mask & ((1u << lane) - 1u));
+      occ_slot[idx] = (uint32_t)h;
+      occ_key[idx] = key;
+    }
+  }
+}
+
+// occ_cnt[c] = points of occupied cell c (0 past the occupied cells), for the scan of cell starts
+__global__ void occ_count_kernel(int64_t n, const uint32_t* __restrict__ occ_slot, const uint32_t* __restrict__ n_occ,
+                                 const CellRec* __restrict__ tab, int32_t* __restrict__ occ_cnt) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n) occ_cnt[c] = c < (int64_t)*n_occ ? tab[occ_slot[c]].cnt : 0;
+}
+__global__ void occ_start_kernel(int64_t n, const uint32_t* __restrict__ occ_slot, const uint32_t* __restrict__ n_occ,
+                                 const int64_t* __restrict__ occ_start, CellRec* __restrict__ tab) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n && c < (int64_t)*n_occ) tab[occ_slot[c]].start = (int32_t)occ_start[c];
 }
 
 __global__ void scatter_kernel(const float* __restrict__ pts, int64_t n, int64_t ld, const FrnnState* fs,
                                const uint32_t* __restrict__ slot_of, const uint32_t* __restrict__ rank_of,
-                               const int64_t* __restrict__ start, int32_t* __restrict__ sorted_idx,
+                               const CellRec* __restrict__ tab, int32_t* __restrict__ sorted_idx,
                                float4* __restrict__ sorted_pts) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n || slot_of[p] == 0xffffffffu) return;
   const int d = fs->gp.d;
   float x[4] = {0.f, 0.f, 0.f, 0.f};
   for (int k = 0; k < d; ++k) x[k] = pts[p * ld + k];
-  const int64_t pos = start[slot_of[p]] + rank_of[p];
+  const int64_t pos = (int64_t)tab[slot_of[p]].start + rank_of[p];
   sorted_idx[pos] = (int32_t)p;
   sorted_pts[pos] = make_float4(x[0], x[1], x[2], x[3]);
 }
@@ -185,15 +251,116 @@ __device__ __forceinline__ bool within_fp64(const float* x, const float* y, doub
   }
   return s <= rr;
 }
-__device__ __forceinline__ int64_t find_slot(const uint64_t* __restrict__ keys, int64_t T, uint64_t key) {
-  uint64_t h = mix64(key) & (uint64_t)(T - 1);
+// The record of the cell with this key: (start, cnt), cnt = 0 when the cell holds no point.
+__device__ __forceinline__ int2 find_cell(const CellRec* __restrict__ tab, int64_t T, uint64_t key) {
+  uint64_t h = slot_hash(key, __ffsll(T) - 1);
   for (int64_t probe = 0; probe < T; ++probe) {
-    const uint64_t k = keys[h];
-    if (k == key) return (int64_t)h;
-    if (k == EMPTY_KEY) return -1;
+    const CellRec r = tab[h];
+    if (r.key == key) return make_int2(r.start, r.cnt);
+    if (r.key == EMPTY_KEY) break;
     h = (h + 1) & (uint64_t)(T - 1);
   }
-  return -1;
+  return make_int2(0, 0);
+}
+
+// The FP64 test as a call of its own: FP64 runs at a small fraction of the FP32 rate here, so it
+// must never be if-converted into the common path.
+template <int D>
+__device__ __noinline__ int within_fp64_call(float x0, float x1, float x2, float x3, float y0, float y1, float y2,
+                                             float y3, double rr) {
+  const float x[4] = {x0, x1, x2, x3}, y[4] = {y0, y1, y2, y3};
+  return within_fp64<D>(x, y, rr) ? 1 : 0;
+}
+
+// Pair decision (called by all 32 lanes together): FP32 squared distance, with the FP64 test inside a
+// 2^-16 relative band of R^2 (or always when R^2 is outside the FP32 range), entered only when some
+// lane of the warp needs it.  x[D] and y[D] are the two points.
+// The FP32 value has a relative error below 6 u (one rounding per difference, one per fused
+// multiply-add), far inside the 2^-16 band, so every pair outside the band is decided as the FP64
+// test would decide it.
+template <int D>
+__device__ __forceinline__ int decide(const float* x, const float* y, const GridParams& gp, bool live) {
+  const float d0 = x[0] - y[0];
+  float s = d0 * d0;
+#pragma unroll
+  for (int t = 1; t < D; ++t) {
+    const float dv = x[t] - y[t];
+    s = fmaf(dv, dv, s);
+  }
+  int in = s < gp.rr_lo ? 1 : 0;
+  const bool band = live && (gp.use64 || (!(s < gp.rr_lo) && !(s > gp.rr_hi)));
+  if (__any_sync(0xffffffffu, band)) {
+    if (band)
+      in = within_fp64_call<D>(x[0], D > 1 ? x[1] : 0.f, D > 2 ? x[2] : 0.f, D > 3 ? x[3] : 0.f, y[0],
+                               D > 1 ? y[1] : 0.f, D > 2 ? y[2] : 0.f, D > 3 ? y[3] : 0.f, gp.rr);
+  }
+  return live ? in : 0;
+}
+
+// Lanes look up the 3^D neighbour cells of cell c (lane handles codes lane PER .. lane PER + PER - 1,
+// code = sum_e (offset_e + 1) 3^e, so the offsets below increase with the code) and the warp lays
+// their points out one after another: off[code] = position of the cell's first candidate, st[code]
+// = its first sorted position, off[S] = the total, which is returned.
+template <int D>
+__device__ __forceinline__ int neighbour_layout(const GridParams& gp, uint64_t key, const int64_t* c,
+                                                const CellRec* __restrict__ tab, int64_t T, int lane, int32_t* off,
+                                                int32_t* st) {
+  constexpr int S = D == 1 ? 3 : D == 2 ? 9 : D == 3 ? 27 : 81, PER = (S + 31) / 32;
+  int2 rec[PER];
+  int mine = 0;
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int code = lane * PER + r;
+    rec[r] = make_int2(0, 0);
+    if (code < S) {
+      // neighbour key = key + sum_e delta_e 2^(e bits): every field stays inside [0, lim)
+      int rem = code;
+      bool inside = true;
+      int64_t koff = 0;
+#pragma unroll
+      for (int e = 0; e < D; ++e) {
+        const int delta = rem % 3 - 1;
+        rem /= 3;
+        const int64_t ce = c[e] + delta;
+        inside &= ce >= 0 && ce < gp.lim;
+        koff += (int64_t)delta << (e * gp.bits);
+      }
+      if (inside) rec[r] = find_cell(tab, T, key + (uint64_t)koff);
+    }
+    mine += rec[r].y;
+  }
+  int incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  int run = incl - mine;
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int code = lane * PER + r;
+    if (code < S) {
+      off[code] = run;
+      st[code] = rec[r].x;
+    }
+    run += rec[r].y;
+  }
+  if (lane == 0) off[S] = total;
+  __syncwarp();
+  return total;
+}
+
+// Sorted position of the candidate at laid-out position t: the last cell whose offset is <= t.
+template <int S>
+__device__ __forceinline__ int64_t cand_pos(const int32_t* off, const int32_t* st, int t) {
+  int lo = 0, hi = S;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= t) lo = mid;
+    else hi = mid;
+  }
+  return (int64_t)st[lo] + (t - off[lo]);
 }
 
 __device__ void sort_segment(int32_t* a, int64_t m) {
@@ -230,73 +397,209 @@ __device__ void sort_segment(int32_t* a, int64_t m) {
   }
 }
 
-// FILL = false: counts[q] = |N(q)|.  FILL = true: writes N(q) at cols[row_ptr[q] ..], sorted.
-// With nshards > 1 only the points of slab `shard` (x cells [shard, shard + 1) * ncx / nshards) are
-// answered; the others get empty rows.  The grid holds every point, so no neighbour is missed.
-// The neighbour loop uses 32-bit indices (n < 2^31) and a branch-free FP32 test with the FP64 test
-// only inside the band: an earlier form with 64-bit indices and an early-return test produced wrong
-// counts for a few warps whose lanes spanned several cells (nvcc 13.0, sm_103a); this form matches
-// the oracle at 2^20 points.
+// Slab of a cell for a sharded query (x cells [shard, shard + 1) * ncx / nshards).
+__device__ __forceinline__ int slab_of(const GridParams& gp, int64_t cx, int nshards) {
+  int64_t slab = cx * nshards / gp.ncx;
+  return (int)(slab < 0 ? 0 : slab >= nshards ? nshards - 1 : slab);
+}
+
+// ------------------------------------------------------------------ cell-parallel query
+// One warp per occupied cell: lanes look up the 3^D neighbour cells at once, the warp stages every
+// candidate point of those cells in shared memory (copies of contiguous cell ranges), then takes
+// the cell's points one after another: each lane tests one staged candidate, a ballot counts the
+// neighbours (count pass) or compacts them into a list whose entries each lane places by rank, so
+// the row is written once, ascending (fill pass).  The next cell's key is loaded one iteration
+// ahead.  Cells with more candidates than the staging buffer holds are listed for the warp-per-point
+// kernel below.
+constexpr int QW = 8;            // warps per block
+constexpr int STAGE_CAP = 256;   // staged candidates per warp
+
+template <int D>
+struct CellStage {
+  static constexpr int S = D == 1 ? 3 : D == 2 ? 9 : D == 3 ? 27 : 81;
+  static constexpr bool PACK = D <= 3;  // the point index rides in the unused fourth coordinate
+  float4 p[STAGE_CAP];
+  int32_t j[PACK ? 1 : STAGE_CAP];
+  int32_t nb[STAGE_CAP];
+  int32_t off[S + 1];
+  int32_t st[S];
+};
+
 template <int D, bool FILL>
-__global__ void grid_query_kernel(int n, const FrnnState* fs, const uint64_t* __restrict__ keys, int64_t T,
-                                  const int32_t* __restrict__ cnt, const int64_t* __restrict__ start,
-                                  const int32_t* __restrict__ sorted_idx, const float4* __restrict__ sorted_pts,
-                                  int32_t* __restrict__ counts, const int64_t* __restrict__ row_ptr,
-                                  int32_t* __restrict__ cols, int shard, int nshards) {
-  const int k = (int)(blockIdx.x * blockDim.x + threadIdx.x);
-  if (k >= n) return;
+__global__ void __launch_bounds__(QW * 32) cell_query_kernel(
+    const FrnnState* fs, const CellRec* __restrict__ tab, int64_t T, const unsigned long long* __restrict__ occ_key,
+    const uint32_t* __restrict__ n_occ, const int32_t* __restrict__ sorted_idx, const float4* __restrict__ sorted_pts,
+    int32_t* __restrict__ counts, const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cols, int64_t n,
+    int64_t cols_cap, uint32_t* __restrict__ fb, uint32_t* __restrict__ n_fb, int shard, int nshards) {
+  using Stage = CellStage<D>;
+  constexpr int S = Stage::S, CENTER = (S - 1) / 2;
+  extern __shared__ __align__(16) uint8_t cq_smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Stage& sm = reinterpret_cast<Stage*>(cq_smem)[warp];
+  if (FILL && row_ptr[n] > cols_cap) return;  // the host reports the capacity error
   const GridParams gp = fs->gp;
-  const int32_t q = sorted_idx[k];
-  const float4 xv = sorted_pts[k];
-  const float x[4] = {xv.x, xv.y, xv.z, xv.w};
-  int64_t c[4];
-  cell_of<D>(gp, x, c);
-  if (nshards > 1) {
-    int64_t slab = c[0] * nshards / gp.ncx;
-    slab = slab < 0 ? 0 : slab >= nshards ? nshards - 1 : slab;
-    if (slab != shard) {
-      if (!FILL) counts[q] = 0;
-      return;
-    }
-  }
-  constexpr int stencil = D == 1 ? 3 : D == 2 ? 9 : D == 3 ? 27 : 81;
-  int found = 0;
-  int32_t* out = FILL ? cols + row_ptr[q] : nullptr;
-  for (int code = 0; code < stencil; ++code) {
-    int64_t cc[4];
-    int rem = code;
-    bool inside = true;
+  const uint64_t cmask = (1ull << gp.bits) - 1ull;
+  const uint32_t lt = (1u << lane) - 1u;
+  const int64_t ncell = *n_occ;
+  const int64_t stride = (int64_t)gridDim.x * QW;
+  int64_t ci = (int64_t)blockIdx.x * QW + warp;
+  uint64_t key = ci < ncell ? occ_key[ci] : 0;
+  for (; ci < ncell; ci += stride) {
+    const uint64_t next = ci + stride < ncell ? occ_key[ci + stride] : 0;  // prefetch
+    int64_t c[4];
 #pragma unroll
-    for (int e = 0; e < D; ++e) {
-      cc[e] = c[e] + (rem % 3) - 1;
-      rem /= 3;
-      inside &= cc[e] >= 0 && cc[e] < gp.lim;
-    }
-    if (!inside) continue;
-    const int h = (int)find_slot(keys, T, key_of<D>(gp, cc));
-    if (h < 0) continue;
-    const int b = (int)start[h], e = b + cnt[h];
-    for (int m = b; m < e; ++m) {
-      const int32_t j = sorted_idx[m];
-      const float4 yv = sorted_pts[m];
-      const float y[4] = {yv.x, yv.y, yv.z, yv.w};
-      float s = 0.f;
-#pragma unroll
-      for (int t = 0; t < D; ++t) {
-        const float dv = __fsub_rn(x[t], y[t]);
-        s = __fadd_rn(s, __fmul_rn(dv, dv));
+    for (int e = 0; e < D; ++e) c[e] = (int64_t)((key >> (e * gp.bits)) & cmask);
+    const int total = neighbour_layout<D>(gp, key, c, tab, T, lane, sm.off, sm.st);
+    const int c0 = sm.off[CENTER], m = sm.off[CENTER + 1] - c0;  // the cell's own points
+    if (nshards > 1 && slab_of(gp, c[0], nshards) != shard) {
+      if (!FILL)
+        for (int a = lane; a < m; a += 32) counts[sorted_idx[sm.st[CENTER] + a]] = 0;
+    } else if (total > STAGE_CAP) {  // too many candidates for the staging buffer
+      if (!FILL) {
+        const uint32_t base = lane == 0 ? atomicAdd(n_fb, (uint32_t)m) : 0u;
+        const uint32_t b = __shfl_sync(0xffffffffu, base, 0);
+        for (int a = lane; a < m; a += 32) fb[b + a] = (uint32_t)(sm.st[CENTER] + a);
       }
-      int in = s < gp.rr_lo ? 1 : 0;
-      if (gp.use64 || (!(s < gp.rr_lo) && !(s > gp.rr_hi))) in = within_fp64<D>(x, y, gp.rr) ? 1 : 0;
-      in = (j != q) ? in : 0;
-      if (FILL && in) out[found] = j;
-      found += in;
+    } else {
+      for (int t = lane; t < total; t += 32) {
+        const int64_t src = cand_pos<S>(sm.off, sm.st, t);
+        float4 v = sorted_pts[src];
+        const int32_t jj = sorted_idx[src];
+        if (Stage::PACK) v.w = __int_as_float(jj);
+        else sm.j[t] = jj;
+        sm.p[t] = v;
+      }
+      __syncwarp();
+      if (!FILL) {
+        // count pass: each lane holds one staged candidate and tests it against every point of the
+        // cell; lane a accumulates the count of point a0 + a
+        for (int a0 = 0; a0 < m; a0 += 32) {
+          const int na = m - a0 < 32 ? m - a0 : 32;
+          int acc = 0;
+          for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            const bool live = t < total;
+            const float4 yv = sm.p[live ? t : 0];
+            const float y[4] = {yv.x, yv.y, yv.z, yv.w};
+            const int32_t j = Stage::PACK ? __float_as_int(yv.w) : sm.j[live ? t : 0];
+            for (int a = 0; a < na; ++a) {
+              const float4 xv = sm.p[c0 + a0 + a];
+              const float x[4] = {xv.x, xv.y, xv.z, xv.w};
+              const int32_t q = Stage::PACK ? __float_as_int(xv.w) : sm.j[c0 + a0 + a];
+              const int cnt_a = __popc(__ballot_sync(0xffffffffu, decide<D>(x, y, gp, live && j != q)));
+              acc += lane == a ? cnt_a : 0;
+            }
+          }
+          if (lane < na) {
+            const int32_t q = Stage::PACK ? __float_as_int(sm.p[c0 + a0 + lane].w) : sm.j[c0 + a0 + lane];
+            counts[q] = acc;
+          }
+        }
+      } else {
+      for (int a = 0; a < m; ++a) {
+        const float4 xv = sm.p[c0 + a];
+        const float x[4] = {xv.x, xv.y, xv.z, xv.w};
+        const int32_t q = Stage::PACK ? __float_as_int(xv.w) : sm.j[c0 + a];
+        int found = 0;
+        for (int t0 = 0; t0 < total; t0 += 32) {
+          const int t = t0 + lane;
+          const bool live = t < total;
+          const float4 yv = sm.p[live ? t : 0];
+          const float y[4] = {yv.x, yv.y, yv.z, yv.w};
+          const int32_t j = Stage::PACK ? __float_as_int(yv.w) : sm.j[live ? t : 0];
+          const int in = decide<D>(x, y, gp, live && j != q);
+          const uint32_t mask = __ballot_sync(0xffffffffu, in);
+          if (FILL && in) sm.nb[found + __popc(mask & lt)] = j;
+          found += __popc(mask);
+        }
+        __syncwarp();
+        int32_t* out = cols + row_ptr[q];
+        for (int e = lane; e < found; e += 32) {  // rank among the row's (distinct) entries
+          const int32_t v = sm.nb[e];
+          int r = 0;
+          for (int f = 0; f < found; ++f) r += sm.nb[f] < v ? 1 : 0;
+          out[r] = v;
+        }
+        __syncwarp();
+      }
+      }
+    }
+    __syncwarp();
+    key = next;
+  }
+}
+
+// One warp per point of a crowded cell (listed by the count pass): the warp walks the laid-out
+// candidates 32 at a time straight from global memory.  Count pass: counts[q].  Fill pass: the row
+// is appended unordered, then sorted in place (rank placement through shared memory for rows of up
+// to SORT_CAP entries, else a heap sort by one lane).
+constexpr int PW = 4;          // warps per block
+constexpr int SORT_CAP = 1024;
+
+template <int D>
+struct PointStage {
+  static constexpr int S = D == 1 ? 3 : D == 2 ? 9 : D == 3 ? 27 : 81;
+  int32_t off[S + 1];
+  int32_t st[S];
+  int32_t buf[SORT_CAP];
+};
+
+template <int D, bool FILL>
+__global__ void __launch_bounds__(PW * 32) crowded_query_kernel(
+    const FrnnState* fs, const CellRec* __restrict__ tab, int64_t T, const int32_t* __restrict__ sorted_idx,
+    const float4* __restrict__ sorted_pts, int32_t* __restrict__ counts, const int64_t* __restrict__ row_ptr,
+    int32_t* __restrict__ cols, int64_t n, int64_t cols_cap, const uint32_t* __restrict__ fb,
+    const uint32_t* __restrict__ n_fb) {
+  using Stage = PointStage<D>;
+  constexpr int S = Stage::S;
+  __shared__ Stage stage[PW];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Stage& sm = stage[warp];
+  if (FILL && row_ptr[n] > cols_cap) return;
+  const GridParams gp = fs->gp;
+  const uint32_t lt = (1u << lane) - 1u;
+  const int64_t m = *n_fb;
+  for (int64_t w = (int64_t)blockIdx.x * PW + warp; w < m; w += (int64_t)gridDim.x * PW) {
+    const int64_t k = fb[w];
+    const int32_t q = sorted_idx[k];
+    const float4 xv = sorted_pts[k];
+    const float x[4] = {xv.x, xv.y, xv.z, xv.w};
+    int64_t c[4];
+    cell_of<D>(gp, x, c);
+    const int total = neighbour_layout<D>(gp, key_of<D>(gp, c), c, tab, T, lane, sm.off, sm.st);
+    int32_t* out = FILL ? cols + row_ptr[q] : nullptr;
+    int64_t found = 0;
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const int t = t0 + lane;
+      const bool live = t < total;
+      const int64_t src = live ? cand_pos<S>(sm.off, sm.st, t) : 0;
+      const float4 yv = sorted_pts[src];
+      const float y[4] = {yv.x, yv.y, yv.z, yv.w};
+      const int32_t j = sorted_idx[src];
+      const int in = decide<D>(x, y, gp, live && j != q);
+      const uint32_t mask = __ballot_sync(0xffffffffu, in);
+      if (FILL && in) out[found + __popc(mask & lt)] = j;
+      found += __popc(mask);
+    }
+    if (!FILL) {
+      if (lane == 0) counts[q] = (int32_t)found;
+    } else if (found <= SORT_CAP) {
+      __syncwarp();
+      for (int e = lane; e < found; e += 32) sm.buf[e] = out[e];
+      __syncwarp();
+      for (int e = lane; e < found; e += 32) {
+        const int32_t v = sm.buf[e];
+        int r = 0;
+        for (int f = 0; f < found; ++f) r += sm.buf[f] < v ? 1 : 0;
+        out[r] = v;
+      }
+      __syncwarp();
+    } else {
+      __syncwarp();
+      if (lane == 0) sort_segment(out, found);
+      __syncwarp();
     }
   }
-  if (FILL)
-    sort_segment(out, found);
-  else
-    counts[q] = found;
 }
 
 // ---------------------------------------------------------------- dense path (d > 4)
@@ -344,13 +647,16 @@ int64_t table_size(int64_t n) {
 
 struct GridLayout {
   FrnnState* fs;
-  uint64_t* keys;
-  int32_t* cnt;
-  int64_t* start;
+  CellRec* tab;        // hash table of the occupied cells
   uint32_t *slot_of, *rank_of;
   int32_t* sorted_idx;
   float4* sorted_pts;
   int32_t* counts;
+  uint32_t* counters;  // [0] occupied cells, [1] points of crowded cells
+  uint32_t *occ_slot, *fb;
+  unsigned long long* occ_key;
+  int32_t* occ_cnt;
+  int64_t* occ_start;
   int64_t* tmp;
   int64_t T;
   size_t bytes;
@@ -361,15 +667,19 @@ GridLayout grid_layout(void* ws, int64_t n) {
   Carver c(ws);
   L.T = table_size(n);
   L.fs = c.take<FrnnState>(1);
-  L.keys = c.take<uint64_t>(L.T);
-  L.cnt = c.take<int32_t>(L.T);
-  L.start = c.take<int64_t>(L.T + 1);
+  L.tab = c.take<CellRec>(L.T);
   L.slot_of = c.take<uint32_t>(n);
   L.rank_of = c.take<uint32_t>(n);
   L.sorted_idx = c.take<int32_t>(n);
   L.sorted_pts = c.take<float4>(n);
   L.counts = c.take<int32_t>(n);
-  L.tmp = c.take<int64_t>(scan_temp_elems(L.T > n ? L.T : n));
+  L.counters = c.take<uint32_t>(2);
+  L.occ_slot = c.take<uint32_t>(n);
+  L.occ_key = c.take<unsigned long long>(n);
+  L.fb = c.take<uint32_t>(n);
+  L.occ_cnt = c.take<int32_t>(n);
+  L.occ_start = c.take<int64_t>(n + 1);
+  L.tmp = c.take<int64_t>(scan_temp_elems(n));
   L.bytes = c.bytes();
   return L;
 }
@@ -414,6 +724,18 @@ RadiusLayout radius_layout(void* ws, int64_t n, int64_t d, size_t ws_bytes) {
   return L;
 }
 
+// Empty hash table: every key EMPTY_KEY, every count 0.
+__global__ void tab_clear_kernel(CellRec* __restrict__ tab, int64_t T) {
+  const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (h < T) {
+    CellRec r;
+    r.key = EMPTY_KEY;
+    r.start = 0;
+    r.cnt = 0;
+    tab[h] = r;
+  }
+}
+
 template <int D>
 int grid_path(const float* pts, int64_t n, int64_t ld, double R, int64_t* row_ptr, int32_t* cols,
               int64_t cols_cap, int64_t* n_pairs_out, void* ws, size_t ws_bytes, cudaStream_t st, int shard = 0,
@@ -422,26 +744,58 @@ int grid_path(const float* pts, int64_t n, int64_t ld, double R, int64_t* row_pt
   GridLayout L = grid_layout(ws, n);
   if (ws_bytes < L.bytes)
     return set_error(CPPGB_ERR_CAPACITY, "workspace too small: %zu bytes given, %zu needed", ws_bytes, L.bytes);
+  if (n >= 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "the grid path needs n < 2^31 - 1");
   const unsigned nb = (unsigned)((n + 255) / 256);
-  frnn_init_kernel<<<1, 1, 0, st>>>(L.fs);
+  int dev = 0, sms = 0;
+  CPPGB_CUDA_TRY(cudaGetDevice(&dev));
+  CPPGB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  frnn_init_kernel<<<1, 1, 0, st>>>(L.fs, L.counters);
   CPPGB_LAUNCH_CHECK();
-  CPPGB_CUDA_TRY(cudaMemsetAsync(L.keys, 0xff, sizeof(uint64_t) * L.T, st));
-  CPPGB_CUDA_TRY(cudaMemsetAsync(L.cnt, 0, sizeof(int32_t) * L.T, st));
-  bbox_kernel<<<nb < 1024u ? nb : 1024u, 256, 0, st>>>(pts, n, d, ld, L.fs);
+  tab_clear_kernel<<<(unsigned)((L.T + 255) / 256), 256, 0, st>>>(L.tab, L.T);
+  CPPGB_LAUNCH_CHECK();
+  bbox_kernel<<<nb < (unsigned)(2 * sms) ? nb : (unsigned)(2 * sms), 256, 0, st>>>(pts, n, d, ld, L.fs);
   CPPGB_LAUNCH_CHECK();
   grid_params_kernel<<<1, 1, 0, st>>>(L.fs, d, R);
   CPPGB_LAUNCH_CHECK();
-  hash_insert_kernel<D><<<nb, 256, 0, st>>>(pts, n, ld, L.fs, L.keys, L.T, L.slot_of, L.cnt, L.rank_of);
+  // the grid: cells hashed by key, points grouped by cell (counting sort over the occupied cells)
+  hash_insert_kernel<D><<<nb, 256, 0, st>>>(pts, n, ld, L.fs, L.tab, L.T, L.slot_of, L.rank_of, L.occ_slot,
+                                            L.occ_key, L.counters);
   CPPGB_LAUNCH_CHECK();
-  int rc = launch_exclusive_scan_i32(L.cnt, L.T, L.start, L.tmp, st);
+  occ_count_kernel<<<nb, 256, 0, st>>>(n, L.occ_slot, L.counters, L.tab, L.occ_cnt);
+  CPPGB_LAUNCH_CHECK();
+  int rc = launch_exclusive_scan_i32(L.occ_cnt, n, L.occ_start, L.tmp, st);
   if (rc) return rc;
-  scatter_kernel<<<nb, 256, 0, st>>>(pts, n, ld, L.fs, L.slot_of, L.rank_of, L.start, L.sorted_idx, L.sorted_pts);
+  occ_start_kernel<<<nb, 256, 0, st>>>(n, L.occ_slot, L.counters, L.occ_start, L.tab);
   CPPGB_LAUNCH_CHECK();
-  const unsigned nq = (unsigned)((n + 127) / 128);
-  grid_query_kernel<D, false><<<nq, 128, 0, st>>>((int)n, L.fs, L.keys, L.T, L.cnt, L.start, L.sorted_idx, L.sorted_pts,
-                                                L.counts, nullptr, nullptr, shard, nshards);
+  scatter_kernel<<<nb, 256, 0, st>>>(pts, n, ld, L.fs, L.slot_of, L.rank_of, L.tab, L.sorted_idx, L.sorted_pts);
+  CPPGB_LAUNCH_CHECK();
+  // count pass, scan, fill pass: one warp per occupied cell, one warp per point of a crowded cell
+  const size_t smem = (size_t)QW * sizeof(CellStage<D>);
+  CPPGB_CUDA_TRY(cudaFuncSetAttribute(cell_query_kernel<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+  CPPGB_CUDA_TRY(cudaFuncSetAttribute(cell_query_kernel<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+  int per_sm = 0;
+  CPPGB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_query_kernel<D, true>, QW * 32, smem));
+  const unsigned cgrid = (unsigned)sms * (unsigned)(per_sm > 0 ? per_sm : 1), pgrid = (unsigned)sms * 4u;
+  const uint32_t* n_occ = L.counters;
+  uint32_t* n_fb = L.counters + 1;
+  cell_query_kernel<D, false><<<cgrid, QW * 32, smem, st>>>(L.fs, L.tab, L.T, L.occ_key, n_occ, L.sorted_idx,
+                                                            L.sorted_pts, L.counts, nullptr, nullptr, n, 0, L.fb,
+                                                            n_fb, shard, nshards);
+  CPPGB_LAUNCH_CHECK();
+  crowded_query_kernel<D, false><<<pgrid, PW * 32, 0, st>>>(L.fs, L.tab, L.T, L.sorted_idx, L.sorted_pts, L.counts,
+                                                            nullptr, nullptr, n, 0, L.fb, n_fb);
   CPPGB_LAUNCH_CHECK();
   if ((rc = launch_exclusive_scan_i32(L.counts, n, row_ptr, L.tmp, st))) return rc;
+  // the fill kernels check row_ptr[n] <= cols_cap on the device and write nothing otherwise
+  cell_query_kernel<D, true><<<cgrid, QW * 32, smem, st>>>(L.fs, L.tab, L.T, L.occ_key, n_occ, L.sorted_idx,
+                                                           L.sorted_pts, nullptr, row_ptr, cols, n, cols_cap, L.fb,
+                                                           n_fb, shard, nshards);
+  CPPGB_LAUNCH_CHECK();
+  crowded_query_kernel<D, true><<<pgrid, PW * 32, 0, st>>>(L.fs, L.tab, L.T, L.sorted_idx, L.sorted_pts, nullptr,
+                                                           row_ptr, cols, n, cols_cap, L.fb, n_fb);
+  CPPGB_LAUNCH_CHECK();
   int64_t total = 0;
   unsigned int status = 0;
   CPPGB_CUDA_TRY(cudaMemcpyAsync(&total, row_ptr + n, sizeof total, cudaMemcpyDeviceToHost, st));
@@ -453,12 +807,6 @@ int grid_path(const float* pts, int64_t n, int64_t ld, double R, int64_t* row_pt
   if (total > cols_cap)
     return set_error(CPPGB_ERR_CAPACITY, "cols_cap %lld is smaller than the %lld neighbour entries",
                      (long long)cols_cap, (long long)total);
-  if (total > 0) {
-    grid_query_kernel<D, true><<<nq, 128, 0, st>>>((int)n, L.fs, L.keys, L.T, L.cnt, L.start, L.sorted_idx, L.sorted_pts,
-                                                 nullptr, row_ptr, cols, shard, nshards);
-    CPPGB_LAUNCH_CHECK();
-  }
-  CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
   return CPPGB_OK;
 }
 

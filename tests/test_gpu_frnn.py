@@ -67,6 +67,23 @@ def test_frnn_radius_zero_and_duplicates():
     assert rp[-1] == 11 * 10
 
 
+@pytest.mark.parametrize("d", [2, 3])
+def test_frnn_crowded_cells(d):
+    """Cells whose neighbourhoods hold more candidates than a warp stages (256) take the per-point
+    path; blobs of 256 and 257 points in one cell sit on either side of that limit."""
+    R = 0.01
+    g = synth.rng_for(20 + d)
+    parts = [g.random((2000, d)),                                   # sparse background
+             0.20 + (R / 4) * g.random((600, d)),                   # 600 points in one cell
+             0.50 + (R / 4) * g.random((256, d)),                   # exactly the staging capacity
+             0.80 + (R / 4) * g.random((257, d))]                   # one more
+    x = np.concatenate(parts).astype(np.float32)
+    x = x[g.permutation(x.shape[0])]
+    rp, _ = _check(x, R)
+    deg = np.diff(rp)
+    assert deg.max() >= 599
+
+
 def test_frnn_capacity_reporting():
     capi = _capi()
     dev = device()
