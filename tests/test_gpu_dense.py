@@ -25,13 +25,26 @@ def _capi(mode):
     return capi
 
 
+def filter_error_bound(r):
+    """The largest |d^2 - D~| the filter's error bound allows for a rechecked candidate: with the
+    reported e_acc (Gram arithmetic) and eps (row rounding), d lies in
+    [sqrt(D~ - e_acc) - eps, sqrt(D~ + e_acc) + eps], so |d^2 - D~| <= e_acc + 2 eps sqrt(D~ + e_acc) + eps^2,
+    and a rechecked candidate has D~ <= theta(U) = (sqrt(U) + eps)^2 + e_acc (1 % for the outward pads)."""
+    e, eps, U = r["filter_e_acc"], r["filter_eps"], r["filter_bound"]
+    theta = (math.sqrt(U) + eps) ** 2 + e
+    return 1.01 * (e + 2 * eps * math.sqrt(theta + e) + eps * eps) + 1e-30
+
+
 def check(r, o):
     oi, oj, od2 = o
     assert (r["i"], r["j"]) == (oi, oj), (r, o)
+    assert r["status"] == 0
     if oi >= 0:
         assert r["dist2"] == od2, (r["dist2"], od2)
         assert abs(r["dist"] - math.sqrt(od2)) <= 1e-9 * math.sqrt(od2)
         assert r["n_rechecked"] >= 1
+        # the observed filter error never exceeds what the bound allows
+        assert r["filter_e_acc"] > 0 and r["filter_err"] <= filter_error_bound(r), r
 
 
 # ---------------------------------------------------------------- closest pair
@@ -166,26 +179,26 @@ def test_tsmm_zero_variance_lmer():
     assert e.value.status == capi.ERR_NUMERIC
 
 
-def test_tsmm_full_size_sampled():
-    """The 262,144-sample random walk, l = 512, excl = 256, in every mode.
-
-    The oracle cannot brute-force 3.4e10 pairs here, so the result is checked where it can be
-    computed one by one: the reported pair's FP64 distance, the best partner of each of its two
-    rows (which must be each other), and the best partners of 16 sampled rows, none of which may
-    beat the reported pair.  All modes must agree exactly.
-    """
+def test_tsmm_full_size(golden_dir):
+    """The 262,144-sample random walk, l = 512, excl = 256, in every mode, against the oracle's
+    answer for the whole search (3.4e10 pairs; tests/golden/tsmm_rw262144_l512_excl256.json,
+    written by tests/golden/make_golden.py), plus the checks the oracle can make one by one: the
+    reported pair's FP64 distance and the best partners of its two rows and of 16 sampled rows."""
+    import json
+    import os
     from paper_1407_5609_gb300 import capi
     dev = device()
     N, l, excl = 262144, 512, 256
     a = synth.make_random_walk(N)
     s = to_dev(a, dev)
-    modes = ["plain_fp32"] + (["filter_fp16", "filter_bf16"] if capi.filters_available() else [])
-    res = [capi.tsmm_motif(s, l, excl, mode=m) for m in modes]
-    r = res[0]
-    for q in res[1:]:
-        assert (q["i"], q["j"], q["dist2"]) == (r["i"], r["j"], r["dist2"])
-    i, j, d2 = r["i"], r["j"], r["dist2"]
-    assert j - i >= excl
+    with open(os.path.join(golden_dir, "tsmm_rw262144_l512_excl256.json")) as f:
+        g = json.load(f)
+    gold = (g["i"], g["j"], float.fromhex(g["dist2"]))
+    modes = ["plain_fp32"] + (["filter_fp16", "filter_bf16", "filter_bf16_prune"] if capi.filters_available() else [])
+    for m in modes:
+        r = capi.tsmm_motif(s, l, excl, mode=m)
+        check(r, gold)
+    i, j, d2 = gold
     assert oracle.tsmm_pairs(a, l, [i], [j])[0] == d2
     rows = np.concatenate([[i, j], synth.rng_for(32).integers(0, N - l + 1, 16)])
     bj, bd = oracle.tsmm_rows(a, l, excl, rows)
