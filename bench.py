@@ -380,6 +380,7 @@ class Batch:
         self.no_tune = args.no_tune
         self.path = args.batch_path
         self.batch = synth.make_batch(count=args.batch_count)
+        self.pairs_in_step = 0
         self.units = sum(b.pts.shape[0] * (b.pts.shape[0] - 1) // 2 for b in self.batch)
         self.flop_per_unit = None
         self.flops = sum(b.pts.shape[0] * (b.pts.shape[0] - 1) // 2 * 2 * b.pts.shape[1] for b in self.batch)
@@ -436,7 +437,8 @@ class Batch:
         for hp, dp in zip(host, dev_buf):
             dp.copy_(hp, non_blocking=True)
         res, counts, pairs = capi.cpp_batch(dev_buf, self.radii, ws=self.ws, pairs=self.pairs, paths=self.path)
-        pairs[:int(counts.sum())].cpu()
+        self.pairs_in_step = int(counts.sum())
+        pairs[:self.pairs_in_step].cpu()
         return {"instances": len(res)}
 
     def host_input(self):
@@ -482,17 +484,18 @@ def recorded_traffic(key):
 
 
 def d2h_bytes(wl, capi):
-    """Bytes a step reads back to the host through the public API."""
+    """Bytes a step reads back to the host through the public API (the result structs, and the
+    FRNN column list or the batch's pair list)."""
     if wl.name in ("tsmm", "cpp"):
-        return 128                                      # the 64-byte scalar block, read twice
+        return ctypes.sizeof(capi.cpp_pair_result)
     if wl.name == "frnn":
-        return 4 * (wl.nnz or 0) + 16                   # the column list plus two status words
+        return 4 * (wl.nnz or 0) + ctypes.sizeof(capi.frnn_result)
     if wl.name == "batch":
-        return len(wl.batch) * (64 + 8) + 24            # per-instance results and pair offsets
+        return len(wl.batch) * (ctypes.sizeof(capi.cpp_pair_result) + 8) + 8 * int(wl.pairs_in_step or 0)
     if wl.name == "hamming":
-        return 32 + 4                                   # the best partial and the status word
+        return ctypes.sizeof(capi.hamming_result)
     if wl.name == "mlba":
-        return 32 + 4                                   # the result block and the status word
+        return ctypes.sizeof(capi.mlba_result)
     return ctypes.sizeof(capi.twolocus_result)
 
 
@@ -604,7 +607,7 @@ def same_as_golden(wl, capi, mode):
     return None
 
 
-def roofline_of(wl, capi, mode, pk, dense_ms, stages, total_ms, steps):
+def roofline_of(wl, capi, mode, pk, dense_ms, stages, total_ms, steps, res=None):
     """The dominant kernel's roofline record for the workload, plus workload-specific extras."""
     extra = {}
     if wl.name in ("tsmm", "cpp"):
@@ -615,8 +618,8 @@ def roofline_of(wl, capi, mode, pk, dense_ms, stages, total_ms, steps):
             extra["alu_peak_microbenchmark"] = alu_peaks(capi)
         else:
             peak, bound, unit, src = pk["bf16_tflops"], "tensor", "TFLOP/s", f"{pk['source']} bf16 burst"
-        if mode.endswith("_prune"):  # only the kept tiles are evaluated
-            kept, total = capi.cpp_prune_stats()
+        if mode.endswith("_prune") and res:  # only the kept tiles are evaluated
+            kept, total = res.get("tiles_kept", -1), res.get("tiles_total", -1)
             if total > 0:
                 flops = flops * kept / total
         ach = flops / (avg_ms / 1e3) / 1e12 if avg_ms else None
@@ -739,7 +742,7 @@ def measure(wl, capi, args, mode, dev, stream, flush, barrier, steps, warmup, ra
         rec["candidates_per_step"] = res["candidates"]
 
     pk = peaks()
-    rec["roofline"], extra = roofline_of(wl, capi, mode, pk, dense_ms, stages, total_ms, steps)
+    rec["roofline"], extra = roofline_of(wl, capi, mode, pk, dense_ms, stages, total_ms, steps, res)
     rec.update(extra)
     rec["clocks"] = clk
 
@@ -797,7 +800,7 @@ def compare(wl, capi, args, mode, res, stream, flush, barrier, steps, pk, dev):
             return r
         pms, pres = timed_steps(pruned, psteps, stream, torch, flush)
         capi.cpp_set_stage_timing(False)
-        kept, total = capi.cpp_prune_stats()
+        kept, total = pres["tiles_kept"], pres["tiles_total"]
         sec = pms / psteps / 1e3
         out["pruned"] = {"mode": pmode, "ms_per_step": pms / psteps,
                          "dense_stage_ms": statistics.mean(dense) if dense else None,

@@ -15,10 +15,19 @@
  *     bytes, 256-byte aligned.  The library allocates nothing on these paths.  For the dense
  *     searches (cpp_closest_pair, tsmm_motif) any workspace beyond that size enlarges the
  *     candidate buffer of the filter stage.
- *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Each call enqueues its
- *     kernels on `stream` and waits for that stream before returning, so the results are
- *     valid on return.  Calls on one stream are serialised; a workspace must not be shared
- *     by calls that may run at the same time.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are asynchronous:
+ *     each enqueues its kernels on `stream` and returns; the result struct is written to the
+ *     caller's host memory by a copy on the same stream and is valid after the stream has been
+ *     synchronised (pass pinned host memory for the call to return before the work is done;
+ *     with pageable memory the copy itself waits).  Exceptions, which wait for the stream before
+ *     returning: twolocus_scan_noalloc, mlba_pair, cpp_gram_tile_dump, cpp_measure_alu_peaks.
+ *     Calls on one stream are serialised; a workspace must not be shared by calls that may run
+ *     at the same time, and the inputs, workspace and result memory must stay valid until the
+ *     stream reaches the call's end.
+ *   - Errors found before any work is enqueued (arguments, workspace size, launch failures)
+ *     are the return value.  Errors that only the device can see (a non-finite input, a
+ *     timed-out wait, more candidates or pairs than the buffers hold) are reported in the
+ *     result's `status` field (CPPGB_OK otherwise), valid after the stream sync.
  *   - Indices are 0-based (the paper counts from 1).  Pairs are reported with i < j.
  *   - Ties are broken towards the lexicographically smallest (i, j).
  *   - Return value: CPPGB_OK or one of the error codes below; cpp_last_error() then
@@ -63,10 +72,18 @@ typedef struct {
   int64_t i, j;          /* the pair, i < j; both -1 when no pair is valid */
   double dist;           /* FP64 Euclidean distance of the pair (Sec. 2) */
   double dist2;          /* its square, summed in coordinate order in FP64 */
-  double filter_err;     /* max |dist2_fp64 - dist2_filter| over the rechecked candidates */
-  double filter_bound;   /* final upper bound on dist2 reached by the dense stage */
-  int64_t n_emitted;     /* candidate pairs the dense stage emitted */
+  double filter_err;     /* max |dist2_fp64 - D~| over the rechecked candidates (D~: the filter's value) */
+  double filter_bound;   /* final upper bound U on dist2 reached by the dense stage */
+  int64_t n_emitted;     /* candidate pairs the dense stage emitted (on CPPGB_ERR_CAPACITY: the number
+                            a workspace would have to hold, 28 bytes each) */
   int64_t n_rechecked;   /* candidates whose lower bound met the final upper bound (FP64-rechecked) */
+  double filter_e_acc;   /* e_acc: bound on |D~ - |x~_i - x~_j|^2| from the Gram arithmetic (x~: stored rows) */
+  double filter_eps;     /* eps_pair: bound on | |x_i - x_j| - |x~_i - x~_j| | from the rows' rounding, so
+                            |dist2 - D~| <= e_acc + 2 eps sqrt(D~ + e_acc) + eps^2 for every rechecked pair */
+  int64_t tiles_kept;    /* CPPGB_MODE_PRUNE: tiles of the dense stage evaluated; -1 otherwise */
+  int64_t tiles_total;   /* CPPGB_MODE_PRUNE: tiles of the schedule; -1 otherwise */
+  int32_t status;        /* CPPGB_OK, or the error the device found (valid after the stream sync) */
+  int32_t reserved;
 } cpp_pair_result;
 
 /*
@@ -75,11 +92,13 @@ typedef struct {
  *   pts    device, row-major [n][ld] of `dtype` (CPPGB_F32 or CPPGB_F64); d <= ld.
  *   n      number of points (0 and 1 give i = j = -1).   d in [1, 4096].
  *   mode   CPPGB_MODE_*.
- *   out    host; filled on CPPGB_OK.
- * Errors: CPPGB_ERR_ARG (sizes, null pointers, mode), CPPGB_ERR_CAPACITY (ws too small, or more
- *         candidate pairs tie within the filter's error bound than the workspace holds: then
- *         out->n_emitted holds the number needed, 24 bytes each), CPPGB_ERR_NUMERIC (non-finite
- *         coordinates), CPPGB_ERR_CUDA.
+ *   out    host (pinned for an asynchronous call); valid after the stream sync.
+ * Errors (return value): CPPGB_ERR_ARG (sizes, null pointers, mode), CPPGB_ERR_CAPACITY (ws too
+ *         small), CPPGB_ERR_CUDA.
+ * Errors (out->status): CPPGB_ERR_CAPACITY (more candidate pairs tie within the filter's error
+ *         bound than the workspace holds: out->n_emitted holds the number needed, 28 bytes each),
+ *         CPPGB_ERR_NUMERIC (non-finite coordinates), CPPGB_ERR_TIMEOUT (a bounded wait of the
+ *         tensor-core stage gave up).
  */
 size_t cpp_closest_pair_workspace_size(int64_t n, int64_t d, int mode);
 int cpp_closest_pair(const void* pts, int dtype, int64_t n, int64_t d, int64_t ld, int mode,
@@ -92,8 +111,8 @@ int cpp_closest_pair(const void* pts, int dtype, int64_t n, int64_t d, int64_t l
  * is eligible when j - i >= excl (trivial-match exclusion).
  *   series device FP32 [N].   l in [2, 4096], N >= l.   excl >= 1.
  *   out    host; dist2 is the FP64 squared distance of the z-normalised l-mers.
- * Errors: CPPGB_ERR_ARG, CPPGB_ERR_CAPACITY (as for cpp_closest_pair), CPPGB_ERR_NUMERIC (an
- *         l-mer of zero variance or a non-finite sample), CPPGB_ERR_CUDA.
+ * Errors as for cpp_closest_pair; out->status = CPPGB_ERR_NUMERIC also for an l-mer of zero
+ *         variance.
  */
 size_t tsmm_motif_workspace_size(int64_t N, int64_t l, int mode);
 int tsmm_motif(const float* series, int64_t N, int64_t l, int64_t excl, int mode,
@@ -120,6 +139,8 @@ typedef struct {
   int32_t countsA[9];  /* cases: countsA[3a+b] = #subjects with g_i = a, g_j = b */
   int32_t countsB[9];  /* controls, same layout */
   double score_real;   /* the score as a real number: |P_A - P_B| (matches), |r_A - r_B| (Pearson) */
+  int32_t status;      /* CPPGB_OK, or the error the device found (valid after the stream sync) */
+  int32_t reserved;
 } twolocus_result;
 
 /*
@@ -146,9 +167,11 @@ int twolocus_scan(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases,
  * device.  Its scratch is a fixed 1 MiB array inside the library, so S is limited to 23,104 SNPs
  * (larger S returns CPPGB_ERR_CAPACITY with a message); every device that loads the library keeps
  * that 1 MiB until the process exits.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call outside any stream capture.  All calls on a
- * device share the array: calls whose work may overlap on the GPU (other streams, other host
- * threads) race and must be serialised by the caller.  Planes and out are as for twolocus_scan.
+ * address (cudaGetSymbolAddress); make that first call outside any stream capture.  Every call
+ * waits for the stream before it returns (it reads the result back through the shared array), so
+ * no call may be made while the stream is being captured.  All calls on a device share the array:
+ * calls whose work may overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Planes and out are as for twolocus_scan; out is valid on return.
  */
 int twolocus_scan_noalloc(const uint64_t* planes, int64_t S, int64_t W, int64_t m_cases, int64_t m_controls,
                           twolocus_result* out, void* stream);
@@ -177,7 +200,8 @@ int twolocus_scan_shard(const uint64_t* planes, int64_t S, int64_t W, int64_t m_
  * tensor-core accumulation is exact.  Arguments as for twolocus_scan (W <= 4096, groups < 2^20
  * subjects); the workspace holds the four FP8 matrices, 4 S W 128 bytes (128 MB at 4096 SNPs x
  * 4096 + 4096 subjects).
- * Errors: CPPGB_ERR_ARG, CPPGB_ERR_CAPACITY (ws), CPPGB_ERR_TIMEOUT, CPPGB_ERR_CUDA.
+ * Errors (return value): CPPGB_ERR_ARG, CPPGB_ERR_CAPACITY (ws), CPPGB_ERR_CUDA; (out->status):
+ * CPPGB_ERR_TIMEOUT.
  */
 #define CPPGB_TL_MATCHES 0
 #define CPPGB_TL_PEARSON 1
@@ -196,6 +220,8 @@ int twolocus_scan_tc_shard(const uint64_t* planes, int64_t S, int64_t W, int64_t
 typedef struct {
   int64_t i, j;        /* the pair, i < j; -1 when n < 2 */
   int64_t mismatches;  /* its Hamming distance */
+  int32_t status;      /* CPPGB_OK, or the error the device found (valid after the stream sync) */
+  int32_t reserved;
 } hamming_result;
 
 /*
@@ -205,8 +231,8 @@ typedef struct {
  * of t sigma entries (the mapping of Sec. 5.5, one 1 per position); the dot product of two rows,
  * accumulated exactly in FP32 on the tensor cores, is the number of agreeing positions.
  *   strs  device uint8 [n][ld], ld >= t.   2 <= sigma <= 256, t <= 2^23.
- * Errors: CPPGB_ERR_ARG (also for a symbol >= sigma), CPPGB_ERR_CAPACITY (ws), CPPGB_ERR_TIMEOUT,
- * CPPGB_ERR_CUDA.
+ * Errors (return value): CPPGB_ERR_ARG, CPPGB_ERR_CAPACITY (ws), CPPGB_ERR_CUDA; (out->status):
+ * CPPGB_ERR_ARG for a symbol >= sigma, CPPGB_ERR_TIMEOUT.
  */
 size_t hamming_pair_workspace_size(int64_t n, int64_t t, int sigma);
 int hamming_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, int least, hamming_result* out,
@@ -222,6 +248,8 @@ typedef struct {
   int64_t i, j;        /* the best candidate pair, i < j; -1 when no pair shared a bucket */
   int64_t mismatches;  /* its Hamming distance; -1 when there is no candidate */
   int64_t candidates;  /* candidate pairs verified, each counted once per iteration it was found in */
+  int32_t status;      /* CPPGB_OK, or the error the device found */
+  int32_t reserved;
 } mlba_result;
 
 /*
@@ -254,6 +282,13 @@ size_t mlba_pair_workspace_size(int64_t n, int64_t t, int sigma, int least, int6
 int mlba_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, int least, const int32_t* cols,
               int64_t iters, int64_t L, mlba_result* out, void* ws, size_t ws_bytes, void* stream);
 
+/* Result of a fixed-radius query. */
+typedef struct {
+  int64_t n_pairs;     /* directed pairs (= row_ptr[n]), also when cols_cap was too small */
+  int32_t status;      /* CPPGB_OK, or the error the device found (valid after the stream sync) */
+  int32_t reserved;
+} frnn_result;
+
 /*
  * frnn_query -- fixed-radius near neighbours (Sec. 3.5): for every point p_i its R-neighbourhood
  * N(i) = { j != i : d(p_i, p_j) <= R }, with j in N(i) iff i in N(j).  The decision is the FP64
@@ -263,12 +298,15 @@ int mlba_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, 
  *   R        radius, finite and >= 0.
  *   row_ptr  device int64 [n+1], CSR offsets (written).
  *   cols     device int32 [cols_cap], neighbour indices ascending within each row (written).
- *   n_pairs_out host; the number of directed pairs (= row_ptr[n]) -- set also when cols_cap is
- *            too small, in which case CPPGB_ERR_CAPACITY is returned and cols is untouched.
+ *   out      host (pinned for an asynchronous call); valid after the stream sync.
+ * Errors (return value): CPPGB_ERR_ARG, CPPGB_ERR_CAPACITY (ws), CPPGB_ERR_CUDA.
+ * Errors (out->status): CPPGB_ERR_CAPACITY (cols_cap < out->n_pairs; cols is then untouched, or,
+ *         on the high-d path, more candidate pairs than the workspace holds), CPPGB_ERR_NUMERIC
+ *         (a non-finite coordinate).
  */
 size_t frnn_query_workspace_size(int64_t n, int d);
 int frnn_query(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t* row_ptr, int32_t* cols,
-               int64_t cols_cap, int64_t* n_pairs_out, void* ws, size_t ws_bytes, void* stream);
+               int64_t cols_cap, frnn_result* out, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * frnn_query_shard -- shard s of nshards of frnn_query on the grid path (1 <= d <= 4): the points
@@ -280,7 +318,7 @@ int frnn_query(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t
  * errors as for frnn_query; CPPGB_ERR_ARG for d > 4 or a bad shard.
  */
 int frnn_query_shard(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t shard, int64_t nshards,
-                     int64_t* row_ptr, int32_t* cols, int64_t cols_cap, int64_t* n_pairs_out, void* ws,
+                     int64_t* row_ptr, int32_t* cols, int64_t cols_cap, frnn_result* out, void* ws,
                      size_t ws_bytes, void* stream);
 
 /* One instance of a batch. */
@@ -300,10 +338,15 @@ typedef struct {
  * kernel (BF16 rows padded to 64, 128, 192 or 256 columns, one tensor map per width); both feed
  * the same FP32 second pass and FP64 recheck, so the answer does not depend on the path.
  *   inst        host array [count].
- *   out_cpp     host [count]: closest pair of each instance (identical to cpp_closest_pair).
- *   pair_counts host int64 [count]: number of undirected pairs (i < j) with d <= R per instance.
+ *   out_cpp     host [count]: closest pair of each instance (identical to cpp_closest_pair; the
+ *               prune fields are -1); valid after the stream sync.
+ *   pair_counts host int64 [count]: number of undirected pairs (i < j) with d <= R per instance;
+ *               valid after the stream sync.
  *   pairs       device int32 [pairs_cap][2]: the (i, j) pairs, instance after instance, ascending (i, j).
- * Errors: CPPGB_ERR_ARG, CPPGB_ERR_CAPACITY (pairs_cap or ws too small), CPPGB_ERR_CUDA.
+ * Errors (return value): CPPGB_ERR_ARG, CPPGB_ERR_CAPACITY (ws), CPPGB_ERR_CUDA.
+ * Errors (status of every out_cpp entry): CPPGB_ERR_CAPACITY (pairs_cap smaller than the pairs
+ *         within R -- pair_counts still holds the counts -- or more candidate pairs than the
+ *         workspace holds), CPPGB_ERR_NUMERIC, CPPGB_ERR_TIMEOUT.
  */
 size_t cpp_batch_workspace_size(const cpp_instance* inst, int64_t count);
 int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp, int64_t* pair_counts,
@@ -312,8 +355,8 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
 /*
  * Diagnostics (no counterpart in the paper; used to measure the library).
  * cpp_set_stage_timing(1) makes the dense searches record CUDA events on their stream around
- * their stages; cpp_stage_times() then copies the last call's stage durations in milliseconds
- * (per calling thread) into ms[0..cap) and returns how many it wrote: [prep, dense all-pairs stage,
+ * their stages; cpp_stage_times() then waits for the last call's events and copies its stage
+ * durations in milliseconds (per calling thread) into ms[0..cap) and returns how many it wrote: [prep, dense all-pairs stage,
  * FP64 recheck] after cpp_closest_pair / tsmm_motif, [preparation, tensor-core tiles, FP32 tiles,
  * second pass + recheck + output] after cpp_batch (events captured in its graph), [pack + keys,
  * radix sort, buckets + pair offsets, verification] after mlba_pair.  cpp_launch_count() returns the number of kernels this library has launched
@@ -327,9 +370,6 @@ void cpp_set_stage_timing(int on);
 int cpp_measure_alu_peaks(double* ffma_tflops, double* popc_tops);
 int cpp_stage_times(double* ms, int cap);
 int64_t cpp_launch_count(void);
-/* Tiles the last pruned dense search on the calling thread evaluated, of all its tiles (-1, -1
- * when the last search did not prune). */
-int cpp_prune_stats(int64_t* tiles_kept, int64_t* tiles_total);
 
 /* 1 when this build carries the tensor-core filter modes (CPPGB_MODE_FILTER_*), else 0. */
 int cpp_filter_available(void);

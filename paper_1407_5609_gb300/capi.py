@@ -3,13 +3,16 @@
 Every function here has the name of the C entry point it calls.  Tensors must already live on
 the current CUDA device; the binding passes their raw pointers, sizes a workspace with the
 matching ``*_workspace_size`` query (allocated through torch), passes the current torch stream,
-and turns a non-OK status into :class:`CppgbError`.  All computation happens in the library's
-CUDA kernels; if ``libcppgb.so`` is missing the import fails loudly (there is no fallback).
+and turns a non-OK status into :class:`CppgbError`.  The C calls are asynchronous: the result
+structs live in pinned host memory, and the binding synchronises the stream before it reads them
+(and their ``status`` field, where the device reports its errors).  All computation happens in the
+library's CUDA kernels; if ``libcppgb.so`` is missing the import fails loudly (there is no fallback).
 """
 from __future__ import annotations
 
 import ctypes
 import os
+import threading
 
 import numpy as np
 import torch
@@ -33,35 +36,44 @@ class CppgbError(RuntimeError):
 class cpp_pair_result(ctypes.Structure):
     _fields_ = [("i", ctypes.c_int64), ("j", ctypes.c_int64), ("dist", ctypes.c_double),
                 ("dist2", ctypes.c_double), ("filter_err", ctypes.c_double), ("filter_bound", ctypes.c_double),
-                ("n_emitted", ctypes.c_int64), ("n_rechecked", ctypes.c_int64)]
+                ("n_emitted", ctypes.c_int64), ("n_rechecked", ctypes.c_int64), ("filter_e_acc", ctypes.c_double),
+                ("filter_eps", ctypes.c_double), ("tiles_kept", ctypes.c_int64), ("tiles_total", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class twolocus_result(ctypes.Structure):
     _fields_ = [("i", ctypes.c_int64), ("j", ctypes.c_int64), ("score", ctypes.c_int64),
-                ("countsA", ctypes.c_int32 * 9), ("countsB", ctypes.c_int32 * 9), ("score_real", ctypes.c_double)]
+                ("countsA", ctypes.c_int32 * 9), ("countsB", ctypes.c_int32 * 9), ("score_real", ctypes.c_double),
+                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {"i": self.i, "j": self.j, "score": self.score, "score_real": self.score_real,
                 "countsA": np.array(list(self.countsA), dtype=np.int32),
-                "countsB": np.array(list(self.countsB), dtype=np.int32)}
+                "countsB": np.array(list(self.countsB), dtype=np.int32), "status": self.status}
 
 
 class hamming_result(ctypes.Structure):
-    _fields_ = [("i", ctypes.c_int64), ("j", ctypes.c_int64), ("mismatches", ctypes.c_int64)]
+    _fields_ = [("i", ctypes.c_int64), ("j", ctypes.c_int64), ("mismatches", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
-        return {"i": self.i, "j": self.j, "mismatches": self.mismatches}
+        return {"i": self.i, "j": self.j, "mismatches": self.mismatches, "status": self.status}
 
 
 class mlba_result(ctypes.Structure):
     _fields_ = [("i", ctypes.c_int64), ("j", ctypes.c_int64), ("mismatches", ctypes.c_int64),
-                ("candidates", ctypes.c_int64)]
+                ("candidates", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
-        return {"i": self.i, "j": self.j, "mismatches": self.mismatches, "candidates": self.candidates}
+        return {"i": self.i, "j": self.j, "mismatches": self.mismatches, "candidates": self.candidates,
+                "status": self.status}
+
+
+class frnn_result(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class cpp_instance(ctypes.Structure):
@@ -99,17 +111,16 @@ SIGNATURES = {
     "twolocus_scan_shard": (_int, [_vp, _i64, _i64, _i64, _i64, _i64, _i64, ctypes.POINTER(twolocus_result), _vp,
                                     _sz, _vp]),
     "frnn_query_workspace_size": (_sz, [_i64, _int]),
-    "frnn_query": (_int, [_vp, _i64, _int, _i64, ctypes.c_double, _vp, _vp, _i64, ctypes.POINTER(_i64), _vp, _sz,
-                          _vp]),
+    "frnn_query": (_int, [_vp, _i64, _int, _i64, ctypes.c_double, _vp, _vp, _i64, ctypes.POINTER(frnn_result), _vp,
+                          _sz, _vp]),
     "frnn_query_shard": (_int, [_vp, _i64, _int, _i64, ctypes.c_double, _i64, _i64, _vp, _vp, _i64,
-                                ctypes.POINTER(_i64), _vp, _sz, _vp]),
+                                ctypes.POINTER(frnn_result), _vp, _sz, _vp]),
     "cpp_batch_workspace_size": (_sz, [ctypes.POINTER(cpp_instance), _i64]),
     "cpp_batch": (_int, [ctypes.POINTER(cpp_instance), _i64, ctypes.POINTER(cpp_pair_result), ctypes.POINTER(_i64),
                          _vp, _i64, _vp, _sz, _vp]),
     "cpp_set_stage_timing": (None, [_int]),
     "cpp_stage_times": (_int, [ctypes.POINTER(ctypes.c_double), _int]),
     "cpp_launch_count": (_i64, []),
-    "cpp_prune_stats": (_int, [ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "cpp_filter_available": (_int, []),
     "cpp_gram_tile_dump": (_int, [_vp, _int, _i64, _i64, _i64, _int, ctypes.POINTER(ctypes.c_int32), _i64, _vp, _vp,
                                    _vp, _sz, _vp]),
@@ -146,9 +157,49 @@ def _raise(status: int):
         raise CppgbError(status, lib().cpp_last_error().decode(errors="replace"))
 
 
+_DEVICE_ERRORS = {ERR_CAPACITY: "the result does not fit the buffers (candidate pairs or output capacity)",
+                  ERR_TIMEOUT: "a bounded wait of a tensor-core kernel gave up",
+                  ERR_NUMERIC: "a non-finite input value or an l-mer of zero variance",
+                  ERR_ARG: "an input value out of range (a symbol >= sigma or a column out of range)",
+                  ERR_CUDA: "an internal table overflowed"}
+
+
+def _raise_status(status: int):
+    """An error the device reported in a result's status field."""
+    if status != OK:
+        raise CppgbError(status, _DEVICE_ERRORS.get(status, "device error"))
+
+
+def _stream_obj(stream=None):
+    return stream if stream is not None else torch.cuda.current_stream()
+
+
 def _stream(stream=None) -> int:
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return int(s.cuda_stream)
+    return int(_stream_obj(stream).cuda_stream)
+
+
+def _sync(stream=None):
+    _stream_obj(stream).synchronize()
+
+
+_pinned_tls = threading.local()
+
+
+def _pinned(ctype, count: int | None = None):
+    """A result struct (count None) or an array of count of them in pinned host memory, reused per
+    thread and type; the asynchronous copy of the C call lands there, so read it only after the
+    stream sync."""
+    cache = getattr(_pinned_tls, "cache", None)
+    if cache is None:
+        cache = _pinned_tls.cache = {}
+    size = ctypes.sizeof(ctype) * (1 if count is None else max(int(count), 1))
+    buf = cache.get(ctype)
+    if buf is None or buf.numel() < size:
+        buf = torch.empty(max(size, 64), dtype=torch.uint8).pin_memory()
+        cache[ctype] = buf
+    if count is None:
+        return ctype.from_address(buf.data_ptr())
+    return (ctype * max(int(count), 1)).from_address(buf.data_ptr())
 
 
 def _workspace(nbytes: int, device) -> torch.Tensor:
@@ -211,13 +262,6 @@ def cpp_launch_count() -> int:
     return int(lib().cpp_launch_count())
 
 
-def cpp_prune_stats() -> tuple:
-    """(tiles kept, tiles in all) of the last pruned search on this thread; (-1, -1) if none."""
-    kept, total = _i64(0), _i64(0)
-    _raise(lib().cpp_prune_stats(ctypes.byref(kept), ctypes.byref(total)))
-    return kept.value, total.value
-
-
 def cpp_gram_tile_dump(pts: torch.Tensor, tiles, mode="filter_bf16", stream=None):
     """Raw tensor-core Gram values of chosen filter-stage tiles (diagnostics, include/cppgb.h).
 
@@ -242,6 +286,19 @@ def cpp_gram_tile_dump(pts: torch.Tensor, tiles, mode="filter_bf16", stream=None
     return S, rows
 
 
+def _dense_call(call, ws, need, out, device, stream):
+    """Run a dense search, wait for its stream, and check its status.  A search whose candidates
+    overflowed the workspace (many exact ties within the filter's error) is run once more with room
+    for all of them (28 bytes each)."""
+    _raise(call(ws))
+    _sync(stream)
+    if out.status == ERR_CAPACITY and out.n_emitted > 0:
+        _raise(call(_workspace(need + 28 * int(out.n_emitted * 1.05) + 8192, device)))
+        _sync(stream)
+    _raise_status(out.status)
+    return out.as_dict()
+
+
 def cpp_closest_pair_workspace_size(n: int, d: int, mode="plain_fp32") -> int:
     return int(lib().cpp_closest_pair_workspace_size(n, d, _mode(mode)))
 
@@ -257,14 +314,10 @@ def cpp_closest_pair(pts: torch.Tensor, mode="plain_fp32", ws: torch.Tensor | No
     need = cpp_closest_pair_workspace_size(n, d, m)
     if ws is None:
         ws = _workspace(need, pts.device)
-    out = cpp_pair_result()
+    out = _pinned(cpp_pair_result)
     call = lambda w: lib().cpp_closest_pair(pts.data_ptr() if n else None, dtype, n, d, pts.stride(0) if n else d,
                                             m, ctypes.byref(out), w.data_ptr(), w.numel(), _stream(stream))
-    st = call(ws)
-    if st == ERR_CAPACITY and out.n_emitted > 0:   # many exact ties: retry once with room for all candidates
-        st = call(_workspace(need + 24 * int(out.n_emitted * 1.05) + 4096, pts.device))
-    _raise(st)
-    return out.as_dict()
+    return _dense_call(call, ws, need, out, pts.device, stream)
 
 
 def tsmm_motif_workspace_size(N: int, l: int, mode="plain_fp32") -> int:
@@ -281,15 +334,10 @@ def tsmm_motif(series: torch.Tensor, l: int, excl: int, mode="plain_fp32", ws: t
     m = _mode(mode)
     if ws is None:
         ws = _workspace(tsmm_motif_workspace_size(N, l, m), series.device)
-    out = cpp_pair_result()
+    out = _pinned(cpp_pair_result)
     call = lambda w: lib().tsmm_motif(series.data_ptr(), N, l, excl, m, ctypes.byref(out), w.data_ptr(), w.numel(),
                                       _stream(stream))
-    st = call(ws)
-    if st == ERR_CAPACITY and out.n_emitted > 0:   # many exact ties: retry once with room for all candidates
-        need = tsmm_motif_workspace_size(N, l, m)
-        st = call(_workspace(need + 24 * int(out.n_emitted * 1.05) + 4096, series.device))
-    _raise(st)
-    return out.as_dict()
+    return _dense_call(call, ws, tsmm_motif_workspace_size(N, l, m), out, series.device, stream)
 
 
 def cpp_closest_pair_shard(pts: torch.Tensor, shard: int, nshards: int, mode="plain_fp32",
@@ -303,11 +351,11 @@ def cpp_closest_pair_shard(pts: torch.Tensor, shard: int, nshards: int, mode="pl
     m = _mode(mode)
     if ws is None:
         ws = _workspace(cpp_closest_pair_workspace_size(n, d, m), pts.device)
-    out = cpp_pair_result()
-    _raise(lib().cpp_closest_pair_shard(pts.data_ptr() if n else None, dtype, n, d, pts.stride(0) if n else d, m,
-                                        shard, nshards, ctypes.byref(out), ws.data_ptr(), ws.numel(),
-                                        _stream(stream)))
-    return out.as_dict()
+    out = _pinned(cpp_pair_result)
+    call = lambda w: lib().cpp_closest_pair_shard(pts.data_ptr() if n else None, dtype, n, d,
+                                                  pts.stride(0) if n else d, m, shard, nshards, ctypes.byref(out),
+                                                  w.data_ptr(), w.numel(), _stream(stream))
+    return _dense_call(call, ws, cpp_closest_pair_workspace_size(n, d, m), out, pts.device, stream)
 
 
 def tsmm_motif_shard(series: torch.Tensor, l: int, excl: int, shard: int, nshards: int, mode="plain_fp32",
@@ -320,10 +368,10 @@ def tsmm_motif_shard(series: torch.Tensor, l: int, excl: int, shard: int, nshard
     m = _mode(mode)
     if ws is None:
         ws = _workspace(tsmm_motif_workspace_size(N, l, m), series.device)
-    out = cpp_pair_result()
-    _raise(lib().tsmm_motif_shard(series.data_ptr(), N, l, excl, m, shard, nshards, ctypes.byref(out),
-                                  ws.data_ptr(), ws.numel(), _stream(stream)))
-    return out.as_dict()
+    out = _pinned(cpp_pair_result)
+    call = lambda w: lib().tsmm_motif_shard(series.data_ptr(), N, l, excl, m, shard, nshards, ctypes.byref(out),
+                                            w.data_ptr(), w.numel(), _stream(stream))
+    return _dense_call(call, ws, tsmm_motif_workspace_size(N, l, m), out, series.device, stream)
 
 
 def twolocus_scan_workspace_size(S: int, W: int) -> int:
@@ -339,9 +387,11 @@ def twolocus_scan(planes: torch.Tensor, m_cases: int, m_controls: int, ws: torch
     S, W = planes.shape[0], planes.shape[3]
     if ws is None:
         ws = _workspace(twolocus_scan_workspace_size(S, W), planes.device)
-    out = twolocus_result()
+    out = _pinned(twolocus_result)
     _raise(lib().twolocus_scan(planes.data_ptr() if S else None, S, W, m_cases, m_controls, ctypes.byref(out),
                                ws.data_ptr(), ws.numel(), _stream(stream)))
+    _sync(stream)
+    _raise_status(out.status)
     return out.as_dict()
 
 
@@ -354,9 +404,11 @@ def twolocus_scan_shard(planes: torch.Tensor, m_cases: int, m_controls: int, sha
     S, W = planes.shape[0], planes.shape[3]
     if ws is None:
         ws = _workspace(twolocus_scan_workspace_size(S, W), planes.device)
-    out = twolocus_result()
+    out = _pinned(twolocus_result)
     _raise(lib().twolocus_scan_shard(planes.data_ptr() if S else None, S, W, m_cases, m_controls, shard, nshards,
                                      ctypes.byref(out), ws.data_ptr(), ws.numel(), _stream(stream)))
+    _sync(stream)
+    _raise_status(out.status)
     return out.as_dict()
 
 
@@ -380,10 +432,12 @@ def twolocus_scan_tc(planes: torch.Tensor, m_cases: int, m_controls: int, measur
     S, W = planes.shape[0], planes.shape[3]
     if ws is None:
         ws = _workspace(twolocus_scan_tc_workspace_size(S, W), planes.device)
-    out = twolocus_result()
+    out = _pinned(twolocus_result)
     m = {"matches": TL_MATCHES, "pearson": TL_PEARSON}.get(measure, measure)
     _raise(lib().twolocus_scan_tc(planes.data_ptr() if S else None, S, W, m_cases, m_controls, int(m),
                                   ctypes.byref(out), ws.data_ptr(), ws.numel(), _stream(stream)))
+    _sync(stream)
+    _raise_status(out.status)
     return out.as_dict()
 
 
@@ -396,10 +450,12 @@ def twolocus_scan_tc_shard(planes: torch.Tensor, m_cases: int, m_controls: int, 
     S, W = planes.shape[0], planes.shape[3]
     if ws is None:
         ws = _workspace(twolocus_scan_tc_workspace_size(S, W), planes.device)
-    out = twolocus_result()
+    out = _pinned(twolocus_result)
     m = {"matches": TL_MATCHES, "pearson": TL_PEARSON}.get(measure, measure)
     _raise(lib().twolocus_scan_tc_shard(planes.data_ptr() if S else None, S, W, m_cases, m_controls, int(m), shard,
                                         nshards, ctypes.byref(out), ws.data_ptr(), ws.numel(), _stream(stream)))
+    _sync(stream)
+    _raise_status(out.status)
     return out.as_dict()
 
 
@@ -412,10 +468,12 @@ def hamming_pair_shard(strings: torch.Tensor, sigma: int, shard: int, nshards: i
     n, t = strings.shape
     if ws is None:
         ws = _workspace(hamming_pair_workspace_size(n, t, sigma), strings.device)
-    out = hamming_result()
+    out = _pinned(hamming_result)
     _raise(lib().hamming_pair_shard(strings.data_ptr() if n else None, n, t, strings.stride(0) if n else t, int(sigma),
                                     1 if least else 0, shard, nshards, ctypes.byref(out), ws.data_ptr(), ws.numel(),
                                     _stream(stream)))
+    _sync(stream)
+    _raise_status(out.status)
     return out.as_dict()
 
 
@@ -428,9 +486,11 @@ def hamming_pair(strings: torch.Tensor, sigma: int, least: bool = False, ws: tor
     n, t = strings.shape
     if ws is None:
         ws = _workspace(hamming_pair_workspace_size(n, t, sigma), strings.device)
-    out = hamming_result()
+    out = _pinned(hamming_result)
     _raise(lib().hamming_pair(strings.data_ptr() if n else None, n, t, strings.stride(0) if n else t, int(sigma),
                               1 if least else 0, ctypes.byref(out), ws.data_ptr(), ws.numel(), _stream(stream)))
+    _sync(stream)
+    _raise_status(out.status)
     return out.as_dict()
 
 
@@ -459,10 +519,12 @@ def mlba_pair(strings: torch.Tensor, sigma: int, cols: torch.Tensor, least: bool
     iters, L = cols.shape
     if ws is None:
         ws = _workspace(mlba_pair_workspace_size(n, t, sigma, least, iters, L), strings.device)
-    out = mlba_result()
+    out = _pinned(mlba_result)
     _raise(lib().mlba_pair(strings.data_ptr() if n else None, n, t, strings.stride(0) if n else t, int(sigma),
                            1 if least else 0, cols.data_ptr() if cols.numel() else None, iters, L,
                            ctypes.byref(out), ws.data_ptr(), ws.numel(), _stream(stream)))
+    _sync(stream)
+    _raise_status(out.status)
     return out.as_dict()
 
 
@@ -473,9 +535,10 @@ def twolocus_scan_noalloc(planes: torch.Tensor, m_cases: int, m_controls: int, s
     if planes.dim() != 4 or planes.shape[1:3] != (2, 2) or planes.element_size() != 8 or not planes.is_contiguous():
         raise ValueError("planes must be a contiguous 64-bit tensor [S][2][2][W]")
     S, W = planes.shape[0], planes.shape[3]
-    out = twolocus_result()
+    out = _pinned(twolocus_result)
     _raise(lib().twolocus_scan_noalloc(planes.data_ptr() if S else None, S, W, m_cases, m_controls,
                                        ctypes.byref(out), _stream(stream)))
+    _raise_status(out.status)
     return out.as_dict()
 
 
@@ -503,19 +566,21 @@ def _frnn(pts, R, cols_cap, ws, stream, shard):
     if ws is None:
         ws = _workspace(frnn_query_workspace_size(n, d), pts.device)
     row_ptr = torch.empty(n + 1, dtype=torch.int64, device=pts.device)
-    total = _i64(0)
+    out = _pinned(frnn_result)
     cap = int(cols_cap) if cols_cap is not None else max(16 * n, 1024)
     while True:
         cols = torch.empty(max(cap, 1), dtype=torch.int32, device=pts.device)
         args = (pts.data_ptr() if n else None, n, d, pts.stride(0) if n else d, float(R))
-        tail = (row_ptr.data_ptr(), cols.data_ptr(), cap, ctypes.byref(total), ws.data_ptr(), ws.numel(),
+        tail = (row_ptr.data_ptr(), cols.data_ptr(), cap, ctypes.byref(out), ws.data_ptr(), ws.numel(),
                 _stream(stream))
-        st = lib().frnn_query(*args, *tail) if shard is None else lib().frnn_query_shard(*args, *shard, *tail)
-        if st == ERR_CAPACITY and cols_cap is None and total.value > cap:
-            cap = total.value
+        _raise(lib().frnn_query(*args, *tail) if shard is None else lib().frnn_query_shard(*args, *shard, *tail))
+        _sync(stream)
+        total = int(out.n_pairs)
+        if out.status == ERR_CAPACITY and cols_cap is None and total > cap:
+            cap = total
             continue
-        _raise(st)
-        return row_ptr, cols[:total.value]
+        _raise_status(out.status)
+        return row_ptr, cols[:total]
 
 
 def cpp_batch_workspace_size(instances) -> int:
@@ -551,8 +616,8 @@ def cpp_batch(points: list, radii: list, pairs_cap: int | None = None, ws: torch
     device = points[0].device if count else torch.device("cuda")
     if ws is None:
         ws = _workspace(int(lib().cpp_batch_workspace_size(arr, count)), device)
-    outs = (cpp_pair_result * max(count, 1))()
-    counts = (_i64 * max(count, 1))()
+    outs = _pinned(cpp_pair_result, count)
+    counts = _pinned(_i64, count)
     if pairs is None:
         cap = int(pairs_cap) if pairs_cap is not None else 1 << 20
         pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=device)
@@ -560,5 +625,8 @@ def cpp_batch(points: list, radii: list, pairs_cap: int | None = None, ws: torch
         cap = int(pairs.shape[0])
     _raise(lib().cpp_batch(arr, count, outs, counts, pairs.data_ptr(), cap, ws.data_ptr(), ws.numel(),
                            _stream(stream)))
+    _sync(stream)
+    for q in range(count):
+        _raise_status(outs[q].status)
     c = np.array(list(counts)[:count], dtype=np.int64)
     return [outs[q].as_dict() for q in range(count)], c, pairs[:int(c.sum())]

@@ -45,11 +45,14 @@ int tuned_dense_band() { return g_dense_band.load(); }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
-// Per-thread CUDA events for the optional stage timing of the dense searches.
+// Per-thread CUDA events for the optional stage timing of the dense searches.  A call records its
+// events and leaves them pending; cpp_stage_times waits for the last one and turns them into
+// stage durations.
 struct StageTimer {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   double ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int n = 0;
+  const cudaEvent_t* pend = nullptr;  // events of the last call, not yet read (n + 1 of them)
   bool ready = false;
   bool init() {
     if (!ready) {
@@ -61,13 +64,18 @@ struct StageTimer {
   }
 };
 static thread_local StageTimer g_timer;
-static thread_local int64_t g_prune_kept = -1, g_prune_total = -1;  // the last pruned search's tiles
 
 bool stage_timing_on() { return g_timing.load() != 0; }
 
 void set_stage_times(const double* ms, int n) {
+  g_timer.pend = nullptr;
   g_timer.n = n < 8 ? n : 8;
   for (int k = 0; k < g_timer.n; ++k) g_timer.ms[k] = ms[k];
+}
+
+void set_stage_events(const cudaEvent_t* ev, int intervals) {
+  g_timer.pend = ev;
+  g_timer.n = intervals < 8 ? intervals : 8;
 }
 
 int set_error(int code, const char* fmt, ...) {
@@ -119,6 +127,7 @@ struct DenseLayout {
   Candidate* cand;
   double* d2buf;
   int32_t* surv;  // the candidates that pass the final screen (l-mer recheck)
+  cpp_pair_result* res;  // the result, copied to the caller's host struct
   size_t bytes;
 };
 
@@ -154,12 +163,13 @@ DenseLayout dense_layout(void* ws, int64_t n, int64_t d, int mode, size_t ws_byt
     L.Xs = c.take<char>((size_t)L.n_pad * L.Kp * L.elem);
     L.norms_s = c.take<float>(L.n_pad);
   }
-  const size_t fixed = c.bytes() + 1024;  // room for the 256-byte rounding of the three arrays below
+  const size_t fixed = c.bytes() + 1536;  // the result slot and the 256-byte rounding of the arrays below
   if (ws_bytes > fixed) {
     int64_t fit = (int64_t)((ws_bytes - fixed) / (sizeof(Candidate) + sizeof(double) + sizeof(int32_t)));
     if (fit > cap) cap = fit;
   }
   L.cap = cap;
+  L.res = c.take<cpp_pair_result>(1);
   L.cand = c.take<Candidate>(L.cap);
   L.d2buf = c.take<double>(L.cap);
   L.surv = c.take<int32_t>(L.cap);
@@ -205,7 +215,7 @@ int dense_search(const Source& src, int64_t n, int64_t d, int64_t excl, int mode
   const bool prune = is_prune(mode);
   mode = base_mode(mode);
   g_timer.n = 0;
-  g_prune_kept = g_prune_total = -1;
+  g_timer.pend = nullptr;
   if (timing) CPPGB_CUDA_TRY(cudaEventRecord(g_timer.ev[0], st));
   int rc;
   if ((rc = launch_init_scalars(L.sc, st))) return rc;
@@ -217,9 +227,11 @@ int dense_search(const Source& src, int64_t n, int64_t d, int64_t excl, int mode
   if ((rc = launch_bounds(L.sc, kappa_for(mode, L.Kp), st))) return rc;
 
   // Reference pruning: distance intervals to the references, a seed bound U0 from pairs that are
-  // neighbours in the order of reference 0, then the list of tiles the intervals cannot exclude.
+  // neighbours in the order of reference 0, then the list of tiles the intervals cannot exclude
+  // (its length stays on the device).
   const int32_t* tlist = nullptr;
   const int64_t* tcount = nullptr;
+  int64_t tiles_total = -1;
   const void* Xd = L.X;          // the dense stage's rows, norms, original-index map and schedule exclusion
   const float* normsd = L.norms;
   const int32_t* permd = nullptr;
@@ -243,89 +255,37 @@ int dense_search(const Source& src, int64_t n, int64_t d, int64_t excl, int mode
       permd = L.perm;
       excl_sched = 1;
     }
-    const int64_t total = gram_tc_tile_count(n, L.n_pad, excl_sched, shard, nshards);
+    tiles_total = gram_tc_tile_count(n, L.n_pad, excl_sched, shard, nshards);
     if ((rc = launch_gram_tc_prune_list(n, L.n_pad, excl_sched, L.pblo, L.pbhi, L.sc, L.flags, L.pos, L.ptmp, L.list,
                                         st, shard, nshards)))
       return rc;
     tlist = L.list;
-    tcount = L.pos + total;
-    int64_t kept = 0;
-    CPPGB_CUDA_TRY(cudaMemcpyAsync(&kept, tcount, sizeof kept, cudaMemcpyDeviceToHost, st));
-    CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
-    g_prune_kept = kept;
-    g_prune_total = total;
+    tcount = L.pos + tiles_total;
   }
   if (timing) CPPGB_CUDA_TRY(cudaEventRecord(g_timer.ev[1], st));
 
-  DenseScalars h;
+  // Two passes of the dense stage; the second runs (on the device's decision) only when the first
+  // overflowed the candidate buffer, and then emits against the final bound U.
   for (int pass = 0; pass < 2; ++pass) {
+    const unsigned int* gate = pass == 0 ? nullptr : &L.sc->redo;
+    if (pass == 1 && (rc = launch_pass2_gate(L.sc, L.cap, st))) return rc;
     if (is_filter(mode))
       rc = launch_gram_tc(Xd, mode, n, L.n_pad, L.Kp, excl_sched, normsd, L.sc, L.cand, L.cap, st, shard, nshards,
-                          tlist, tcount, permd, excl);
+                          tlist, tcount, permd, excl, nullptr, 0, gate);
     else
-      rc = launch_gram_simt((const float*)L.X, n, L.Kp, excl, L.norms, L.sc, L.cand, L.cap, st, shard, nshards);
+      rc = launch_gram_simt((const float*)L.X, n, L.Kp, excl, L.norms, L.sc, L.cand, L.cap, st, shard, nshards, gate);
     if (rc) return rc;
-    if (timing) CPPGB_CUDA_TRY(cudaEventRecord(g_timer.ev[2], st));
-    CPPGB_CUDA_TRY(cudaMemcpyAsync(&h, L.sc, sizeof h, cudaMemcpyDeviceToHost, st));
-    CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
-    if (h.status & 1u) return set_error(CPPGB_ERR_NUMERIC, "non-finite input value");
-    if (h.status & 2u) return set_error(CPPGB_ERR_NUMERIC, "an l-mer has zero variance");
-    if (h.status & 4u) return set_error(CPPGB_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
-    if ((int64_t)h.n_cand <= L.cap) break;
-    if (pass == 1) {
-      // report the number of candidates a larger workspace would have to hold
-      memset(out, 0, sizeof *out);
-      out->i = out->j = -1;
-      out->n_emitted = (int64_t)h.n_cand;
-      return set_error(CPPGB_ERR_CAPACITY,
-                       "candidate buffer overflow (%llu > %lld) at the final bound: many pairs tie within the "
-                       "filter's error; pass a workspace of %zu bytes",
-                       (unsigned long long)h.n_cand, (long long)L.cap,
-                       dense_layout(nullptr, n, d, mode | (prune ? CPPGB_MODE_PRUNE : 0)).bytes +
-                           (size_t)(h.n_cand - L.cap) * (sizeof(Candidate) + sizeof(double) + sizeof(int32_t)) + 4096);
-    }
-    // The bound U is final now; a second pass emits only pairs whose lower bound meets it.
-    CPPGB_CUDA_TRY(cudaMemsetAsync(&L.sc->n_cand, 0, sizeof(L.sc->n_cand), st));
   }
-  const int64_t n_live = (int64_t)h.n_cand;
+  if (timing) CPPGB_CUDA_TRY(cudaEventRecord(g_timer.ev[2], st));
   if (src.lmers)
-    rc = launch_recheck_lmers(src.series, src.l, L.sc, L.surv, L.cand, L.cap, L.d2buf, n_live, st);
+    rc = launch_recheck_lmers(src.series, src.l, L.sc, L.surv, L.cand, L.cap, L.d2buf, st);
   else
-    rc = launch_recheck_points(src.pts, src.dtype, d, src.ld, L.sc, L.cand, L.cap, L.d2buf, n_live, st);
+    rc = launch_recheck_points(src.pts, src.dtype, d, src.ld, L.sc, L.cand, L.cap, L.d2buf, st);
   if (rc) return rc;
   if (timing) CPPGB_CUDA_TRY(cudaEventRecord(g_timer.ev[3], st));
-  CPPGB_CUDA_TRY(cudaMemcpyAsync(&h, L.sc, sizeof h, cudaMemcpyDeviceToHost, st));
-  CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
-  if (timing) {
-    float a = 0, b = 0, c = 0;
-    CPPGB_CUDA_TRY(cudaEventElapsedTime(&a, g_timer.ev[0], g_timer.ev[1]));
-    CPPGB_CUDA_TRY(cudaEventElapsedTime(&b, g_timer.ev[1], g_timer.ev[2]));
-    CPPGB_CUDA_TRY(cudaEventElapsedTime(&c, g_timer.ev[2], g_timer.ev[3]));
-    g_timer.ms[0] = a; g_timer.ms[1] = b; g_timer.ms[2] = c;
-    g_timer.n = 3;
-  }
-
-  cpp_pair_result r;
-  memset(&r, 0, sizeof r);
-  double best;
-  memcpy(&best, &h.best_bits, sizeof best);
-  if (h.best_ij == ~0ull || !(best < INFINITY)) {
-    r.i = r.j = -1;
-    r.dist = r.dist2 = INFINITY;
-  } else {
-    r.i = (int64_t)(h.best_ij >> 32);
-    r.j = (int64_t)(h.best_ij & 0xffffffffu);
-    r.dist2 = best;
-    r.dist = sqrt(best);
-  }
-  float fe, fb;
-  memcpy(&fe, &h.ferr_bits, 4);
-  memcpy(&fb, &h.U_bits, 4);
-  r.filter_err = fe;
-  r.filter_bound = fb;
-  r.n_emitted = (int64_t)h.n_cand;
-  r.n_rechecked = (int64_t)h.n_rech;
-  *out = r;
+  if ((rc = launch_dense_result(L.sc, L.cap, tcount, tiles_total, L.res, st))) return rc;
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(out, L.res, sizeof *out, cudaMemcpyDeviceToHost, st));
+  if (timing) set_stage_events(g_timer.ev, 3);  // [prep (+ pruning set-up), dense stage, FP64 recheck]
   return CPPGB_OK;
 }
 
@@ -385,6 +345,19 @@ int cpp_get_tuning(int kind, int32_t* values, int count) {
 void cpp_set_stage_timing(int on) { g_timing.store(on ? 1 : 0); }
 
 int cpp_stage_times(double* ms, int cap) {
+  if (g_timer.pend) {  // the last call's events: wait for them, then take the intervals
+    const cudaEvent_t* ev = g_timer.pend;
+    g_timer.pend = nullptr;
+    if (cudaEventSynchronize(ev[g_timer.n]) != cudaSuccess) {
+      g_timer.n = 0;
+      return 0;
+    }
+    for (int k = 0; k < g_timer.n; ++k) {
+      float v = 0.f;
+      if (cudaEventElapsedTime(&v, ev[k], ev[k + 1]) != cudaSuccess) v = 0.f;
+      g_timer.ms[k] = v;
+    }
+  }
   int k = 0;
   for (; k < g_timer.n && k < cap; ++k) ms[k] = g_timer.ms[k];
   return k;
@@ -392,12 +365,6 @@ int cpp_stage_times(double* ms, int cap) {
 
 int64_t cpp_launch_count(void) { return (int64_t)g_launches.load(); }
 
-int cpp_prune_stats(int64_t* tiles_kept, int64_t* tiles_total) {
-  if (!tiles_kept || !tiles_total) return set_error(CPPGB_ERR_ARG, "NULL argument");
-  *tiles_kept = g_prune_kept;
-  *tiles_total = g_prune_total;
-  return CPPGB_OK;
-}
 
 // ------------------------------------------------------------------ closest pair
 size_t cpp_closest_pair_workspace_size(int64_t n, int64_t d, int mode) {
@@ -561,11 +528,7 @@ static int twolocus_common(const uint64_t* planes, int64_t S, int64_t W, int64_t
   const int64_t np = twolocus_num_partials(S);
   void* partials = c.take<char>((size_t)16 * (size_t)(np > 0 ? np : 1));
   if ((rc = launch_twolocus(planes, S, W, m_cases, m_controls, partials, np, dres, st, shard, nshards))) return rc;
-  twolocus_result h;
-  CPPGB_CUDA_TRY(cudaMemcpyAsync(&h, dres, sizeof h, cudaMemcpyDeviceToHost, st));
-  CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
-  h.score_real = h.i >= 0 ? (double)h.score / ((double)m_cases * (double)m_controls) : -1.0;
-  *out = h;
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(out, dres, sizeof *out, cudaMemcpyDeviceToHost, st));
   return CPPGB_OK;
 }
 

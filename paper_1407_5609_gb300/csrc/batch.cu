@@ -952,10 +952,12 @@ __global__ void batch_fill_kernel(const BatchGlobals* g, const BatchCand* __rest
 // one thread per instance: sort its (i, j) pairs ascending; write its result record
 __global__ void batch_finish_kernel(const BatchState* st, int count, const int64_t* __restrict__ pair_offs,
                                     int32_t* __restrict__ pairs, int64_t pairs_cap, const BatchGlobals* g,
-                                    cpp_pair_result* __restrict__ res) {
+                                    int64_t cap, cpp_pair_result* __restrict__ res,
+                                    int64_t* __restrict__ counts64) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= count) return;
   const int64_t b = pair_offs[q], e = pair_offs[q + 1];
+  counts64[q] = e - b;
   if (e <= pairs_cap) {
     uint64_t* P = reinterpret_cast<uint64_t*>(pairs);  // (i, j) as one little-endian word: j high, i low
     for (int64_t u = b + 1; u < e; ++u) {             // insertion sort on (i, j)
@@ -987,6 +989,13 @@ __global__ void batch_finish_kernel(const BatchState* st, int count, const int64
   r.filter_bound = __uint_as_float(s.U_bits);
   r.n_emitted = (int64_t)g->n_cand;
   r.n_rechecked = s.n_rech;
+  r.filter_e_acc = s.bp.e_acc;   // the bound of the FP32 pass whose candidates are rechecked
+  r.filter_eps = s.bp.eps_pair;
+  r.tiles_kept = r.tiles_total = -1;
+  const unsigned int gs = g->status;
+  r.status = (gs & 1u) ? CPPGB_ERR_NUMERIC : (gs & 4u) ? CPPGB_ERR_TIMEOUT
+             : ((int64_t)g->n_cand > cap || pair_offs[count] > pairs_cap) ? CPPGB_ERR_CAPACITY : CPPGB_OK;
+  r.reserved = 0;
   res[q] = r;
 }
 
@@ -1009,6 +1018,7 @@ struct BatchLayout {
   uint8_t* keep;
   TileRec* trec;
   cpp_pair_result* res;
+  int64_t* counts64;  // pairs within R per instance, copied to the caller's pair_counts
   int64_t cap, trec_cap;
   size_t bytes;
 };
@@ -1067,6 +1077,7 @@ BatchLayout batch_layout(void* ws, int64_t count, const Totals& t, size_t ws_byt
   L.pair_offs = c.take<int64_t>(count + 1);
   L.tmp = c.take<int64_t>(scan_temp_elems(count + 1));
   L.res = c.take<cpp_pair_result>(count);
+  L.counts64 = c.take<int64_t>(count);
   L.X = c.take<float>(t.xfloats + 16);
   L.norms = c.take<float>(t.rows + 1);
   for (int k = 0; k < NCLS; ++k)  // at least 256 rows each, so every class has a valid tensor map
@@ -1220,7 +1231,7 @@ int enqueue_batch(const BatchLayout& L, int64_t count, const Totals& t, int32_t*
   batch_fill_kernel<<<cb, 256, 0, st>>>(L.g, L.cand, L.cap, L.keep, L.pair_offs, L.st, pairs, pairs_cap);
   CPPGB_LAUNCH_CHECK();
   batch_finish_kernel<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(L.st, ci, L.pair_offs, pairs, pairs_cap, L.g,
-                                                                      L.res);
+                                                                      L.cap, L.res, L.counts64);
   CPPGB_LAUNCH_CHECK();
   if (timing) CPPGB_CUDA_TRY(cudaEventRecordWithFlags(g_bev[4], st, cudaEventRecordExternal));
   return CPPGB_OK;
@@ -1376,31 +1387,10 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
     CPPGB_CUDA_TRY(cudaGraphLaunch(g_exec, st));
     note_launches(g_graph_kernels);
   }
-  BatchGlobals hg;
-  std::vector<int64_t> hoff((size_t)count + 1);
   CPPGB_CUDA_TRY(cudaMemcpyAsync(out_cpp, L.res, sizeof(cpp_pair_result) * count, cudaMemcpyDeviceToHost, st));
-  CPPGB_CUDA_TRY(cudaMemcpyAsync(hoff.data(), L.pair_offs, sizeof(int64_t) * (count + 1), cudaMemcpyDeviceToHost, st));
-  CPPGB_CUDA_TRY(cudaMemcpyAsync(&hg, L.g, sizeof hg, cudaMemcpyDeviceToHost, st));
-  CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
-  if (timing) {  // [preparation, tensor-core tiles, FP32 tiles, second pass + recheck + output]
-    double ms[4];
-    for (int k = 0; k < 4; ++k) {
-      float v = 0.f;
-      CPPGB_CUDA_TRY(cudaEventElapsedTime(&v, g_bev[k], g_bev[k + 1]));
-      ms[k] = v;
-    }
-    set_stage_times(ms, 4);
-  }
-  for (int64_t q = 0; q < count; ++q) pair_counts[q] = hoff[(size_t)q + 1] - hoff[(size_t)q];
-  if (hg.status & 1u) return set_error(CPPGB_ERR_NUMERIC, "non-finite coordinate");
-  if (hg.status & 4u) return set_error(CPPGB_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
-  if ((int64_t)hg.n_cand > L.cap)
-    return set_error(CPPGB_ERR_CAPACITY, "%llu candidate pairs exceed the workspace's %lld; pass %zu bytes",
-                     (unsigned long long)hg.n_cand, (long long)L.cap,
-                     L.bytes + (size_t)((int64_t)hg.n_cand - L.cap) * (sizeof(BatchCand) + sizeof(double) + 1) + 4096);
-  if (hoff[(size_t)count] > pairs_cap)
-    return set_error(CPPGB_ERR_CAPACITY, "pairs_cap %lld is smaller than the %lld pairs within R",
-                     (long long)pairs_cap, (long long)hoff[(size_t)count]);
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(pair_counts, L.counts64, sizeof(int64_t) * count, cudaMemcpyDeviceToHost, st));
+  // [preparation, tensor-core tiles, FP32 tiles, second pass + recheck + output]
+  if (timing) set_stage_events(g_bev, 4);
   return CPPGB_OK;
 }
 

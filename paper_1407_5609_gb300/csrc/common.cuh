@@ -75,6 +75,8 @@ struct DenseScalars {
   unsigned long long best_ij;   // (i << 32) | j of the best pair among equal d^2
   unsigned int ferr_bits;       // max |d2_fp64 - D~| over rechecked candidates (float bits)
   unsigned int n_surv;          // l-mer recheck: candidates that pass the final screen (listed)
+  unsigned int redo;            // 1: the first pass overflowed the candidate buffer, run the second
+  unsigned int pad;
 };
 
 // True distance d of a pair with filtered value D~ satisfies
@@ -123,9 +125,10 @@ int launch_prep_lmers(const float* series, int64_t n, int64_t l, int mode, void*
 
 // Dense all-pairs stage on FP32 CUDA cores.
 // shard / nshards: only the tiles t with t % nshards == shard are evaluated (a slice of the pair space).
+// gate (optional, device): the kernel returns at once unless *gate is non-zero (the second pass).
 int launch_gram_simt(const float* X, int64_t n, int64_t Kp, int64_t excl, const float* norms,
                      DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st, int64_t shard = 0,
-                     int64_t nshards = 1);
+                     int64_t nshards = 1, const unsigned int* gate = nullptr);
 // Fixed-radius variant: emits every pair i < j with D~ <= theta(rr) (rr = R^2 rounded up to FP32).
 int launch_gram_simt_radius(const float* X, int64_t n, int64_t Kp, const float* norms, DenseScalars* sc,
                             Candidate* cand, int64_t cap, float rr, cudaStream_t st);
@@ -135,7 +138,7 @@ int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp
                    int64_t shard = 0, int64_t nshards = 1,
                    const int32_t* tlist = nullptr, const int64_t* tcount = nullptr,
                    const int32_t* perm = nullptr, int64_t excl_orig = 1, float* dump = nullptr,
-                   int64_t dump_tiles = 0);
+                   int64_t dump_tiles = 0, const unsigned int* gate = nullptr);
 // (dump != nullptr: tlist holds dump_tiles (bi, bj) pairs and each tile's raw accumulator is written
 // to dump[t][128][256]; nothing else is computed.)
 bool gram_tc_available();
@@ -157,18 +160,26 @@ constexpr int TUNE_NB = 4, TUNE_DC = 4;  // batch n-buckets (n < 1024, 4096, 163
 int tuned_batch_path(int64_t n, int d);   // 1 (FP32 tiles) or 2 (tensor-core tiles)
 int tuned_dense_band();                   // column blocks per band of the tensor-core dense stage
 
-// Stage timing (cpp_set_stage_timing): whether it is on, and the last call's stage durations.
+// Stage timing (cpp_set_stage_timing): whether it is on, and the last call's stage durations --
+// given directly, or as intervals + 1 events recorded on the call's stream (read when asked for).
 bool stage_timing_on();
 void set_stage_times(const double* ms, int n);
+void set_stage_events(const cudaEvent_t* ev, int intervals);
 
 // FP64 recheck of the surviving candidates and the lexicographic (d^2, i, j) minimum.
-// Source of the exact coordinates: points (dtype F32/F64, [n][ld]) or a series with l-mers.
-// n_live = min(candidates emitted, cap), read back by the host after the dense stage.
-int launch_recheck_points(const void* pts, int dtype, int64_t d, int64_t ld, DenseScalars* sc, const Candidate* cand, int64_t cap, double* d2buf,
-                          int64_t n_live, cudaStream_t st);
+// Source of the exact coordinates: points (dtype F32/F64, [n][ld]) or a series with l-mers.  The
+// kernels read the live candidate count, min(emitted, cap), on the device (grid-stride loops).
+int launch_recheck_points(const void* pts, int dtype, int64_t d, int64_t ld, DenseScalars* sc, const Candidate* cand,
+                          int64_t cap, double* d2buf, cudaStream_t st);
 int launch_recheck_lmers(const float* series, int64_t l, DenseScalars* sc, int32_t* surv,
-                         const Candidate* cand, int64_t cap, double* d2buf, int64_t n_live,
-                         cudaStream_t st);
+                         const Candidate* cand, int64_t cap, double* d2buf, cudaStream_t st);
+// Between the two passes of the dense stage: sc->redo = 1 (and the candidate count reset) when the
+// first pass overflowed the buffer and found no error, else 0.
+int launch_pass2_gate(DenseScalars* sc, int64_t cap, cudaStream_t st);
+// The search's result from the scalars (status, pair, distances, bound terms, counts); tcount
+// (optional, device) is the number of tiles a pruned search kept, of tiles_total.
+int launch_dense_result(const DenseScalars* sc, int64_t cap, const int64_t* tcount, int64_t tiles_total,
+                        cpp_pair_result* res, cudaStream_t st);
 
 // Scalars reset and the bound parameters: e_acc = kappa * max_i |x~_i|^2, eps_pair = 2 max_i eps_i.
 int launch_init_scalars(DenseScalars* sc, cudaStream_t st);

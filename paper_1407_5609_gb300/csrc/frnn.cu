@@ -603,40 +603,62 @@ __global__ void __launch_bounds__(PW * 32) crowded_query_kernel(
 }
 
 // ---------------------------------------------------------------- dense path (d > 4)
+// The high-d path's candidates (grid-stride over the live count on the device): the FP64 test,
+// then the rows, once the counts are scanned and only when every candidate was kept and the
+// neighbour entries fit cols_cap.
 __global__ void radius_check_kernel(const float* __restrict__ pts, int64_t d, int64_t ld, double rr,
-                                    const DenseScalars* sc, const Candidate* __restrict__ cand, int64_t n_live,
-                                    float th_unused, uint8_t* __restrict__ keep, int32_t* __restrict__ counts) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n_live) return;
-  const Candidate cd = cand[c];
-  const float* x = pts + (int64_t)cd.i * ld;
-  const float* y = pts + (int64_t)cd.j * ld;
-  double s = 0.0;
-  for (int64_t k = 0; k < d; ++k) {
-    const double t = __dsub_rn((double)x[k], (double)y[k]);
-    s = __dadd_rn(s, __dmul_rn(t, t));
-  }
-  const bool in = s <= rr;
-  keep[c] = in ? 1 : 0;
-  if (in) {
-    atomicAdd(&counts[cd.i], 1);
-    atomicAdd(&counts[cd.j], 1);
+                                    const DenseScalars* sc, const Candidate* __restrict__ cand, int64_t cap,
+                                    uint8_t* __restrict__ keep, int32_t* __restrict__ counts) {
+  const int64_t live = (int64_t)sc->n_cand < cap ? (int64_t)sc->n_cand : cap;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < live; c += (int64_t)gridDim.x * blockDim.x) {
+    const Candidate cd = cand[c];
+    const float* x = pts + (int64_t)cd.i * ld;
+    const float* y = pts + (int64_t)cd.j * ld;
+    double s = 0.0;
+    for (int64_t k = 0; k < d; ++k) {
+      const double t = __dsub_rn((double)x[k], (double)y[k]);
+      s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    const bool in = s <= rr;
+    keep[c] = in ? 1 : 0;
+    if (in) {
+      atomicAdd(&counts[cd.i], 1);
+      atomicAdd(&counts[cd.j], 1);
+    }
   }
 }
 
-__global__ void radius_fill_kernel(const Candidate* __restrict__ cand, int64_t n_live, const uint8_t* __restrict__ keep,
-                                   const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cursor,
-                                   int32_t* __restrict__ cols) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n_live || !keep[c]) return;
-  const Candidate cd = cand[c];
-  cols[row_ptr[cd.i] + atomicAdd(&cursor[cd.i], 1)] = cd.j;
-  cols[row_ptr[cd.j] + atomicAdd(&cursor[cd.j], 1)] = cd.i;
+__global__ void radius_fill_kernel(const DenseScalars* sc, const Candidate* __restrict__ cand, int64_t cap,
+                                   const uint8_t* __restrict__ keep, const int64_t* __restrict__ row_ptr, int64_t n,
+                                   int64_t cols_cap, int32_t* __restrict__ cursor, int32_t* __restrict__ cols) {
+  if ((int64_t)sc->n_cand > cap || row_ptr[n] > cols_cap) return;
+  const int64_t live = (int64_t)sc->n_cand;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < live; c += (int64_t)gridDim.x * blockDim.x) {
+    if (!keep[c]) continue;
+    const Candidate cd = cand[c];
+    cols[row_ptr[cd.i] + atomicAdd(&cursor[cd.i], 1)] = cd.j;
+    cols[row_ptr[cd.j] + atomicAdd(&cursor[cd.j], 1)] = cd.i;
+  }
 }
 
-__global__ void sort_rows_kernel(int64_t n, const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cols) {
+__global__ void sort_rows_kernel(int64_t n, const int64_t* __restrict__ row_ptr, int64_t cols_cap,
+                                 int32_t* __restrict__ cols) {
+  if (row_ptr[n] > cols_cap) return;
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n) sort_segment(cols + row_ptr[r], row_ptr[r + 1] - row_ptr[r]);
+}
+
+// The query's result: the directed pair count and the status (grid path: fs, high-d path: sc).
+__global__ void frnn_result_kernel(const FrnnState* fs, const DenseScalars* sc, int64_t cap,
+                                   const int64_t* __restrict__ row_ptr, int64_t n, int64_t cols_cap,
+                                   frnn_result* res) {
+  frnn_result r;
+  r.n_pairs = row_ptr[n];
+  const unsigned int st = fs ? fs->status : sc->status;
+  r.status = (st & 1u) ? CPPGB_ERR_NUMERIC : (st & 8u) ? CPPGB_ERR_CUDA
+             : ((sc && (int64_t)sc->n_cand > cap) || r.n_pairs > cols_cap) ? CPPGB_ERR_CAPACITY : CPPGB_OK;
+  r.reserved = 0;
+  *res = r;
 }
 
 int64_t table_size(int64_t n) {
@@ -658,6 +680,7 @@ struct GridLayout {
   int32_t* occ_cnt;
   int64_t* occ_start;
   int64_t* tmp;
+  frnn_result* res;
   int64_t T;
   size_t bytes;
 };
@@ -680,6 +703,7 @@ GridLayout grid_layout(void* ws, int64_t n) {
   L.occ_cnt = c.take<int32_t>(n);
   L.occ_start = c.take<int64_t>(n + 1);
   L.tmp = c.take<int64_t>(scan_temp_elems(n));
+  L.res = c.take<frnn_result>(1);
   L.bytes = c.bytes();
   return L;
 }
@@ -693,7 +717,9 @@ struct RadiusLayout {
   Candidate* cand;
   uint8_t* keep;
   int32_t* counts;
+  int32_t* cursor;
   int64_t* tmp;
+  frnn_result* res;
   int64_t n_pad, Kp, cap;
   size_t bytes;
 };
@@ -709,7 +735,9 @@ RadiusLayout radius_layout(void* ws, int64_t n, int64_t d, size_t ws_bytes) {
   L.eps = c.take<float>(L.n_pad);
   L.X = c.take<float>((size_t)L.n_pad * L.Kp);
   L.counts = c.take<int32_t>(n + 1);
+  L.cursor = c.take<int32_t>(n + 1);
   L.tmp = c.take<int64_t>(scan_temp_elems(n + 1));
+  L.res = c.take<frnn_result>(1);
   int64_t cap = 16 * n;
   cap = cap < (1 << 16) ? (1 << 16) : cap;
   const size_t fixed = c.bytes() + 512;
@@ -738,7 +766,7 @@ __global__ void tab_clear_kernel(CellRec* __restrict__ tab, int64_t T) {
 
 template <int D>
 int grid_path(const float* pts, int64_t n, int64_t ld, double R, int64_t* row_ptr, int32_t* cols,
-              int64_t cols_cap, int64_t* n_pairs_out, void* ws, size_t ws_bytes, cudaStream_t st, int shard = 0,
+              int64_t cols_cap, frnn_result* out, void* ws, size_t ws_bytes, cudaStream_t st, int shard = 0,
               int nshards = 1) {
   const int d = D;
   GridLayout L = grid_layout(ws, n);
@@ -796,22 +824,14 @@ int grid_path(const float* pts, int64_t n, int64_t ld, double R, int64_t* row_pt
   crowded_query_kernel<D, true><<<pgrid, PW * 32, 0, st>>>(L.fs, L.tab, L.T, L.sorted_idx, L.sorted_pts, nullptr,
                                                            row_ptr, cols, n, cols_cap, L.fb, n_fb);
   CPPGB_LAUNCH_CHECK();
-  int64_t total = 0;
-  unsigned int status = 0;
-  CPPGB_CUDA_TRY(cudaMemcpyAsync(&total, row_ptr + n, sizeof total, cudaMemcpyDeviceToHost, st));
-  CPPGB_CUDA_TRY(cudaMemcpyAsync(&status, &L.fs->status, sizeof status, cudaMemcpyDeviceToHost, st));
-  CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
-  if (status & 1u) return set_error(CPPGB_ERR_NUMERIC, "non-finite coordinate");
-  if (status & 8u) return set_error(CPPGB_ERR_CUDA, "internal: cell hash table full");
-  *n_pairs_out = total;
-  if (total > cols_cap)
-    return set_error(CPPGB_ERR_CAPACITY, "cols_cap %lld is smaller than the %lld neighbour entries",
-                     (long long)cols_cap, (long long)total);
+  frnn_result_kernel<<<1, 1, 0, st>>>(L.fs, nullptr, 0, row_ptr, n, cols_cap, L.res);
+  CPPGB_LAUNCH_CHECK();
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(out, L.res, sizeof *out, cudaMemcpyDeviceToHost, st));
   return CPPGB_OK;
 }
 
 int dense_path(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t* row_ptr, int32_t* cols,
-               int64_t cols_cap, int64_t* n_pairs_out, void* ws, size_t ws_bytes, cudaStream_t st) {
+               int64_t cols_cap, frnn_result* out, void* ws, size_t ws_bytes, cudaStream_t st) {
   RadiusLayout L = radius_layout(ws, n, d, ws_bytes);
   if (ws_bytes < L.bytes)
     return set_error(CPPGB_ERR_CAPACITY, "workspace too small: %zu bytes given, %zu needed", ws_bytes, L.bytes);
@@ -824,39 +844,21 @@ int dense_path(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t
   if ((rc = launch_bounds(L.sc, (float)((4.0 * g + 8.0 * u) * 1.01), st))) return rc;
   const float rr32 = (float)(R * R) * (1.f + 0x1p-20f);
   if ((rc = launch_gram_simt_radius(L.X, n, L.Kp, L.norms, L.sc, L.cand, L.cap, rr32, st))) return rc;
-  DenseScalars h;
-  CPPGB_CUDA_TRY(cudaMemcpyAsync(&h, L.sc, sizeof h, cudaMemcpyDeviceToHost, st));
-  CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
-  if (h.status & 1u) return set_error(CPPGB_ERR_NUMERIC, "non-finite coordinate");
-  if ((int64_t)h.n_cand > L.cap)
-    return set_error(CPPGB_ERR_CAPACITY,
-                     "%llu candidate pairs lie within the radius bound; pass a workspace of %zu bytes",
-                     (unsigned long long)h.n_cand,
-                     L.bytes + (size_t)((int64_t)h.n_cand - L.cap) * (sizeof(Candidate) + 1) + 4096);
-  const int64_t n_live = (int64_t)h.n_cand;
+  // every candidate's FP64 test, the row counts, their scan, the rows, then each row sorted
   CPPGB_CUDA_TRY(cudaMemsetAsync(L.counts, 0, sizeof(int32_t) * (n + 1), st));
-  if (n_live > 0) {
-    radius_check_kernel<<<(unsigned)((n_live + 255) / 256), 256, 0, st>>>(pts, d, ld, R * R, L.sc, L.cand,
-                                                                           n_live, 0.f, L.keep, L.counts);
-    CPPGB_LAUNCH_CHECK();
-  }
+  CPPGB_CUDA_TRY(cudaMemsetAsync(L.cursor, 0, sizeof(int32_t) * (n + 1), st));
+  const int64_t cb = (L.cap + 255) / 256;
+  const unsigned cgrid = (unsigned)(cb < 152 * 8 ? cb : 152 * 8);
+  radius_check_kernel<<<cgrid, 256, 0, st>>>(pts, d, ld, R * R, L.sc, L.cand, L.cap, L.keep, L.counts);
+  CPPGB_LAUNCH_CHECK();
   if ((rc = launch_exclusive_scan_i32(L.counts, n, row_ptr, L.tmp, st))) return rc;
-  int64_t total = 0;
-  CPPGB_CUDA_TRY(cudaMemcpyAsync(&total, row_ptr + n, sizeof total, cudaMemcpyDeviceToHost, st));
-  CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
-  *n_pairs_out = total;
-  if (total > cols_cap)
-    return set_error(CPPGB_ERR_CAPACITY, "cols_cap %lld is smaller than the %lld neighbour entries",
-                     (long long)cols_cap, (long long)total);
-  if (total > 0) {
-    CPPGB_CUDA_TRY(cudaMemsetAsync(L.counts, 0, sizeof(int32_t) * (n + 1), st));
-    radius_fill_kernel<<<(unsigned)((n_live + 255) / 256), 256, 0, st>>>(L.cand, n_live, L.keep, row_ptr, L.counts,
-                                                                          cols);
-    CPPGB_LAUNCH_CHECK();
-    sort_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, row_ptr, cols);
-    CPPGB_LAUNCH_CHECK();
-  }
-  CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
+  radius_fill_kernel<<<cgrid, 256, 0, st>>>(L.sc, L.cand, L.cap, L.keep, row_ptr, n, cols_cap, L.cursor, cols);
+  CPPGB_LAUNCH_CHECK();
+  sort_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, row_ptr, cols_cap, cols);
+  CPPGB_LAUNCH_CHECK();
+  frnn_result_kernel<<<1, 1, 0, st>>>(nullptr, L.sc, L.cap, row_ptr, n, cols_cap, L.res);
+  CPPGB_LAUNCH_CHECK();
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(out, L.res, sizeof *out, cudaMemcpyDeviceToHost, st));
   return CPPGB_OK;
 }
 
@@ -866,10 +868,12 @@ int dense_path(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t
 using namespace cppgb;
 
 static int frnn_common(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t* row_ptr, int32_t* cols,
-                int64_t cols_cap, int64_t* n_pairs_out, void* ws, size_t ws_bytes, void* stream, int64_t shard,
+                int64_t cols_cap, frnn_result* out, void* ws, size_t ws_bytes, void* stream, int64_t shard,
                 int64_t nshards) {
-  if (!n_pairs_out) return set_error(CPPGB_ERR_ARG, "n_pairs_out is NULL");
-  *n_pairs_out = 0;
+  if (!out) return set_error(CPPGB_ERR_ARG, "out is NULL");
+  out->n_pairs = 0;
+  out->status = CPPGB_OK;
+  out->reserved = 0;
   if (n < 0 || n > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "n out of range");
   if (d < 1 || d > 4096 || ld < d) return set_error(CPPGB_ERR_ARG, "need 1 <= d <= 4096 and ld >= d");
   if (!(R >= 0.0) || !isfinite(R)) return set_error(CPPGB_ERR_ARG, "R must be finite and >= 0");
@@ -880,17 +884,16 @@ static int frnn_common(const float* pts, int64_t n, int d, int64_t ld, double R,
   cudaStream_t st = (cudaStream_t)stream;
   if (n == 0) {
     CPPGB_CUDA_TRY(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st));
-    CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
     return CPPGB_OK;
   }
   const int sh = (int)shard, ns = (int)nshards;
   switch (d) {
-    case 1: return grid_path<1>(pts, n, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, st, sh, ns);
-    case 2: return grid_path<2>(pts, n, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, st, sh, ns);
-    case 3: return grid_path<3>(pts, n, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, st, sh, ns);
-    case 4: return grid_path<4>(pts, n, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, st, sh, ns);
+    case 1: return grid_path<1>(pts, n, ld, R, row_ptr, cols, cols_cap, out, ws, ws_bytes, st, sh, ns);
+    case 2: return grid_path<2>(pts, n, ld, R, row_ptr, cols, cols_cap, out, ws, ws_bytes, st, sh, ns);
+    case 3: return grid_path<3>(pts, n, ld, R, row_ptr, cols, cols_cap, out, ws, ws_bytes, st, sh, ns);
+    case 4: return grid_path<4>(pts, n, ld, R, row_ptr, cols, cols_cap, out, ws, ws_bytes, st, sh, ns);
   }
-  return dense_path(pts, n, d, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, st);
+  return dense_path(pts, n, d, ld, R, row_ptr, cols, cols_cap, out, ws, ws_bytes, st);
 }
 
 extern "C" {
@@ -903,18 +906,17 @@ size_t frnn_query_workspace_size(int64_t n, int d) {
 
 
 int frnn_query(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t* row_ptr, int32_t* cols,
-               int64_t cols_cap, int64_t* n_pairs_out, void* ws, size_t ws_bytes, void* stream) {
-  return frnn_common(pts, n, d, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, stream, 0, 1);
+               int64_t cols_cap, frnn_result* out, void* ws, size_t ws_bytes, void* stream) {
+  return frnn_common(pts, n, d, ld, R, row_ptr, cols, cols_cap, out, ws, ws_bytes, stream, 0, 1);
 }
 
 int frnn_query_shard(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t shard, int64_t nshards,
-                     int64_t* row_ptr, int32_t* cols, int64_t cols_cap, int64_t* n_pairs_out, void* ws,
+                     int64_t* row_ptr, int32_t* cols, int64_t cols_cap, frnn_result* out, void* ws,
                      size_t ws_bytes, void* stream) {
-  if (n_pairs_out) *n_pairs_out = 0;
   if (d < 1 || d > 4) return set_error(CPPGB_ERR_ARG, "frnn_query_shard needs 1 <= d <= 4 (the grid path)");
   if (nshards < 1 || nshards > 65536 || shard < 0 || shard >= nshards)
     return set_error(CPPGB_ERR_ARG, "need 0 <= shard < nshards <= 65536");
-  return frnn_common(pts, n, d, ld, R, row_ptr, cols, cols_cap, n_pairs_out, ws, ws_bytes, stream, shard, nshards);
+  return frnn_common(pts, n, d, ld, R, row_ptr, cols, cols_cap, out, ws, ws_bytes, stream, shard, nshards);
 }
 
 }  // extern "C"

@@ -22,9 +22,11 @@ template <bool RADIUS>
 __global__ void __launch_bounds__(NT, 2)
     gram_simt_kernel(const float* __restrict__ X, int64_t n, int64_t Kp, int64_t excl, int64_t delta,
                      const float* __restrict__ norms, DenseScalars* sc,
-                     Candidate* __restrict__ cand, int64_t cap, float rr, int64_t shard, int64_t nshards) {
+                     Candidate* __restrict__ cand, int64_t cap, float rr, int64_t shard, int64_t nshards,
+                     const unsigned int* __restrict__ gate) {
   __shared__ __align__(16) TileSmem sm;
   __shared__ float red[NT / 32];
+  if (gate && *gate == 0u) return;  // a second pass that is not needed
 
   int64_t bi, bj;
   tri_decode((int64_t)blockIdx.x * nshards + shard, delta, &bi, &bj);
@@ -95,7 +97,8 @@ __global__ void __launch_bounds__(NT, 2)
 
 template <bool RADIUS>
 static int launch_simt(const float* X, int64_t n, int64_t Kp, int64_t excl, const float* norms, DenseScalars* sc,
-                       Candidate* cand, int64_t cap, float rr, cudaStream_t st, int64_t shard, int64_t nshards) {
+                       Candidate* cand, int64_t cap, float rr, cudaStream_t st, int64_t shard, int64_t nshards,
+                       const unsigned int* gate) {
   if (Kp % BK) return set_error(CPPGB_ERR_ARG, "internal: Kp %% 16 != 0");
   const int64_t nb = (n + BM - 1) / BM;
   // smallest block offset whose tiles hold a pair with j - i >= excl
@@ -106,19 +109,20 @@ static int launch_simt(const float* X, int64_t n, int64_t Kp, int64_t excl, cons
   if (tiles <= 0) return CPPGB_OK;
   if (tiles > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "too many tiles (%lld)", (long long)tiles);
   gram_simt_kernel<RADIUS><<<(unsigned)tiles, NT, 0, st>>>(X, n, Kp, excl, delta, norms, sc, cand, cap, rr,
-                                                                   shard, nshards);
+                                                                   shard, nshards, gate);
   CPPGB_LAUNCH_CHECK();
   return CPPGB_OK;
 }
 
 int launch_gram_simt(const float* X, int64_t n, int64_t Kp, int64_t excl, const float* norms, DenseScalars* sc,
-                     Candidate* cand, int64_t cap, cudaStream_t st, int64_t shard, int64_t nshards) {
-  return launch_simt<false>(X, n, Kp, excl, norms, sc, cand, cap, 0.f, st, shard, nshards);
+                     Candidate* cand, int64_t cap, cudaStream_t st, int64_t shard, int64_t nshards,
+                     const unsigned int* gate) {
+  return launch_simt<false>(X, n, Kp, excl, norms, sc, cand, cap, 0.f, st, shard, nshards, gate);
 }
 
 int launch_gram_simt_radius(const float* X, int64_t n, int64_t Kp, const float* norms, DenseScalars* sc,
                             Candidate* cand, int64_t cap, float rr, cudaStream_t st) {
-  return launch_simt<true>(X, n, Kp, 1, norms, sc, cand, cap, rr, st, 0, 1);
+  return launch_simt<true>(X, n, Kp, 1, norms, sc, cand, cap, rr, st, 0, 1, nullptr);
 }
 
 }  // namespace cppgb

@@ -273,7 +273,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                    uint32_t ab_fmt, const float* __restrict__ norms, DenseScalars* sc, Candidate* __restrict__ cand,
                    int64_t cap, int64_t kchunks, int64_t shard, int64_t nshards, const int32_t* __restrict__ tlist,
                    const int64_t* __restrict__ tcount, const int32_t* __restrict__ perm, int64_t excl_orig,
-                   float* __restrict__ dump) {
+                   float* __restrict__ dump, const unsigned int* __restrict__ gate) {
+  if (gate && *gate == 0u) return;  // a second pass that is not needed (before any set-up)
   // the tiles: k < total of this shard (t = k * nshards + shard), or the entries of a pruned list
   const int64_t total = tcount ? *tcount : total_arg;
   extern __shared__ uint8_t smem_raw[];
@@ -517,7 +518,7 @@ int launch_gram_tc_prune_list(int64_t n, int64_t n_pad, int64_t excl, const floa
 int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp, int64_t excl, const float* norms,
                    DenseScalars* sc, Candidate* cand, int64_t cap, cudaStream_t st, int64_t shard, int64_t nshards,
                    const int32_t* tlist, const int64_t* tcount, const int32_t* perm, int64_t excl_orig,
-                   float* dump, int64_t dump_tiles) {
+                   float* dump, int64_t dump_tiles, const unsigned int* gate) {
   if (Kp % BK || n_pad % BN) return set_error(CPPGB_ERR_ARG, "internal: tensor-core stage needs Kp %% 64 == 0");
   if (((uintptr_t)X & 15) != 0) return set_error(CPPGB_ERR_ARG, "internal: row matrix must be 16-byte aligned");
   if (n_pad > 0x7fffffffLL || Kp > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "problem too large for TMA coordinates");
@@ -551,17 +552,18 @@ int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp
         cudaFuncSetAttribute(gram_tc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t g = dump_tiles < sms ? dump_tiles : sms;
     gram_tc_kernel<false, true><<<(unsigned)g, NTHREADS, smem, st>>>(
-        tmap, ts, dump_tiles, ab, norms, sc, cand, cap, Kp / BK, 0, 1, tlist, nullptr, nullptr, 1, dump);
+        tmap, ts, dump_tiles, ab, norms, sc, cand, cap, Kp / BK, 0, 1, tlist, nullptr, nullptr, 1, dump, nullptr);
   } else if (perm) {
     CPPGB_CUDA_TRY(
         cudaFuncSetAttribute(gram_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     gram_tc_kernel<true, false><<<(unsigned)grid, NTHREADS, smem, st>>>(
-        tmap, ts, total, ab, norms, sc, cand, cap, Kp / BK, shard, nshards, tlist, tcount, perm, excl_orig, nullptr);
+        tmap, ts, total, ab, norms, sc, cand, cap, Kp / BK, shard, nshards, tlist, tcount, perm, excl_orig, nullptr,
+        gate);
   } else {
     CPPGB_CUDA_TRY(
         cudaFuncSetAttribute(gram_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     gram_tc_kernel<false, false><<<(unsigned)grid, NTHREADS, smem, st>>>(
-        tmap, ts, total, ab, norms, sc, cand, cap, Kp / BK, shard, nshards, tlist, tcount, nullptr, 1, nullptr);
+        tmap, ts, total, ab, norms, sc, cand, cap, Kp / BK, shard, nshards, tlist, tcount, nullptr, 1, nullptr, gate);
   }
   CPPGB_LAUNCH_CHECK();
   return CPPGB_OK;

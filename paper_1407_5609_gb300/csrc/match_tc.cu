@@ -546,10 +546,45 @@ TLLayout tl_layout(void* ws, int64_t S, int64_t W) {
   return L;
 }
 
+// The results on the device (copied to the caller's host struct): the Pearson score from its
+// bits, the status from the kernels' flags (1: a symbol >= sigma, 4: a timed-out wait).
+__global__ void tl_tc_result_kernel(twolocus_result* r, const unsigned int* status, int pearson) {
+  twolocus_result v = *r;
+  if (pearson && v.i >= 0) {
+    v.score_real = __longlong_as_double((long long)v.score);
+    v.score = -1;  // the Pearson measure has no integer score
+  }
+  v.status = (*status & 4u) ? CPPGB_ERR_TIMEOUT : CPPGB_OK;
+  if (v.status != CPPGB_OK) {
+    v.i = v.j = -1;
+    v.score = -1;
+    v.score_real = -1.0;
+  }
+  v.reserved = 0;
+  *r = v;
+}
+
+__global__ void ham_result_kernel(const MatchPartial* best, const unsigned int* status, int least, int64_t t,
+                                  hamming_result* out) {
+  hamming_result r;
+  r.i = r.j = -1;
+  r.mismatches = -1;
+  r.reserved = 0;
+  const unsigned int s = *status;
+  r.status = (s & 1u) ? CPPGB_ERR_ARG : (s & 4u) ? CPPGB_ERR_TIMEOUT : CPPGB_OK;
+  if (r.status == CPPGB_OK && best->i >= 0) {
+    r.i = best->i;
+    r.j = best->j;
+    r.mismatches = least ? best->key : t - best->key;
+  }
+  *out = r;
+}
+
 struct HamLayout {
   uint8_t* X;
   MatchPartial *partials, *best;
   unsigned int* status;
+  hamming_result* res;
   size_t bytes;
 };
 
@@ -561,6 +596,7 @@ HamLayout ham_layout(void* ws, int64_t n, int64_t K) {
   L.partials = c.take<MatchPartial>(1024);
   L.best = c.take<MatchPartial>(1);
   L.status = c.take<unsigned int>(1);
+  L.res = c.take<hamming_result>(1);
   L.bytes = c.bytes();
   return L;
 }
@@ -637,22 +673,9 @@ int twolocus_scan_tc_shard(const uint64_t* planes, int64_t S, int64_t W, int64_t
   int64_t np = 0;
   if ((rc = launch_match(maps, mp, L.partials, &np, L.status, st))) return rc;
   if ((rc = launch_twolocus_finish(planes, W, m_cases, m_controls, L.partials, np, L.dres, st))) return rc;
-  twolocus_result h;
-  unsigned int status = 0;
-  CPPGB_CUDA_TRY(cudaMemcpyAsync(&h, L.dres, sizeof h, cudaMemcpyDeviceToHost, st));
-  CPPGB_CUDA_TRY(cudaMemcpyAsync(&status, L.status, sizeof status, cudaMemcpyDeviceToHost, st));
-  CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
-  if (status & 4u) return set_error(CPPGB_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
-  if (mode == MATCH_TL_PEARSON && h.i >= 0) {
-    long long bits = h.score;
-    double v;
-    memcpy(&v, &bits, sizeof v);
-    h.score = -1;  // the Pearson measure has no integer score
-    h.score_real = v;
-  } else {
-    h.score_real = h.i >= 0 ? (double)h.score / ((double)m_cases * (double)m_controls) : -1.0;
-  }
-  *out = h;
+  tl_tc_result_kernel<<<1, 1, 0, st>>>(L.dres, L.status, mode == MATCH_TL_PEARSON ? 1 : 0);
+  CPPGB_LAUNCH_CHECK();
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(out, L.dres, sizeof *out, cudaMemcpyDeviceToHost, st));
   return CPPGB_OK;
 }
 
@@ -673,6 +696,8 @@ int hamming_pair_shard(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, in
   if (nshards < 1 || shard < 0 || shard >= nshards) return set_error(CPPGB_ERR_ARG, "need 0 <= shard < nshards");
   out->i = out->j = -1;
   out->mismatches = -1;
+  out->status = CPPGB_OK;
+  out->reserved = 0;
   if (n < 0 || n > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "n out of range");
   if (t < 1 || sigma < 2 || sigma > 256 || ld < t) return set_error(CPPGB_ERR_ARG, "need t >= 1, 2 <= sigma <= 256, ld >= t");
   if (t > (1 << 23)) return set_error(CPPGB_ERR_ARG, "strings longer than 2^23 symbols are not supported");
@@ -708,18 +733,9 @@ int hamming_pair_shard(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, in
   if ((rc = launch_match(maps, mp, L.partials, &np, L.status, st))) return rc;
   match_finish_kernel<<<1, 256, 0, st>>>(L.partials, np, L.best);
   CPPGB_LAUNCH_CHECK();
-  MatchPartial b;
-  unsigned int status = 0;
-  CPPGB_CUDA_TRY(cudaMemcpyAsync(&b, L.best, sizeof b, cudaMemcpyDeviceToHost, st));
-  CPPGB_CUDA_TRY(cudaMemcpyAsync(&status, L.status, sizeof status, cudaMemcpyDeviceToHost, st));
-  CPPGB_CUDA_TRY(cudaStreamSynchronize(st));
-  if (status & 1u) return set_error(CPPGB_ERR_ARG, "a symbol is >= sigma");
-  if (status & 4u) return set_error(CPPGB_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
-  if (b.i >= 0) {
-    out->i = b.i;
-    out->j = b.j;
-    out->mismatches = least ? b.key : t - b.key;
-  }
+  ham_result_kernel<<<1, 1, 0, st>>>(L.best, L.status, least ? 1 : 0, t, L.res);
+  CPPGB_LAUNCH_CHECK();
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(out, L.res, sizeof *out, cudaMemcpyDeviceToHost, st));
   return CPPGB_OK;
 }
 

@@ -637,6 +637,8 @@ int mlba_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, 
   out->i = out->j = -1;
   out->mismatches = -1;
   out->candidates = 0;
+  out->status = CPPGB_OK;
+  out->reserved = 0;
   least = least ? 1 : 0;
   if (n < 0 || t < 1 || sigma < 2 || sigma > 256 || ld < t || iters < 0)
     return set_error(CPPGB_ERR_ARG, "need n >= 0, t >= 1, 2 <= sigma <= 256, ld >= t, iters >= 0");
@@ -709,8 +711,10 @@ int mlba_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, 
     }
     set_stage_times(ms, 4);
   }
-  if (status & 1u) return set_error(CPPGB_ERR_ARG, "a symbol is >= sigma");
-  if (status & 2u) return set_error(CPPGB_ERR_ARG, "a sampled column is out of range");
+  if (status & 3u) {
+    out->status = CPPGB_ERR_ARG;
+    return set_error(CPPGB_ERR_ARG, (status & 1u) ? "a symbol is >= sigma" : "a sampled column is out of range");
+  }
   out->i = o.i;
   out->j = o.j;
   out->mismatches = o.h;

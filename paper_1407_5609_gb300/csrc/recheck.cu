@@ -32,19 +32,20 @@ __device__ __forceinline__ int64_t live_count(const DenseScalars* sc, int64_t ca
 template <class Getter>
 __device__ void recheck_body(Getter get, DenseScalars* sc, const Candidate* __restrict__ cand,
                              int64_t cap, double* __restrict__ d2buf) {
-  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= live_count(sc, cap)) return;
+  const int64_t live = live_count(sc, cap);
   const float th = theta_of(__uint_as_float(sc->U_bits), sc->bp);
-  Candidate cd = cand[c];
-  if (!(cd.d2f <= th) || !(cd.d2f < __int_as_float(0x7f800000))) {
-    d2buf[c] = -1.0;
-    return;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < live; c += (int64_t)gridDim.x * blockDim.x) {
+    const Candidate cd = cand[c];
+    if (!(cd.d2f <= th) || !(cd.d2f < __int_as_float(0x7f800000))) {
+      d2buf[c] = -1.0;
+      continue;
+    }
+    const double s = get(cd.i, cd.j);
+    d2buf[c] = s;
+    atomicMin(&sc->best_bits, (unsigned long long)__double_as_longlong(s));
+    atomicAdd(&sc->n_rech, 1ull);
+    atomic_max_nonneg(&sc->ferr_bits, (float)fabs(__dsub_rn(s, (double)cd.d2f)));
   }
-  double s = get(cd.i, cd.j);
-  d2buf[c] = s;
-  atomicMin(&sc->best_bits, (unsigned long long)__double_as_longlong(s));
-  atomicAdd(&sc->n_rech, 1ull);
-  atomic_max_nonneg(&sc->ferr_bits, (float)fabs(__dsub_rn(s, (double)cd.d2f)));
 }
 
 template <class Src>
@@ -65,12 +66,13 @@ constexpr int RW = 4, RCH = 512, RGRID = 152 * 16;
 
 __global__ void screen_lmers_kernel(DenseScalars* sc, const Candidate* __restrict__ cand, int64_t cap,
                                     double* __restrict__ d2buf, int32_t* __restrict__ surv) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= live_count(sc, cap)) return;
+  const int64_t live = live_count(sc, cap);
   const float th = theta_of(__uint_as_float(sc->U_bits), sc->bp);
-  const float d2f = cand[c].d2f;
-  if (d2f <= th && d2f < __int_as_float(0x7f800000)) surv[atomicAdd(&sc->n_surv, 1u)] = (int32_t)c;
-  else d2buf[c] = -1.0;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < live; c += (int64_t)gridDim.x * blockDim.x) {
+    const float d2f = cand[c].d2f;
+    if (d2f <= th && d2f < __int_as_float(0x7f800000)) surv[atomicAdd(&sc->n_surv, 1u)] = (int32_t)c;
+    else d2buf[c] = -1.0;
+  }
 }
 
 // sum_k t_k in index order, the terms written by `term` (all lanes) into buf[q], RCH at a time;
@@ -136,14 +138,50 @@ __global__ void __launch_bounds__(32 * RW) recheck_lmers_kernel(const float* __r
 // Pass B: among the survivors at the minimal d^2, the lexicographically smallest (i, j).
 __global__ void argmin_pair_kernel(DenseScalars* sc, const Candidate* __restrict__ cand, int64_t cap,
                                    const double* __restrict__ d2buf) {
-  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= live_count(sc, cap)) return;
-  double s = d2buf[c];
-  if (s < 0.0) return;
-  if ((unsigned long long)__double_as_longlong(s) == sc->best_bits) {
-    Candidate cd = cand[c];
-    atomicMin(&sc->best_ij, ((unsigned long long)(uint32_t)cd.i << 32) | (uint32_t)cd.j);
+  const int64_t live = live_count(sc, cap);
+  const unsigned long long best = sc->best_bits;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < live; c += (int64_t)gridDim.x * blockDim.x) {
+    const double s = d2buf[c];
+    if (s < 0.0) continue;
+    if ((unsigned long long)__double_as_longlong(s) == best) {
+      const Candidate cd = cand[c];
+      atomicMin(&sc->best_ij, ((unsigned long long)(uint32_t)cd.i << 32) | (uint32_t)cd.j);
+    }
   }
+}
+
+__global__ void pass2_gate_kernel(DenseScalars* sc, int64_t cap) {
+  const bool redo = sc->status == 0u && (int64_t)sc->n_cand > cap;
+  sc->redo = redo ? 1u : 0u;
+  if (redo) sc->n_cand = 0ull;  // the bound U is final now; the second pass emits against it
+}
+
+__global__ void dense_result_kernel(const DenseScalars* sc, int64_t cap, const int64_t* tcount, int64_t tiles_total,
+                                    cpp_pair_result* res) {
+  cpp_pair_result r;
+  const unsigned int st = sc->status;
+  r.status = (st & 3u) ? CPPGB_ERR_NUMERIC : (st & 4u) ? CPPGB_ERR_TIMEOUT
+             : (int64_t)sc->n_cand > cap ? CPPGB_ERR_CAPACITY : CPPGB_OK;
+  const double best = __longlong_as_double((long long)sc->best_bits);
+  if (r.status != CPPGB_OK || sc->best_ij == ~0ull || !(best < __longlong_as_double(0x7ff0000000000000ll))) {
+    r.i = r.j = -1;
+    r.dist = r.dist2 = __longlong_as_double(0x7ff0000000000000ll);
+  } else {
+    r.i = (int64_t)(sc->best_ij >> 32);
+    r.j = (int64_t)(sc->best_ij & 0xffffffffu);
+    r.dist2 = best;
+    r.dist = __dsqrt_rn(best);
+  }
+  r.filter_err = (double)__uint_as_float(sc->ferr_bits);
+  r.filter_bound = (double)__uint_as_float(sc->U_bits);
+  r.n_emitted = (int64_t)sc->n_cand;
+  r.n_rechecked = (int64_t)sc->n_rech;
+  r.filter_e_acc = (double)sc->bp.e_acc;
+  r.filter_eps = (double)sc->bp.eps_pair;
+  r.tiles_kept = tcount ? *tcount : -1;
+  r.tiles_total = tcount ? tiles_total : -1;
+  r.reserved = 0;
+  *res = r;
 }
 
 __global__ void init_scalars_kernel(DenseScalars* sc) {
@@ -160,6 +198,8 @@ __global__ void init_scalars_kernel(DenseScalars* sc) {
   z.best_ij = ~0ull;
   z.ferr_bits = 0u;
   z.n_surv = 0u;
+  z.redo = 0u;
+  z.pad = 0u;
   *sc = z;
 }
 
@@ -183,35 +223,49 @@ int launch_bounds(DenseScalars* sc, float kappa, cudaStream_t st) {
   return CPPGB_OK;
 }
 
-static int finish(DenseScalars* sc, const Candidate* cand, int64_t cap, double* d2buf, int64_t blocks,
-                  cudaStream_t st) {
-  argmin_pair_kernel<<<(unsigned)blocks, 128, 0, st>>>(sc, cand, cap, d2buf);
+constexpr unsigned RB = 128, RBLOCKS = 152 * 8;  // grid-stride candidate kernels
+
+static unsigned cand_blocks(int64_t cap) {
+  const int64_t b = (cap + RB - 1) / RB;
+  return (unsigned)(b < RBLOCKS ? (b > 0 ? b : 1) : RBLOCKS);
+}
+
+int launch_recheck_points(const void* pts, int dtype, int64_t d, int64_t ld, DenseScalars* sc,
+                          const Candidate* cand, int64_t cap, double* d2buf, cudaStream_t st) {
+  const unsigned blocks = cand_blocks(cap);
+  if (dtype == CPPGB_F64)
+    recheck_points_kernel<double><<<blocks, RB, 0, st>>>((const double*)pts, d, ld, sc, cand, cap, d2buf);
+  else
+    recheck_points_kernel<float><<<blocks, RB, 0, st>>>((const float*)pts, d, ld, sc, cand, cap, d2buf);
+  CPPGB_LAUNCH_CHECK();
+  argmin_pair_kernel<<<blocks, RB, 0, st>>>(sc, cand, cap, d2buf);
   CPPGB_LAUNCH_CHECK();
   return CPPGB_OK;
 }
 
-int launch_recheck_points(const void* pts, int dtype, int64_t d, int64_t ld, DenseScalars* sc,
-                          const Candidate* cand, int64_t cap, double* d2buf, int64_t n_live, cudaStream_t st) {
-  const int64_t blocks = (n_live + 127) / 128;
-  if (blocks == 0) return CPPGB_OK;
-  if (dtype == CPPGB_F64)
-    recheck_points_kernel<double><<<(unsigned)blocks, 128, 0, st>>>((const double*)pts, d, ld, sc, cand, cap, d2buf);
-  else
-    recheck_points_kernel<float><<<(unsigned)blocks, 128, 0, st>>>((const float*)pts, d, ld, sc, cand, cap, d2buf);
+int launch_recheck_lmers(const float* series, int64_t l, DenseScalars* sc, int32_t* surv, const Candidate* cand,
+                         int64_t cap, double* d2buf, cudaStream_t st) {
+  const unsigned blocks = cand_blocks(cap);
+  screen_lmers_kernel<<<blocks, RB, 0, st>>>(sc, cand, cap, d2buf, surv);
   CPPGB_LAUNCH_CHECK();
-  return finish(sc, cand, cap, d2buf, blocks, st);
+  recheck_lmers_kernel<<<RGRID, 32 * RW, 0, st>>>(series, l, sc, cand, surv, d2buf);
+  CPPGB_LAUNCH_CHECK();
+  argmin_pair_kernel<<<blocks, RB, 0, st>>>(sc, cand, cap, d2buf);
+  CPPGB_LAUNCH_CHECK();
+  return CPPGB_OK;
 }
 
-int launch_recheck_lmers(const float* series, int64_t l, DenseScalars* sc, int32_t* surv, const Candidate* cand,
-                         int64_t cap, double* d2buf, int64_t n_live, cudaStream_t st) {
-  if (n_live <= 0) return CPPGB_OK;
-  const int64_t blocks = (n_live + 127) / 128;
-  screen_lmers_kernel<<<(unsigned)blocks, 128, 0, st>>>(sc, cand, cap, d2buf, surv);
+int launch_pass2_gate(DenseScalars* sc, int64_t cap, cudaStream_t st) {
+  pass2_gate_kernel<<<1, 1, 0, st>>>(sc, cap);
   CPPGB_LAUNCH_CHECK();
-  const int64_t want = (n_live + RW - 1) / RW;  // at most one survivor per warp is ever needed
-  recheck_lmers_kernel<<<(unsigned)(want < RGRID ? want : RGRID), 32 * RW, 0, st>>>(series, l, sc, cand, surv, d2buf);
+  return CPPGB_OK;
+}
+
+int launch_dense_result(const DenseScalars* sc, int64_t cap, const int64_t* tcount, int64_t tiles_total,
+                        cpp_pair_result* res, cudaStream_t st) {
+  dense_result_kernel<<<1, 1, 0, st>>>(sc, cap, tcount, tiles_total, res);
   CPPGB_LAUNCH_CHECK();
-  return finish(sc, cand, cap, d2buf, blocks, st);
+  return CPPGB_OK;
 }
 
 }  // namespace cppgb

@@ -160,6 +160,9 @@ __global__ void __launch_bounds__(NT)
     if (tid == 0) {
       out->i = -1; out->j = -1; out->score = -1;
       for (int q = 0; q < 9; ++q) { out->countsA[q] = 0; out->countsB[q] = 0; }
+      out->score_real = -1.0;
+      out->status = CPPGB_OK;
+      out->reserved = 0;
     }
     return;
   }
@@ -180,6 +183,9 @@ __global__ void __launch_bounds__(NT)
   __syncthreads();
   if (tid == 0) {
     out->i = b.i; out->j = b.j; out->score = b.score;
+    out->score_real = (double)b.score / ((double)m1 * (double)m2);  // |P_A - P_B| of the match measure
+    out->status = CPPGB_OK;
+    out->reserved = 0;
     for (int g = 0; g < 2; ++g) {
       const long long m = g == 0 ? m1 : m2;
       const long long n11 = cnt[g][0], n12 = cnt[g][1], n21 = cnt[g][2], n22 = cnt[g][3];

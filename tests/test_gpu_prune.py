@@ -25,7 +25,7 @@ def test_tsmm_pruned_exact(mode, N, l, excl, seed):
     a = synth.make_random_walk(N, seed=seed)
     s = to_dev(a, device())
     r = capi.tsmm_motif(s, l, excl, mode=mode)
-    kept, total = capi.cpp_prune_stats()
+    kept, total = r["tiles_kept"], r["tiles_total"]
     oi, oj, od2 = oracle.tsmm(a, l, excl)
     assert (r["i"], r["j"], r["dist2"]) == (oi, oj, od2)
     assert 0 < kept <= total
@@ -36,11 +36,11 @@ def test_tsmm_pruning_skips_tiles_on_a_random_walk():
     a = synth.make_random_walk(65536, seed=123)
     s = to_dev(a, device())
     r = capi.tsmm_motif(s, 512, 256, mode="filter_bf16_prune")
-    kept, total = capi.cpp_prune_stats()
+    kept, total = r["tiles_kept"], r["tiles_total"]
     full = capi.tsmm_motif(s, 512, 256, mode="filter_bf16")
     assert (r["i"], r["j"], r["dist2"]) == (full["i"], full["j"], full["dist2"])
     assert kept < total            # the reference bound excludes part of the tiles
-    assert capi.cpp_prune_stats() == (-1, -1)  # the unpruned call reports no pruning
+    assert (full["tiles_kept"], full["tiles_total"]) == (-1, -1)  # the unpruned call reports no pruning
 
 
 @pytest.mark.parametrize("kind", ["uniform", "clusters", "ties", "small"])
