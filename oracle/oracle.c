@@ -489,7 +489,8 @@ int oracle_twolocus_rows(const int8_t* g, int64_t S, int64_t m1, int64_t m2, con
 /* ------------------------------------------------------------------ Pearson two-locus */
 /* Pearson's r of the genotype values (0, 1, 2) of SNPs i and j over the subjects [lo, hi):
  * r = (m Sxy - Sx Sy) / sqrt(vx vy), vx = m Sxx - Sx^2, vy = m Syy - Sy^2, all sums exact in
- * integers; vx vy is exact in FP64 (below 2^53 for m < 2^20); 0 when vx or vy is 0. */
+ * integers (vx and vy each exact in FP64); their product vx vy, which can exceed 2^53, is one
+ * rounded FP64 multiplication, followed by the square root and the division; 0 when vx or vy is 0. */
 static double pearson_of(const int8_t* gi, const int8_t* gj, int64_t lo, int64_t hi) {
   int64_t sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0, m = hi - lo;
   for (int64_t t = lo; t < hi; ++t) {

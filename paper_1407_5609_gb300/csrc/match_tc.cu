@@ -1,8 +1,10 @@
 // Exact match counts of categorical rows on the tensor cores.
 //
-// Two rows of symbols are compared through the dot products of 0/1/2-valued encodings (BF16, exact),
-// accumulated in FP32 on tcgen05: every product and every partial sum is an integer below 2^24, so
-// the accumulators hold the exact integer counts.
+// Two rows of symbols are compared through the dot products of small-integer encodings: FP8 (E4M3)
+// operands with values in {0, 1, 2, 4} (all exact in E4M3), tcgen05.mma kind::f8f6f4 accumulating in
+// FP32.  Every product is at most 16 and every partial sum at most 16 m < 2^24 -- the entry points
+// reject groups of 2^20 or more subjects (and strings of more than 2^23 positions) -- so the
+// accumulators hold the exact integer counts.
 //
 //  * Two-locus (Sec. 6) with the one-hot planes of Sec. 5.3 (a = [g_i = 1], b = [g_i = 2],
 //    c = [g_j = 1], d = [g_j = 2] per subject): the number of subjects whose genotypes match is
@@ -16,9 +18,10 @@
 //    with the most (fewest) matches is the closest (least correlated) pair under the Hamming distance.
 //
 // Kernel: one persistent CTA per SM over the 128 x 128 tiles (bi <= bj) of the upper triangle; warp
-// 0 loads K-chunks of the left and right rows with TMA (6 stages), warp 1 issues the MMAs into one
-// 128-column TMEM accumulator per group (two tiles in flight), warps 2-5 turn each pair's counts into
-// a 64-bit key (larger is better, ties to the smaller (i, j)) and keep the best per CTA.
+// 0 loads K-chunks of the left and right rows with TMA (6 stages of 32 KB), warp 1 issues the MMAs
+// into 128-column TMEM accumulators (four tiles in flight with one group, two with two groups), and
+// eight epilogue warps (two per TMEM lane quarter, each on half the columns) turn each pair's counts
+// into a 64-bit key (larger is better, ties to the smaller (i, j)) and keep the best per CTA.
 #include <cuda_bf16.h>
 
 #include <cstring>
