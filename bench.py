@@ -860,6 +860,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     build.build()
+    if args.dense_shape:
+        capi.cpp_set_tuning(capi.TUNE_DENSE_SHAPE, [args.dense_shape])
     wl = WORKLOADS[args.workload](args)
     wl.setup(dev)
     mode = args.mode or ("filter_bf16" if capi.filters_available() else "plain_fp32")
@@ -954,6 +956,9 @@ def main():
                          "two-locus and batch workloads)")
     ap.add_argument("--batch-path", type=int, choices=[0, 1, 2], default=0,
                     help="batch tiles: 0 the tuned policy, 1 FP32 CUDA-core tiles, 2 tensor-core tiles")
+    ap.add_argument("--dense-shape", type=int, choices=[1, 2], default=None,
+                    help="tile of the tensor-core dense stage: 1 = 128 x 256 on one SM, 2 = 256 x 256 on a CTA pair "
+                         "(default: the library's policy)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the library's built-in tile policy instead of the autotuner's (e.g. under a profiler)")
     args = ap.parse_args()

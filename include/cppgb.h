@@ -422,11 +422,17 @@ int cpp_set_fault_injection(int kind);
  *                          d-class: ceil(d / 64) - 1.  Default: all 2 when the tensor-core kernels exist.
  *   CPPGB_TUNE_DENSE_BAND  values = int32 [1]: column blocks per band of the tensor-core dense stage's
  *                          tile order (1 .. 4096; 0 from cpp_get_tuning means the built-in 16).
+ *   CPPGB_TUNE_DENSE_SHAPE values = int32 [1]: tile of the tensor-core dense stage (unpruned searches):
+ *                          1 = 128 x 256 on one SM (M = 128 MMAs), 2 = 256 x 256 on a cluster of two SMs
+ *                          (tcgen05 cta_group::2, M = 256 MMAs; each SM loads half of the column
+ *                          block).  Default 1 (measured faster on GB300: the single-SM tiles run at the
+ *                          same tensor-pipe occupancy with less synchronisation).
  * Both return CPPGB_ERR_ARG for an unknown kind, a short array or an invalid entry; the choice only
  * changes speed, never a result.
  */
 #define CPPGB_TUNE_BATCH_PATH 1
 #define CPPGB_TUNE_DENSE_BAND 2
+#define CPPGB_TUNE_DENSE_SHAPE 3
 int cpp_set_tuning(int kind, const int32_t* values, int count);
 int cpp_get_tuning(int kind, int32_t* values, int count);
 

@@ -10,8 +10,9 @@ Candidates:
 
 * batch tiles per (n-bucket, d-class) -- FP32 CUDA-core 128 x 128 tiles (path 1) or BF16 tcgen05
   128 x 256 tiles with the norms folded into the MMA (path 2);
-* the tensor-core dense stage (closest pair, motif search) -- column blocks per band of its tile
-  order, which sets how much of the B panel set stays in L2.
+* the tensor-core dense stage (closest pair, motif search) -- the tile shape (128 x 256 on one SM,
+  or 256 x 256 on a cluster of two SMs with tcgen05 cta_group::2) and the column blocks per band of
+  its tile order, which sets how much of the B panel set stays in L2.
 
 The cache lives in ``$CPPGB_TUNE_CACHE`` or else ``$XDG_CACHE_HOME/cppgb/tune.json``
 (``~/.cache/cppgb/tune.json``).
@@ -32,7 +33,8 @@ N_BUCKETS = ((256, 1023), (1024, 4095), (4096, 16383), (16384, 65536))
 D_CLASSES = ((1, 64), (65, 128), (129, 192), (193, 256))
 D_SAMPLES = ((16, 64), (96, 128), (160, 192), (224, 256))  # dimensions timed per class
 BANDS = (8, 16, 32, 64)
-CACHE_VERSION = 1
+SHAPES = (1, 2)  # dense-stage tiles: 1 = 128 x 256 on one SM, 2 = 256 x 256 on a CTA pair
+CACHE_VERSION = 2
 
 
 # ---------------------------------------------------------------- pure selection logic
@@ -54,6 +56,11 @@ def path_for(table, n: int, d: int) -> int:
 def choose_band(ms: dict) -> int:
     """ms[band] = time -> the fastest band (ties: the smaller band)."""
     return min(sorted(ms), key=lambda b: ms[b])
+
+
+def choose_dense(ms: dict) -> tuple:
+    """ms[(shape, band)] = time -> the fastest (shape, band) (ties: the smaller shape, then band)."""
+    return min(sorted(ms), key=lambda k: ms[k])
 
 
 def cache_path() -> str:
@@ -99,6 +106,8 @@ def install(entry: dict) -> None:
         capi.cpp_set_tuning(capi.TUNE_BATCH_PATH, np.asarray(entry["batch_path"], dtype=np.int32))
     if "dense_band" in entry:
         capi.cpp_set_tuning(capi.TUNE_DENSE_BAND, [int(entry["dense_band"])])
+    if "dense_shape" in entry:
+        capi.cpp_set_tuning(capi.TUNE_DENSE_SHAPE, [int(entry["dense_shape"])])
 
 
 # ---------------------------------------------------------------- measurements (GPU)
@@ -159,22 +168,28 @@ def measure_batch(target_pairs: float = 2e9, reps: int = 3, cells=None) -> dict:
     return ms
 
 
-def measure_dense_band(N: int = 131072, l: int = 512, excl: int = 256, reps: int = 3) -> dict:
+def measure_dense(N: int = 131072, l: int = 512, excl: int = 256, reps: int = 3) -> dict:
+    """ms[(shape, band)] of a motif search of N samples (the dense stage dominates it)."""
     import torch
     if not capi.filters_available():
         return {}
     dev = torch.device("cuda", torch.cuda.current_device())
     series = torch.from_numpy(synth.make_random_walk(N=N, seed=1100).astype(np.float32)).to(dev)
     ws = capi._workspace(capi.tsmm_motif_workspace_size(N, l, "filter_bf16"), dev)
-    before = capi.cpp_get_tuning(capi.TUNE_DENSE_BAND)
+    before_band = capi.cpp_get_tuning(capi.TUNE_DENSE_BAND)
+    before_shape = capi.cpp_get_tuning(capi.TUNE_DENSE_SHAPE)
     ms = {}
     try:
-        for band in BANDS:
-            capi.cpp_set_tuning(capi.TUNE_DENSE_BAND, [band])
-            ms[band] = _time_ms(lambda: capi.tsmm_motif(series, l, excl, mode="filter_bf16", ws=ws), reps)
+        for shape in SHAPES:
+            capi.cpp_set_tuning(capi.TUNE_DENSE_SHAPE, [shape])
+            for band in BANDS:
+                capi.cpp_set_tuning(capi.TUNE_DENSE_BAND, [band])
+                ms[(shape, band)] = _time_ms(lambda: capi.tsmm_motif(series, l, excl, mode="filter_bf16", ws=ws),
+                                             reps)
     finally:
-        if before[0] > 0:
-            capi.cpp_set_tuning(capi.TUNE_DENSE_BAND, before)
+        if before_band[0] > 0:
+            capi.cpp_set_tuning(capi.TUNE_DENSE_BAND, before_band)
+        capi.cpp_set_tuning(capi.TUNE_DENSE_SHAPE, before_shape)
     return ms
 
 
@@ -185,10 +200,10 @@ def tune(batch: bool = True, dense: bool = True, target_pairs: float = 2e9, reps
         entry["batch_path"] = choose_batch_table(ms)
         entry["batch_ms"] = {f"{nb},{dc}": {"fp32": t[1], "tc": t[2]} for (nb, dc), t in sorted(ms.items())}
     if dense:
-        ms = measure_dense_band(reps=reps)
+        ms = measure_dense(reps=reps)
         if ms:
-            entry["dense_band"] = choose_band(ms)
-            entry["dense_ms"] = {str(b): t for b, t in sorted(ms.items())}
+            entry["dense_shape"], entry["dense_band"] = choose_dense(ms)
+            entry["dense_ms"] = {f"{sh},{b}": t for (sh, b), t in sorted(ms.items())}
     return entry
 
 
@@ -199,7 +214,7 @@ def load_or_tune(batch: bool = True, dense: bool = True, force: bool = False, pa
     data = load_cache(path)
     entry = dict(data["entries"].get(key, {}))
     need_batch = batch and (force or "batch_path" not in entry)
-    need_dense = dense and (force or "dense_band" not in entry)
+    need_dense = dense and (force or "dense_band" not in entry or "dense_shape" not in entry)
     if need_batch or need_dense:
         entry.update(tune(batch=need_batch, dense=need_dense, **kw))
         data["entries"][key] = entry

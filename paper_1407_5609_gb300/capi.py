@@ -230,12 +230,12 @@ def cpp_set_fault_injection(kind: int) -> None:
     _raise(lib().cpp_set_fault_injection(int(kind)))
 
 
-TUNE_BATCH_PATH, TUNE_DENSE_BAND = 1, 2
-TUNE_SIZES = {TUNE_BATCH_PATH: 16, TUNE_DENSE_BAND: 1}
+TUNE_BATCH_PATH, TUNE_DENSE_BAND, TUNE_DENSE_SHAPE = 1, 2, 3
+TUNE_SIZES = {TUNE_BATCH_PATH: 16, TUNE_DENSE_BAND: 1, TUNE_DENSE_SHAPE: 1}
 
 
 def cpp_set_tuning(kind: int, values) -> None:
-    """Install a tuning table (see include/cppgb.h): 16 batch paths or one dense band."""
+    """Install a tuning table (see include/cppgb.h): 16 batch paths, one dense band or one dense tile shape."""
     vals = [int(v) for v in np.asarray(values).reshape(-1)]
     arr = (ctypes.c_int32 * max(len(vals), 1))(*vals)
     _raise(lib().cpp_set_tuning(int(kind), arr, len(vals)))

@@ -16,6 +16,7 @@ static std::atomic<int> g_timing{0};
 // tuning policy: batch path per (n-bucket, d-class), tensor-core dense band (0: the launcher's default)
 static std::atomic<int> g_batch_path[TUNE_NB * TUNE_DC];
 static std::atomic<int> g_dense_band{0};
+static std::atomic<int> g_dense_shape{1};
 static std::atomic<int> g_tuning_init{0};
 
 static void init_tuning() {
@@ -41,6 +42,7 @@ int tuned_batch_path(int64_t n, int d) {
 }
 
 int tuned_dense_band() { return g_dense_band.load(); }
+int tuned_dense_shape() { return g_dense_shape.load(); }
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -324,6 +326,12 @@ int cpp_set_tuning(int kind, const int32_t* values, int count) {
     g_dense_band.store(values[0]);
     return CPPGB_OK;
   }
+  if (kind == CPPGB_TUNE_DENSE_SHAPE) {
+    if (!values || count != 1 || (values[0] != 1 && values[0] != 2))
+      return set_error(CPPGB_ERR_ARG, "dense tile shape must be one value, 1 or 2");
+    g_dense_shape.store(values[0]);
+    return CPPGB_OK;
+  }
   return set_error(CPPGB_ERR_ARG, "unknown tuning kind %d", kind);
 }
 
@@ -337,6 +345,11 @@ int cpp_get_tuning(int kind, int32_t* values, int count) {
   if (kind == CPPGB_TUNE_DENSE_BAND) {
     if (!values || count < 1) return set_error(CPPGB_ERR_ARG, "dense band needs one entry");
     values[0] = g_dense_band.load();
+    return CPPGB_OK;
+  }
+  if (kind == CPPGB_TUNE_DENSE_SHAPE) {
+    if (!values || count < 1) return set_error(CPPGB_ERR_ARG, "dense tile shape needs one entry");
+    values[0] = g_dense_shape.load();
     return CPPGB_OK;
   }
   return set_error(CPPGB_ERR_ARG, "unknown tuning kind %d", kind);

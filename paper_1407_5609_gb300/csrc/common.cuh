@@ -159,6 +159,7 @@ int set_fault_match(int on);
 constexpr int TUNE_NB = 4, TUNE_DC = 4;  // batch n-buckets (n < 1024, 4096, 16384, rest) x d-classes ceil(d / 64)
 int tuned_batch_path(int64_t n, int d);   // 1 (FP32 tiles) or 2 (tensor-core tiles)
 int tuned_dense_band();                   // column blocks per band of the tensor-core dense stage
+int tuned_dense_shape();                  // 1: 128 x 256 tiles on one CTA, 2: 256 x 256 tiles on CTA pairs
 
 // Stage timing (cpp_set_stage_timing): whether it is on, and the last call's stage durations --
 // given directly, or as intervals + 1 events recorded on the call's stream (read when asked for).

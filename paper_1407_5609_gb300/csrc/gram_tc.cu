@@ -37,6 +37,7 @@ constexpr uint32_t TMEM_COLS = 512;
 struct TileSched {
   int64_t n, excl;
   int32_t nbands, nbi, nbj, band;
+  int32_t rstep, pad;  // 128-row blocks per schedule row: 1 (one CTA) or 2 (a CTA pair)
   int64_t off[MAX_BANDS + 1];
   int32_t nfull[MAX_BANDS];
 };
@@ -73,7 +74,7 @@ __device__ __forceinline__ void decode_tile(const TileSched& ts, int64_t t, int*
   }
   r -= full;
   for (int64_t row = ts.nfull[b]; row < ts.nbi; ++row) {
-    const int64_t c = row_count(row, bj0, bj1, ts.n, ts.excl);
+    const int64_t c = row_count(row * ts.rstep, bj0, bj1, ts.n, ts.excl);
     if (r < c) {
       *bi = row;
       *bj = bj1 - c + r;
@@ -96,6 +97,73 @@ __device__ __forceinline__ void epi_init(EpiState& es, DenseScalars* sc, const B
   es.Usnap = __uint_as_float(*reinterpret_cast<volatile unsigned int*>(&sc->U_bits));
   // -inf until this thread has a finite bound, so masked (+inf) entries can never pass it
   es.th = es.Usnap < __int_as_float(0x7f800000) ? theta_of(es.Usnap, bp) : __int_as_float(0xff800000);
+}
+
+// One 32-column chunk c of a thread's accumulator row (r = the raw Gram values x~_i . x~_j).
+template <bool PERM>
+__device__ __forceinline__ void epi_chunk(const uint32_t (&r)[32], int c, int64_t i, float nx, int32_t oi,
+                                          bool edge, bool pmask, int32_t xoff, uint32_t xspan, int64_t col0,
+                                          int64_t n, int64_t excl, const float* __restrict__ norms,
+                                          const BoundParams& bp, DenseScalars* sc, Candidate* __restrict__ cand,
+                                          int64_t cap, EpiState& es, const int32_t* __restrict__ perm) {
+  const float4* ny4 = reinterpret_cast<const float4*>(norms + col0 + c * 32);
+  float dp[32];
+  float cmin = __int_as_float(0x7f800000);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 v = __ldg(ny4 + q);
+    dp[4 * q + 0] = fmaf(-2.f, __uint_as_float(r[4 * q + 0]), v.x);
+    dp[4 * q + 1] = fmaf(-2.f, __uint_as_float(r[4 * q + 1]), v.y);
+    dp[4 * q + 2] = fmaf(-2.f, __uint_as_float(r[4 * q + 2]), v.z);
+    dp[4 * q + 3] = fmaf(-2.f, __uint_as_float(r[4 * q + 3]), v.w);
+  }
+  if (edge) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const int64_t j = col0 + c * 32 + k;
+      if (!(i < n && j < n && j - i >= excl)) dp[k] = __int_as_float(0x7f800000);
+    }
+  }
+  if (PERM && pmask) {  // original indices of the chunk's columns (the same for every lane: broadcast loads)
+    const int4* pj4 = reinterpret_cast<const int4*>(perm + col0 + c * 32);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int4 o = __ldg(pj4 + q);
+      const int32_t oj[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if ((uint32_t)(oi - oj[e] + xoff) < xspan) dp[4 * q + e] = __int_as_float(0x7f800000);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 32; ++k) cmin = fminf(cmin, dp[k]);
+  const float cD = nx + cmin;
+  if (cD < es.tmin) {
+    es.tmin = cD;
+    es.th = theta_of(fminf(es.Usnap, upper_d2(es.tmin, bp)), bp);
+  }
+  if (cD <= es.th) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const float D = nx + dp[k];
+      if (D <= es.th) {
+        const unsigned long long slot = atomicAdd(&sc->n_cand, 1ull);
+        if ((int64_t)slot < cap) {
+          Candidate cd;
+          int32_t a = (int32_t)i, b = (int32_t)(col0 + c * 32 + k);
+          if (PERM) {
+            a = oi;
+            b = perm[col0 + c * 32 + k];
+          }
+          cd.i = a < b ? a : b;
+          cd.j = a < b ? b : a;
+          cd.d2f = D;
+          cd.pad = 0.f;
+          cand[slot] = cd;
+        }
+      }
+    }
+  }
 }
 
 // One thread = one accumulator row (TMEM lane) of a 128 x 256 tile: D~ = nx + (ny - 2 S) for its 256
@@ -122,64 +190,7 @@ __device__ __forceinline__ void epi_tile(int64_t row0, int64_t col0, uint32_t tb
     uint32_t r[32];
     __syncwarp();
     tmem_ld32(tbase + (uint32_t)(c * 32), r);
-    const float4* ny4 = reinterpret_cast<const float4*>(norms + col0 + c * 32);
-    float dp[32];
-    float cmin = __int_as_float(0x7f800000);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float4 v = __ldg(ny4 + q);
-      dp[4 * q + 0] = fmaf(-2.f, __uint_as_float(r[4 * q + 0]), v.x);
-      dp[4 * q + 1] = fmaf(-2.f, __uint_as_float(r[4 * q + 1]), v.y);
-      dp[4 * q + 2] = fmaf(-2.f, __uint_as_float(r[4 * q + 2]), v.z);
-      dp[4 * q + 3] = fmaf(-2.f, __uint_as_float(r[4 * q + 3]), v.w);
-    }
-    if (edge) {
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        const int64_t j = col0 + c * 32 + k;
-        if (!(i < n && j < n && j - i >= excl)) dp[k] = __int_as_float(0x7f800000);
-      }
-    }
-    if (PERM && pmask) {  // original indices of the chunk's columns (the same for every lane: broadcast loads)
-      const int4* pj4 = reinterpret_cast<const int4*>(perm + col0 + c * 32);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int4 o = __ldg(pj4 + q);
-        const int32_t oj[4] = {o.x, o.y, o.z, o.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if ((uint32_t)(oi - oj[e] + xoff) < xspan) dp[4 * q + e] = __int_as_float(0x7f800000);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 32; ++k) cmin = fminf(cmin, dp[k]);
-    const float cD = nx + cmin;
-    if (cD < es.tmin) {
-      es.tmin = cD;
-      es.th = theta_of(fminf(es.Usnap, upper_d2(es.tmin, bp)), bp);
-    }
-    if (cD <= es.th) {
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        const float D = nx + dp[k];
-        if (D <= es.th) {
-          const unsigned long long slot = atomicAdd(&sc->n_cand, 1ull);
-          if ((int64_t)slot < cap) {
-            Candidate cd;
-            int32_t a = (int32_t)i, b = (int32_t)(col0 + c * 32 + k);
-            if (PERM) {
-              a = oi;
-              b = perm[col0 + c * 32 + k];
-            }
-            cd.i = a < b ? a : b;
-            cd.j = a < b ? b : a;
-            cd.d2f = D;
-            cd.pad = 0.f;
-            cand[slot] = cd;
-          }
-        }
-      }
-    }
+    epi_chunk<PERM>(r, c, i, nx, oi, edge, pmask, xoff, xspan, col0, n, excl, norms, bp, sc, cand, cap, es, perm);
   }
 }
 
@@ -435,6 +446,197 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
+// ------------------------------------------------------------------ CTA pairs (cta_group::2)
+// A cluster of two CTAs on two SMs computes one 256 x 256 tile: CTA r holds the 128 rows of row
+// block 2 bi2 + r (A) and rows 128 r .. 128 r + 127 of the column block (its half of B), both in
+// 6 stages of 32 KB; the leader (r = 0) issues tcgen05.mma.cta_group::2 with M = 256, N = 256,
+// which reads both CTAs' halves, and each CTA's TMEM receives the 128 x 256 accumulator of its own
+// rows.  Per pair of SMs a 64-deep K step moves 64 KB from L2 for 256 x 256 x 64 MACs, against
+// 96 KB for two single-CTA 128 x 256 tiles: a third less traffic through the L2 -> SM crossbar.
+// Barriers: each CTA's copies complete on the leader's full[s] (armed by the leader for both CTAs'
+// bytes); the leader's commits arrive on both CTAs' empty[s], tfull[a] and drain; the epilogue
+// warps of both CTAs arrive on the leader's tempty[a] (count 8).  Every wait is bounded as in the
+// single-CTA kernel, and both CTAs meet in a cluster barrier before freeing TMEM and exiting.
+constexpr int P_STAGES = 6;
+constexpr int PA_BYTES = BM * BK * 2, PB_BYTES = (BN / 2) * BK * 2, P_STAGE_BYTES = PA_BYTES + PB_BYTES;
+
+struct PairCtl {
+  uint64_t full[P_STAGES], empty[P_STAGES], tfull[2], tempty[2], drain;
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+    gram_tc_pair_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TileSched ts,
+                        int64_t total, uint32_t ab_fmt, const float* __restrict__ norms, DenseScalars* sc,
+                        Candidate* __restrict__ cand, int64_t cap, int64_t kchunks, int64_t shard, int64_t nshards,
+                        const unsigned int* __restrict__ gate) {
+  if (gate && *gate == 0u) return;  // a second pass that is not needed (both CTAs of every cluster)
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  PairCtl* ctl = (PairCtl*)(smem + P_STAGES * P_STAGE_BYTES);
+  volatile int* abort_flag = &ctl->abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();
+  const int64_t cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;  // this cluster and the number of clusters
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P_STAGES; ++s) {
+      mbar_init(&ctl->full[s], 1);
+      mbar_init(&ctl->empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&ctl->tfull[a], 1);
+      mbar_init(&ctl->tempty[a], 8);
+    }
+    mbar_init(&ctl->drain, 1);
+    ctl->abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {  // one warp of each CTA of the pair allocates the pair's TMEM together
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // both CTAs' barriers are initialised before any cross-CTA arrive
+  tc_fence_after();
+  const uint32_t tmem_base = ctl->tmem_base;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA producer (both CTAs)
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmap) : "memory");
+      uint32_t stage = 0, phase = 0;
+      int64_t issued = 0;
+      int band = 0;
+      bool ok = true;
+      const bool skip = *reinterpret_cast<volatile int*>(&g_fault_skip_tma) != 0;
+      for (int64_t t = cl; t < total && ok && !skip; t += ncl) {
+        int64_t bi2, bj;
+        decode_tile(ts, t * nshards + shard, &band, &bi2, &bj);
+        const int ya = (int)((2 * bi2 + rank) * BM), yb = (int)(bj * BN + rank * (BN / 2));
+        for (int64_t kc = 0; kc < kchunks; ++kc) {
+          if (!mbar_wait(&ctl->empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
+          uint8_t* sa = smem + stage * P_STAGE_BYTES;
+          const uint32_t full_c = mapa_shared(smem_u32(&ctl->full[stage]), 0u);  // the leader's full[stage]
+          if (rank == 0) mbar_arrive_expect_tx(&ctl->full[stage], 2 * P_STAGE_BYTES);
+          tma_load_2d_pair(sa, &tmap, full_c, (int)(kc * BK), ya);
+          tma_load_2d_pair(sa + PA_BYTES, &tmap, full_c, (int)(kc * BK), yb);
+          ++issued;
+          if (++stage == P_STAGES) { stage = 0; phase ^= 1u; }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(&sc->status, 4u);
+      }
+      // drain (leader): the last stages' copies of both CTAs land on its full barriers
+      if (rank == 0) {
+        const int64_t last = issued < P_STAGES ? issued : P_STAGES;
+        for (int64_t q = 1; q <= last; ++q) {
+          const int64_t u = issued - q;
+          const uint32_t s = (uint32_t)(u % P_STAGES), par = (uint32_t)((u / P_STAGES) & 1);
+          const uint64_t t0 = globaltimer();
+          while (!mbar_try_wait(&ctl->full[s], par) && globaltimer() - t0 < WAIT_NS) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 0) {
+      // ---------------------------------------------------------------- pair MMA issuer (leader)
+      const uint32_t idesc = make_idesc(ab_fmt, 2 * BM, BN);
+      uint32_t stage = 0, phase = 0;
+      int64_t it = 0;
+      bool ok = true;
+      for (int64_t t = cl; t < total && ok; t += ncl, ++it) {
+        const uint32_t acc = (uint32_t)(it & 1), use = (uint32_t)((it >> 1) & 1);
+        if (!mbar_wait(&ctl->tempty[acc], use ^ 1u, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t dtmem = tmem_base + acc * (uint32_t)BN;
+        for (int64_t kc = 0; kc < kchunks; ++kc) {
+          if (!mbar_wait(&ctl->full[stage], phase, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + stage * P_STAGE_BYTES);
+          const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + PA_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            mma_f16_pair(dtmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (kc | kk) != 0);
+          const uint32_t e = smem_u32(&ctl->empty[stage]);
+          mma_commit_pair(e);
+          mma_commit_pair(mapa_shared(e, 1u));
+          if (++stage == P_STAGES) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        const uint32_t f = smem_u32(&ctl->tfull[acc]);
+        mma_commit_pair(f);
+        mma_commit_pair(mapa_shared(f, 1u));
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(&sc->status, 4u);
+      }
+      // drain: the commits arrive once every pair MMA issued so far has completed
+      const uint32_t dr = smem_u32(&ctl->drain);
+      mma_commit_pair(dr);
+      mma_commit_pair(mapa_shared(dr, 1u));
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(&ctl->drain, 0) && globaltimer() - t0 < WAIT_NS) {
+      }
+    } else if (lane == 0) {
+      // the peer: its TMEM and shared memory are in use until the leader's last pair MMA completes
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(&ctl->drain, 0) && globaltimer() - t0 < WAIT_NS) {
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue (warps 2..5, both CTAs)
+    const uint32_t quarter = (uint32_t)(warp & 3);
+    const BoundParams bp = sc->bp;
+    EpiState es;
+    epi_init(es, sc, bp);
+    int64_t it = 0;
+    int band = 0;
+    for (int64_t t = cl; t < total; t += ncl, ++it) {
+      int64_t bi2, bj;
+      decode_tile(ts, t * nshards + shard, &band, &bi2, &bj);
+      const uint32_t acc = (uint32_t)(it & 1), use = (uint32_t)((it >> 1) & 1);
+      const bool got = __all_sync(0xffffffffu, mbar_wait(&ctl->tfull[acc], use, abort_flag));
+      if (!got) {
+        if (lane == 0) {
+          *abort_flag = 1;
+          atomicOr(&sc->status, 4u);
+        }
+        break;
+      }
+      tc_fence_after();
+      const uint32_t tbase = tmem_base + ((quarter * 32u) << 16) + acc * (uint32_t)BN;
+      epi_tile<false>((2 * bi2 + (int64_t)rank) * BM, bj * BN, tbase, lane, quarter, ts.n, ts.excl, norms, bp, sc,
+                      cand, cap, es, nullptr, 1);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {  // the leader's tempty[acc]: a local arrive in the leader, a remote one from the peer
+        if (rank == 0) mbar_arrive(&ctl->tempty[acc]);
+        else mbar_arrive_cluster(mapa_shared(smem_u32(&ctl->tempty[acc]), 0u));
+      }
+      epi_publish(lane, bp, sc, es);
+      if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
+    }
+    tc_fence_before();
+  }
+
+  __syncthreads();
+  cluster_sync();  // no cross-CTA arrive or commit is pending past this point
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+}
+
 }  // namespace
 
 bool gram_tc_available() { return true; }
@@ -458,11 +660,15 @@ int set_fault_gram_tc(int on) {
 }
 
 namespace {
-// The band schedule of all tiles; returns their number.
-int64_t build_sched(int64_t n, int64_t n_pad, int64_t excl, TileSched& ts) {
+// The band schedule of all tiles; returns their number.  rstep = 2: the rows of the schedule are
+// pairs of 128-row blocks (a CTA pair's 256 x 256 tile); a pair's columns start where its first
+// (lower) row block's do.
+int64_t build_sched(int64_t n, int64_t n_pad, int64_t excl, TileSched& ts, int rstep = 1) {
   ts.n = n;
   ts.excl = excl;
-  ts.nbi = (int32_t)(n_pad / BM);
+  ts.rstep = rstep;
+  ts.pad = 0;
+  ts.nbi = (int32_t)(n_pad / (BM * rstep));
   ts.nbj = (int32_t)(n_pad / BN);
   int band = tuned_dense_band() > 0 ? tuned_dense_band() : BAND;
   while ((ts.nbj + band - 1) / band > MAX_BANDS) band *= 2;
@@ -476,7 +682,7 @@ int64_t build_sched(int64_t n, int64_t n_pad, int64_t excl, TileSched& ts) {
     int32_t nf = 0;
     bool in_full = true;
     for (int64_t bi = 0; bi < ts.nbi; ++bi) {
-      const int64_t c = row_count(bi, bj0, bj1, n, excl);
+      const int64_t c = row_count(bi * rstep, bj0, bj1, n, excl);
       if (in_full && c == bj1 - bj0) ++nf;
       else in_full = false;
       total += c;
@@ -545,6 +751,28 @@ int launch_gram_tc(const void* X, int mode, int64_t n, int64_t n_pad, int64_t Kp
   CPPGB_CUDA_TRY(cudaGetDevice(&dev));
   CPPGB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const uint32_t ab = mode == CPPGB_MODE_FILTER_BF16 ? 1u : 0u;
+  if (!dump && !perm && !tlist && tuned_dense_shape() == 2) {
+    // 256 x 256 tiles on CTA pairs: the schedule's rows are pairs of 128-row blocks
+    TileSched ts2;
+    const int64_t all2 = build_sched(n, n_pad, excl, ts2, 2);
+    const int64_t total2 = all2 > shard ? (all2 - shard + nshards - 1) / nshards : 0;
+    if (total2 == 0) return CPPGB_OK;
+    const size_t smem2 = (size_t)P_STAGES * P_STAGE_BYTES + sizeof(PairCtl) + 1024;
+    CPPGB_CUDA_TRY(cudaFuncSetAttribute(gram_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+    int clusters = 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(sms & ~1));
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = smem2;
+    cfg.stream = st;
+    CPPGB_CUDA_TRY(cudaOccupancyMaxActiveClusters(&clusters, gram_tc_pair_kernel, &cfg));
+    if (clusters < 1) return set_error(CPPGB_ERR_CUDA, "no CTA pair of the dense stage fits on the device");
+    const int64_t ncl = total2 < clusters ? total2 : clusters;
+    gram_tc_pair_kernel<<<(unsigned)(2 * ncl), NTHREADS, smem2, st>>>(tmap, ts2, total2, ab, norms, sc, cand, cap,
+                                                                      Kp / BK, shard, nshards, gate);
+    CPPGB_LAUNCH_CHECK();
+    return CPPGB_OK;
+  }
   const size_t smem = (size_t)STAGES * STAGE_BYTES + sizeof(SmemCtl) + 1024;
   const int64_t grid = total < sms ? total : sms;
   if (dump) {

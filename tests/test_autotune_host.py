@@ -37,6 +37,11 @@ def test_choose_band():
     assert autotune.choose_band({8: 2.0, 16: 2.0}) == 8
 
 
+def test_choose_dense_shape_and_band():
+    assert autotune.choose_dense({(1, 8): 3.0, (1, 16): 2.0, (2, 8): 1.5, (2, 16): 2.5}) == (2, 8)
+    assert autotune.choose_dense({(1, 16): 2.0, (2, 8): 2.0}) == (1, 16)   # ties: the smaller shape
+
+
 def test_cache_round_trip(tmp_path):
     p = str(tmp_path / "sub" / "tune.json")
     assert autotune.load_cache(p) == {"version": autotune.CACHE_VERSION, "entries": {}}
@@ -58,14 +63,18 @@ def test_cache_path_from_environment(monkeypatch, tmp_path):
 
 def test_install_reaches_the_library(capi):
     table = [[1, 2, 1, 2], [2, 2, 2, 2], [1, 1, 1, 1], [2, 1, 2, 1]]
-    autotune.install({"batch_path": table, "dense_band": 32})
+    autotune.install({"batch_path": table, "dense_band": 32, "dense_shape": 2})
     assert capi.cpp_get_tuning(capi.TUNE_BATCH_PATH) == list(np.asarray(table).reshape(-1))
     assert capi.cpp_get_tuning(capi.TUNE_DENSE_BAND) == [32]
+    assert capi.cpp_get_tuning(capi.TUNE_DENSE_SHAPE) == [2]
+    autotune.install({"dense_shape": 1})
+    assert capi.cpp_get_tuning(capi.TUNE_DENSE_SHAPE) == [1]
 
 
 def test_tuning_argument_errors(capi):
     for kind, vals in [(capi.TUNE_BATCH_PATH, [2] * 15), (capi.TUNE_BATCH_PATH, [2] * 15 + [3]),
-                       (capi.TUNE_DENSE_BAND, [0]), (capi.TUNE_DENSE_BAND, [5000]), (7, [1])]:
+                       (capi.TUNE_DENSE_BAND, [0]), (capi.TUNE_DENSE_BAND, [5000]), (capi.TUNE_DENSE_SHAPE, [0]),
+                       (capi.TUNE_DENSE_SHAPE, [3]), (7, [1])]:
         with pytest.raises(capi.CppgbError) as e:
             capi.cpp_set_tuning(kind, vals)
         assert e.value.status == capi.ERR_ARG

@@ -20,7 +20,9 @@ def test_tune_installs_a_valid_policy(tmp_path):
         assert len(entry["batch_ms"]) == 16
         assert capi.cpp_get_tuning(capi.TUNE_BATCH_PATH) == list(table.reshape(-1))
         if capi.filters_available():
-            assert entry["dense_band"] in autotune.BANDS
+            assert entry["dense_band"] in autotune.BANDS and entry["dense_shape"] in autotune.SHAPES
+            assert len(entry["dense_ms"]) == len(autotune.BANDS) * len(autotune.SHAPES)
+            assert capi.cpp_get_tuning(capi.TUNE_DENSE_SHAPE) == [entry["dense_shape"]]
         again = autotune.load_or_tune(path=str(tmp_path / "tune.json"))  # served from the cache
         assert again["when"] == entry["when"]
         # the tuned default path gives the oracle's closest pairs
@@ -32,6 +34,7 @@ def test_tune_installs_a_valid_policy(tmp_path):
             assert (r["i"], r["j"], r["dist2"]) == (oi, oj, od2)
     finally:
         capi.cpp_set_tuning(capi.TUNE_BATCH_PATH, before)
+        capi.cpp_set_tuning(capi.TUNE_DENSE_SHAPE, [1])
 
 
 @pytest.mark.parametrize("band", [1, 8, 64])
