@@ -102,12 +102,23 @@ def test_frnn_non_finite():
     assert e.value.status == capi.ERR_NUMERIC
 
 
-def test_frnn_full_size_sampled():
-    """2^20 points of the 64-component mixture, R = 0.002: sampled rows against the oracle, and
-    the global invariants (symmetric pair count, ascending rows, no self pairs)."""
+def test_frnn_full_size(golden_dir):
+    """2^20 points of the 64-component mixture, R = 0.002: the whole CSR against the oracle's (its
+    pair count and the SHA-256 digests of row_ptr and cols stored in
+    tests/golden/frnn_mix1048576_d3_r0.002.json by tests/golden/make_golden.py), sampled rows against
+    the oracle directly, and the global invariants (symmetric pair count, ascending rows, no self
+    pairs)."""
+    import hashlib
+    import json
+    import os
     x = synth.make_frnn_mixture()
     rp, cols = _run(x, 0.002)
     n = x.shape[0]
+    with open(os.path.join(golden_dir, "frnn_mix1048576_d3_r0.002.json")) as f:
+        g = json.load(f)
+    assert int(rp[-1]) == g["n_pairs"]
+    assert hashlib.sha256(np.ascontiguousarray(rp, dtype="<i8").tobytes()).hexdigest() == g["row_ptr_sha256"]
+    assert hashlib.sha256(np.ascontiguousarray(cols, dtype="<i4").tobytes()).hexdigest() == g["cols_sha256"]
     assert rp.shape == (n + 1,) and rp[0] == 0 and rp[-1] % 2 == 0
     assert np.all(np.diff(rp) >= 0)
     deg = np.diff(rp)
