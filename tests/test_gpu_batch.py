@@ -147,3 +147,36 @@ def test_batch_generator_workload_sampled():
             assert [tuple(p) for p in pairs[offs[q]:offs[q + 1]]] == sorted(got)
             checked += 1
     assert checked >= 20
+
+
+def _golden_batch():
+    import hashlib
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batch_2048inst.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("paths", [None, 1, 2])
+def test_batch_generator_workload_against_stored_oracle(paths):
+    """All 2048 instances of make_batch() against the oracle's stored answer
+    (tests/golden/batch_2048inst.json, written by make_golden.py from oracle/ alone): every closest
+    pair with its exact FP64 distance, every pair count, and the SHA-256 of every instance's (i, j)
+    list, for the tuned path choice and for each path forced."""
+    import hashlib
+    g = _golden_batch()
+    capi = _capi()
+    dev = device()
+    batch = synth.make_batch()
+    assert len(batch) == len(g["instances"])
+    pts = [to_dev(b.pts, dev) for b in batch]
+    res, counts, pairs = capi.cpp_batch(pts, [b.R for b in batch], paths=paths)
+    pairs = pairs.cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    for q, (r, gi) in enumerate(zip(res, g["instances"])):
+        assert (batch[q].pts.shape[0], batch[q].pts.shape[1]) == (gi["n"], gi["d"])
+        assert (r["i"], r["j"], r["dist2"]) == (gi["i"], gi["j"], float.fromhex(gi["dist2"])), q
+        assert int(counts[q]) == gi["n_pairs"], q
+        digest = hashlib.sha256(np.ascontiguousarray(pairs[offs[q]:offs[q + 1]], dtype="<i4").tobytes()).hexdigest()
+        assert digest == gi["pairs_sha256"], q
