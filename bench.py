@@ -462,11 +462,18 @@ WORKLOADS = {"tsmm": TSMM, "twolocus": TwoLocus, "cpp": CPP, "frnn": FRNN, "batc
 
 # ------------------------------------------------------------------ helpers
 def source_hash(files):
+    """Hash of the kernel sources' code: comments and blank lines are left out, so that a change of
+    wording keeps a traffic record and any change of code drops it."""
+    import re
     h = hashlib.sha256()
     for f in files:
         p = os.path.join(ROOT, "paper_1407_5609_gb300", "csrc", f)
         if os.path.exists(p):
-            h.update(open(p, "rb").read())
+            text = re.sub(r"/\*.*?\*/", "", open(p).read(), flags=re.S)
+            for line in text.splitlines():
+                line = line.split("//", 1)[0].rstrip()
+                if line:
+                    h.update(line.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -5,7 +5,8 @@
 // d <= 4: uniform grid with the floor function (the grid idea the paper cites in Sec. 1 for
 //   constant dimension).  Cells have side s >= R (1 + delta), so every pair within R lies in the
 //   same or adjacent cells; occupied cells live in an open-addressing hash table of 64-bit cell
-//   keys; points are grouped by cell with a counting sort; each point scans its 3^d neighbour cells
+//   keys; points are grouped by cell with a counting sort; one warp per occupied cell stages the
+//   points of its 3^d neighbour cells in shared memory and tests the cell's points against them
 //   twice (count, then fill).  A pair is decided in FP32 unless its FP32 squared distance lies
 //   within a 2^-16 relative band of R^2, where the FP64 test decides.
 // d > 4: the FP32 Gram tiles with a radius epilogue emit every pair whose lower bound can be <= R;
