@@ -560,25 +560,55 @@ __device__ __forceinline__ float chunk_max(uint32_t (&r)[32], int64_t i, int64_t
 // The 8 chunks of a warp's 32 rows x 256 columns, branch-free within each pair of chunks: chunk
 // c + 1 loads from TMEM while chunk c is reduced.  Returns the rows' largest a; `hits` gets bit c when some entry of
 // chunk c may lie within the radius (D~ <= th_r), for the rare second look after the loop.
+__device__ __forceinline__ void tmem_ld64_nowait(uint32_t taddr, uint32_t (&r)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,"
+      "%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]),
+        "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]),
+        "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
+        "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+        "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld64(uint32_t (&r)[64]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+                 "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]),
+                 "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                 "+r"(r[30]), "+r"(r[31]), "+r"(r[32]), "+r"(r[33]), "+r"(r[34]), "+r"(r[35]), "+r"(r[36]),
+                 "+r"(r[37]), "+r"(r[38]), "+r"(r[39]), "+r"(r[40]), "+r"(r[41]), "+r"(r[42]), "+r"(r[43]),
+                 "+r"(r[44]), "+r"(r[45]), "+r"(r[46]), "+r"(r[47]), "+r"(r[48]), "+r"(r[49]), "+r"(r[50]),
+                 "+r"(r[51]), "+r"(r[52]), "+r"(r[53]), "+r"(r[54]), "+r"(r[55]), "+r"(r[56]), "+r"(r[57]),
+                 "+r"(r[58]), "+r"(r[59]), "+r"(r[60]), "+r"(r[61]), "+r"(r[62]), "+r"(r[63])
+               :
+               : "memory");
+}
 template <bool EDGE>
 __device__ __forceinline__ float tile_rows(uint32_t tbase, int64_t i, int64_t col0, int64_t n, float nx, float th_r,
                                            uint32_t& hits) {
   float rmax = __int_as_float(0xff800000);
-  uint32_t ra[32], rb[32];
-  tmem_ld32_nowait(tbase, ra);
-  tmem_wait_ld(ra);
+  // one 64-column TMEM load and one wait per pair of 32-column chunks
+  uint32_t ra[64];
 #pragma unroll 1
   for (int c = 0; c < BN / 32; c += 2) {
-    tmem_ld32_nowait(tbase + (uint32_t)((c + 1) * 32), rb);
-    float m = chunk_max<EDGE>(ra, i, col0 + c * 32, n);
+    __syncwarp();
+    tmem_ld64_nowait(tbase + (uint32_t)(c * 32), ra);
+    tmem_wait_ld64(ra);
+    uint32_t (&lo)[32] = *reinterpret_cast<uint32_t(*)[32]>(&ra[0]);
+    uint32_t (&hi)[32] = *reinterpret_cast<uint32_t(*)[32]>(&ra[32]);
+    float m = chunk_max<EDGE>(lo, i, col0 + c * 32, n);
     hits |= (fmaf(-2.f, m, nx) <= th_r ? 1u : 0u) << c;
     rmax = fmaxf(rmax, m);
-    tmem_wait_ld(rb);
-    if (c + 2 < BN / 32) tmem_ld32_nowait(tbase + (uint32_t)((c + 2) * 32), ra);
-    m = chunk_max<EDGE>(rb, i, col0 + (c + 1) * 32, n);
+    m = chunk_max<EDGE>(hi, i, col0 + (c + 1) * 32, n);
     hits |= (fmaf(-2.f, m, nx) <= th_r ? 1u : 0u) << (c + 1);
     rmax = fmaxf(rmax, m);
-    if (c + 2 < BN / 32) tmem_wait_ld(ra);
   }
   return rmax;
 }

@@ -34,7 +34,8 @@ struct FrnnState {
   GridParams gp;
   unsigned int mm[8];   // ordered-float keys: min of dim k at [k], max at [4 + k]
   unsigned int status;  // 1: non-finite coordinate, 8: hash table full
-  unsigned int pad;
+  unsigned int spill;   // 1: the row buffer overflowed (the rows are then written by a second pass)
+  unsigned long long cursor;  // entries of the row buffer handed out
 };
 
 __device__ __forceinline__ unsigned int ord_key(float f) {
@@ -64,6 +65,8 @@ __global__ void frnn_init_kernel(FrnnState* fs, uint32_t* counters) {
     fs->mm[4 + k] = 0u;
   }
   fs->status = 0u;
+  fs->spill = 0u;
+  fs->cursor = 0ull;
   if (counters) counters[0] = counters[1] = 0u;
 }
 
@@ -407,13 +410,21 @@ __device__ __forceinline__ int slab_of(const GridParams& gp, int64_t cx, int nsh
 // ------------------------------------------------------------------ cell-parallel query
 // One warp per occupied cell: lanes look up the 3^D neighbour cells at once, the warp stages every
 // candidate point of those cells in shared memory (copies of contiguous cell ranges), then takes
-// the cell's points one after another: each lane tests one staged candidate, a ballot counts the
-// neighbours (count pass) or compacts them into a list whose entries each lane places by rank, so
-// the row is written once, ascending (fill pass).  The next cell's key is loaded one iteration
-// ahead.  Cells with more candidates than the staging buffer holds are listed for the warp-per-point
-// kernel below.
+// the cell's points one after another: each lane tests one staged candidate and a ballot compacts
+// the neighbours into a list whose entries each lane places by rank, so a row is written once,
+// ascending.  The next cell's key is loaded one iteration ahead.  Cells with more candidates than
+// the staging buffer holds are listed for the warp-per-point kernel below.
+//
+// ROWS pass (the query's only neighbour search when the row buffer suffices): every row goes to
+// the row buffer at a position the warp takes from its current chunk (chunks of ROW_CHUNK entries
+// come from one global cursor), and the point's count and position are recorded; past the buffer's
+// capacity the row is dropped and the spill flag set.  FILL pass (only after a spill): every row
+// goes straight to its place in the CSR, whose row pointers are then known.
 constexpr int QW = 8;            // warps per block
 constexpr int STAGE_CAP = 256;   // staged candidates per warp
+constexpr int ROW_CHUNK = 1024;  // row-buffer entries a warp takes at a time
+constexpr int ROWS_PER_POINT = 24;  // row-buffer capacity per point
+static_assert(STAGE_CAP <= ROW_CHUNK, "a row must fit one chunk");
 
 template <int D>
 struct CellStage {
@@ -428,21 +439,23 @@ struct CellStage {
 
 template <int D, bool FILL>
 __global__ void __launch_bounds__(QW * 32) cell_query_kernel(
-    const FrnnState* fs, const CellRec* __restrict__ tab, int64_t T, const unsigned long long* __restrict__ occ_key,
+    FrnnState* fs, const CellRec* __restrict__ tab, int64_t T, const unsigned long long* __restrict__ occ_key,
     const uint32_t* __restrict__ n_occ, const int32_t* __restrict__ sorted_idx, const float4* __restrict__ sorted_pts,
-    int32_t* __restrict__ counts, const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cols, int64_t n,
-    int64_t cols_cap, uint32_t* __restrict__ fb, uint32_t* __restrict__ n_fb, int shard, int nshards) {
+    int32_t* __restrict__ counts, int64_t* __restrict__ row_at, int32_t* __restrict__ rowbuf, int64_t rowbuf_cap,
+    const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cols, int64_t n, int64_t cols_cap,
+    uint32_t* __restrict__ fb, uint32_t* __restrict__ n_fb, int shard, int nshards) {
   using Stage = CellStage<D>;
   constexpr int S = Stage::S, CENTER = (S - 1) / 2;
   extern __shared__ __align__(16) uint8_t cq_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   Stage& sm = reinterpret_cast<Stage*>(cq_smem)[warp];
-  if (FILL && row_ptr[n] > cols_cap) return;  // the host reports the capacity error
+  if (FILL && (!fs->spill || row_ptr[n] > cols_cap)) return;  // no spill, or the host reports the capacity error
   const GridParams gp = fs->gp;
   const uint64_t cmask = (1ull << gp.bits) - 1ull;
   const uint32_t lt = (1u << lane) - 1u;
   const int64_t ncell = *n_occ;
   const int64_t stride = (int64_t)gridDim.x * QW;
+  int64_t chunk = 0, chunk_left = 0;  // ROWS pass: the warp's free range of the row buffer
   int64_t ci = (int64_t)blockIdx.x * QW + warp;
   uint64_t key = ci < ncell ? occ_key[ci] : 0;
   for (; ci < ncell; ci += stride) {
@@ -471,32 +484,6 @@ __global__ void __launch_bounds__(QW * 32) cell_query_kernel(
         sm.p[t] = v;
       }
       __syncwarp();
-      if (!FILL) {
-        // count pass: each lane holds one staged candidate and tests it against every point of the
-        // cell; lane a accumulates the count of point a0 + a
-        for (int a0 = 0; a0 < m; a0 += 32) {
-          const int na = m - a0 < 32 ? m - a0 : 32;
-          int acc = 0;
-          for (int t0 = 0; t0 < total; t0 += 32) {
-            const int t = t0 + lane;
-            const bool live = t < total;
-            const float4 yv = sm.p[live ? t : 0];
-            const float y[4] = {yv.x, yv.y, yv.z, yv.w};
-            const int32_t j = Stage::PACK ? __float_as_int(yv.w) : sm.j[live ? t : 0];
-            for (int a = 0; a < na; ++a) {
-              const float4 xv = sm.p[c0 + a0 + a];
-              const float x[4] = {xv.x, xv.y, xv.z, xv.w};
-              const int32_t q = Stage::PACK ? __float_as_int(xv.w) : sm.j[c0 + a0 + a];
-              const int cnt_a = __popc(__ballot_sync(0xffffffffu, decide<D>(x, y, gp, live && j != q)));
-              acc += lane == a ? cnt_a : 0;
-            }
-          }
-          if (lane < na) {
-            const int32_t q = Stage::PACK ? __float_as_int(sm.p[c0 + a0 + lane].w) : sm.j[c0 + a0 + lane];
-            counts[q] = acc;
-          }
-        }
-      } else {
       for (int a = 0; a < m; ++a) {
         const float4 xv = sm.p[c0 + a];
         const float x[4] = {xv.x, xv.y, xv.z, xv.w};
@@ -510,19 +497,46 @@ __global__ void __launch_bounds__(QW * 32) cell_query_kernel(
           const int32_t j = Stage::PACK ? __float_as_int(yv.w) : sm.j[live ? t : 0];
           const int in = decide<D>(x, y, gp, live && j != q);
           const uint32_t mask = __ballot_sync(0xffffffffu, in);
-          if (FILL && in) sm.nb[found + __popc(mask & lt)] = j;
+          if (in) sm.nb[found + __popc(mask & lt)] = j;
           found += __popc(mask);
         }
         __syncwarp();
-        int32_t* out = cols + row_ptr[q];
-        for (int e = lane; e < found; e += 32) {  // rank among the row's (distinct) entries
-          const int32_t v = sm.nb[e];
-          int r = 0;
-          for (int f = 0; f < found; ++f) r += sm.nb[f] < v ? 1 : 0;
-          out[r] = v;
+        int32_t* out = nullptr;
+        if (FILL) {
+          out = cols + row_ptr[q];
+        } else {
+          // the row's place in the row buffer (warp-uniform: every lane keeps the same chunk)
+          int64_t at = 0;
+          if (found > 0) {
+            if (found > chunk_left) {  // a fresh chunk (a row never exceeds STAGE_CAP <= ROW_CHUNK)
+              unsigned long long base = 0;
+              if (lane == 0) base = atomicAdd(&fs->cursor, (unsigned long long)ROW_CHUNK);
+              chunk = (int64_t)__shfl_sync(0xffffffffu, base, 0);
+              chunk_left = ROW_CHUNK;
+            }
+            at = chunk;
+            chunk += found;
+            chunk_left -= found;
+          }
+          if (lane == 0) {
+            counts[q] = found;
+            row_at[q] = at;
+          }
+          if (at + found <= rowbuf_cap) {
+            out = rowbuf + at;
+          } else if (lane == 0) {
+            fs->spill = 1u;
+          }
+        }
+        if (out) {
+          for (int e = lane; e < found; e += 32) {  // rank among the row's (distinct) entries
+            const int32_t v = sm.nb[e];
+            int r = 0;
+            for (int f = 0; f < found; ++f) r += sm.nb[f] < v ? 1 : 0;
+            out[r] = v;
+          }
         }
         __syncwarp();
-      }
       }
     }
     __syncwarp();
@@ -530,10 +544,44 @@ __global__ void __launch_bounds__(QW * 32) cell_query_kernel(
   }
 }
 
-// One warp per point of a crowded cell (listed by the count pass): the warp walks the laid-out
-// candidates 32 at a time straight from global memory.  Count pass: counts[q].  Fill pass: the row
-// is appended unordered, then sorted in place (rank placement through shared memory for rows of up
-// to SORT_CAP entries, else a heap sort by one lane).
+// The rows of the row buffer copied to their places in the CSR, when nothing spilled and the CSR
+// fits: each warp takes 32 consecutive points, whose rows are one contiguous range of cols, and its
+// lanes walk that range 32 entries at a time (each entry's row found by a search over the 33 row
+// pointers held one per lane).  Rows with row_at < 0 (points of crowded cells) are left to the
+// crowded fill pass.
+__global__ void __launch_bounds__(256) rows_copy_kernel(const FrnnState* fs, const int64_t* __restrict__ row_ptr,
+                                                        const int64_t* __restrict__ row_at,
+                                                        const int32_t* __restrict__ rowbuf, int32_t* __restrict__ cols,
+                                                        int64_t n, int64_t cols_cap) {
+  if (fs->spill || row_ptr[n] > cols_cap) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t q0 = ((int64_t)blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; q0 < n; q0 += (int64_t)gridDim.x * wpb * 32) {
+    const int64_t q = q0 + lane;
+    const int64_t rp = row_ptr[q < n ? q : n];          // lanes past the last point hold row_ptr[n]
+    const int64_t at = q < n ? row_at[q] : -1;
+    const int64_t end = row_ptr[q0 + 32 < n ? q0 + 32 : n];
+    const int64_t first = __shfl_sync(0xffffffffu, rp, 0);
+    for (int64_t e0 = first; e0 < end; e0 += 32) {
+      const int64_t e = e0 + lane;
+      int r = 0;  // the last lane whose row starts at or before e
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int64_t v = __shfl_sync(0xffffffffu, rp, r + step);
+        if (v <= e) r += step;
+      }
+      const int64_t src_at = __shfl_sync(0xffffffffu, at, r);
+      const int64_t src_rp = __shfl_sync(0xffffffffu, rp, r);
+      if (e < end && src_at >= 0) cols[e] = rowbuf[src_at + (e - src_rp)];
+    }
+  }
+}
+
+// One warp per point of a crowded cell (listed by the rows pass): the warp walks the laid-out
+// candidates 32 at a time straight from global memory.  Count pass: counts[q], and row_at[q] = -1
+// (the row is not in the row buffer).  Fill pass: the row is appended unordered, then sorted in
+// place (rank placement through shared memory for rows of up to SORT_CAP entries, else a heap sort
+// by one lane).
 constexpr int PW = 4;          // warps per block
 constexpr int SORT_CAP = 1024;
 
@@ -548,9 +596,9 @@ struct PointStage {
 template <int D, bool FILL>
 __global__ void __launch_bounds__(PW * 32) crowded_query_kernel(
     const FrnnState* fs, const CellRec* __restrict__ tab, int64_t T, const int32_t* __restrict__ sorted_idx,
-    const float4* __restrict__ sorted_pts, int32_t* __restrict__ counts, const int64_t* __restrict__ row_ptr,
-    int32_t* __restrict__ cols, int64_t n, int64_t cols_cap, const uint32_t* __restrict__ fb,
-    const uint32_t* __restrict__ n_fb) {
+    const float4* __restrict__ sorted_pts, int32_t* __restrict__ counts, int64_t* __restrict__ row_at,
+    const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cols, int64_t n, int64_t cols_cap,
+    const uint32_t* __restrict__ fb, const uint32_t* __restrict__ n_fb) {
   using Stage = PointStage<D>;
   constexpr int S = Stage::S;
   __shared__ Stage stage[PW];
@@ -583,7 +631,10 @@ __global__ void __launch_bounds__(PW * 32) crowded_query_kernel(
       found += __popc(mask);
     }
     if (!FILL) {
-      if (lane == 0) counts[q] = (int32_t)found;
+      if (lane == 0) {
+        counts[q] = (int32_t)found;
+        row_at[q] = -1;
+      }
     } else if (found <= SORT_CAP) {
       __syncwarp();
       for (int e = lane; e < found; e += 32) sm.buf[e] = out[e];
@@ -681,8 +732,10 @@ struct GridLayout {
   int32_t* occ_cnt;
   int64_t* occ_start;
   int64_t* tmp;
+  int64_t* row_at;     // each point's row in the row buffer (-1: written by the crowded fill pass)
+  int32_t* rowbuf;     // the rows pass's output, ROWS_PER_POINT entries per point
   frnn_result* res;
-  int64_t T;
+  int64_t T, rowbuf_cap;
   size_t bytes;
 };
 
@@ -704,6 +757,9 @@ GridLayout grid_layout(void* ws, int64_t n) {
   L.occ_cnt = c.take<int32_t>(n);
   L.occ_start = c.take<int64_t>(n + 1);
   L.tmp = c.take<int64_t>(scan_temp_elems(n));
+  L.row_at = c.take<int64_t>(n);
+  L.rowbuf_cap = (int64_t)ROWS_PER_POINT * n;
+  L.rowbuf = c.take<int32_t>(L.rowbuf_cap);
   L.res = c.take<frnn_result>(1);
   L.bytes = c.bytes();
   return L;
@@ -798,32 +854,37 @@ int grid_path(const float* pts, int64_t n, int64_t ld, double R, int64_t* row_pt
   CPPGB_LAUNCH_CHECK();
   scatter_kernel<<<nb, 256, 0, st>>>(pts, n, ld, L.fs, L.slot_of, L.rank_of, L.tab, L.sorted_idx, L.sorted_pts);
   CPPGB_LAUNCH_CHECK();
-  // count pass, scan, fill pass: one warp per occupied cell, one warp per point of a crowded cell
+  // rows pass (counts, rows into the row buffer), crowded counts, scan, copy of the buffered rows;
+  // then the crowded cells' rows, and, only after a spill, the fill pass of every other row
   const size_t smem = (size_t)QW * sizeof(CellStage<D>);
   CPPGB_CUDA_TRY(cudaFuncSetAttribute(cell_query_kernel<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
   CPPGB_CUDA_TRY(cudaFuncSetAttribute(cell_query_kernel<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
   int per_sm = 0;
-  CPPGB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_query_kernel<D, true>, QW * 32, smem));
+  CPPGB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_query_kernel<D, false>, QW * 32, smem));
   const unsigned cgrid = (unsigned)sms * (unsigned)(per_sm > 0 ? per_sm : 1), pgrid = (unsigned)sms * 4u;
   const uint32_t* n_occ = L.counters;
   uint32_t* n_fb = L.counters + 1;
-  cell_query_kernel<D, false><<<cgrid, QW * 32, smem, st>>>(L.fs, L.tab, L.T, L.occ_key, n_occ, L.sorted_idx,
-                                                            L.sorted_pts, L.counts, nullptr, nullptr, n, 0, L.fb,
-                                                            n_fb, shard, nshards);
+  cell_query_kernel<D, false><<<cgrid, QW * 32, smem, st>>>(
+      L.fs, L.tab, L.T, L.occ_key, n_occ, L.sorted_idx, L.sorted_pts, L.counts, L.row_at, L.rowbuf, L.rowbuf_cap,
+      nullptr, nullptr, n, 0, L.fb, n_fb, shard, nshards);
   CPPGB_LAUNCH_CHECK();
   crowded_query_kernel<D, false><<<pgrid, PW * 32, 0, st>>>(L.fs, L.tab, L.T, L.sorted_idx, L.sorted_pts, L.counts,
-                                                            nullptr, nullptr, n, 0, L.fb, n_fb);
+                                                            L.row_at, nullptr, nullptr, n, 0, L.fb, n_fb);
   CPPGB_LAUNCH_CHECK();
   if ((rc = launch_exclusive_scan_i32(L.counts, n, row_ptr, L.tmp, st))) return rc;
-  // the fill kernels check row_ptr[n] <= cols_cap on the device and write nothing otherwise
-  cell_query_kernel<D, true><<<cgrid, QW * 32, smem, st>>>(L.fs, L.tab, L.T, L.occ_key, n_occ, L.sorted_idx,
-                                                           L.sorted_pts, nullptr, row_ptr, cols, n, cols_cap, L.fb,
-                                                           n_fb, shard, nshards);
+  // the copy and fill kernels check row_ptr[n] <= cols_cap on the device and write nothing otherwise
+  const int64_t copy_blocks = (n + 255) / 256;
+  rows_copy_kernel<<<(unsigned)(copy_blocks < (int64_t)sms * 8 ? copy_blocks : (int64_t)sms * 8), 256, 0, st>>>(
+      L.fs, row_ptr, L.row_at, L.rowbuf, cols, n, cols_cap);
   CPPGB_LAUNCH_CHECK();
   crowded_query_kernel<D, true><<<pgrid, PW * 32, 0, st>>>(L.fs, L.tab, L.T, L.sorted_idx, L.sorted_pts, nullptr,
-                                                           row_ptr, cols, n, cols_cap, L.fb, n_fb);
+                                                           nullptr, row_ptr, cols, n, cols_cap, L.fb, n_fb);
+  CPPGB_LAUNCH_CHECK();
+  cell_query_kernel<D, true><<<cgrid, QW * 32, smem, st>>>(
+      L.fs, L.tab, L.T, L.occ_key, n_occ, L.sorted_idx, L.sorted_pts, nullptr, nullptr, nullptr, 0, row_ptr, cols,
+      n, cols_cap, L.fb, n_fb, shard, nshards);
   CPPGB_LAUNCH_CHECK();
   frnn_result_kernel<<<1, 1, 0, st>>>(L.fs, nullptr, 0, row_ptr, n, cols_cap, L.res);
   CPPGB_LAUNCH_CHECK();

@@ -84,6 +84,32 @@ def test_frnn_crowded_cells(d):
     assert deg.max() >= 599
 
 
+@pytest.mark.parametrize("d,n,R,seed", [(1, 6000, 0.01, 24), (2, 8000, 0.05, 25), (3, 6000, 0.12, 26)])
+def test_frnn_row_buffer_spill(d, n, R, seed):
+    """Dense uniform points with up to about 200 candidates per cell (no crowded cells) and far more
+    than 24 neighbours per point: the rows pass's buffer (24 entries per point) overflows, and the
+    rows come from the second, direct fill pass."""
+    x = synth.rng_for(seed).random((n, d)).astype(np.float32)
+    rp, _ = _check(x, R)
+    assert rp[-1] > 24 * n                    # more entries than the buffer holds
+
+
+@pytest.mark.parametrize("nshards", [2, 3])
+def test_frnn_row_buffer_spill_shards(nshards):
+    from paper_1407_5609_gb300 import shards
+    capi = _capi()
+    x = synth.rng_for(27).random((8000, 2)).astype(np.float32)
+    xd = to_dev(x, device())
+    parts = []
+    for s in range(nshards):
+        rp, cols = capi.frnn_query_shard(xd, 0.05, s, nshards)
+        parts.append((rp.cpu().numpy(), cols.cpu().numpy()))
+    rp, cols = shards.merge_frnn(parts)
+    orp, ocols = oracle.frnn(x.astype(np.float64), 0.05)
+    np.testing.assert_array_equal(rp, orp)
+    np.testing.assert_array_equal(cols, ocols)
+
+
 def test_frnn_capacity_reporting():
     capi = _capi()
     dev = device()
