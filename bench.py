@@ -394,13 +394,14 @@ class Batch:
         import torch
         from paper_1407_5609_gb300 import autotune, capi
         # the autotuner's tile choice per (n-bucket, d-class): cached, or measured now (outside the timing)
+        shape = (len(autotune.N_BUCKETS), len(autotune.D_CLASSES))
         if self.path:
-            table = [[self.path] * 4 for _ in range(4)]
+            table = [[self.path] * shape[1] for _ in range(shape[0])]
         elif self.no_tune:
-            table = np.asarray(capi.cpp_get_tuning(capi.TUNE_BATCH_PATH)).reshape(4, 4).tolist()
+            table = np.asarray(capi.cpp_get_tuning(capi.TUNE_BATCH_PATH)).reshape(shape).tolist()
         else:
             table = autotune.load_or_tune(dense=False)["batch_path"]
-        self.tc = [autotune.path_for(table, b.pts.shape[0], b.pts.shape[1]) == 2 for b in self.batch]
+        self.tc = [autotune.path_for(table, b.pts.shape[0], b.pts.shape[1]) >= 2 for b in self.batch]
         self.tc_flops = sum(f for f, t in zip(self._flops(), self.tc) if t)
         self.config["batch_paths"] = table
         self.config["tensor_core_instances"] = int(sum(self.tc))
@@ -961,8 +962,9 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="time only --workload (by default the motif line also times the closest-pair, FRNN, "
                          "two-locus and batch workloads)")
-    ap.add_argument("--batch-path", type=int, choices=[0, 1, 2], default=0,
-                    help="batch tiles: 0 the tuned policy, 1 FP32 CUDA-core tiles, 2 tensor-core tiles")
+    ap.add_argument("--batch-path", type=int, choices=[0, 1, 2, 3], default=0,
+                    help="batch tiles: 0 the tuned policy, 1 FP32 CUDA-core tiles, 2 tensor-core tiles with four "
+                         "epilogue groups, 3 with two")
     ap.add_argument("--dense-shape", type=int, choices=[1, 2], default=None,
                     help="tile of the tensor-core dense stage: 1 = 128 x 256 on one SM, 2 = 256 x 256 on a CTA pair "
                          "(default: the library's policy)")

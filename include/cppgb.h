@@ -326,8 +326,9 @@ typedef struct {
   const float* pts; /* device FP32 [n][d] row-major (ld = d) */
   int64_t n;
   int32_t d;        /* 1 .. 256 */
-  int32_t path;     /* 0: library default (tensor cores from d >= 16), 1: FP32 CUDA-core tiles,
-                       2: BF16 tensor-core tiles -- the answer is exact either way */
+  int32_t path;     /* 0: the tuning policy's choice, 1: FP32 CUDA-core tiles, 2: BF16 tensor-core
+                       tiles read by four epilogue groups (128 columns each), 3: the same tiles read
+                       by two (256 columns each) -- the answer is exact either way */
   double R;         /* FRNN radius for this instance (< 0: no FRNN output) */
 } cpp_instance;
 
@@ -335,7 +336,7 @@ typedef struct {
  * cpp_batch -- many independent CPP + FRNN instances of uneven n and d in one persistent launch
  * (the problems of Sec. 3 and Sec. 3.5, instance by instance).  Instances on the FP32 path share
  * one persistent CUDA-core tile kernel, those on the tensor-core path one persistent tcgen05
- * kernel (BF16 rows padded to 64, 128, 192 or 256 columns, one tensor map per width); both feed
+ * kernel (BF16 rows padded to 16, 32, 64, 128, 192 or 256 columns, one tensor map per width); both feed
  * the same FP32 second pass and FP64 recheck, so the answer does not depend on the path.
  *   inst        host array [count].
  *   out_cpp     host [count]: closest pair of each instance (identical to cpp_closest_pair; the
@@ -416,10 +417,13 @@ int cpp_set_fault_injection(int kind);
 /*
  * Tuning policy (process-wide; no counterpart in the paper).  The project's autotuner times the
  * candidates on the device, caches its choice as JSON and installs it here; every later call reads it.
- *   CPPGB_TUNE_BATCH_PATH  values = int32 [4 n-buckets][4 d-classes], count 16, each 1 (FP32 128 x 128
- *                          CUDA-core tiles) or 2 (BF16 128 x 256 tensor-core tiles); used by cpp_batch
- *                          instances whose path is 0.  n-buckets: n < 1024, < 4096, < 16384, the rest;
- *                          d-class: ceil(d / 64) - 1.  Default: all 2 when the tensor-core kernels exist.
+ *   CPPGB_TUNE_BATCH_PATH  values = int32 [4 n-buckets][6 d-classes], count 24, each 1 (FP32 128 x 128
+ *                          CUDA-core tiles), 2 (BF16 128 x 256 tensor-core tiles, four epilogue groups
+ *                          of 128 columns) or 3 (the same tiles, two epilogue groups of 256 columns);
+ *                          used by cpp_batch instances whose path is 0.
+ *                          n-buckets: n < 1024, < 4096, < 16384, the rest; d-classes: d <= 16, <= 32,
+ *                          <= 64, <= 128, <= 192, <= 256.  Default (when the tensor-core kernels exist):
+ *                          2 for d <= 16, 3 above (measured on GB300).
  *   CPPGB_TUNE_DENSE_BAND  values = int32 [1]: column blocks per band of the tensor-core dense stage's
  *                          tile order (1 .. 4096; 0 from cpp_get_tuning means the built-in 16).
  *   CPPGB_TUNE_DENSE_SHAPE values = int32 [1]: tile of the tensor-core dense stage (unpruned searches):

@@ -9,7 +9,9 @@ the speed: every candidate returns the same, exact answer.
 Candidates:
 
 * batch tiles per (n-bucket, d-class) -- FP32 CUDA-core 128 x 128 tiles (path 1) or BF16 tcgen05
-  128 x 256 tiles with the norms folded into the MMA (path 2);
+  128 x 256 tiles with the norms folded into the MMA, whose accumulators are read by four epilogue
+  groups of 128 columns (path 2) or two of 256 columns (path 3); the d-classes are the tensor-core
+  widths (rows padded to 16, 32, 64, 128, 192 or 256 columns);
 * the tensor-core dense stage (closest pair, motif search) -- the tile shape (128 x 256 on one SM,
   or 256 x 256 on a cluster of two SMs with tcgen05 cta_group::2) and the column blocks per band of
   its tile order, which sets how much of the B panel set stays in L2.
@@ -30,26 +32,28 @@ from . import capi, synth
 
 # must match the library's buckets (csrc/api.cu: tuned_batch_path)
 N_BUCKETS = ((256, 1023), (1024, 4095), (4096, 16383), (16384, 65536))
-D_CLASSES = ((1, 64), (65, 128), (129, 192), (193, 256))
-D_SAMPLES = ((16, 64), (96, 128), (160, 192), (224, 256))  # dimensions timed per class
+D_CLASSES = ((1, 16), (17, 32), (33, 64), (65, 128), (129, 192), (193, 256))
+D_SAMPLES = ((8, 16), (24, 32), (48, 64), (96, 128), (160, 192), (224, 256))  # dimensions timed per class
+PATHS = (1, 2, 3)
 BANDS = (8, 16, 32, 64)
 SHAPES = (1, 2)  # dense-stage tiles: 1 = 128 x 256 on one SM, 2 = 256 x 256 on a CTA pair
-CACHE_VERSION = 2
+CACHE_VERSION = 3
 
 
 # ---------------------------------------------------------------- pure selection logic
 def choose_batch_table(ms: dict) -> list:
-    """ms[(nb, dc)] = {1: t_fp32, 2: t_tc} -> 4 x 4 table of the faster path (ties: tensor cores)."""
+    """ms[(nb, dc)] = {path: time} -> n-bucket x d-class table of the fastest path (ties: the higher
+    path); unmeasured cells keep 2."""
     table = [[2] * len(D_CLASSES) for _ in N_BUCKETS]
     for (nb, dc), t in ms.items():
-        table[nb][dc] = 1 if t[1] < t[2] else 2
+        table[nb][dc] = min(sorted(t, reverse=True), key=lambda p: t[p])
     return table
 
 
 def path_for(table, n: int, d: int) -> int:
     """The table entry the library uses for an instance of n points in d dimensions (path 0)."""
     nb = 0 if n < 1024 else 1 if n < 4096 else 2 if n < 16384 else 3
-    dc = min(max((d + 63) // 64 - 1, 0), len(D_CLASSES) - 1)
+    dc = next((k for k, (lo, hi) in enumerate(D_CLASSES) if d <= hi), len(D_CLASSES) - 1)
     return int(table[nb][dc])
 
 
@@ -158,7 +162,7 @@ def measure_batch(target_pairs: float = 2e9, reps: int = 3, cells=None) -> dict:
         pts = [torch.from_numpy(x).to(dev) for x in xs]
         radii = [-1.0] * len(pts)
         t = {}
-        for path in (1, 2):
+        for path in PATHS:
             inst = [capi.cpp_instance(p.data_ptr(), p.shape[0], p.shape[1], path, -1.0) for p in pts]
             ws = capi._workspace(capi.cpp_batch_workspace_size(inst), dev)
             pairs = torch.empty((1, 2), dtype=torch.int32, device=dev)
@@ -198,7 +202,7 @@ def tune(batch: bool = True, dense: bool = True, target_pairs: float = 2e9, reps
     if batch:
         ms = measure_batch(target_pairs=target_pairs, reps=reps)
         entry["batch_path"] = choose_batch_table(ms)
-        entry["batch_ms"] = {f"{nb},{dc}": {"fp32": t[1], "tc": t[2]} for (nb, dc), t in sorted(ms.items())}
+        entry["batch_ms"] = {f"{nb},{dc}": {str(p): t[p] for p in sorted(t)} for (nb, dc), t in sorted(ms.items())}
     if dense:
         ms = measure_dense(reps=reps)
         if ms:

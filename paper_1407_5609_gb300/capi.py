@@ -231,11 +231,11 @@ def cpp_set_fault_injection(kind: int) -> None:
 
 
 TUNE_BATCH_PATH, TUNE_DENSE_BAND, TUNE_DENSE_SHAPE = 1, 2, 3
-TUNE_SIZES = {TUNE_BATCH_PATH: 16, TUNE_DENSE_BAND: 1, TUNE_DENSE_SHAPE: 1}
+TUNE_SIZES = {TUNE_BATCH_PATH: 24, TUNE_DENSE_BAND: 1, TUNE_DENSE_SHAPE: 1}
 
 
 def cpp_set_tuning(kind: int, values) -> None:
-    """Install a tuning table (see include/cppgb.h): 16 batch paths, one dense band or one dense tile shape."""
+    """Install a tuning table (see include/cppgb.h): 24 batch paths, one dense band or one dense tile shape."""
     vals = [int(v) for v in np.asarray(values).reshape(-1)]
     arr = (ctypes.c_int32 * max(len(vals), 1))(*vals)
     _raise(lib().cpp_set_tuning(int(kind), arr, len(vals)))
@@ -588,7 +588,7 @@ def cpp_batch_workspace_size(instances) -> int:
     return int(lib().cpp_batch_workspace_size(arr, len(instances)))
 
 
-PATH_DEFAULT, PATH_FP32, PATH_TC = 0, 1, 2
+PATH_DEFAULT, PATH_FP32, PATH_TC, PATH_TC2 = 0, 1, 2, 3
 
 
 def cpp_batch(points: list, radii: list, pairs_cap: int | None = None, ws: torch.Tensor | None = None,
@@ -596,8 +596,8 @@ def cpp_batch(points: list, radii: list, pairs_cap: int | None = None, ws: torch
     """Closest pair + R-pairs of every instance in one call.
 
     ``points`` is a list of float32 [n][d] CUDA tensors (contiguous), ``radii`` their R (< 0: no
-    pair list), ``paths`` an optional per-instance tile path (PATH_DEFAULT, PATH_FP32 or
-    PATH_TC; a single int applies to all).  Repeated calls with the same workspace and ``pairs``
+    pair list), ``paths`` an optional per-instance tile path (PATH_DEFAULT, PATH_FP32, PATH_TC (four
+    epilogue groups) or PATH_TC2 (two); a single int applies to all).  Repeated calls with the same workspace and ``pairs``
     buffer replay the library's captured CUDA graph.  Returns (list of result dicts, pair_counts
     int64 numpy, pairs int32 tensor [P][2]).
     """

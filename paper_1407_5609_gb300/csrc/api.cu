@@ -26,19 +26,19 @@ static void init_tuning() {
     }
     return;
   }
-  // measured default: the tensor-core tiles win at every class and size this library runs
-  const int def = gram_tc_available() ? 2 : 1;
-  for (int k = 0; k < TUNE_NB * TUNE_DC; ++k) g_batch_path[k].store(def);
+  // measured default: the tensor-core tiles win at every class and size this library runs; their
+  // epilogue of four groups for d <= 16, of two groups from d = 17 on
+  const bool tc = gram_tc_available();
+  for (int k = 0; k < TUNE_NB * TUNE_DC; ++k) g_batch_path[k].store(!tc ? 1 : k % TUNE_DC == 0 ? 2 : 3);
   g_tuning_init.store(2);
 }
 
 int tuned_batch_path(int64_t n, int d) {
   init_tuning();
   const int nb = n < 1024 ? 0 : n < 4096 ? 1 : n < 16384 ? 2 : 3;
-  int dc = (d + 63) / 64 - 1;
-  dc = dc < 0 ? 0 : dc >= TUNE_DC ? TUNE_DC - 1 : dc;
+  const int dc = d <= 16 ? 0 : d <= 32 ? 1 : d <= 64 ? 2 : d <= 128 ? 3 : d <= 192 ? 4 : 5;
   const int p = g_batch_path[nb * TUNE_DC + dc].load();
-  return (p == 2 && !gram_tc_available()) ? 1 : p;
+  return (p >= 2 && !gram_tc_available()) ? 1 : p;
 }
 
 int tuned_dense_band() { return g_dense_band.load(); }
@@ -317,7 +317,7 @@ int cpp_set_tuning(int kind, const int32_t* values, int count) {
   if (kind == CPPGB_TUNE_BATCH_PATH) {
     if (!values || count != TUNE_NB * TUNE_DC) return set_error(CPPGB_ERR_ARG, "batch path table needs %d entries", TUNE_NB * TUNE_DC);
     for (int k = 0; k < count; ++k)
-      if (values[k] != 1 && values[k] != 2) return set_error(CPPGB_ERR_ARG, "batch path entries must be 1 or 2");
+      if (values[k] < 1 || values[k] > 3) return set_error(CPPGB_ERR_ARG, "batch path entries must be 1, 2 or 3");
     for (int k = 0; k < count; ++k) g_batch_path[k].store(values[k]);
     return CPPGB_OK;
   }

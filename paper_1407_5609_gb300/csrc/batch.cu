@@ -19,6 +19,7 @@
 // same second pass.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -39,13 +40,12 @@ struct BatchInst {
   float rr32;        // R^2 rounded up to FP32 (radius emission)
   float kappa;       // FP32 accumulation bound coefficient for Kp
   // tensor-core path
-  int32_t tc, cls;        // tc = 1: BF16 tcgen05 tiles; class = Kp16 / 64 - 1
+  int32_t tc, cls;        // tc = 1: BF16 tcgen05 tiles (epilogue of four or two groups: path 2 or 3); class of Kp16
   int32_t nbj16, nrow16;  // 256-column blocks; 128-row blocks that hold pairs
   int64_t row_off16;      // rows before this instance in its class matrix
   int64_t grow_off16;     // rows before this instance over all tensor-core instances (BF16 norms)
-  int64_t tile_off16;     // tensor-core tiles before this instance
+  int64_t tile_off16;     // tiles before this instance in its tensor-core kernel's tile list
   float kappa16;          // BF16 / tensor-core accumulation bound coefficient for Kp16
-  float pad;
 };
 
 struct BatchState {
@@ -57,7 +57,17 @@ struct BatchState {
   int32_t n_rech, cursor;
 };
 
-constexpr int NCLS = 4;  // tensor-core classes: Kp16 = 64, 128, 192, 256
+// Tensor-core classes by padded width Kp16 = 16, 32, 64, 128, 192, 256.  A tile's K runs in stages
+// of `chunk` columns: one stage of 16, 32 or 64 columns (32-, 64- or 128-byte swizzle) up to
+// Kp16 = 64, then stages of 64.
+constexpr int NCLS = 6;
+__host__ __device__ constexpr int cls_kp16(int c) { return c == 0 ? 16 : c == 1 ? 32 : 64 * (c - 1); }
+__host__ __device__ constexpr int cls_chunk(int c) { return c == 0 ? 16 : c == 1 ? 32 : 64; }
+__host__ __device__ constexpr int cls_nchunks(int c) { return c < 3 ? 1 : c - 1; }
+inline int cls_of_d(int d) { return d <= 16 ? 0 : d <= 32 ? 1 : (d + 63) / 64 + 1; }
+struct X16Set {
+  __nv_bfloat16* p[NCLS];
+};
 struct BatchMaps {
   CUtensorMap m[NCLS];
   CUtensorMap h;  // [rows16][16] BF16: -|x~|^2 / 2 as three BF16 pieces, then zeros
@@ -183,8 +193,7 @@ __global__ void batch_bounds_kernel(const BatchInst* __restrict__ inst, BatchSta
 // residual |x - x~| (exact in FP32) bounds the rounding, as in the dense stage's preparation.
 __global__ void __launch_bounds__(256) batch_prep16_kernel(const BatchInst* __restrict__ inst,
                                                            const int64_t* __restrict__ grow_offs, int count,
-                                                           int64_t rows16, __nv_bfloat16* X16_0, __nv_bfloat16* X16_1,
-                                                           __nv_bfloat16* X16_2, __nv_bfloat16* X16_3,
+                                                           int64_t rows16, X16Set X16,
                                                            float* __restrict__ norms16, __nv_bfloat16* __restrict__ H16,
                                                            BatchState* st) {
   const int lane = threadIdx.x & 31;
@@ -209,9 +218,8 @@ __global__ void __launch_bounds__(256) batch_prep16_kernel(const BatchInst* __re
       in = inst[q];
     }
     const int64_t lr = r - in.grow_off16;
-    const int Kp16 = 64 * (in.cls + 1);
-    __nv_bfloat16* base = in.cls == 0 ? X16_0 : in.cls == 1 ? X16_1 : in.cls == 2 ? X16_2 : X16_3;
-    __nv_bfloat16* out = base + (in.row_off16 + lr) * Kp16;
+    const int Kp16 = cls_kp16(in.cls);
+    __nv_bfloat16* out = X16.p[in.cls] + (in.row_off16 + lr) * Kp16;
     float n2 = 0.f, dd = 0.f;
     for (int k = lane; k < Kp16; k += 32) {
       float v = 0.f;
@@ -423,12 +431,27 @@ __global__ void __launch_bounds__(TILE_NT, 2)
 namespace btc {
 using namespace tc;
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+// A stage holds one K chunk (16, 32 or 64 columns) of the tile's A rows and B rows at fixed offsets
+// sized for 64 columns, and on the first chunk the B rows' norm pieces H.  Every region starts on a
+// 1024-byte boundary, and the B rows 128..255 start 128 rows (a multiple of the swizzle atom) after
+// row 0, so the same offsets serve all three swizzle widths.
 constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, H_BYTES = BN * 16 * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES + H_BYTES;  // H: the B rows' norm pieces (first K chunk only)
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES + H_BYTES;
 constexpr int ONES_BYTES = 256;                           // 8 x 32-byte rows of the constant operand
-constexpr int GROUPS = 2;                         // epilogue groups, one TMEM accumulator each
-constexpr int NTHREADS = 64 + GROUPS * 128 + 32;  // producer, MMA, 2 x 4 epilogue warps, tile decoder
-constexpr int DECODER = NTHREADS / 32 - 1;        // the decoder's warp
+// Epilogue shape G (the kernel's template parameter): G groups of four warps.  With G = 2 group a
+// reads the whole accumulator a of the CTA's tiles a, a + 2, ...; with G = 4 group 2 h + a reads half
+// h of it (TMEM columns 256 a + 128 h .. + 127), so twice the warps share each tile.  Either way every
+// 128-column half of a tile is a block of its own for the minimum, the record and the bound update.
+// Four groups pay off where the MMAs are short (small d: the epilogue paces the kernel), two where
+// they are long (fewer warps pay the per-tile bookkeeping); the tuning policy picks per class.
+template <int G>
+struct Shape {
+  static_assert(G == 2 || G == 4, "two or four epilogue groups");
+  static constexpr int HALVES = 4 / G;                // 128-column halves per group and tile
+  static constexpr int NTHREADS = 64 + G * 128 + 32;  // producer, MMA, the epilogue warps, tile decoder
+  static constexpr int DECODER = NTHREADS / 32 - 1;   // the decoder's warp
+  static constexpr int RING_READERS = 1 + 4 * (G / 2);  // producer and the warps of the tile's groups
+};
 constexpr uint32_t TMEM_COLS = 512;
 
 // What the decoder warp publishes about each of the CTA's tiles (ring slot = tile iteration % RING).
@@ -436,29 +459,36 @@ struct TileInfo {
   int32_t q, bi, bj, n;
   int64_t grow;      // first BF16 row of the instance (norms, norm pieces)
   int64_t row16;     // first row of the instance in its class matrix
-  int32_t cls;       // class: K chunks of 64 = cls + 1
+  int32_t cls;       // width class (cls_kp16, cls_chunk, cls_nchunks)
   float th_r;        // radius emission threshold on D~ (-inf: no radius output)
   BoundParams bp;    // the instance's tensor-core bound parameters
 };
 constexpr int RING = 16;         // tile records in flight
-constexpr int RING_READERS = 6;  // producer, MMA issuer, the four warps of the tile's epilogue group
+
+// Shared-memory descriptor of a K-major operand region whose rows hold `chunk` 16-bit values.
+__device__ __forceinline__ uint64_t op_desc(uint32_t saddr, int chunk) {
+  return chunk == 64 ? sw128_desc(saddr) : chunk == 32 ? sw64_desc(saddr) : sw32_desc(saddr, 256);
+}
 
 // Fault injection for the tests of the bounded waits (cpp_set_fault_injection): when non-zero the TMA
 // producer issues no copy (and consumes no tile record), so the MMA issuer's, the epilogue's and the
 // decoder's waits run out and the batch reports CPPGB_ERR_TIMEOUT.  Zero unless a test sets it.
 __device__ int g_fault_skip_tma = 0;
 
+template <int G>
 struct Ctl {
-  uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
+  uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;  // tfull / tempty per accumulator
+  uint32_t shdr[STAGES];  // what the stage holds: chunk width | chunk index << 8 | chunks of the tile << 16
   uint64_t info_full[RING], info_empty[RING];
   TileInfo info[RING];
-  unsigned int wmin[GROUPS][2][4];  // per group and tile parity: each warp's minimum (float bits, >= 0)
-  unsigned int arrived[GROUPS][2];  // warps that have stored their minimum
+  unsigned int wmin[G][2][Shape<G>::HALVES][4];  // per group, parity of its tile count and half: each warp's minimum
+  unsigned int arrived[G][2];                    // warps that have stored their minima
   uint32_t tmem_base;
   int abort_flag;
 };
-constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + ONES_BYTES + sizeof(Ctl) + 1024;  // + alignment slack
-static_assert(SMEM_BYTES <= 232448, "dynamic shared memory above the 227 KB opt-in limit");
+template <int G>
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + ONES_BYTES + sizeof(Ctl<G>) + 1024;  // + alignment slack
+static_assert(SMEM_BYTES<2> <= 232448 && SMEM_BYTES<4> <= 232448, "dynamic shared memory above the 227 KB opt-in limit");
 
 // Tiles (bi, bj) of one instance: 128-row blocks bi < nrow16, 256-column blocks bj with
 // bj >= bi / 2 (every such tile holds a pair i < j).  Rows 2k and 2k + 1 have nbj - k tiles, so
@@ -539,13 +569,13 @@ struct TileWalker {
 // smallest D~ comes from its largest a (a depth-5 tree).  EDGE tiles mask entries off the triangle
 // and past n to -inf.
 template <bool EDGE>
-__device__ __forceinline__ float chunk_max(uint32_t (&r)[32], int64_t i, int64_t j0, int64_t n) {
+// Indices are 32-bit (n < 2^31): entry k (column j0 + k) is kept iff i < n and i < j0 + k < n.
+__device__ __forceinline__ float chunk_max(uint32_t (&r)[32], int32_t i, int32_t j0, int32_t n) {
   if (EDGE) {
+    const int32_t klo = i - j0, khi = i < n ? n - j0 : -1;  // keep klo < k < khi
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      const int64_t j = j0 + k;
-      if (!(i < n && j < n && j > i)) r[k] = __float_as_uint(__int_as_float(0xff800000));
-    }
+    for (int k = 0; k < 32; ++k)
+      if (!(k > klo && k < khi)) r[k] = __float_as_uint(__int_as_float(0xff800000));
   }
   float m[16];
 #pragma unroll
@@ -557,9 +587,8 @@ __device__ __forceinline__ float chunk_max(uint32_t (&r)[32], int64_t i, int64_t
   return fmaxf(fmaxf(m[0], m[2]), fmaxf(m[1], m[3]));
 }
 
-// The 8 chunks of a warp's 32 rows x 256 columns, branch-free within each pair of chunks: chunk
-// c + 1 loads from TMEM while chunk c is reduced.  Returns the rows' largest a; `hits` gets bit c when some entry of
-// chunk c may lie within the radius (D~ <= th_r), for the rare second look after the loop.
+// 64-column TMEM loads, split into issue and wait (the wait names the destination registers, so no
+// use of them is scheduled before it).
 __device__ __forceinline__ void tmem_ld64_nowait(uint32_t taddr, uint32_t (&r)[64]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
@@ -590,25 +619,77 @@ __device__ __forceinline__ void tmem_wait_ld64(uint32_t (&r)[64]) {
                :
                : "memory");
 }
+// Two 32-column chunks of one 64-column load: the rows' largest a so far, and bit c / c + 1 of
+// `hits` when some entry of that chunk may lie within the radius (D~ <= th_r).
 template <bool EDGE>
-__device__ __forceinline__ float tile_rows(uint32_t tbase, int64_t i, int64_t col0, int64_t n, float nx, float th_r,
+__device__ __forceinline__ void reduce64(uint32_t (&r)[64], int32_t i, int32_t j0, int32_t n, float nx, float th_r,
+                                         int c, uint32_t& hits, float& rmax) {
+  uint32_t (&lo)[32] = *reinterpret_cast<uint32_t(*)[32]>(&r[0]);
+  uint32_t (&hi)[32] = *reinterpret_cast<uint32_t(*)[32]>(&r[32]);
+  float m = chunk_max<EDGE>(lo, i, j0, n);
+  hits |= (fmaf(-2.f, m, nx) <= th_r ? 1u : 0u) << c;
+  rmax = fmaxf(rmax, m);
+  m = chunk_max<EDGE>(hi, i, j0 + 32, n);
+  hits |= (fmaf(-2.f, m, nx) <= th_r ? 1u : 0u) << (c + 1);
+  rmax = fmaxf(rmax, m);
+}
+
+// 32-column TMEM load into `r` that also names `keep` (the chunk being reduced meanwhile) as
+// read-write, so the reduction of `keep` cannot be moved above the load's issue.
+__device__ __forceinline__ void tmem_ld32_after(uint32_t taddr, uint32_t (&r)[32], uint32_t (&keep)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+      "[%64];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "+r"(keep[0]), "+r"(keep[1]), "+r"(keep[2]), "+r"(keep[3]), "+r"(keep[4]), "+r"(keep[5]), "+r"(keep[6]), "+r"(keep[7]), "+r"(keep[8]), "+r"(keep[9]), "+r"(keep[10]), "+r"(keep[11]), "+r"(keep[12]), "+r"(keep[13]), "+r"(keep[14]), "+r"(keep[15]), "+r"(keep[16]), "+r"(keep[17]), "+r"(keep[18]), "+r"(keep[19]), "+r"(keep[20]), "+r"(keep[21]), "+r"(keep[22]), "+r"(keep[23]), "+r"(keep[24]), "+r"(keep[25]), "+r"(keep[26]), "+r"(keep[27]), "+r"(keep[28]), "+r"(keep[29]), "+r"(keep[30]), "+r"(keep[31])
+      : "r"(taddr)
+      : "memory");
+}
+// Wait for the loads in flight; `after` (computed from the previous chunk) is an input, so that
+// computation stays before the wait.
+__device__ __forceinline__ void tmem_wait_ld32_after(uint32_t (&r)[32], float after) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               : "f"(after)
+               : "memory");
+}
+
+// A warp's 32 rows x (64 NLD) columns from TMEM.  Returns the rows' largest a; `hits` gets bit c for
+// the 32-column chunks c that may hold radius pairs, for the rare second look.  Interior tiles issue
+// each 32-column load before the previous chunk is reduced (the asm operands pin that order), so the
+// load latency overlaps the max trees; EDGE tiles (masked entries, a small share of the work) load,
+// wait and reduce 64 columns at a time.
+template <bool EDGE, int NLD>
+__device__ __forceinline__ float tile_rows(uint32_t tbase, int32_t i, int32_t col0, int32_t n, float nx, float th_r,
                                            uint32_t& hits) {
   float rmax = __int_as_float(0xff800000);
-  // one 64-column TMEM load and one wait per pair of 32-column chunks
-  uint32_t ra[64];
+  if (EDGE) {
+    uint32_t ra[64];
 #pragma unroll 1
-  for (int c = 0; c < BN / 32; c += 2) {
-    __syncwarp();
-    tmem_ld64_nowait(tbase + (uint32_t)(c * 32), ra);
-    tmem_wait_ld64(ra);
-    uint32_t (&lo)[32] = *reinterpret_cast<uint32_t(*)[32]>(&ra[0]);
-    uint32_t (&hi)[32] = *reinterpret_cast<uint32_t(*)[32]>(&ra[32]);
-    float m = chunk_max<EDGE>(lo, i, col0 + c * 32, n);
+    for (int c = 0; c < NLD; ++c) {
+      __syncwarp();
+      tmem_ld64_nowait(tbase + (uint32_t)(c * 64), ra);
+      tmem_wait_ld64(ra);
+      reduce64<true>(ra, i, col0 + c * 64, n, nx, th_r, 2 * c, hits, rmax);
+    }
+    return rmax;
+  }
+  uint32_t ra[32], rb[32];
+  __syncwarp();
+  tmem_ld32_nowait(tbase, ra);
+  tmem_wait_ld(ra);
+#pragma unroll
+  for (int c = 0; c < 2 * NLD; c += 2) {
+    tmem_ld32_after(tbase + (uint32_t)((c + 1) * 32), rb, ra);
+    float m = chunk_max<false>(ra, i, col0 + c * 32, n);
     hits |= (fmaf(-2.f, m, nx) <= th_r ? 1u : 0u) << c;
     rmax = fmaxf(rmax, m);
-    m = chunk_max<EDGE>(hi, i, col0 + (c + 1) * 32, n);
+    tmem_wait_ld32_after(rb, rmax);
+    if (c + 2 < 2 * NLD) tmem_ld32_after(tbase + (uint32_t)((c + 2) * 32), ra, rb);
+    m = chunk_max<false>(rb, i, col0 + (c + 1) * 32, n);
     hits |= (fmaf(-2.f, m, nx) <= th_r ? 1u : 0u) << (c + 1);
     rmax = fmaxf(rmax, m);
+    if (c + 2 < 2 * NLD) tmem_wait_ld32_after(ra, rmax);
   }
   return rmax;
 }
@@ -646,7 +727,10 @@ __device__ __noinline__ void emit_radius(uint32_t tbase, uint32_t flags, int64_t
   }
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1)
+// 19 warps (four groups): five of them share an SM sub-partition's 16,384 registers, so at most 96
+// each; 11 warps (two groups): three per sub-partition, at most 168.
+template <int G>
+__global__ void __maxnreg__(G == 4 ? 96 : 168)
     batch_tc_kernel(const __grid_constant__ BatchMaps maps, const BatchInst* __restrict__ inst,
                     const int64_t* __restrict__ tile_offs16, int count, int64_t total, const float* __restrict__ norms16,
                     BatchState* st, BatchGlobals* g, BatchCand* __restrict__ cand, int64_t cap,
@@ -654,7 +738,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* ones = smem + STAGES * STAGE_BYTES;  // 1024-aligned
-  Ctl* ctl = (Ctl*)(ones + ONES_BYTES);
+  using S = Shape<G>;
+  Ctl<G>* ctl = (Ctl<G>*)(ones + ONES_BYTES);
   volatile int* abort_flag = &ctl->abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // this CTA's tiles: t = blockIdx.x + it * gridDim.x, it < ntl
@@ -678,14 +763,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&ctl->tfull[a], 1);
-      mbar_init(&ctl->tempty[a], 4);
+      mbar_init(&ctl->tempty[a], 4 * (G / 2));  // the warps of the accumulator's epilogue groups
     }
     for (int r = 0; r < RING; ++r) {
       mbar_init(&ctl->info_full[r], 1);
-      mbar_init(&ctl->info_empty[r], RING_READERS);
+      mbar_init(&ctl->info_empty[r], S::RING_READERS);
     }
     mbar_init(&ctl->drain, 1);
-    for (int a = 0; a < GROUPS; ++a)
+    for (int a = 0; a < G; ++a)
       for (int b = 0; b < 2; ++b) ctl->arrived[a][b] = 0u;
     ctl->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -701,7 +786,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = ctl->tmem_base;
 
-  if (warp == DECODER) {
+  if (warp == S::DECODER) {
     if (lane == 0) {  // ---------------------------------------------- tile decoder
       TileWalker w;
       w.init(tile_offs16, inst, count);
@@ -751,13 +836,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const CUtensorMap* map = &maps.m[ti.cls];
         const int ya = (int)(ti.row16 + (int64_t)ti.bi * BM), yb = (int)(ti.row16 + (int64_t)ti.bj * BN);
         const int yh = (int)(ti.grow + (int64_t)ti.bj * BN);
-        for (int kc = 0; kc <= ti.cls; ++kc) {
+        const int kch = cls_nchunks(ti.cls), kcw = cls_chunk(ti.cls);
+        const uint32_t rows128 = (uint32_t)(BM * kcw * 2);  // bytes of 128 rows of one chunk
+        for (int kc = 0; kc < kch; ++kc) {
           if (!mbar_wait(&ctl->empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
           uint8_t* sa = smem + stage * STAGE_BYTES;
-          mbar_arrive_expect_tx(&ctl->full[stage], A_BYTES + B_BYTES + (kc == 0 ? H_BYTES : 0));
-          tma_load_2d(sa, map, &ctl->full[stage], kc * BK, ya);
-          tma_load_2d(sa + A_BYTES, map, &ctl->full[stage], kc * BK, yb);
-          tma_load_2d(sa + A_BYTES + BM * BK * 2, map, &ctl->full[stage], kc * BK, yb + BM);
+          ctl->shdr[stage] = (uint32_t)kcw | ((uint32_t)kc << 8) | ((uint32_t)kch << 16);  // released by the arrive
+          mbar_arrive_expect_tx(&ctl->full[stage], 3u * rows128 + (kc == 0 ? H_BYTES : 0));
+          tma_load_2d(sa, map, &ctl->full[stage], kc * kcw, ya);
+          tma_load_2d(sa + A_BYTES, map, &ctl->full[stage], kc * kcw, yb);
+          tma_load_2d(sa + A_BYTES + rows128, map, &ctl->full[stage], kc * kcw, yb + BM);
           if (kc == 0) tma_load_2d(sa + A_BYTES + B_BYTES, &maps.h, &ctl->full[stage], 0, yh);
           ++issued;
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -778,31 +866,40 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---------------------------------------------- MMA issuer
-      const uint32_t idesc = make_idesc(1u, BM, BN);  // BF16 operands
+      // Driven by the stages alone: each stage's header (written by the producer before the stage's
+      // arrive, read after the full wait) gives the chunk's width, its index and the tile's chunk
+      // count, so between two tiles this thread only waits for the next stage and, on a tile's first
+      // chunk, for the accumulator.  Tile it goes to accumulator it & 1 (columns 256 (it & 1) ..);
+      // one N = 256 MMA per K = 16 step, then one more that adds the B rows' norm pieces.
+      const uint32_t idesc = make_idesc(1u, BM, BN);
+      const uint64_t ones_d = sw32_desc(smem_u32(ones), 0);
       uint32_t stage = 0, phase = 0;
       bool ok = true;
       for (int64_t it = 0; it < ntl && ok; ++it) {
         const uint32_t acc = (uint32_t)(it & 1), use = (uint32_t)((it >> 1) & 1);
-        if (!mbar_wait(&ctl->tempty[acc], use ^ 1u, abort_flag)) { ok = false; break; }
-        tc_fence_after();
         const uint32_t dtmem = tmem_base + acc * (uint32_t)BN;
-        const uint32_t slot = (uint32_t)(it % RING);
-        if (!mbar_wait(&ctl->info_full[slot], (uint32_t)((it / RING) & 1), abort_flag)) { ok = false; break; }
-        const int kch = ctl->info[slot].cls + 1;
-        mbar_arrive(&ctl->info_empty[slot]);
-        for (int kc = 0; kc < kch; ++kc) {
+        int kc = 0, kch = 1;
+        do {
           if (!mbar_wait(&ctl->full[stage], phase, abort_flag)) { ok = false; break; }
+          const uint32_t hdr = ctl->shdr[stage];
+          const int kcw = (int)(hdr & 0xffu);
+          kc = (int)((hdr >> 8) & 0xffu);
+          kch = (int)(hdr >> 16);
+          if (kc == 0 && !mbar_wait(&ctl->tempty[acc], use ^ 1u, abort_flag)) { ok = false; break; }
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
-          const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk)
-            mma_f16(dtmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (kc | kk) != 0);
+          const uint64_t ad = op_desc(sa, kcw), bd = op_desc(sa + A_BYTES, kcw);
+          mma_f16(dtmem, ad, bd, idesc, kc != 0);
+          if (kcw >= 32) mma_f16(dtmem, ad + 2, bd + 2, idesc, 1u);
+          if (kcw == 64) {
+            mma_f16(dtmem, ad + 4, bd + 4, idesc, 1u);
+            mma_f16(dtmem, ad + 6, bd + 6, idesc, 1u);
+          }
           if (kc == 0)  // + ones x (B rows' norm pieces): a_ij = x~_i.x~_j - |x~_j|^2 / 2
-            mma_f16(dtmem, sw32_desc(smem_u32(ones), 0), sw32_desc(sa + A_BYTES + B_BYTES, 256), idesc, 1u);
+            mma_f16(dtmem, ones_d, sw32_desc(sa + A_BYTES + B_BYTES, 256), idesc, 1u);
           mma_commit(&ctl->empty[stage]);
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-        }
+        } while (kc + 1 < kch);
         if (!ok) break;
         mma_commit(&ctl->tfull[acc]);
       }
@@ -816,85 +913,105 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
   } else {  // -------------------------------------------------------- epilogue groups
-    // Group grp takes the CTA's tiles it = grp, grp + 2, ... and their accumulator grp; warp
-    // (warp & 3) reads TMEM lanes 32 (warp & 3) .. + 31 (the rows it may access).  The warps of a
-    // group never wait for one another: each stores its minimum, and the last to arrive takes the
-    // tile's record decision.
-    const int grp = (warp - 2) >> 2;
+    // Group grp takes the CTA's tiles it = a, a + 2, ... in accumulator a and, of each, the 128-column
+    // halves h0 .. h0 + HALVES - 1; warp (warp & 3) reads TMEM lanes 32 (warp & 3) .. + 31 (the rows
+    // it may access).  Each half is a 128 x 128 block of its own: its minimum, its record for the FP32
+    // second pass and its bound update.  The groups never wait for one another, nor do the warps of
+    // a group: each stores its minima, and the last to arrive takes the halves' record decisions.
+    constexpr int HALVES = S::HALVES;
+    const int grp = (warp - 2) >> 2, par_a = grp % 2, h0 = (grp / 2) * HALVES;
     const uint32_t quarter = (uint32_t)(warp & 3);
     const float INF = __int_as_float(0x7f800000);
-    // the record and row norm of the group's next tile are read one tile ahead
-    TileInfo nxt;
+    // A warp keeps its tile's ring slot until the tile is done and reads the record's fields from
+    // shared memory where it needs them (few registers stay live across the TMEM reads); the row
+    // norm of the group's next tile is loaded one tile ahead.
     float nx_n = 0.f;
     bool ok = true;
     auto fetch = [&](int64_t it) -> bool {
-      const bool got =
-          __all_sync(0xffffffffu, mbar_wait(&ctl->info_full[it % RING], (uint32_t)((it / RING) & 1), abort_flag));
+      const uint32_t slot = (uint32_t)(it % RING);
+      const bool got = __all_sync(0xffffffffu, mbar_wait(&ctl->info_full[slot], (uint32_t)((it / RING) & 1), abort_flag));
       if (!got) return false;
-      nxt = ctl->info[it % RING];
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&ctl->info_empty[it % RING]);
-      nx_n = norms16[nxt.grow + (int64_t)nxt.bi * BM + quarter * 32 + lane];
+      const TileInfo* ti = &ctl->info[slot];
+      nx_n = norms16[ti->grow + (int64_t)ti->bi * BM + quarter * 32 + lane];
       return true;
     };
-    if (grp < ntl) ok = fetch(grp);
+    if (par_a < ntl) ok = fetch(par_a);
     int64_t k = 0;
-    for (int64_t it = grp; it < ntl && ok; it += GROUPS, ++k) {
-      const TileInfo cur = nxt;
+    const uint32_t tb = tmem_base + ((quarter * 32u) << 16) + (uint32_t)par_a * (uint32_t)BN + (uint32_t)h0 * (BN / 2);
+    for (int64_t it = par_a; it < ntl && ok; it += 2, ++k) {
+      const TileInfo* cur = &ctl->info[it % RING];
       const float nx = nx_n;
-      const int q = cur.q;
-      const float Ug = __uint_as_float(*reinterpret_cast<volatile unsigned int*>(&st[q].U_bits));  // early load
-      if (it + GROUPS < ntl && !fetch(it + GROUPS)) { ok = false; break; }
+      const float Ug = __uint_as_float(*reinterpret_cast<volatile unsigned int*>(&st[cur->q].U_bits));  // early load
+      if (it + 2 < ntl && !fetch(it + 2)) { ok = false; break; }
       const uint32_t par = (uint32_t)(k & 1);
-      if (!__all_sync(0xffffffffu, mbar_wait(&ctl->tfull[grp], par, abort_flag))) { ok = false; break; }
+      if (!__all_sync(0xffffffffu, mbar_wait(&ctl->tfull[par_a], par, abort_flag))) { ok = false; break; }
       tc_fence_after();
-      const int64_t n = cur.n, row0 = (int64_t)cur.bi * BM, col0 = (int64_t)cur.bj * BN;
-      const int64_t i = row0 + quarter * 32 + lane;
-      const bool edge = (row0 + BM - 1 >= n) || (col0 + BN - 1 >= n) || (col0 < row0 + BM);
-      const uint32_t tbase = tmem_base + ((quarter * 32u) << 16) + (uint32_t)grp * (uint32_t)BN;
-      uint32_t hits = 0u;
-      const float rmax = edge ? tile_rows<true>(tbase, i, col0, n, nx, cur.th_r, hits)
-                              : tile_rows<false>(tbase, i, col0, n, nx, cur.th_r, hits);
-      const uint32_t flags = __reduce_or_sync(0xffffffffu, hits);
-      if (flags) emit_radius(tbase, flags, i, col0, n, nx, cur.th_r, q, g, cand, cap);
+      float rmax[HALVES];
+#pragma unroll
+      for (int hh = 0; hh < HALVES; ++hh) {
+        const int32_t n = cur->n, row0 = cur->bi * BM, c0 = cur->bj * BN + (h0 + hh) * (BN / 2);
+        const int32_t i = row0 + (int32_t)quarter * 32 + lane;
+        const bool edge = (row0 + BM - 1 >= n) || (c0 + BN / 2 - 1 >= n) || (c0 < row0 + BM);
+        const float th_r = cur->th_r;
+        const uint32_t t = tb + (uint32_t)hh * (BN / 2);
+        uint32_t hits = 0u;
+        rmax[hh] = edge ? tile_rows<true, 2>(t, i, c0, n, nx, th_r, hits) : tile_rows<false, 2>(t, i, c0, n, nx, th_r, hits);
+        const uint32_t flags = __reduce_or_sync(0xffffffffu, hits);
+        if (flags) emit_radius(t, flags, i, c0, n, nx, th_r, cur->q, g, cand, cap);
+      }
       // The accumulator has been read for the last time: release it now, so that the MMA of the
       // group's next tile overlaps the reductions and the record decision below.
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&ctl->tempty[grp]);
-      // this warp's smallest D~ (+inf for masked rows), clamped at 0 (a looser but valid bound),
-      // so the float bits order like the values
-      const unsigned int wm = __reduce_min_sync(0xffffffffu, __float_as_uint(fmaxf(fmaf(-2.f, rmax, nx), 0.f)));
-      // The minimum slots [grp][par] are reused two tiles later.  That tile's MMA needs every warp's
-      // release of the tile in between, which each warp gives only after this publication (and the
-      // last warp after its reset below), so no warp can overwrite a slot still being read.
+      if (lane == 0) mbar_arrive(&ctl->tempty[par_a]);
+      // this warp's smallest D~ per half (+inf for masked rows), clamped at 0 (a looser but valid
+      // bound), so the float bits order like the values
+      unsigned int wm[HALVES];
+#pragma unroll
+      for (int hh = 0; hh < HALVES; ++hh)
+        wm[hh] = __reduce_min_sync(0xffffffffu, __float_as_uint(fmaxf(fmaf(-2.f, rmax[hh], nx), 0.f)));
+      // The minimum slots [grp][par] are reused two of the group's tiles later.  That tile's MMA needs
+      // every warp's release of the group's tile in between, which each warp gives only after this
+      // publication (and the last warp after its reset below), so no warp can overwrite a slot still
+      // being read.
       bool last = false;
-      float tmin = INF;
+      float tmin[HALVES];
       if (lane == 0) {
-        ctl->wmin[grp][par][quarter] = wm;
+#pragma unroll
+        for (int hh = 0; hh < HALVES; ++hh) ctl->wmin[grp][par][hh][quarter] = wm[hh];
         __threadfence_block();
         last = atomicAdd(&ctl->arrived[grp][par], 1u) == 3u;
         if (last) {
           __threadfence_block();
-          const volatile unsigned int* v = ctl->wmin[grp][par];
-          tmin = __uint_as_float(min(min(v[0], v[1]), min(v[2], v[3])));
+#pragma unroll
+          for (int hh = 0; hh < HALVES; ++hh) {
+            const volatile unsigned int* v = ctl->wmin[grp][par][hh];
+            tmin[hh] = __uint_as_float(min(min(v[0], v[1]), min(v[2], v[3])));
+          }
           ctl->arrived[grp][par] = 0u;
         }
       }
-      if (last && tmin < INF) {  // the tile record and the bound update
-        if (tmin <= theta_of(Ug, cur.bp)) {
-          atomic_min_nonneg(&st[q].tmin16_bits, tmin);
-          // record the 128-column halves that hold a pair i < j < n for the FP32 second pass (the
-          // FP32 rows of an instance are padded to 128 only, so a half past n must not be read)
-          for (int64_t h = 2 * (int64_t)cur.bj; h <= 2 * (int64_t)cur.bj + 1; ++h) {
-            if (h < cur.bi || h * BM >= n) continue;
+      if (last) {  // each half's record and the bound update
+        const int q = cur->q;
+        const int32_t bi = cur->bi;
+        const BoundParams bp = cur->bp;
+        float ub = INF;
+#pragma unroll
+        for (int hh = 0; hh < HALVES; ++hh) {
+          if (!(tmin[hh] < INF)) continue;
+          // record the half for the FP32 second pass when its minimum can reach the bound (a half
+          // with a finite minimum holds a pair i < j < n, so its FP32 rows exist)
+          if (tmin[hh] <= theta_of(Ug, bp)) {
+            atomic_min_nonneg(&st[q].tmin16_bits, tmin[hh]);
             const unsigned long long kr = atomicAdd(&g->n_trec, 1ull);
-            if ((int64_t)kr < trec_cap) trec[kr] = TileRec{q | TC_FLAG, cur.bi, (int32_t)h, tmin};
+            if ((int64_t)kr < trec_cap) trec[kr] = TileRec{q | TC_FLAG, bi, 2 * cur->bj + h0 + hh, tmin[hh]};
           }
+          ub = fminf(ub, upper_d2(tmin[hh], bp));
         }
-        const float ub = upper_d2(tmin, cur.bp);
         if (ub < Ug) atomic_min_nonneg(&st[q].U_bits, ub);
       }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl->info_empty[it % RING]);  // the record is no longer read
     }
     if (!ok && lane == 0) {
       *abort_flag = 1;
@@ -1032,7 +1149,7 @@ __global__ void batch_finish_kernel(const BatchState* st, int count, const int64
 // ---------------------------------------------------------------- host side
 struct BatchLayout {
   BatchInst* inst;
-  int64_t *row_offs, *tile_offs, *grow_offs16, *tile_offs16;
+  int64_t *row_offs, *tile_offs, *grow_offs16, *tile_offs16[2];  // tensor-core tile lists: four-group, two-group kernel
   BatchState* st;
   BatchGlobals* g;
   int32_t* pair_counts;
@@ -1053,16 +1170,18 @@ struct BatchLayout {
   size_t bytes;
 };
 
-// Path of one instance: 1 = FP32 CUDA-core tiles, 2 = BF16 tensor-core tiles; 0 takes the tuning
-// policy's entry for the instance's n-bucket and d-class.
+// Path of one instance: 1 = FP32 CUDA-core tiles, 2 = BF16 tensor-core tiles read by four epilogue
+// groups, 3 = the same tiles read by two; 0 takes the tuning policy's entry for the instance's
+// n-bucket and d-class.
 int path_of(const cpp_instance& c) {
-  if (c.path == 1 || c.path == 2) return c.path;
+  if (c.path >= 1 && c.path <= 3) return c.path;
   return tuned_batch_path(c.n, c.d);
 }
 
 struct Totals {
   int64_t rows = 0, xfloats = 0, tiles = 0;         // FP32 layout (all instances) and FP32-path tiles
-  int64_t rows16 = 0, tiles16 = 0, crow16[NCLS] = {0, 0, 0, 0};
+  int64_t rows16 = 0, tiles16 = 0, crow16[NCLS] = {0, 0, 0, 0, 0, 0};
+  int64_t tiles16s[2] = {0, 0};  // tensor-core tiles of path 2 (four-group kernel) and path 3 (two-group)
 };
 
 int64_t nrow16_of(int64_t n) { return n >= 2 ? (n - 2) / 128 + 1 : 0; }
@@ -1081,11 +1200,12 @@ Totals totals_of(const cpp_instance* inst, int64_t count) {
     const int64_t nb = npad / TILE_BM;
     t.rows += npad;
     t.xfloats += npad * Kp;
-    if (path_of(inst[q]) == 2) {
+    if (path_of(inst[q]) >= 2) {
       const int64_t npad16 = (n + 255) / 256 * 256;
       t.rows16 += npad16;
-      t.crow16[(inst[q].d + 63) / 64 - 1] += npad16;
+      t.crow16[cls_of_d(inst[q].d)] += npad16;
       t.tiles16 += tiles16_of(n);
+      t.tiles16s[path_of(inst[q]) - 2] += tiles16_of(n);
     } else {
       t.tiles += n >= 2 ? nb * (nb + 1) / 2 : 0;
     }
@@ -1100,7 +1220,8 @@ BatchLayout batch_layout(void* ws, int64_t count, const Totals& t, size_t ws_byt
   L.row_offs = c.take<int64_t>(count + 1);
   L.tile_offs = c.take<int64_t>(count + 1);
   L.grow_offs16 = c.take<int64_t>(count + 1);
-  L.tile_offs16 = c.take<int64_t>(count + 1);
+  L.tile_offs16[0] = c.take<int64_t>(count + 1);
+  L.tile_offs16[1] = c.take<int64_t>(count + 1);
   L.st = c.take<BatchState>(count);
   L.g = c.take<BatchGlobals>(1);
   L.pair_counts = c.take<int32_t>(count + 1);
@@ -1111,7 +1232,7 @@ BatchLayout batch_layout(void* ws, int64_t count, const Totals& t, size_t ws_byt
   L.X = c.take<float>(t.xfloats + 16);
   L.norms = c.take<float>(t.rows + 1);
   for (int k = 0; k < NCLS; ++k)  // at least 256 rows each, so every class has a valid tensor map
-    L.X16[k] = c.take<__nv_bfloat16>((size_t)(t.crow16[k] > 256 ? t.crow16[k] : 256) * 64 * (k + 1));
+    L.X16[k] = c.take<__nv_bfloat16>((size_t)(t.crow16[k] > 256 ? t.crow16[k] : 256) * cls_kp16(k));
   L.norms16 = c.take<float>(t.rows16 + 1);
   L.H16 = c.take<__nv_bfloat16>((size_t)(t.rows16 > 256 ? t.rows16 : 256) * 16);
   L.trec_cap = 2 * (t.tiles + t.tiles16) + 2;  // at most one record per 128 x 128 tile
@@ -1168,15 +1289,19 @@ int encode_h_map(CUtensorMap* m, void* base, int64_t rows) {
   return CPPGB_OK;
 }
 
-int encode_class_map(CUtensorMap* m, void* base, int64_t rows, int64_t Kp) {
+// rows of class cls: [rows][Kp16] BF16, box chunk x 128 with the swizzle of the chunk's row length
+int encode_class_map(CUtensorMap* m, void* base, int64_t rows, int cls) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return CPPGB_ERR_CUDA;
+  const int Kp = cls_kp16(cls), chunk = cls_chunk(cls);
   const cuuint64_t gdim[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
   const cuuint64_t gstride[1] = {(cuuint64_t)Kp * 2};
-  const cuuint32_t box[2] = {64, 128};
+  const cuuint32_t box[2] = {(cuuint32_t)chunk, 128};
   const cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapSwizzle sw = chunk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : chunk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
   const CUresult cr = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, gdim, gstride, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return set_error(CPPGB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
   return CPPGB_OK;
@@ -1186,14 +1311,15 @@ int encode_class_map(CUtensorMap* m, void* base, int64_t rows, int64_t Kp) {
 struct GraphKey {
   void* ws;
   size_t ws_bytes;
-  int64_t count, rows, tiles, cap, rows16, tiles16, c0, c1, c2, c3;
+  int64_t count, rows, tiles, cap, rows16, tiles16, t2, t3, c[NCLS];
   int32_t* pairs;
   int64_t pairs_cap;
   bool timing;
   bool operator==(const GraphKey& o) const {
     return timing == o.timing && ws == o.ws && ws_bytes == o.ws_bytes && count == o.count && rows == o.rows && tiles == o.tiles &&
-           cap == o.cap && rows16 == o.rows16 && tiles16 == o.tiles16 && c0 == o.c0 && c1 == o.c1 && c2 == o.c2 &&
-           c3 == o.c3 && pairs == o.pairs && pairs_cap == o.pairs_cap;
+           cap == o.cap && rows16 == o.rows16 && tiles16 == o.tiles16 && t2 == o.t2 && t3 == o.t3 &&
+           std::equal(c, c + NCLS, o.c) &&
+           pairs == o.pairs && pairs_cap == o.pairs_cap;
   }
 };
 std::mutex g_graph_mu;
@@ -1216,20 +1342,25 @@ int enqueue_batch(const BatchLayout& L, int64_t count, const Totals& t, int32_t*
                                                                   L.g);
   CPPGB_LAUNCH_CHECK();
   if (t.rows16 > 0) {
-    batch_prep16_kernel<<<(unsigned)((t.rows16 + 8 * PREP_RUN - 1) / (8 * PREP_RUN)), 256, 0, st>>>(L.inst, L.grow_offs16, ci, t.rows16, L.X16[0],
-                                                                        L.X16[1], L.X16[2], L.X16[3], L.norms16, L.H16,
-                                                                        L.st);
+    X16Set xs;
+    for (int k = 0; k < NCLS; ++k) xs.p[k] = L.X16[k];
+    batch_prep16_kernel<<<(unsigned)((t.rows16 + 8 * PREP_RUN - 1) / (8 * PREP_RUN)), 256, 0, st>>>(
+        L.inst, L.grow_offs16, ci, t.rows16, xs, L.norms16, L.H16, L.st);
     CPPGB_LAUNCH_CHECK();
   }
   batch_bounds_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(L.inst, L.st, ci);
   CPPGB_LAUNCH_CHECK();
   if (timing) CPPGB_CUDA_TRY(cudaEventRecordWithFlags(g_bev[1], st, cudaEventRecordExternal));
-  if (t.tiles16 > 0) {
-    const size_t smem = btc::SMEM_BYTES;
-    const int64_t grid = t.tiles16 < sms ? t.tiles16 : sms;
-    btc::batch_tc_kernel<<<(unsigned)grid, btc::NTHREADS, smem, st>>>(maps, L.inst, L.tile_offs16, ci, t.tiles16,
-                                                                       L.norms16, L.st, L.g, L.cand, L.cap, L.trec,
-                                                                       L.trec_cap);
+  if (t.tiles16s[0] > 0) {  // path 2: four epilogue groups
+    const int64_t grid = t.tiles16s[0] < sms ? t.tiles16s[0] : sms;
+    btc::batch_tc_kernel<4><<<(unsigned)grid, btc::Shape<4>::NTHREADS, btc::SMEM_BYTES<4>, st>>>(
+        maps, L.inst, L.tile_offs16[0], ci, t.tiles16s[0], L.norms16, L.st, L.g, L.cand, L.cap, L.trec, L.trec_cap);
+    CPPGB_LAUNCH_CHECK();
+  }
+  if (t.tiles16s[1] > 0) {  // path 3: two epilogue groups
+    const int64_t grid = t.tiles16s[1] < sms ? t.tiles16s[1] : sms;
+    btc::batch_tc_kernel<2><<<(unsigned)grid, btc::Shape<2>::NTHREADS, btc::SMEM_BYTES<2>, st>>>(
+        maps, L.inst, L.tile_offs16[1], ci, t.tiles16s[1], L.norms16, L.st, L.g, L.cand, L.cap, L.trec, L.trec_cap);
     CPPGB_LAUNCH_CHECK();
   }
   if (timing) CPPGB_CUDA_TRY(cudaEventRecordWithFlags(g_bev[2], st, cudaEventRecordExternal));
@@ -1297,7 +1428,7 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
     const cpp_instance& c = inst[q];
     if (c.n < 0 || c.n > (1 << 30)) return set_error(CPPGB_ERR_ARG, "instance %lld: n out of range", (long long)q);
     if (c.d < 1 || c.d > 256) return set_error(CPPGB_ERR_ARG, "instance %lld: d must be in [1, 256]", (long long)q);
-    if (c.path < 0 || c.path > 2) return set_error(CPPGB_ERR_ARG, "instance %lld: path must be 0, 1 or 2", (long long)q);
+    if (c.path < 0 || c.path > 3) return set_error(CPPGB_ERR_ARG, "instance %lld: path must be 0, 1, 2 or 3", (long long)q);
     if (c.n > 0 && !c.pts) return set_error(CPPGB_ERR_ARG, "instance %lld: pts is NULL", (long long)q);
     if (!isfinite(c.R)) return set_error(CPPGB_ERR_ARG, "instance %lld: R must be finite", (long long)q);
   }
@@ -1309,8 +1440,9 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
 
   // instance table (host-built, copied before the graph runs)
   std::vector<BatchInst> hi((size_t)count);
-  std::vector<int64_t> hro((size_t)count + 1), hto((size_t)count + 1), hgo((size_t)count + 1), hto16((size_t)count + 1);
-  int64_t xo = 0, ro = 0, to = 0, go = 0, to16 = 0, co[NCLS] = {0, 0, 0, 0};
+  std::vector<int64_t> hro((size_t)count + 1), hto((size_t)count + 1), hgo((size_t)count + 1);
+  std::vector<int64_t> hto16[2] = {std::vector<int64_t>((size_t)count + 1), std::vector<int64_t>((size_t)count + 1)};
+  int64_t xo = 0, ro = 0, to = 0, go = 0, to16[2] = {0, 0}, co[NCLS] = {0, 0, 0, 0, 0, 0};
   for (int64_t q = 0; q < count; ++q) {
     const cpp_instance& c = inst[q];
     BatchInst b;
@@ -1326,27 +1458,29 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
     b.rr32 = c.R >= 0.0 ? (float)(c.R * c.R) * (1.f + 0x1p-20f) : 0.f;
     b.kappa = kappa_fp32(b.Kp);
     const int64_t npad = (c.n + TILE_BM - 1) / TILE_BM * TILE_BM, nb = npad / TILE_BM;
-    b.tc = path_of(c) == 2;
-    b.cls = (c.d + 63) / 64 - 1;
+    const int path = path_of(c);
+    const int kl = path == 3 ? 1 : 0;  // tensor-core tile list (kernel) of the instance
+    b.tc = path >= 2;
+    b.cls = cls_of_d(c.d);
     b.nbj16 = (int32_t)((c.n + 255) / 256);
     b.nrow16 = (int32_t)nrow16_of(c.n);
     b.row_off16 = b.tc ? co[b.cls] : 0;
     b.grow_off16 = go;
-    b.tile_off16 = to16;
-    b.kappa16 = kappa_tc(64 * (b.cls + 1));
-    b.pad = 0.f;
+    b.tile_off16 = to16[kl];
+    b.kappa16 = kappa_tc(cls_kp16(b.cls));
     if (b.tc) b.tile_off = to;  // no FP32-path tiles
     hro[(size_t)q] = ro;
     hto[(size_t)q] = to;
     hgo[(size_t)q] = go;
-    hto16[(size_t)q] = to16;
+    hto16[0][(size_t)q] = to16[0];
+    hto16[1][(size_t)q] = to16[1];
     xo += npad * b.Kp;
     ro += npad;
     if (b.tc) {
       const int64_t npad16 = (c.n + 255) / 256 * 256;
       co[b.cls] += npad16;
       go += npad16;
-      to16 += tiles16_of(c.n);
+      to16[kl] += tiles16_of(c.n);
     } else {
       to += c.n >= 2 ? nb * (nb + 1) / 2 : 0;
     }
@@ -1355,15 +1489,18 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
   hro[(size_t)count] = ro;
   hto[(size_t)count] = to;
   hgo[(size_t)count] = go;
-  hto16[(size_t)count] = to16;
+  hto16[0][(size_t)count] = to16[0];
+  hto16[1][(size_t)count] = to16[1];
   CPPGB_CUDA_TRY(cudaMemcpyAsync(L.inst, hi.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, st));
   CPPGB_CUDA_TRY(cudaMemcpyAsync(L.row_offs, hro.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
   CPPGB_CUDA_TRY(cudaMemcpyAsync(L.tile_offs, hto.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
   CPPGB_CUDA_TRY(cudaMemcpyAsync(L.grow_offs16, hgo.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
-  CPPGB_CUDA_TRY(cudaMemcpyAsync(L.tile_offs16, hto16.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
+  for (int k = 0; k < 2; ++k)
+    CPPGB_CUDA_TRY(
+        cudaMemcpyAsync(L.tile_offs16[k], hto16[k].data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
   BatchMaps maps;
   for (int k = 0; k < NCLS; ++k) {
-    const int rc = encode_class_map(&maps.m[k], L.X16[k], t.crow16[k] > 256 ? t.crow16[k] : 256, 64 * (k + 1));
+    const int rc = encode_class_map(&maps.m[k], L.X16[k], t.crow16[k] > 256 ? t.crow16[k] : 256, k);
     if (rc) return rc;
   }
   {
@@ -1374,17 +1511,21 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
   int dev = 0, sms = 0;
   CPPGB_CUDA_TRY(cudaGetDevice(&dev));
   CPPGB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  if (t.tiles16 > 0)
-    CPPGB_CUDA_TRY(
-        cudaFuncSetAttribute(btc::batch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)btc::SMEM_BYTES));
+  if (t.tiles16s[0] > 0)
+    CPPGB_CUDA_TRY(cudaFuncSetAttribute(btc::batch_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)btc::SMEM_BYTES<4>));
+  if (t.tiles16s[1] > 0)
+    CPPGB_CUDA_TRY(cudaFuncSetAttribute(btc::batch_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)btc::SMEM_BYTES<2>));
   bool timing = stage_timing_on();
   if (timing && !g_bev[0])
     for (auto& e : g_bev)
       if (cudaEventCreate(&e) != cudaSuccess) timing = false;
   {
     std::lock_guard<std::mutex> lock(g_graph_mu);
-    const GraphKey key{ws, ws_bytes, count, t.rows, t.tiles, L.cap, t.rows16, t.tiles16, t.crow16[0], t.crow16[1],
-                       t.crow16[2], t.crow16[3], pairs, pairs_cap, timing};
+    GraphKey key{ws,        ws_bytes,     count, t.rows, t.tiles,   L.cap, t.rows16, t.tiles16,
+                 t.tiles16s[0], t.tiles16s[1], {},    pairs,  pairs_cap, timing};
+    std::copy(t.crow16, t.crow16 + NCLS, key.c);
     if (!(g_exec && key == g_key && g_dev == dev)) {
       if (g_exec) {
         cudaGraphExecDestroy(g_exec);

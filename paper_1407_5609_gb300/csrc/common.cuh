@@ -156,8 +156,10 @@ int set_fault_batch(int on);
 int set_fault_match(int on);
 
 // Tuning policy, process-wide (set through cpp_set_tuning, normally from the autotuner's cache).
-constexpr int TUNE_NB = 4, TUNE_DC = 4;  // batch n-buckets (n < 1024, 4096, 16384, rest) x d-classes ceil(d / 64)
-int tuned_batch_path(int64_t n, int d);   // 1 (FP32 tiles) or 2 (tensor-core tiles)
+// batch n-buckets (n < 1024, 4096, 16384, rest) x d-classes (the tensor-core widths d <= 16, 32, 64,
+// 128, 192, 256)
+constexpr int TUNE_NB = 4, TUNE_DC = 6;
+int tuned_batch_path(int64_t n, int d);  // 1 (FP32 tiles), 2 or 3 (tensor-core tiles, 4- or 2-group epilogue)
 int tuned_dense_band();                   // column blocks per band of the tensor-core dense stage
 int tuned_dense_shape();                  // 1: 128 x 256 tiles on one CTA, 2: 256 x 256 tiles on CTA pairs
 

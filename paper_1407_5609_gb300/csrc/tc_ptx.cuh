@@ -96,6 +96,17 @@ __device__ __forceinline__ uint64_t sw32_desc(uint32_t saddr, uint32_t sbo) {
   return d;
 }
 
+// K-major tile with the 64-byte swizzle (32 BF16 per row, two K = 16 steps 32 bytes apart): rows
+// of 64 bytes, 8-row groups 512 bytes apart, layout type 4 (64 B).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
 // Instruction descriptor, kind::f16: D = F32, A = B = F16 (0) or BF16 (1), both K-major, N, M.
 __host__ __device__ constexpr uint32_t make_idesc(uint32_t ab, uint32_t M, uint32_t N) {
   return (1u << 4) | (ab << 7) | (ab << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);

@@ -16,8 +16,8 @@ def test_tune_installs_a_valid_policy(tmp_path):
     try:
         entry = autotune.load_or_tune(path=str(tmp_path / "tune.json"), target_pairs=5e7, reps=1)
         table = np.asarray(entry["batch_path"])
-        assert table.shape == (4, 4) and set(table.reshape(-1)) <= {1, 2}
-        assert len(entry["batch_ms"]) == 16
+        assert table.shape == (4, 6) and set(table.reshape(-1)) <= {1, 2, 3}
+        assert len(entry["batch_ms"]) == 24
         assert capi.cpp_get_tuning(capi.TUNE_BATCH_PATH) == list(table.reshape(-1))
         if capi.filters_available():
             assert entry["dense_band"] in autotune.BANDS and entry["dense_shape"] in autotune.SHAPES

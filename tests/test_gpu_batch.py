@@ -61,17 +61,18 @@ def _mixed_instances():
     return insts, radii
 
 
-@pytest.mark.parametrize("paths", [None, 1, 2, "alternate"])
+@pytest.mark.parametrize("paths", [None, 1, 2, 3, "alternate"])
 def test_batch_mixed_instances_twice(paths):
-    """Both tile paths (FP32 CUDA cores, BF16 tensor cores), the default choice and a mix give
-    the oracle's answer; the second call replays the captured graph."""
+    """Every tile path (FP32 CUDA cores; BF16 tensor cores read by four or by two epilogue groups,
+    which run as two persistent kernels), the default choice and a mix of all three give the
+    oracle's answer; the second call replays the captured graph."""
     insts, radii = _mixed_instances()
     if paths == "alternate":
-        paths = [1 + (q % 2) for q in range(len(insts))]
+        paths = [1 + (q % 3) for q in range(len(insts))]
     _check_batch(insts, radii, repeat=2, paths=paths)
 
 
-@pytest.mark.parametrize("paths", [1, 2])
+@pytest.mark.parametrize("paths", [1, 2, 3])
 def test_batch_edge_instances(paths):
     g = synth.rng_for(72)
     ident = np.tile(g.random((1, 6)).astype(np.float32), (40, 1))
@@ -81,22 +82,25 @@ def test_batch_edge_instances(paths):
     assert counts[2] == 40 * 39 // 2
 
 
-def test_batch_tensor_core_ties_and_widths():
-    """Tensor-core path on exact ties (integer lattices: many pairs at the same distance, the
-    lexicographically smallest must win), on every padded width (d = 1, 64, 65, 128, 129, 192,
-    193, 256), on sizes around the 128/256 tile edges, and with an R whose square overflows FP32
-    (every pair is within R; masked tile entries must not be emitted)."""
+@pytest.mark.parametrize("path", [2, 3])
+def test_batch_tensor_core_ties_and_widths(path):
+    """Tensor-core paths (four- and two-group epilogues) on exact ties (integer lattices: many pairs at the
+    same distance, the lexicographically smallest must win), on every padded width class and its
+    edges (d = 1, 16, 17, 32, 33, 64, 65, 128, 129, 192, 193, 256), on sizes around the 128/256
+    tile edges, and with an R whose square overflows FP32 (every pair is within R; masked tile
+    entries must not be emitted)."""
     g = synth.rng_for(73)
     insts, radii = [], []
     lat = np.stack(np.meshgrid(*[np.arange(5, dtype=np.float32)] * 3, indexing="ij"), -1).reshape(-1, 3)
     insts.append(np.concatenate([lat, np.zeros((125, 29), np.float32)], 1))  # d = 32, min distance 1, ties
     radii.append(1.0)
-    for d, n in [(1, 300), (64, 255), (65, 256), (128, 257), (129, 383), (192, 129), (193, 128), (256, 511)]:
+    for d, n in [(1, 300), (16, 700), (17, 129), (32, 513), (33, 384), (64, 255), (65, 256), (128, 257), (129, 383),
+                 (192, 129), (193, 128), (256, 511)]:
         insts.append(g.standard_normal((n, d)).astype(np.float32))
         radii.append(float(np.sqrt(2 * d) * 0.8))
     insts.append(g.random((300, 24)).astype(np.float32))
     radii.append(1e20)
-    res, counts = _check_batch(insts, radii, paths=2)
+    res, counts = _check_batch(insts, radii, paths=path)
     assert counts[-1] == 300 * 299 // 2
 
 
@@ -109,11 +113,12 @@ def test_batch_paths_agree_on_generator_workload():
     pts = [to_dev(b.pts, dev) for b in batch]
     radii = [b.R for b in batch]
     r1, c1, p1 = capi.cpp_batch(pts, radii, paths=1)
-    r2, c2, p2 = capi.cpp_batch(pts, radii, paths=2)
-    for a, b in zip(r1, r2):
-        assert (a["i"], a["j"], a["dist2"]) == (b["i"], b["j"], b["dist2"])
-    np.testing.assert_array_equal(c1, c2)
-    assert torch_equal(p1, p2)
+    for path in (2, 3):
+        r2, c2, p2 = capi.cpp_batch(pts, radii, paths=path)
+        for a, b in zip(r1, r2):
+            assert (a["i"], a["j"], a["dist2"]) == (b["i"], b["j"], b["dist2"])
+        np.testing.assert_array_equal(c1, c2)
+        assert torch_equal(p1, p2)
 
 
 def torch_equal(a, b):
@@ -158,7 +163,7 @@ def _golden_batch():
         return json.load(f)
 
 
-@pytest.mark.parametrize("paths", [None, 1, 2])
+@pytest.mark.parametrize("paths", [None, 1, 2, 3])
 def test_batch_generator_workload_against_stored_oracle(paths):
     """All 2048 instances of make_batch() against the oracle's stored answer
     (tests/golden/batch_2048inst.json, written by make_golden.py from oracle/ alone): every closest

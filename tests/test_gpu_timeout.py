@@ -71,17 +71,19 @@ def test_motif_times_out_then_recovers(capi):
     assert (r["i"], r["j"], r["dist2"]) == oracle.tsmm(a, 64, 32)
 
 
-def test_batch_times_out_then_recovers(capi):
-    """The batch's captured graph is replayed: the fault is read by the kernel, not baked into the graph."""
+@pytest.mark.parametrize("path", [2, 3])
+def test_batch_times_out_then_recovers(capi, path):
+    """The batch's captured graph is replayed: the fault is read by the kernel, not baked into the
+    graph.  Both tensor-core kernels (four- and two-group epilogues) give up and recover."""
     import torch
     dev = device()
     inst = synth.make_batch(count=6, seed=74, n_hi=3000)
     pts = [to_dev(b.pts, dev) for b in inst]
     radii = [b.R for b in inst]
-    desc = [capi.cpp_instance(p.data_ptr(), p.shape[0], p.shape[1], capi.PATH_TC, R) for p, R in zip(pts, radii)]
+    desc = [capi.cpp_instance(p.data_ptr(), p.shape[0], p.shape[1], path, R) for p, R in zip(pts, radii)]
     ws = torch.empty(capi.cpp_batch_workspace_size(desc), dtype=torch.uint8, device=dev)
     pairs = torch.empty((1 << 12, 2), dtype=torch.int32, device=dev)
-    call = lambda: capi.cpp_batch(pts, radii, paths=capi.PATH_TC, ws=ws, pairs=pairs)
+    call = lambda: capi.cpp_batch(pts, radii, paths=path, ws=ws, pairs=pairs)
     _times_out(capi, call)
     res, counts, got = call()
     got = got.cpu().numpy()
