@@ -644,7 +644,8 @@ def roofline_of(wl, capi, mode, pk, dense_ms, stages, total_ms, steps, res=None)
             ach = wl.tc_flops / (tc_ms / 1e3) / 1e12
             return {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
                     "frac": ach / pk["bf16_tflops"], "traffic": recorded_traffic("batch_tc@batch"),
-                    "kernel": "batch_tc_kernel (persistent tcgen05 tiles of all tensor-core instances)",
+                    "kernel": "batch_tc_kernel<4> + batch_tc_kernel<2> (persistent tcgen05 tiles of all tensor-core "
+                              "instances, four- and two-group epilogues)",
                     "peak_source": f"{pk['source']} bf16 burst", "launch_ms": tc_ms,
                     "algorithmic_flop_per_launch": wl.tc_flops}, extra
         ach = wl.flops / (per_step_ms / 1e3) / 1e12
