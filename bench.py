@@ -640,6 +640,9 @@ def roofline_of(wl, capi, mode, pk, dense_ms, stages, total_ms, steps, res=None)
         # dominant kernel: the persistent tensor-core tile kernel (its time from events captured in
         # the batch's graph); algorithmic work 2 d flop per pair of the instances it runs
         tc_ms = statistics.mean(dense_ms) if dense_ms else None
+        if stages:  # per stage [preparation, tensor-core tiles, FP32 tiles, second pass + recheck + output]
+            extra["stages_ms"] = dict(zip(("prep", "tensor_core_tiles", "fp32_tiles", "second_pass_recheck_output"),
+                                          (statistics.mean(x[k] for x in stages) for k in range(4))))
         if wl.tc_flops and tc_ms:
             ach = wl.tc_flops / (tc_ms / 1e3) / 1e12
             return {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",

@@ -130,54 +130,77 @@ __global__ void batch_init_kernel(BatchState* st, int count, BatchGlobals* g) {
   st[q] = s;
 }
 
-// Consecutive rows per warp in the preparation kernels: the per-instance maxima are reduced in
-// registers over the run and flushed with one atomic per instance touched (a per-row atomic on
-// one address per instance serialises millions of updates).
-constexpr int PREP_RUN = 16;
+// Preparation kernels: each block takes rows of one instance only (blocks numbered per instance by
+// a host-built offset table, so every row of a block has the same width), several rows per warp with
+// each lane of a row's lane group handling 16 bytes of output; the row norms are summed in the lane
+// group and the per-instance maxima flushed with one atomic per block.
+constexpr int PREP_NT = 256;
 
-// FP32 rows of every instance (padded to Kp columns and to 128 rows) and their squared norms.
-__global__ void __launch_bounds__(256) batch_prep_kernel(const BatchInst* __restrict__ inst, const int64_t* __restrict__ row_offs,
-                                                         int count, int64_t total_rows, float* __restrict__ X,
-                                                         float* __restrict__ norms, BatchState* st, BatchGlobals* g) {
-  const int lane = threadIdx.x & 31;
-  const int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * PREP_RUN;
-  if (r0 >= total_rows) return;
-  const int64_t r1 = r0 + PREP_RUN < total_rows ? r0 + PREP_RUN : total_rows;
-  int q = find_inst(row_offs, count, r0);
-  int64_t next = row_offs[q + 1];
-  BatchInst in = inst[q];
-  float m2 = 0.f;
-  bool bad = false;
-  for (int64_t r = r0; r < r1; ++r) {
-    if (r >= next) {
-      if (lane == 0) atomic_max_nonneg(&st[q].n2_bits, m2 * (1.f + 0x1p-12f));
-      m2 = 0.f;
-      do {
-        ++q;
-        next = row_offs[q + 1];
-      } while (r >= next);
-      in = inst[q];
-    }
-    const int64_t lr = r - in.row_off;
-    float* out = X + in.x_off + lr * in.Kp;
-    float n2 = 0.f;
-    for (int k = lane; k < in.Kp; k += 32) {
-      float v = 0.f;
-      if (lr < in.n && k < in.d) {
-        v = in.pts[lr * in.d + k];
-        bad |= !isfinite(v);
-      }
-      out[k] = v;
-      n2 = fmaf(v, v, n2);
-    }
+// Lanes per row: a power of two that covers the row's 16-byte output chunks (at most 32).
+__host__ __device__ constexpr int prep_lanes(int chunks) {
+  return chunks <= 1 ? 1 : chunks <= 2 ? 2 : chunks <= 4 ? 4 : chunks <= 8 ? 8 : chunks <= 16 ? 16 : 32;
+}
+__host__ __device__ constexpr int prep_log2(int l) { return l >= 32 ? 5 : l >= 16 ? 4 : l >= 8 ? 3 : l >= 4 ? 2 : l >= 2 ? 1 : 0; }
+
+// Loads columns c .. c + 3 of an input row (zeros past d).
+__device__ __forceinline__ float4 load4(const float* __restrict__ row, int c, int d, bool vec) {
+  if (vec && c + 3 < d) return *reinterpret_cast<const float4*>(row + c);
+  float4 v;
+  v.x = c < d ? row[c] : 0.f;
+  v.y = c + 1 < d ? row[c + 1] : 0.f;
+  v.z = c + 2 < d ? row[c + 2] : 0.f;
+  v.w = c + 3 < d ? row[c + 3] : 0.f;
+  return v;
+}
+
+// Block maximum of a non-negative value, flushed with one atomic (every thread calls it).
+__device__ __forceinline__ void block_max_flush(float v, unsigned int* dst, float pad, float* red) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
-    if (lane == 0) norms[r] = n2;
-    m2 = fmaxf(m2, n2);
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = red[0];
+    for (int w = 1; w < PREP_NT / 32; ++w) m = fmaxf(m, red[w]);
+    atomic_max_nonneg(dst, m * pad);
   }
-  if (lane == 0) atomic_max_nonneg(&st[q].n2_bits, m2 * (1.f + 0x1p-12f));
-  bad = __any_sync(0xffffffffu, bad);
-  if (bad && lane == 0) atomicOr(&g->status, 1u);
+  __syncthreads();
+}
+
+// FP32 rows of every instance (padded to Kp columns and to 128 rows) and their squared norms.  Block
+// b serves instance q = the last with blk_offs[q] <= b, rows (b - blk_offs[q]) * rows_per_block ...
+__global__ void __launch_bounds__(PREP_NT) batch_prep_kernel(const BatchInst* __restrict__ inst,
+                                                             const int64_t* __restrict__ blk_offs, int count,
+                                                             float* __restrict__ X, float* __restrict__ norms,
+                                                             BatchState* st, BatchGlobals* g) {
+  __shared__ float red[PREP_NT / 32];
+  const int q = find_inst(blk_offs, count, blockIdx.x);
+  const BatchInst in = inst[q];
+  const int ch = in.Kp / 4, L = prep_lanes(ch), rpb = PREP_NT / L;  // float4 chunks, lanes per row, rows per block
+  const int64_t npad = (int64_t)(in.n + TILE_BM - 1) / TILE_BM * TILE_BM;
+  const int64_t r = (blockIdx.x - blk_offs[q]) * rpb + threadIdx.x / L;
+  const int gl = threadIdx.x % L;
+  const bool vec = (in.d % 4 == 0) && ((reinterpret_cast<uintptr_t>(in.pts) & 15) == 0);
+  float n2 = 0.f;
+  bool bad = false;
+  if (r < npad) {
+    const float* row = in.pts + r * in.d;
+    float* out = X + in.x_off + r * in.Kp;
+    for (int c = gl; c < ch; c += L) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < in.n) v = load4(row, 4 * c, in.d, vec);
+      bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+      *reinterpret_cast<float4*>(out + 4 * c) = v;
+      n2 = fmaf(v.x, v.x, n2);
+      n2 = fmaf(v.y, v.y, n2);
+      n2 = fmaf(v.z, v.z, n2);
+      n2 = fmaf(v.w, v.w, n2);
+    }
+  }
+  for (int o = L / 2; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+  if (r < npad && gl == 0) norms[in.row_off + r] = n2;
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&g->status, 1u);
+  block_max_flush(r < npad ? n2 : 0.f, &st[q].n2_bits, 1.f + 0x1p-12f, red);
 }
 
 __global__ void batch_bounds_kernel(const BatchInst* __restrict__ inst, BatchState* st, int count) {
@@ -189,70 +212,78 @@ __global__ void batch_bounds_kernel(const BatchInst* __restrict__ inst, BatchSta
   st[q].bp16.e_acc = inst[q].kappa16 * __uint_as_float(st[q].n2_16_bits) * (1.f + 0x1p-20f);
 }
 
-// BF16 rows of the tensor-core instances (a run of PREP_RUN padded rows per warp); the row's
-// residual |x - x~| (exact in FP32) bounds the rounding, as in the dense stage's preparation.
-__global__ void __launch_bounds__(256) batch_prep16_kernel(const BatchInst* __restrict__ inst,
-                                                           const int64_t* __restrict__ grow_offs, int count,
-                                                           int64_t rows16, X16Set X16,
-                                                           float* __restrict__ norms16, __nv_bfloat16* __restrict__ H16,
-                                                           BatchState* st) {
-  const int lane = threadIdx.x & 31;
-  const int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * PREP_RUN;
-  if (r0 >= rows16) return;
-  const int64_t r1 = r0 + PREP_RUN < rows16 ? r0 + PREP_RUN : rows16;
-  int q = find_inst(grow_offs, count, r0);
-  int64_t next = grow_offs[q + 1];
-  BatchInst in = inst[q];
-  float m2 = 0.f, me = 0.f;
-  for (int64_t r = r0; r < r1; ++r) {
-    if (r >= next) {
-      if (lane == 0) {
-        atomic_max_nonneg(&st[q].n2_16_bits, m2 * (1.f + 0x1p-12f));
-        atomic_max_nonneg(&st[q].eps16_bits, me * (1.f + 0x1p-10f));
-      }
-      m2 = me = 0.f;
-      do {
-        ++q;
-        next = grow_offs[q + 1];
-      } while (r >= next);
-      in = inst[q];
-    }
-    const int64_t lr = r - in.grow_off16;
-    const int Kp16 = cls_kp16(in.cls);
-    __nv_bfloat16* out = X16.p[in.cls] + (in.row_off16 + lr) * Kp16;
-    float n2 = 0.f, dd = 0.f;
-    for (int k = lane; k < Kp16; k += 32) {
-      float v = 0.f;
-      if (lr < in.n && k < in.d) v = in.pts[lr * in.d + k];
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
-      const float hv = __bfloat162float(h);
-      const float dl = v - hv;  // exact in FP32
-      out[k] = h;
-      n2 = fmaf(hv, hv, n2);
-      dd = fmaf(dl, dl, dd);
-    }
+// BF16 rows of the tensor-core instances (padded to their class width and to 256 rows), their FP32
+// squared norms, and the norm pieces of the norm MMA; each lane converts 8 values (one 16-byte
+// store).  The row's residual |x - x~| (exact in FP32) bounds the rounding, as in the dense stage's
+// preparation.  Blocks as in batch_prep_kernel, over the tensor-core instances' 256-row blocks.
+__global__ void __launch_bounds__(PREP_NT) batch_prep16_kernel(const BatchInst* __restrict__ inst,
+                                                               const int64_t* __restrict__ blk_offs, int count,
+                                                               X16Set X16, float* __restrict__ norms16,
+                                                               __nv_bfloat16* __restrict__ H16, BatchState* st) {
+  __shared__ float red[PREP_NT / 32];
+  const int q = find_inst(blk_offs, count, blockIdx.x);
+  const BatchInst in = inst[q];
+  const int Kp16 = cls_kp16(in.cls), ch = Kp16 / 8, L = prep_lanes(ch), rpb = PREP_NT / L;
+  const int64_t npad = (int64_t)(in.n + 255) / 256 * 256;
+  const int64_t r = (blockIdx.x - blk_offs[q]) * rpb + threadIdx.x / L;
+  const int gl = threadIdx.x % L;
+  const bool vec = (in.d % 4 == 0) && ((reinterpret_cast<uintptr_t>(in.pts) & 15) == 0);
+  float n2 = 0.f, dd = 0.f;
+  if (r < npad) {
+    const float* row = in.pts + r * in.d;
+    // (a select chain: indexing the parameter array with a runtime class would copy it to local memory)
+    __nv_bfloat16* base = X16.p[0];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      n2 += __shfl_xor_sync(0xffffffffu, n2, o);
-      dd += __shfl_xor_sync(0xffffffffu, dd, o);
+    for (int k = 1; k < NCLS; ++k) base = in.cls == k ? X16.p[k] : base;
+    __nv_bfloat16* out = base + (in.row_off16 + r) * Kp16;
+    for (int c = gl; c < ch; c += L) {
+      float v[8];
+      if (r < in.n) {
+        const float4 a = load4(row, 8 * c, in.d, vec), b = load4(row, 8 * c + 4, in.d, vec);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = 0.f;
+      }
+      uint32_t w[4];
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[k]), h1 = __float2bfloat16_rn(v[k + 1]);
+        const float f0 = __bfloat162float(h0), f1 = __bfloat162float(h1);
+        const float d0 = v[k] - f0, d1 = v[k + 1] - f1;  // exact in FP32
+        n2 = fmaf(f0, f0, n2);
+        n2 = fmaf(f1, f1, n2);
+        dd = fmaf(d0, d0, dd);
+        dd = fmaf(d1, d1, dd);
+        w[k / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+      }
+      *reinterpret_cast<uint4*>(out + 8 * c) = make_uint4(w[0], w[1], w[2], w[3]);
     }
-    if (lane == 0) norms16[r] = n2;
-    if (lane < 16) {  // -n2 / 2 = -(h1 + h2 + h3) to 2^-27 relative; each residual is exact in FP32
-      const float v = 0.5f * n2;
-      const float h1 = __bfloat162float(__float2bfloat16_rn(v));
-      const float r1 = v - h1;
-      const float h2 = __bfloat162float(__float2bfloat16_rn(r1));
-      const float h3 = r1 - h2;
-      const float hv = lane == 0 ? h1 : lane == 1 ? h2 : lane == 2 ? h3 : 0.f;
-      H16[r * 16 + lane] = __float2bfloat16_rn(-hv);
+  }
+  for (int o = L / 2; o > 0; o >>= 1) {
+    n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+    dd += __shfl_xor_sync(0xffffffffu, dd, o);
+  }
+  if (r < npad) {
+    const int64_t gr = in.grow_off16 + r;
+    if (gl == 0) norms16[gr] = n2;
+    if (gl < 2) {  // -n2 / 2 = -(h1 + h2 + h3) to 2^-27 relative; each residual is exact in FP32
+      uint32_t w0 = 0u, w1 = 0u;
+      if (gl == 0) {
+        const float v = 0.5f * n2;
+        const float h1 = __bfloat162float(__float2bfloat16_rn(v));
+        const float r1 = v - h1;
+        const float h2 = __bfloat162float(__float2bfloat16_rn(r1));
+        const float h3 = r1 - h2;
+        w0 = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(-h1)) |
+             ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(-h2)) << 16);
+        w1 = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(-h3));
+      }
+      *reinterpret_cast<uint4*>(H16 + gr * 16 + 8 * gl) = make_uint4(w0, w1, 0u, 0u);
     }
-    m2 = fmaxf(m2, n2);
-    me = fmaxf(me, sqrtf(dd));
   }
-  if (lane == 0) {
-    atomic_max_nonneg(&st[q].n2_16_bits, m2 * (1.f + 0x1p-12f));
-    atomic_max_nonneg(&st[q].eps16_bits, me * (1.f + 0x1p-10f));
-  }
+  block_max_flush(r < npad ? n2 : 0.f, &st[q].n2_16_bits, 1.f + 0x1p-12f, red);
+  block_max_flush(r < npad ? sqrtf(dd) : 0.f, &st[q].eps16_bits, 1.f + 0x1p-10f, red);
 }
 
 // Persistent FP32 tile kernel over the concatenated tile lists.
@@ -1149,7 +1180,8 @@ __global__ void batch_finish_kernel(const BatchState* st, int count, const int64
 // ---------------------------------------------------------------- host side
 struct BatchLayout {
   BatchInst* inst;
-  int64_t *row_offs, *tile_offs, *grow_offs16, *tile_offs16[2];  // tensor-core tile lists: four-group, two-group kernel
+  int64_t *tile_offs, *tile_offs16[2];  // FP32-path tiles; tensor-core tile lists (four-group, two-group kernel)
+  int64_t *pblk32, *pblk16;  // preparation blocks before each instance (FP32 rows; BF16 rows)
   BatchState* st;
   BatchGlobals* g;
   int32_t* pair_counts;
@@ -1182,9 +1214,18 @@ struct Totals {
   int64_t rows = 0, xfloats = 0, tiles = 0;         // FP32 layout (all instances) and FP32-path tiles
   int64_t rows16 = 0, tiles16 = 0, crow16[NCLS] = {0, 0, 0, 0, 0, 0};
   int64_t tiles16s[2] = {0, 0};  // tensor-core tiles of path 2 (four-group kernel) and path 3 (two-group)
+  int64_t blk32 = 0, blk16 = 0;  // preparation blocks (FP32 rows of every instance, BF16 rows of the tensor-core ones)
 };
 
 int64_t nrow16_of(int64_t n) { return n >= 2 ? (n - 2) / 128 + 1 : 0; }
+int64_t prep_blocks32(int64_t npad, int64_t Kp) {
+  const int64_t rpb = PREP_NT / prep_lanes((int)(Kp / 4));
+  return (npad + rpb - 1) / rpb;
+}
+int64_t prep_blocks16(int64_t npad16, int64_t Kp16) {
+  const int64_t rpb = PREP_NT / prep_lanes((int)(Kp16 / 8));
+  return (npad16 + rpb - 1) / rpb;
+}
 int64_t tiles16_of(int64_t n) {
   const int64_t nbj = (n + 255) / 256, nr = nrow16_of(n);
   int64_t t = 0;
@@ -1200,12 +1241,14 @@ Totals totals_of(const cpp_instance* inst, int64_t count) {
     const int64_t nb = npad / TILE_BM;
     t.rows += npad;
     t.xfloats += npad * Kp;
+    t.blk32 += prep_blocks32(npad, Kp);
     if (path_of(inst[q]) >= 2) {
       const int64_t npad16 = (n + 255) / 256 * 256;
       t.rows16 += npad16;
       t.crow16[cls_of_d(inst[q].d)] += npad16;
       t.tiles16 += tiles16_of(n);
       t.tiles16s[path_of(inst[q]) - 2] += tiles16_of(n);
+      t.blk16 += prep_blocks16(npad16, cls_kp16(cls_of_d(inst[q].d)));
     } else {
       t.tiles += n >= 2 ? nb * (nb + 1) / 2 : 0;
     }
@@ -1217,9 +1260,9 @@ BatchLayout batch_layout(void* ws, int64_t count, const Totals& t, size_t ws_byt
   BatchLayout L;
   Carver c(ws);
   L.inst = c.take<BatchInst>(count);
-  L.row_offs = c.take<int64_t>(count + 1);
   L.tile_offs = c.take<int64_t>(count + 1);
-  L.grow_offs16 = c.take<int64_t>(count + 1);
+  L.pblk32 = c.take<int64_t>(count + 1);
+  L.pblk16 = c.take<int64_t>(count + 1);
   L.tile_offs16[0] = c.take<int64_t>(count + 1);
   L.tile_offs16[1] = c.take<int64_t>(count + 1);
   L.st = c.take<BatchState>(count);
@@ -1261,11 +1304,13 @@ float kappa_fp32(int64_t Kp) {
 // Tensor-core tiles compute a_ij = x~_i.x~_j - h_j (h_j: three BF16 pieces of |x~_j|^2 / 2, within
 // 2^-27 relative) with K' = Kp + 16 exact products whose magnitudes sum to at most
 // |x~_i||x~_j| + 1.01 |x~_j|^2 / 2 <= 1.51 m (m = max |x~|^2); the accumulation error is padded to
-// 2 K' 2^-22 of that sum.  D~ = fma(-2, a, |x~_i|^2) adds the FP32 norm error of both rows
-// (32-lane warp sums: (Kp/32 + 5) u each), the split error and one rounding of |D~| <= 4.03 m.
+// 2 K' 2^-22 of that sum.  D~ = fma(-2, a, |x~_i|^2) adds the FP32 norm error of both rows (each norm
+// is eight fused products per lane, then a tree over the row's L lanes: at most 8 + log2 L
+// roundings), the split error and one rounding of |D~| <= 4.03 m.
 float kappa_tc(int64_t Kp) {
   const double K = (double)Kp, K2 = K + 16.0, u = 0x1p-24;
-  return (float)((2.0 * 1.51 * 2.0 * K2 * 0x1p-22 + 2.0 * (K / 32.0 + 5.0) * 1.01 * u + 0x1p-27 + 4.03 * u) * 1.01);
+  const double nrm = 8.0 + prep_log2(prep_lanes((int)(Kp / 8)));
+  return (float)((2.0 * 1.51 * 2.0 * K2 * 0x1p-22 + 2.0 * nrm * 1.01 * u + 0x1p-27 + 4.03 * u) * 1.01);
 }
 
 EncodeTiledFn encode_fn() {
@@ -1338,14 +1383,14 @@ int enqueue_batch(const BatchLayout& L, int64_t count, const Totals& t, int32_t*
   batch_init_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(L.st, ci, L.g);
   CPPGB_LAUNCH_CHECK();
   CPPGB_CUDA_TRY(cudaMemsetAsync(L.pair_counts, 0, sizeof(int32_t) * (count + 1), st));
-  batch_prep_kernel<<<(unsigned)((t.rows + 8 * PREP_RUN - 1) / (8 * PREP_RUN)), 256, 0, st>>>(L.inst, L.row_offs, ci, t.rows, L.X, L.norms, L.st,
-                                                                  L.g);
-  CPPGB_LAUNCH_CHECK();
+  if (t.blk32 > 0) {
+    batch_prep_kernel<<<(unsigned)t.blk32, PREP_NT, 0, st>>>(L.inst, L.pblk32, ci, L.X, L.norms, L.st, L.g);
+    CPPGB_LAUNCH_CHECK();
+  }
   if (t.rows16 > 0) {
     X16Set xs;
     for (int k = 0; k < NCLS; ++k) xs.p[k] = L.X16[k];
-    batch_prep16_kernel<<<(unsigned)((t.rows16 + 8 * PREP_RUN - 1) / (8 * PREP_RUN)), 256, 0, st>>>(
-        L.inst, L.grow_offs16, ci, t.rows16, xs, L.norms16, L.H16, L.st);
+    batch_prep16_kernel<<<(unsigned)t.blk16, PREP_NT, 0, st>>>(L.inst, L.pblk16, ci, xs, L.norms16, L.H16, L.st);
     CPPGB_LAUNCH_CHECK();
   }
   batch_bounds_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(L.inst, L.st, ci);
@@ -1440,9 +1485,9 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
 
   // instance table (host-built, copied before the graph runs)
   std::vector<BatchInst> hi((size_t)count);
-  std::vector<int64_t> hro((size_t)count + 1), hto((size_t)count + 1), hgo((size_t)count + 1);
+  std::vector<int64_t> hto((size_t)count + 1), hb32((size_t)count + 1), hb16((size_t)count + 1);
   std::vector<int64_t> hto16[2] = {std::vector<int64_t>((size_t)count + 1), std::vector<int64_t>((size_t)count + 1)};
-  int64_t xo = 0, ro = 0, to = 0, go = 0, to16[2] = {0, 0}, co[NCLS] = {0, 0, 0, 0, 0, 0};
+  int64_t xo = 0, ro = 0, to = 0, go = 0, to16[2] = {0, 0}, co[NCLS] = {0, 0, 0, 0, 0, 0}, pb32 = 0, pb16 = 0;
   for (int64_t q = 0; q < count; ++q) {
     const cpp_instance& c = inst[q];
     BatchInst b;
@@ -1469,32 +1514,34 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
     b.tile_off16 = to16[kl];
     b.kappa16 = kappa_tc(cls_kp16(b.cls));
     if (b.tc) b.tile_off = to;  // no FP32-path tiles
-    hro[(size_t)q] = ro;
+    hb32[(size_t)q] = pb32;
+    hb16[(size_t)q] = pb16;
     hto[(size_t)q] = to;
-    hgo[(size_t)q] = go;
     hto16[0][(size_t)q] = to16[0];
     hto16[1][(size_t)q] = to16[1];
     xo += npad * b.Kp;
     ro += npad;
+    pb32 += prep_blocks32(npad, b.Kp);
     if (b.tc) {
       const int64_t npad16 = (c.n + 255) / 256 * 256;
       co[b.cls] += npad16;
       go += npad16;
+      pb16 += prep_blocks16(npad16, cls_kp16(b.cls));
       to16[kl] += tiles16_of(c.n);
     } else {
       to += c.n >= 2 ? nb * (nb + 1) / 2 : 0;
     }
     hi[(size_t)q] = b;
   }
-  hro[(size_t)count] = ro;
+  hb32[(size_t)count] = pb32;
+  hb16[(size_t)count] = pb16;
   hto[(size_t)count] = to;
-  hgo[(size_t)count] = go;
   hto16[0][(size_t)count] = to16[0];
   hto16[1][(size_t)count] = to16[1];
   CPPGB_CUDA_TRY(cudaMemcpyAsync(L.inst, hi.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, st));
-  CPPGB_CUDA_TRY(cudaMemcpyAsync(L.row_offs, hro.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(L.pblk32, hb32.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
+  CPPGB_CUDA_TRY(cudaMemcpyAsync(L.pblk16, hb16.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
   CPPGB_CUDA_TRY(cudaMemcpyAsync(L.tile_offs, hto.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
-  CPPGB_CUDA_TRY(cudaMemcpyAsync(L.grow_offs16, hgo.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
   for (int k = 0; k < 2; ++k)
     CPPGB_CUDA_TRY(
         cudaMemcpyAsync(L.tile_offs16[k], hto16[k].data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
