@@ -495,6 +495,7 @@ struct TileInfo {
   BoundParams bp;    // the instance's tensor-core bound parameters
 };
 constexpr int RING = 16;         // tile records in flight
+constexpr int TILE_RUN = 16;     // consecutive tiles a CTA takes at a time
 
 // Shared-memory descriptor of a K-major operand region whose rows hold `chunk` 16-bit values.
 __device__ __forceinline__ uint64_t op_desc(uint32_t saddr, int chunk) {
@@ -773,8 +774,15 @@ __global__ void __maxnreg__(G == 4 ? 96 : 168)
   Ctl<G>* ctl = (Ctl<G>*)(ones + ONES_BYTES);
   volatile int* abort_flag = &ctl->abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // this CTA's tiles: t = blockIdx.x + it * gridDim.x, it < ntl
-  const int64_t ntl = (total - blockIdx.x + gridDim.x - 1) / gridDim.x;
+  // This CTA's tiles: runs r = blockIdx.x, blockIdx.x + gridDim.x, ... of TILE_RUN consecutive tile
+  // indices (tile_at below), so consecutive tiles of a CTA mostly share their row block.
+  int64_t ntl = 0;
+  {
+    const int64_t nruns = (total + TILE_RUN - 1) / TILE_RUN;
+    const int64_t mine = nruns > blockIdx.x ? (nruns - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    ntl = mine * TILE_RUN;
+    if (mine > 0 && blockIdx.x + (mine - 1) * gridDim.x == nruns - 1) ntl -= nruns * TILE_RUN - total;
+  }
 
   if (threadIdx.x < 64) {
     // Constant A operand of the norm MMA: every row is (1, 1, 1, 0, ..., 0) in BF16.  In the
@@ -830,7 +838,7 @@ __global__ void __maxnreg__(G == 4 ? 96 : 168)
           ok = false;
           break;
         }
-        w.go(blockIdx.x + it * gridDim.x);
+        w.go((blockIdx.x + (it / TILE_RUN) * gridDim.x) * TILE_RUN + it % TILE_RUN);
         if (w.q != bq) {
           bq = w.q;
           ti.q = w.q;
@@ -956,14 +964,21 @@ __global__ void __maxnreg__(G == 4 ? 96 : 168)
     // A warp keeps its tile's ring slot until the tile is done and reads the record's fields from
     // shared memory where it needs them (few registers stay live across the TMEM reads); the row
     // norm of the group's next tile is loaded one tile ahead.
+    // The norms are reloaded only when the row block changes (consecutive tiles mostly share it).
     float nx_n = 0.f;
+    int32_t f_q = -1, f_bi = -1;
     bool ok = true;
     auto fetch = [&](int64_t it) -> bool {
       const uint32_t slot = (uint32_t)(it % RING);
       const bool got = __all_sync(0xffffffffu, mbar_wait(&ctl->info_full[slot], (uint32_t)((it / RING) & 1), abort_flag));
       if (!got) return false;
       const TileInfo* ti = &ctl->info[slot];
-      nx_n = norms16[ti->grow + (int64_t)ti->bi * BM + quarter * 32 + lane];
+      const int32_t q = ti->q, bi = ti->bi;
+      if (q != f_q || bi != f_bi) {
+        nx_n = norms16[ti->grow + (int64_t)bi * BM + quarter * 32 + lane];
+        f_q = q;
+        f_bi = bi;
+      }
       return true;
     };
     if (par_a < ntl) ok = fetch(par_a);
@@ -1397,13 +1412,13 @@ int enqueue_batch(const BatchLayout& L, int64_t count, const Totals& t, int32_t*
   CPPGB_LAUNCH_CHECK();
   if (timing) CPPGB_CUDA_TRY(cudaEventRecordWithFlags(g_bev[1], st, cudaEventRecordExternal));
   if (t.tiles16s[0] > 0) {  // path 2: four epilogue groups
-    const int64_t grid = t.tiles16s[0] < sms ? t.tiles16s[0] : sms;
+    const int64_t runs = (t.tiles16s[0] + btc::TILE_RUN - 1) / btc::TILE_RUN, grid = runs < sms ? runs : sms;
     btc::batch_tc_kernel<4><<<(unsigned)grid, btc::Shape<4>::NTHREADS, btc::SMEM_BYTES<4>, st>>>(
         maps, L.inst, L.tile_offs16[0], ci, t.tiles16s[0], L.norms16, L.st, L.g, L.cand, L.cap, L.trec, L.trec_cap);
     CPPGB_LAUNCH_CHECK();
   }
   if (t.tiles16s[1] > 0) {  // path 3: two epilogue groups
-    const int64_t grid = t.tiles16s[1] < sms ? t.tiles16s[1] : sms;
+    const int64_t runs = (t.tiles16s[1] + btc::TILE_RUN - 1) / btc::TILE_RUN, grid = runs < sms ? runs : sms;
     btc::batch_tc_kernel<2><<<(unsigned)grid, btc::Shape<2>::NTHREADS, btc::SMEM_BYTES<2>, st>>>(
         maps, L.inst, L.tile_offs16[1], ci, t.tiles16s[1], L.norms16, L.st, L.g, L.cand, L.cap, L.trec, L.trec_cap);
     CPPGB_LAUNCH_CHECK();
