@@ -257,7 +257,7 @@ class FRNN:
     def shard_step(self, capi, mode, rank, world):
         from paper_1407_5609_gb300 import shards
         rp, cols = capi.frnn_query_shard(self.dev_x, self.R, rank, world)
-        rp, cols = shards.allgather_frnn(rp.cpu().numpy(), cols.cpu().numpy())
+        rp, cols = shards.allgather_frnn(rp, cols)  # tensor collectives, merged on the device
         return {"n_pairs_directed": int(cols.shape[0])}
 
     def e2e_step(self, capi, mode, host, dev_buf):

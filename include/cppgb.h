@@ -286,7 +286,7 @@ int mlba_pair(const uint8_t* strs, int64_t n, int64_t t, int64_t ld, int sigma, 
 typedef struct {
   int64_t n_pairs;     /* directed pairs (= row_ptr[n]), also when cols_cap was too small */
   int32_t status;      /* CPPGB_OK, or the error the device found (valid after the stream sync) */
-  int32_t reserved;
+  int32_t n_rows;      /* points whose rows the call wrote: n, or for frnn_query_shard its slab's */
 } frnn_result;
 
 /*
@@ -310,9 +310,11 @@ int frnn_query(const float* pts, int64_t n, int d, int64_t ld, double R, int64_t
 
 /*
  * frnn_query_shard -- shard s of nshards of frnn_query on the grid path (1 <= d <= 4): the points
- * are split into nshards slabs of equal width in x-cells (cells of side >= R over the bounding box)
- * and only the points of slab s get their neighbour lists; every other row is empty (row_ptr has
- * n + 1 entries as usual).  Each shard still builds the grid over all points, so the neighbours of
+ * are split into nshards slabs along x, each a range of whole x-cells (cells of side >= R over the
+ * bounding box) holding an equal share of the points (up to one of 4096 equal-width bins of the
+ * x-cells, so clustered data balances too), and only the points of slab s get their neighbour
+ * lists; every other row is empty (row_ptr has n + 1 entries as usual); out->n_rows is the number of
+ * points of slab s.  Each shard still builds the grid over all points, so the neighbours of
  * a slab's points in the adjacent slabs (the halo) are found.  Concatenating, point by point, the
  * rows of the point's own shard gives exactly the CSR of frnn_query.  Arguments, workspace and
  * errors as for frnn_query; CPPGB_ERR_ARG for d > 4 or a bad shard.

@@ -73,7 +73,7 @@ class mlba_result(ctypes.Structure):
 
 
 class frnn_result(ctypes.Structure):
-    _fields_ = [("n_pairs", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+    _fields_ = [("n_pairs", ctypes.c_int64), ("status", ctypes.c_int32), ("n_rows", ctypes.c_int32)]
 
 
 class cpp_instance(ctypes.Structure):
@@ -547,18 +547,20 @@ def frnn_query_workspace_size(n: int, d: int) -> int:
 
 
 def frnn_query(pts: torch.Tensor, R: float, cols_cap: int | None = None, ws: torch.Tensor | None = None,
-               stream=None):
-    """R-neighbourhoods of the rows of float32 ``pts`` [n][d]: returns (row_ptr int64, cols int32)."""
-    return _frnn(pts, R, cols_cap, ws, stream, None)
+               stream=None, result: dict | None = None):
+    """R-neighbourhoods of the rows of float32 ``pts`` [n][d]: returns (row_ptr int64, cols int32).
+    ``result``, when given, receives the call's result struct (n_pairs, status, n_rows)."""
+    return _frnn(pts, R, cols_cap, ws, stream, None, result)
 
 
 def frnn_query_shard(pts: torch.Tensor, R: float, shard: int, nshards: int, cols_cap: int | None = None,
-                     ws: torch.Tensor | None = None, stream=None):
-    """Slab `shard` of `nshards` of frnn_query (d <= 4): (row_ptr, cols) with only that slab's rows."""
-    return _frnn(pts, R, cols_cap, ws, stream, (int(shard), int(nshards)))
+                     ws: torch.Tensor | None = None, stream=None, result: dict | None = None):
+    """Slab `shard` of `nshards` of frnn_query (d <= 4): (row_ptr, cols) with only that slab's rows;
+    ``result["n_rows"]`` (when ``result`` is given) is the number of points of the slab."""
+    return _frnn(pts, R, cols_cap, ws, stream, (int(shard), int(nshards)), result)
 
 
-def _frnn(pts, R, cols_cap, ws, stream, shard):
+def _frnn(pts, R, cols_cap, ws, stream, shard, result=None):
     _check_cuda(pts, "pts")
     if pts.dim() != 2 or pts.dtype != torch.float32 or pts.stride(1) != 1:
         raise ValueError("pts must be float32 [n][d] with unit column stride")
@@ -580,6 +582,8 @@ def _frnn(pts, R, cols_cap, ws, stream, shard):
             cap = total
             continue
         _raise_status(out.status)
+        if result is not None:
+            result.update(n_pairs=total, status=int(out.status), n_rows=int(out.n_rows))
         return row_ptr, cols[:total]
 
 

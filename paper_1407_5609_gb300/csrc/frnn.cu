@@ -27,7 +27,7 @@ struct GridParams {
   float rr_lo, rr_hi;  // FP32 band around R^2: below -> inside, above -> outside, else FP64
   int32_t use64;    // 1: decide every pair in FP64
   int32_t pad;
-  int64_t ncx;      // cells along x that hold points (slabs of a sharded query split them evenly)
+  int64_t ncx;      // cells along x that hold points (slabs of a sharded query: see slab_table_kernel)
 };
 
 struct FrnnState {
@@ -36,6 +36,7 @@ struct FrnnState {
   unsigned int status;  // 1: non-finite coordinate, 8: hash table full
   unsigned int spill;   // 1: the row buffer overflowed (the rows are then written by a second pass)
   unsigned long long cursor;  // entries of the row buffer handed out
+  long long n_rows;           // points whose rows this call writes (its slab's, or all of them)
 };
 
 __device__ __forceinline__ unsigned int ord_key(float f) {
@@ -59,7 +60,7 @@ struct __align__(16) CellRec {
   int32_t start, cnt;
 };
 
-__global__ void frnn_init_kernel(FrnnState* fs, uint32_t* counters) {
+__global__ void frnn_init_kernel(FrnnState* fs, uint32_t* counters, int64_t n) {
   for (int k = 0; k < 4; ++k) {
     fs->mm[k] = 0xffffffffu;
     fs->mm[4 + k] = 0u;
@@ -67,6 +68,7 @@ __global__ void frnn_init_kernel(FrnnState* fs, uint32_t* counters) {
   fs->status = 0u;
   fs->spill = 0u;
   fs->cursor = 0ull;
+  fs->n_rows = n;  // a sharded query's slab table sets its own count
   if (counters) counters[0] = counters[1] = 0u;
 }
 
@@ -401,10 +403,82 @@ __device__ void sort_segment(int32_t* a, int64_t m) {
   }
 }
 
-// Slab of a cell for a sharded query (x cells [shard, shard + 1) * ncx / nshards).
-__device__ __forceinline__ int slab_of(const GridParams& gp, int64_t cx, int nshards) {
-  int64_t slab = cx * nshards / gp.ncx;
-  return (int)(slab < 0 ? 0 : slab >= nshards ? nshards - 1 : slab);
+// Slabs of a sharded query: the x cells [0, ncx) fall into SLAB_BINS bins of equal width; each bin
+// goes to the slab in which its first point falls when the points are ranked by bin (slab s takes
+// ranks [s n / nshards, (s + 1) n / nshards)), so the slabs hold equal numbers of points up to one
+// bin's worth, whatever the distribution along x.  A slab is a range of whole bins, contiguous in x.
+constexpr int SLAB_BINS = 4096;
+__device__ __forceinline__ int slab_bin(const GridParams& gp, int64_t cx) {
+  int64_t b = gp.ncx > 0 ? cx * SLAB_BINS / gp.ncx : 0;
+  return (int)(b < 0 ? 0 : b >= SLAB_BINS ? SLAB_BINS - 1 : b);
+}
+
+// Points per slab bin: the occupied cells' counts (occ_cnt) added by the bin of their x cell, in
+// shared memory first, then one global atomic per non-empty bin and block.
+__global__ void __launch_bounds__(256) slab_hist_kernel(const FrnnState* fs, const unsigned long long* __restrict__ occ_key,
+                                                        const int32_t* __restrict__ occ_cnt,
+                                                        const uint32_t* __restrict__ n_occ, int32_t* __restrict__ hist) {
+  __shared__ int32_t h[SLAB_BINS];
+  for (int b = threadIdx.x; b < SLAB_BINS; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  const GridParams gp = fs->gp;
+  const uint64_t cmask = (1ull << gp.bits) - 1ull;
+  const int64_t ncell = *n_occ;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&h[slab_bin(gp, (int64_t)(occ_key[c] & cmask))], occ_cnt[c]);
+  __syncthreads();
+  for (int b = threadIdx.x; b < SLAB_BINS; b += blockDim.x)
+    if (h[b]) atomicAdd(&hist[b], h[b]);
+}
+
+// One block of 1024 threads: the exclusive scan of the bin counts, each bin's slab from the rank of
+// its first point, and the number of points of this call's slab.
+__global__ void __launch_bounds__(1024) slab_table_kernel(FrnnState* fs, const int32_t* __restrict__ hist,
+                                                          int32_t* __restrict__ slab_tab, int64_t n, int shard,
+                                                          int nshards) {
+  constexpr int PER = SLAB_BINS / 1024;
+  __shared__ int64_t wsum[32];
+  __shared__ unsigned long long mine;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (t == 0) mine = 0ull;
+  int64_t v[PER], loc = 0;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    v[k] = hist[t * PER + k];
+    loc += v[k];
+  }
+  int64_t incl = loc;  // inclusive scan over the block
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int64_t x = wsum[lane], xi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += y;
+    }
+    wsum[lane] = xi - x;  // exclusive prefix of the warps
+  }
+  __syncthreads();
+  int64_t run = wsum[w] + incl - loc;  // points before this thread's first bin
+  const int64_t total = n > 0 ? n : 1;
+  unsigned long long cnt = 0ull;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    int64_t sl = run * nshards / total;
+    sl = sl >= nshards ? nshards - 1 : sl;
+    slab_tab[t * PER + k] = (int32_t)sl;
+    if (sl == shard) cnt += (unsigned long long)v[k];
+    run += v[k];
+  }
+  atomicAdd(&mine, cnt);
+  __syncthreads();
+  if (t == 0) fs->n_rows = (long long)mine;
 }
 
 // ------------------------------------------------------------------ cell-parallel query
@@ -443,7 +517,8 @@ __global__ void __launch_bounds__(QW * 32) cell_query_kernel(
     const uint32_t* __restrict__ n_occ, const int32_t* __restrict__ sorted_idx, const float4* __restrict__ sorted_pts,
     int32_t* __restrict__ counts, int64_t* __restrict__ row_at, int32_t* __restrict__ rowbuf, int64_t rowbuf_cap,
     const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cols, int64_t n, int64_t cols_cap,
-    uint32_t* __restrict__ fb, uint32_t* __restrict__ n_fb, int shard, int nshards) {
+    uint32_t* __restrict__ fb, uint32_t* __restrict__ n_fb, const int32_t* __restrict__ slab_tab, int shard,
+    int nshards) {
   using Stage = CellStage<D>;
   constexpr int S = Stage::S, CENTER = (S - 1) / 2;
   extern __shared__ __align__(16) uint8_t cq_smem[];
@@ -465,7 +540,7 @@ __global__ void __launch_bounds__(QW * 32) cell_query_kernel(
     for (int e = 0; e < D; ++e) c[e] = (int64_t)((key >> (e * gp.bits)) & cmask);
     const int total = neighbour_layout<D>(gp, key, c, tab, T, lane, sm.off, sm.st);
     const int c0 = sm.off[CENTER], m = sm.off[CENTER + 1] - c0;  // the cell's own points
-    if (nshards > 1 && slab_of(gp, c[0], nshards) != shard) {
+    if (nshards > 1 && slab_tab[slab_bin(gp, c[0])] != shard) {
       if (!FILL)
         for (int a = lane; a < m; a += 32) counts[sorted_idx[sm.st[CENTER] + a]] = 0;
     } else if (total > STAGE_CAP) {  // too many candidates for the staging buffer
@@ -706,10 +781,11 @@ __global__ void frnn_result_kernel(const FrnnState* fs, const DenseScalars* sc, 
                                    frnn_result* res) {
   frnn_result r;
   r.n_pairs = row_ptr[n];
+  const long long rows = fs ? fs->n_rows : (long long)n;
+  r.n_rows = (int32_t)(rows < 0x7fffffffLL ? rows : 0x7fffffffLL);
   const unsigned int st = fs ? fs->status : sc->status;
   r.status = (st & 1u) ? CPPGB_ERR_NUMERIC : (st & 8u) ? CPPGB_ERR_CUDA
              : ((sc && (int64_t)sc->n_cand > cap) || r.n_pairs > cols_cap) ? CPPGB_ERR_CAPACITY : CPPGB_OK;
-  r.reserved = 0;
   *res = r;
 }
 
@@ -734,6 +810,7 @@ struct GridLayout {
   int64_t* tmp;
   int64_t* row_at;     // each point's row in the row buffer (-1: written by the crowded fill pass)
   int32_t* rowbuf;     // the rows pass's output, ROWS_PER_POINT entries per point
+  int32_t *slab_hist, *slab_tab;  // sharded queries: points per slab bin, slab of each bin
   frnn_result* res;
   int64_t T, rowbuf_cap;
   size_t bytes;
@@ -760,6 +837,8 @@ GridLayout grid_layout(void* ws, int64_t n) {
   L.row_at = c.take<int64_t>(n);
   L.rowbuf_cap = (int64_t)ROWS_PER_POINT * n;
   L.rowbuf = c.take<int32_t>(L.rowbuf_cap);
+  L.slab_hist = c.take<int32_t>(SLAB_BINS);
+  L.slab_tab = c.take<int32_t>(SLAB_BINS);
   L.res = c.take<frnn_result>(1);
   L.bytes = c.bytes();
   return L;
@@ -834,7 +913,7 @@ int grid_path(const float* pts, int64_t n, int64_t ld, double R, int64_t* row_pt
   int dev = 0, sms = 0;
   CPPGB_CUDA_TRY(cudaGetDevice(&dev));
   CPPGB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  frnn_init_kernel<<<1, 1, 0, st>>>(L.fs, L.counters);
+  frnn_init_kernel<<<1, 1, 0, st>>>(L.fs, L.counters, n);
   CPPGB_LAUNCH_CHECK();
   tab_clear_kernel<<<(unsigned)((L.T + 255) / 256), 256, 0, st>>>(L.tab, L.T);
   CPPGB_LAUNCH_CHECK();
@@ -848,6 +927,14 @@ int grid_path(const float* pts, int64_t n, int64_t ld, double R, int64_t* row_pt
   CPPGB_LAUNCH_CHECK();
   occ_count_kernel<<<nb, 256, 0, st>>>(n, L.occ_slot, L.counters, L.tab, L.occ_cnt);
   CPPGB_LAUNCH_CHECK();
+  if (nshards > 1) {  // slabs of equal point counts (slab_table_kernel)
+    CPPGB_CUDA_TRY(cudaMemsetAsync(L.slab_hist, 0, sizeof(int32_t) * SLAB_BINS, st));
+    slab_hist_kernel<<<nb < (unsigned)(2 * sms) ? nb : (unsigned)(2 * sms), 256, 0, st>>>(L.fs, L.occ_key, L.occ_cnt,
+                                                                                         L.counters, L.slab_hist);
+    CPPGB_LAUNCH_CHECK();
+    slab_table_kernel<<<1, 1024, 0, st>>>(L.fs, L.slab_hist, L.slab_tab, n, shard, nshards);
+    CPPGB_LAUNCH_CHECK();
+  }
   int rc = launch_exclusive_scan_i32(L.occ_cnt, n, L.occ_start, L.tmp, st);
   if (rc) return rc;
   occ_start_kernel<<<nb, 256, 0, st>>>(n, L.occ_slot, L.counters, L.occ_start, L.tab);
@@ -868,7 +955,7 @@ int grid_path(const float* pts, int64_t n, int64_t ld, double R, int64_t* row_pt
   uint32_t* n_fb = L.counters + 1;
   cell_query_kernel<D, false><<<cgrid, QW * 32, smem, st>>>(
       L.fs, L.tab, L.T, L.occ_key, n_occ, L.sorted_idx, L.sorted_pts, L.counts, L.row_at, L.rowbuf, L.rowbuf_cap,
-      nullptr, nullptr, n, 0, L.fb, n_fb, shard, nshards);
+      nullptr, nullptr, n, 0, L.fb, n_fb, L.slab_tab, shard, nshards);
   CPPGB_LAUNCH_CHECK();
   crowded_query_kernel<D, false><<<pgrid, PW * 32, 0, st>>>(L.fs, L.tab, L.T, L.sorted_idx, L.sorted_pts, L.counts,
                                                             L.row_at, nullptr, nullptr, n, 0, L.fb, n_fb);
@@ -884,7 +971,7 @@ int grid_path(const float* pts, int64_t n, int64_t ld, double R, int64_t* row_pt
   CPPGB_LAUNCH_CHECK();
   cell_query_kernel<D, true><<<cgrid, QW * 32, smem, st>>>(
       L.fs, L.tab, L.T, L.occ_key, n_occ, L.sorted_idx, L.sorted_pts, nullptr, nullptr, nullptr, 0, row_ptr, cols,
-      n, cols_cap, L.fb, n_fb, shard, nshards);
+      n, cols_cap, L.fb, n_fb, L.slab_tab, shard, nshards);
   CPPGB_LAUNCH_CHECK();
   frnn_result_kernel<<<1, 1, 0, st>>>(L.fs, nullptr, 0, row_ptr, n, cols_cap, L.res);
   CPPGB_LAUNCH_CHECK();
@@ -935,7 +1022,7 @@ static int frnn_common(const float* pts, int64_t n, int d, int64_t ld, double R,
   if (!out) return set_error(CPPGB_ERR_ARG, "out is NULL");
   out->n_pairs = 0;
   out->status = CPPGB_OK;
-  out->reserved = 0;
+  out->n_rows = 0;
   if (n < 0 || n > 0x7fffffffLL) return set_error(CPPGB_ERR_ARG, "n out of range");
   if (d < 1 || d > 4096 || ld < d) return set_error(CPPGB_ERR_ARG, "need 1 <= d <= 4096 and ld >= d");
   if (!(R >= 0.0) || !isfinite(R)) return set_error(CPPGB_ERR_ARG, "R must be finite and >= 0");

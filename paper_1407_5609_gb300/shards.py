@@ -5,8 +5,10 @@
   (``reduce_results``; ``allreduce_result`` across the ranks of a torch.distributed group).
 * Two-locus (``twolocus_scan_shard``): the answer is the shard result with the largest score, then
   the smallest (i, j) (``reduce_twolocus`` / ``allreduce_twolocus``).
-* FRNN on the grid (``frnn_query_shard``): each shard answers the points of its x-slab; the CSR of
-  the whole query takes each point's row from its own shard (``merge_frnn`` / ``allgather_frnn``).
+* FRNN on the grid (``frnn_query_shard``): each shard answers the points of its x-slab (slabs of
+  equal point counts); the CSR of the whole query takes each point's row from its own shard
+  (``merge_frnn`` on the host, ``merge_frnn_tensors`` on a device; ``allgather_frnn`` exchanges the
+  pieces with tensor collectives and merges on the pieces' device).
 * Two-locus on the tensor cores (``twolocus_scan_tc_shard``): as two-locus, with Pearson's results
   ranked by ``score_real`` (``reduce_twolocus``).
 * Strings (``hamming_pair_shard``): the fewest (closest) or most (least correlated) mismatches, then
@@ -151,9 +153,61 @@ def merge_frnn(parts: list):
     return row_ptr, cols
 
 
+def merge_frnn_tensors(rp_parts: list, col_parts: list):
+    """merge_frnn on torch tensors (on any one device): each piece's entries are placed at their rows'
+    offsets in the merged CSR by index arithmetic, without leaving the device."""
+    import torch
+    n = rp_parts[0].numel() - 1
+    dev = rp_parts[0].device
+    deg = torch.zeros(n, dtype=torch.int64, device=dev)
+    degs = []
+    for rp in rp_parts:
+        dk = rp[1:].to(torch.int64) - rp[:-1].to(torch.int64)
+        degs.append(dk)
+        deg += dk
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(deg, 0, out=row_ptr[1:])
+    cols = torch.empty(int(row_ptr[-1].item()), dtype=torch.int32, device=dev)
+    rows = torch.arange(n, device=dev)
+    for rp, dk, c in zip(rp_parts, degs, col_parts):
+        m = int(rp[-1].item())
+        if m == 0:
+            continue
+        r = torch.repeat_interleave(rows, dk)                  # the row of every entry of this piece
+        cols[row_ptr[r] + (torch.arange(m, device=dev) - rp[r].to(torch.int64))] = c[:m].to(torch.int32)
+    return row_ptr, cols
+
+
 def allgather_frnn(row_ptr, cols, group=None):
-    """Exchange step of a sharded FRNN query: every rank receives every slab's piece and merges."""
+    """Exchange step of a sharded FRNN query: every rank receives every slab's piece and merges.
+
+    Tensor collectives only (NCCL for device tensors, gloo for host ones): the pieces' row degrees
+    (n int32 each) and their columns, padded to the longest piece, are all-gathered, and the merge is
+    index arithmetic on the same device.  numpy inputs give numpy outputs (through host tensors)."""
+    import torch
     import torch.distributed as dist
-    gathered = [None] * dist.get_world_size(group)
-    dist.all_gather_object(gathered, (np.asarray(row_ptr), np.asarray(cols)), group=group)
-    return merge_frnn(gathered)
+    as_numpy = isinstance(row_ptr, np.ndarray)
+    rp = torch.as_tensor(np.asarray(row_ptr) if as_numpy else row_ptr).to(torch.int64)
+    cl = torch.as_tensor(np.asarray(cols, dtype=np.int32) if as_numpy else cols).to(torch.int32)
+    world = dist.get_world_size(group)
+    n = rp.numel() - 1
+    m = int(rp[-1].item())
+    deg = (rp[1:] - rp[:-1]).to(torch.int32)
+    sizes = [torch.zeros(1, dtype=torch.int64, device=rp.device) for _ in range(world)]
+    dist.all_gather(sizes, torch.tensor([m], dtype=torch.int64, device=rp.device), group=group)
+    mmax = max(int(t.item()) for t in sizes)
+    degs = [torch.empty(n, dtype=torch.int32, device=rp.device) for _ in range(world)]
+    dist.all_gather(degs, deg.contiguous(), group=group)
+    padded = torch.zeros(max(mmax, 1), dtype=torch.int32, device=rp.device)
+    padded[:m] = cl[:m]
+    pieces = [torch.empty(max(mmax, 1), dtype=torch.int32, device=rp.device) for _ in range(world)]
+    dist.all_gather(pieces, padded, group=group)
+    rps = []
+    for dk in degs:
+        r = torch.zeros(n + 1, dtype=torch.int64, device=rp.device)
+        torch.cumsum(dk.to(torch.int64), 0, out=r[1:])
+        rps.append(r)
+    out_rp, out_cols = merge_frnn_tensors(rps, pieces)
+    if as_numpy:
+        return out_rp.cpu().numpy(), out_cols.cpu().numpy()
+    return out_rp, out_cols

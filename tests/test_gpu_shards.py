@@ -84,6 +84,33 @@ def test_frnn_slabs_concatenate_exactly(d, nshards):
         assert sum(o.astype(int) for o in owned).max() <= 1
 
 
+def test_frnn_slabs_hold_equal_point_counts():
+    """Slabs are ranges of x-cells with equal shares of the points, not of equal width: with 90 % of
+    the points in the first tenth of x, each of 4 slabs still answers about a quarter of them (one
+    x-cell column is about 900 points here), their counts add up to n, and the pieces still
+    concatenate to the unsharded CSR."""
+    from paper_1407_5609_gb300 import capi
+    g = synth.rng_for(197)
+    n, R, N = 20000, 0.005, 4
+    x = g.random((n, 3)).astype(np.float32)
+    x[:18000, 0] *= np.float32(0.1)
+    t = to_dev(x, device())
+    counts, parts = [], []
+    for k in range(N):
+        res = {}
+        rp, cols = capi.frnn_query_shard(t, R, k, N, result=res)
+        counts.append(res["n_rows"])
+        parts.append((rp.cpu().numpy(), cols.cpu().numpy()))
+    assert sum(counts) == n
+    assert max(counts) <= 1.25 * n / N and min(counts) >= 0.75 * n / N, counts
+    full = {}
+    frp, fcols = capi.frnn_query(t, R, result=full)
+    assert full["n_rows"] == n
+    rp, cols = shards.merge_frnn(parts)
+    np.testing.assert_array_equal(rp, frp.cpu().numpy())
+    np.testing.assert_array_equal(cols, fcols.cpu().numpy())
+
+
 def test_new_shard_argument_errors():
     from paper_1407_5609_gb300 import capi
     dev = device()

@@ -84,8 +84,11 @@ def _rank_main_twolocus_frnn(rank, world, port, out_path):
     prp = np.concatenate([[0], np.cumsum(deg)])
     pcols = np.concatenate([cols[rp[i]:rp[i + 1]] for i in range(800) if own[i]] or [np.zeros(0, np.int32)])
     mrp, mcols = shards.allgather_frnn(prp, pcols)
+    import torch
+    trp, tcols = shards.allgather_frnn(torch.from_numpy(prp), torch.from_numpy(pcols.astype(np.int32)))
     if rank == 0:
-        np.savez(out_path, tl=np.array([tl["i"], tl["j"], tl["score"]]), rp=mrp, cols=mcols)
+        np.savez(out_path, tl=np.array([tl["i"], tl["j"], tl["score"]]), rp=mrp, cols=mcols, trp=trp.numpy(),
+                 tcols=tcols.numpy())
     dist.barrier()
     dist.destroy_process_group()
 
@@ -102,6 +105,29 @@ def test_twolocus_and_frnn_exchange_two_gloo_ranks(tmp_path):
     rp, cols = oracle.frnn(x, 0.03)
     np.testing.assert_array_equal(z["rp"], rp)
     np.testing.assert_array_equal(z["cols"], cols)
+    np.testing.assert_array_equal(z["trp"], rp)       # torch tensors in, torch tensors out
+    np.testing.assert_array_equal(z["tcols"], cols)
+
+
+def test_merge_frnn_tensors_matches_numpy_merge():
+    """The on-device merge (index arithmetic on tensors) gives the same CSR as the numpy merge,
+    including empty pieces and rows answered by no piece."""
+    import torch
+    x = synth.make_frnn_mixture(n=500, d=3, k=4, sigma=0.05, seed=131).astype(np.float64)
+    rp, cols = oracle.frnn(x, 0.04)
+    owner = synth.rng_for(132).integers(0, 4, size=500)        # 3 pieces + rows of no piece
+    parts = []
+    for k in range(3):
+        deg = np.where(owner == k, np.diff(rp), 0)
+        prp = np.concatenate([[0], np.cumsum(deg)])
+        pcols = np.concatenate([cols[rp[i]:rp[i + 1]] for i in range(500) if owner[i] == k] or [np.zeros(0, np.int32)])
+        parts.append((prp, pcols.astype(np.int32)))
+    parts.append((np.zeros(501, np.int64), np.zeros(0, np.int32)))
+    nrp, ncols = shards.merge_frnn(parts)
+    trp, tcols = shards.merge_frnn_tensors([torch.from_numpy(p[0]) for p in parts],
+                                           [torch.from_numpy(p[1]) for p in parts])
+    np.testing.assert_array_equal(trp.numpy(), nrp)
+    np.testing.assert_array_equal(tcols.numpy(), ncols)
 
 
 def test_reduce_twolocus_order():
