@@ -34,6 +34,7 @@ struct BatchInst {
   const float* pts;  // caller's FP32 [n][d]
   int32_t n, d, Kp, has_r;
   int64_t x_off;     // floats before this instance's rows in the packed FP32 X
+  int64_t c_off;     // columns before this instance in the bounding-box key arrays (Kp per instance)
   int64_t row_off;   // rows before this instance (FP32 norms)
   int64_t tile_off;  // FP32-path tiles before this instance
   double rr;         // R * R (FP64 decision value)
@@ -52,6 +53,7 @@ struct BatchState {
   BoundParams bp, bp16;
   unsigned int U_bits, n2_bits, status, ferr_bits;
   unsigned int n2_16_bits, eps16_bits;
+  unsigned int eps32_bits;   // largest rounding distance of an FP32 row shifted to the centre
   unsigned int tmin16_bits;  // smallest recorded tensor-core tile minimum (clamped at 0)
   unsigned long long best_bits, best_ij;
   int32_t n_rech, cursor;
@@ -118,6 +120,7 @@ __global__ void batch_init_kernel(BatchState* st, int count, BatchGlobals* g) {
   s.bp16 = s.bp;
   s.n2_16_bits = 0u;
   s.eps16_bits = 0u;
+  s.eps32_bits = 0u;
   s.tmin16_bits = 0x7f800000u;
   s.U_bits = 0x7f800000u;
   s.n2_bits = 0u;
@@ -167,12 +170,16 @@ __device__ __forceinline__ void block_max_flush(float v, unsigned int* dst, floa
   __syncthreads();
 }
 
-// FP32 rows of every instance (padded to Kp columns and to 128 rows) and their squared norms.  Block
-// b serves instance q = the last with blk_offs[q] <= b, rows (b - blk_offs[q]) * rows_per_block ...
+// FP32 rows of every instance, shifted to the instance's centre c (batch_center_kernel) and padded
+// to Kp columns and to 128 rows, and their squared norms.  v = fl(x - c) differs from x - c by at
+// most 2^-24 (1 + 2^-24) |v| per coordinate, so a row lies within 2^-23 |v| of its exact shifted
+// position (eps32).  Block b serves instance q = the last with blk_offs[q] <= b, rows
+// (b - blk_offs[q]) * rows_per_block ...
 __global__ void __launch_bounds__(PREP_NT) batch_prep_kernel(const BatchInst* __restrict__ inst,
                                                              const int64_t* __restrict__ blk_offs, int count,
                                                              float* __restrict__ X, float* __restrict__ norms,
-                                                             BatchState* st, BatchGlobals* g) {
+                                                             BatchState* st, BatchGlobals* g,
+                                                             const float* __restrict__ center) {
   __shared__ float red[PREP_NT / 32];
   const int q = find_inst(blk_offs, count, blockIdx.x);
   const BatchInst in = inst[q];
@@ -188,8 +195,15 @@ __global__ void __launch_bounds__(PREP_NT) batch_prep_kernel(const BatchInst* __
     float* out = X + in.x_off + r * in.Kp;
     for (int c = gl; c < ch; c += L) {
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r < in.n) v = load4(row, 4 * c, in.d, vec);
-      bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+      if (r < in.n) {
+        v = load4(row, 4 * c, in.d, vec);
+        bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+        const float4 cc = load4(center + in.c_off, 4 * c, in.d, true);  // 16-byte aligned (c_off % 16 == 0); zeros past d
+        v.x -= cc.x;
+        v.y -= cc.y;
+        v.z -= cc.z;
+        v.w -= cc.w;
+      }
       *reinterpret_cast<float4*>(out + 4 * c) = v;
       n2 = fmaf(v.x, v.x, n2);
       n2 = fmaf(v.y, v.y, n2);
@@ -201,12 +215,38 @@ __global__ void __launch_bounds__(PREP_NT) batch_prep_kernel(const BatchInst* __
   if (r < npad && gl == 0) norms[in.row_off + r] = n2;
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&g->status, 1u);
   block_max_flush(r < npad ? n2 : 0.f, &st[q].n2_bits, 1.f + 0x1p-12f, red);
+  block_max_flush(r < npad ? 0x1p-23f * sqrtf(n2) : 0.f, &st[q].eps32_bits, 1.f + 0x1p-10f, red);
+}
+
+// The centre each instance's FP32 and BF16 rows are shifted to: the midpoint of the bounding box
+// of its first (at most) 256 points, per column.  Any centre leaves the distances unchanged; one
+// near the middle of the points keeps their norms, and so the Gram error bound, small.  One block
+// of 256 threads per instance, a thread per column.
+__global__ void __launch_bounds__(256) batch_center_kernel(const BatchInst* __restrict__ inst,
+                                                           float* __restrict__ center) {
+  const BatchInst in = inst[blockIdx.x];
+  if (threadIdx.x >= in.d) return;
+  const int k = threadIdx.x;
+  const int m = in.n < 256 ? (int)in.n : 256;
+  if (m == 0) {
+    center[in.c_off + k] = 0.f;
+    return;
+  }
+  float lo = in.pts[k], hi = lo;
+#pragma unroll 8
+  for (int r = 1; r < m; ++r) {
+    const float v = in.pts[(int64_t)r * in.d + k];
+    lo = fminf(lo, v);
+    hi = fmaxf(hi, v);
+  }
+  const float c = 0.5f * lo + 0.5f * hi;
+  center[in.c_off + k] = isfinite(c) ? c : 0.f;
 }
 
 __global__ void batch_bounds_kernel(const BatchInst* __restrict__ inst, BatchState* st, int count) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= count) return;
-  st[q].bp.eps_pair = 0.f;  // FP32 input stored exactly
+  st[q].bp.eps_pair = 2.f * __uint_as_float(st[q].eps32_bits) * (1.f + 0x1p-20f);  // the shift's rounding
   st[q].bp.e_acc = inst[q].kappa * __uint_as_float(st[q].n2_bits) * (1.f + 0x1p-20f);
   st[q].bp16.eps_pair = 2.f * __uint_as_float(st[q].eps16_bits) * (1.f + 0x1p-20f);
   st[q].bp16.e_acc = inst[q].kappa16 * __uint_as_float(st[q].n2_16_bits) * (1.f + 0x1p-20f);
@@ -214,12 +254,17 @@ __global__ void batch_bounds_kernel(const BatchInst* __restrict__ inst, BatchSta
 
 // BF16 rows of the tensor-core instances (padded to their class width and to 256 rows), their FP32
 // squared norms, and the norm pieces of the norm MMA; each lane converts 8 values (one 16-byte
-// store).  The row's residual |x - x~| (exact in FP32) bounds the rounding, as in the dense stage's
-// preparation.  Blocks as in batch_prep_kernel, over the tensor-core instances' 256-row blocks.
+// store).  Every point is first shifted by its instance's centre c (batch_center_kernel; distances
+// do not change, while the norms, and with them the Gram error bound, shrink: for points in
+// [0, 1]^d from up to d to about d / 4, and far more for points far from the origin).  The row's distance from its exact shifted position is at most the residual
+// |v - x~| (exact in FP32) plus the rounding of v = fl(x - c), |v - (x - c)| <= 2^-24 (1 + 2^-24) |v|
+// per coordinate; eps bounds their sum with 2^-23 |v|.  Blocks as in batch_prep_kernel, over the
+// tensor-core instances' 256-row blocks.
 __global__ void __launch_bounds__(PREP_NT) batch_prep16_kernel(const BatchInst* __restrict__ inst,
                                                                const int64_t* __restrict__ blk_offs, int count,
                                                                X16Set X16, float* __restrict__ norms16,
-                                                               __nv_bfloat16* __restrict__ H16, BatchState* st) {
+                                                               __nv_bfloat16* __restrict__ H16, BatchState* st,
+                                                               const float* __restrict__ center) {
   __shared__ float red[PREP_NT / 32];
   const int q = find_inst(blk_offs, count, blockIdx.x);
   const BatchInst in = inst[q];
@@ -228,7 +273,7 @@ __global__ void __launch_bounds__(PREP_NT) batch_prep16_kernel(const BatchInst* 
   const int64_t r = (blockIdx.x - blk_offs[q]) * rpb + threadIdx.x / L;
   const int gl = threadIdx.x % L;
   const bool vec = (in.d % 4 == 0) && ((reinterpret_cast<uintptr_t>(in.pts) & 15) == 0);
-  float n2 = 0.f, dd = 0.f;
+  float n2 = 0.f, dd = 0.f, vv = 0.f;
   if (r < npad) {
     const float* row = in.pts + r * in.d;
     // (a select chain: indexing the parameter array with a runtime class would copy it to local memory)
@@ -241,6 +286,14 @@ __global__ void __launch_bounds__(PREP_NT) batch_prep16_kernel(const BatchInst* 
       if (r < in.n) {
         const float4 a = load4(row, 8 * c, in.d, vec), b = load4(row, 8 * c + 4, in.d, vec);
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int col = 8 * c + k;
+          if (col < in.d) {
+            v[k] = v[k] - center[in.c_off + col];
+            vv = fmaf(v[k], v[k], vv);
+          }
+        }
       } else {
 #pragma unroll
         for (int k = 0; k < 8; ++k) v[k] = 0.f;
@@ -263,6 +316,7 @@ __global__ void __launch_bounds__(PREP_NT) batch_prep16_kernel(const BatchInst* 
   for (int o = L / 2; o > 0; o >>= 1) {
     n2 += __shfl_xor_sync(0xffffffffu, n2, o);
     dd += __shfl_xor_sync(0xffffffffu, dd, o);
+    vv += __shfl_xor_sync(0xffffffffu, vv, o);
   }
   if (r < npad) {
     const int64_t gr = in.grow_off16 + r;
@@ -283,7 +337,7 @@ __global__ void __launch_bounds__(PREP_NT) batch_prep16_kernel(const BatchInst* 
     }
   }
   block_max_flush(r < npad ? n2 : 0.f, &st[q].n2_16_bits, 1.f + 0x1p-12f, red);
-  block_max_flush(r < npad ? sqrtf(dd) : 0.f, &st[q].eps16_bits, 1.f + 0x1p-10f, red);
+  block_max_flush(r < npad ? sqrtf(dd) + 0x1p-23f * sqrtf(vv) : 0.f, &st[q].eps16_bits, 1.f + 0x1p-10f, red);
 }
 
 // Persistent FP32 tile kernel over the concatenated tile lists.
@@ -1197,6 +1251,7 @@ struct BatchLayout {
   BatchInst* inst;
   int64_t *tile_offs, *tile_offs16[2];  // FP32-path tiles; tensor-core tile lists (four-group, two-group kernel)
   int64_t *pblk32, *pblk16;  // preparation blocks before each instance (FP32 rows; BF16 rows)
+  float* center;  // per instance and column: the centre its FP32 and BF16 rows are shifted to
   BatchState* st;
   BatchGlobals* g;
   int32_t* pair_counts;
@@ -1230,6 +1285,7 @@ struct Totals {
   int64_t rows16 = 0, tiles16 = 0, crow16[NCLS] = {0, 0, 0, 0, 0, 0};
   int64_t tiles16s[2] = {0, 0};  // tensor-core tiles of path 2 (four-group kernel) and path 3 (two-group)
   int64_t blk32 = 0, blk16 = 0;  // preparation blocks (FP32 rows of every instance, BF16 rows of the tensor-core ones)
+  int64_t cols = 0;              // padded columns of all instances (the centres)
 };
 
 int64_t nrow16_of(int64_t n) { return n >= 2 ? (n - 2) / 128 + 1 : 0; }
@@ -1257,6 +1313,7 @@ Totals totals_of(const cpp_instance* inst, int64_t count) {
     t.rows += npad;
     t.xfloats += npad * Kp;
     t.blk32 += prep_blocks32(npad, Kp);
+    t.cols += Kp;
     if (path_of(inst[q]) >= 2) {
       const int64_t npad16 = (n + 255) / 256 * 256;
       t.rows16 += npad16;
@@ -1277,6 +1334,7 @@ BatchLayout batch_layout(void* ws, int64_t count, const Totals& t, size_t ws_byt
   L.inst = c.take<BatchInst>(count);
   L.tile_offs = c.take<int64_t>(count + 1);
   L.pblk32 = c.take<int64_t>(count + 1);
+  L.center = c.take<float>(t.cols + 1);
   L.pblk16 = c.take<int64_t>(count + 1);
   L.tile_offs16[0] = c.take<int64_t>(count + 1);
   L.tile_offs16[1] = c.take<int64_t>(count + 1);
@@ -1398,14 +1456,17 @@ int enqueue_batch(const BatchLayout& L, int64_t count, const Totals& t, int32_t*
   batch_init_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(L.st, ci, L.g);
   CPPGB_LAUNCH_CHECK();
   CPPGB_CUDA_TRY(cudaMemsetAsync(L.pair_counts, 0, sizeof(int32_t) * (count + 1), st));
+  batch_center_kernel<<<(unsigned)count, 256, 0, st>>>(L.inst, L.center);
+  CPPGB_LAUNCH_CHECK();
   if (t.blk32 > 0) {
-    batch_prep_kernel<<<(unsigned)t.blk32, PREP_NT, 0, st>>>(L.inst, L.pblk32, ci, L.X, L.norms, L.st, L.g);
+    batch_prep_kernel<<<(unsigned)t.blk32, PREP_NT, 0, st>>>(L.inst, L.pblk32, ci, L.X, L.norms, L.st, L.g, L.center);
     CPPGB_LAUNCH_CHECK();
   }
   if (t.rows16 > 0) {
     X16Set xs;
     for (int k = 0; k < NCLS; ++k) xs.p[k] = L.X16[k];
-    batch_prep16_kernel<<<(unsigned)t.blk16, PREP_NT, 0, st>>>(L.inst, L.pblk16, ci, xs, L.norms16, L.H16, L.st);
+    batch_prep16_kernel<<<(unsigned)t.blk16, PREP_NT, 0, st>>>(L.inst, L.pblk16, ci, xs, L.norms16, L.H16, L.st,
+                                                               L.center);
     CPPGB_LAUNCH_CHECK();
   }
   batch_bounds_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(L.inst, L.st, ci);
@@ -1502,7 +1563,8 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
   std::vector<BatchInst> hi((size_t)count);
   std::vector<int64_t> hto((size_t)count + 1), hb32((size_t)count + 1), hb16((size_t)count + 1);
   std::vector<int64_t> hto16[2] = {std::vector<int64_t>((size_t)count + 1), std::vector<int64_t>((size_t)count + 1)};
-  int64_t xo = 0, ro = 0, to = 0, go = 0, to16[2] = {0, 0}, co[NCLS] = {0, 0, 0, 0, 0, 0}, pb32 = 0, pb16 = 0;
+  int64_t xo = 0, ro = 0, to = 0, go = 0, to16[2] = {0, 0}, co[NCLS] = {0, 0, 0, 0, 0, 0}, pb32 = 0, pb16 = 0,
+          cofs = 0;
   for (int64_t q = 0; q < count; ++q) {
     const cpp_instance& c = inst[q];
     BatchInst b;
@@ -1512,6 +1574,7 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
     b.Kp = (c.d + 15) / 16 * 16;
     b.has_r = c.R >= 0.0;
     b.x_off = xo;
+    b.c_off = cofs;
     b.row_off = ro;
     b.tile_off = to;
     b.rr = c.R >= 0.0 ? c.R * c.R : -1.0;
@@ -1535,6 +1598,7 @@ int cpp_batch(const cpp_instance* inst, int64_t count, cpp_pair_result* out_cpp,
     hto16[0][(size_t)q] = to16[0];
     hto16[1][(size_t)q] = to16[1];
     xo += npad * b.Kp;
+    cofs += b.Kp;
     ro += npad;
     pb32 += prep_blocks32(npad, b.Kp);
     if (b.tc) {

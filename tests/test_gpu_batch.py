@@ -104,6 +104,23 @@ def test_batch_tensor_core_ties_and_widths(path):
     assert counts[-1] == 300 * 299 // 2
 
 
+@pytest.mark.parametrize("path", [2, 3])
+def test_batch_tensor_core_far_from_the_origin(path):
+    """Points far from the origin (coordinates near 1000, or near -500): the tensor-core rows are
+    shifted to a centre of their instance, so the Gram error bound stays that of unit-scale data and
+    the filter still emits only a few candidates (unshifted, the bound would pass every pair); the
+    answers are the oracle's."""
+    g = synth.rng_for(74)
+    insts, radii = [], []
+    for n, d, off in [(3000, 8, 1000.0), (1500, 16, -500.0), (700, 64, 250.0)]:
+        x = (off + g.random((n, d))).astype(np.float32)
+        x[n - 1] = x[n // 2] + np.float32(1e-3) * np.ones(d, np.float32) / np.float32(np.sqrt(d))
+        insts.append(x)
+        radii.append(2e-3)
+    res, counts = _check_batch(insts, radii, paths=path)
+    assert res[0]["n_emitted"] <= sum(x.shape[0] for x in insts)
+
+
 def test_batch_paths_agree_on_generator_workload():
     """The 2048-instance workload through each path: identical closest pairs, distances and pair
     lists (both are exact, so they cannot differ)."""
