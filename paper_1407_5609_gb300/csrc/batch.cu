@@ -13,10 +13,11 @@
 // { (i, j) : i < j, d <= R_q } (ascending).  The whole sequence is captured once into a CUDA graph
 // per argument set and replayed.
 //
-// Each instance takes one of two tile paths (cpp_instance.path): FP32 CUDA-core tiles of 128 x 128,
-// or BF16 tensor-core tiles of 128 x 256 (tcgen05, the dense-stage kernel's pipeline with one TMA
-// tensor map per 64-column class of d).  Tiles recorded by either path are recomputed in FP32 by the
-// same second pass.
+// Each instance takes one of the tile paths (cpp_instance.path): FP32 CUDA-core tiles of 128 x 128,
+// or BF16 tensor-core tiles of 128 x 256 (tcgen05 with TMA-staged operands, one tensor map per width
+// class of d) whose accumulators are read by four epilogue groups (path 2) or two (path 3), two
+// persistent kernels.  Every instance's rows are first shifted to a centre of its points.  Blocks
+// recorded by any path are recomputed in FP32 by the same second pass.
 #include <cuda_bf16.h>
 
 #include <algorithm>
