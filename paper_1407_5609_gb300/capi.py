@@ -588,36 +588,80 @@ def _frnn(pts, R, cols_cap, ws, stream, shard, result=None):
 
 
 def cpp_batch_workspace_size(instances) -> int:
-    arr = (cpp_instance * len(instances))(*instances)
+    """Workspace bytes of cpp_batch for a list of cpp_instance or a BatchInstances."""
+    if isinstance(instances, BatchInstances):
+        return int(lib().cpp_batch_workspace_size(instances.arr, instances.count))
+    arr = (cpp_instance * max(len(instances), 1))(*instances)
     return int(lib().cpp_batch_workspace_size(arr, len(instances)))
 
 
 PATH_DEFAULT, PATH_FP32, PATH_TC, PATH_TC2 = 0, 1, 2, 3
 
 
-def cpp_batch(points: list, radii: list, pairs_cap: int | None = None, ws: torch.Tensor | None = None,
-              stream=None, pairs: torch.Tensor | None = None, paths=None):
-    """Closest pair + R-pairs of every instance in one call.
+class BatchInstances:
+    """The cpp_instance array of a batch, validated and built once (``batch_instances``), so that
+    repeated cpp_batch calls on the same tensors skip the per-instance Python work.  The tensors
+    must stay alive and unchanged in shape while it is used."""
 
-    ``points`` is a list of float32 [n][d] CUDA tensors (contiguous), ``radii`` their R (< 0: no
-    pair list), ``paths`` an optional per-instance tile path (PATH_DEFAULT, PATH_FP32, PATH_TC (four
-    epilogue groups) or PATH_TC2 (two); a single int applies to all).  Repeated calls with the same workspace and ``pairs``
-    buffer replay the library's captured CUDA graph.  Returns (list of result dicts, pair_counts
-    int64 numpy, pairs int32 tensor [P][2]).
-    """
+    def __init__(self, arr, count: int, device):
+        self.arr, self.count, self.device = arr, count, device
+
+
+def batch_instances(points: list, radii: list, paths=None) -> BatchInstances:
+    """Validate the instances of a batch and build their cpp_instance array (see cpp_batch)."""
     count = len(points)
     if paths is None or isinstance(paths, int):
         paths = [paths or 0] * count
-    if len(paths) != count:
-        raise ValueError("paths must give one entry per instance")
+    if len(paths) != count or len(radii) != count:
+        raise ValueError("radii and paths must give one entry per instance")
     inst = []
     for p, R, path in zip(points, radii, paths):
         _check_cuda(p, "points")
         if p.dim() != 2 or p.dtype != torch.float32 or not p.is_contiguous():
             raise ValueError("each instance must be a contiguous float32 [n][d] tensor")
         inst.append(cpp_instance(p.data_ptr(), p.shape[0], p.shape[1], int(path), float(R)))
-    arr = (cpp_instance * count)(*inst)
-    device = points[0].device if count else torch.device("cuda")
+    arr = (cpp_instance * max(count, 1))(*inst)
+    return BatchInstances(arr, count, points[0].device if count else torch.device("cuda"))
+
+
+class BatchResults:
+    """Per-instance results of cpp_batch.  ``records`` is a numpy record array with one field per
+    cpp_pair_result member (vectorised access: ``res.records["i"]``); ``res[q]`` is instance q's
+    result as a dict, as the other searches return it."""
+
+    _dtype = np.dtype(cpp_pair_result)
+
+    def __init__(self, records):
+        self.records = records
+
+    def __len__(self):
+        return len(self.records)
+
+    def __getitem__(self, q):
+        if isinstance(q, slice):
+            return [self[k] for k in range(*q.indices(len(self)))]
+        r = self.records[q]
+        return {k: r[k].item() for k in self._dtype.names if k != "reserved"}
+
+    def __iter__(self):
+        return (self[q] for q in range(len(self)))
+
+
+def cpp_batch(points: list, radii: list, pairs_cap: int | None = None, ws: torch.Tensor | None = None,
+              stream=None, pairs: torch.Tensor | None = None, paths=None,
+              instances: BatchInstances | None = None):
+    """Closest pair + R-pairs of every instance in one call.
+
+    ``points`` is a list of float32 [n][d] CUDA tensors (contiguous), ``radii`` their R (< 0: no
+    pair list), ``paths`` an optional per-instance tile path (PATH_DEFAULT, PATH_FP32, PATH_TC (four
+    epilogue groups) or PATH_TC2 (two); a single int applies to all); or ``instances``, the array
+    ``batch_instances`` built for them once.  Repeated calls with the same workspace and ``pairs``
+    buffer replay the library's captured CUDA graph.  Returns (BatchResults, pair_counts int64 numpy,
+    pairs int32 tensor [P][2]).
+    """
+    if instances is None:
+        instances = batch_instances(points, radii, paths)
+    arr, count, device = instances.arr, instances.count, instances.device
     if ws is None:
         ws = _workspace(int(lib().cpp_batch_workspace_size(arr, count)), device)
     outs = _pinned(cpp_pair_result, count)
@@ -630,7 +674,11 @@ def cpp_batch(points: list, radii: list, pairs_cap: int | None = None, ws: torch
     _raise(lib().cpp_batch(arr, count, outs, counts, pairs.data_ptr(), cap, ws.data_ptr(), ws.numel(),
                            _stream(stream)))
     _sync(stream)
-    for q in range(count):
-        _raise_status(outs[q].status)
-    c = np.array(list(counts)[:count], dtype=np.int64)
-    return [outs[q].as_dict() for q in range(count)], c, pairs[:int(c.sum())]
+    rec = np.frombuffer((ctypes.c_char * (BatchResults._dtype.itemsize * max(count, 1))).from_address(
+        ctypes.addressof(outs)), dtype=BatchResults._dtype, count=count).copy()
+    bad = np.nonzero(rec["status"])[0]
+    if bad.size:
+        _raise_status(int(rec["status"][bad[0]]))
+    c = np.frombuffer((ctypes.c_char * (8 * max(count, 1))).from_address(ctypes.addressof(counts)),
+                      dtype=np.int64, count=count).copy()
+    return BatchResults(rec), c, pairs[:int(c.sum())]

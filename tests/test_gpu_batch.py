@@ -121,6 +121,23 @@ def test_batch_tensor_core_far_from_the_origin(path):
     assert res[0]["n_emitted"] <= sum(x.shape[0] for x in insts)
 
 
+def test_batch_prepared_instances_give_the_same_answer():
+    """An instance array built once (batch_instances) gives the same results as building it per
+    call; the vectorised records agree with the per-instance dicts."""
+    capi = _capi()
+    insts, radii = _mixed_instances()
+    pts = [to_dev(np.ascontiguousarray(x, dtype=np.float32), device()) for x in insts]
+    r1, c1, p1 = capi.cpp_batch(pts, radii)
+    prepared = capi.batch_instances(pts, radii)
+    for _ in range(2):
+        r2, c2, p2 = capi.cpp_batch(None, None, instances=prepared)
+        assert [(a["i"], a["j"], a["dist2"]) for a in r1] == [(b["i"], b["j"], b["dist2"]) for b in r2]
+        np.testing.assert_array_equal(c1, c2)
+        assert torch_equal(p1, p2)
+    np.testing.assert_array_equal(r2.records["i"], [a["i"] for a in r1])
+    np.testing.assert_array_equal(r2.records["dist2"], [a["dist2"] for a in r1])
+
+
 def test_batch_paths_agree_on_generator_workload():
     """The 2048-instance workload through each path: identical closest pairs, distances and pair
     lists (both are exact, so they cannot differ)."""
